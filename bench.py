@@ -1,0 +1,375 @@
+"""Benchmark: fp64 Jacobi-PCG time to a 1e-8 relative residual on one GB300.
+
+Default workload: 3-D 7-point Poisson on a 256^3 grid (n = 16,777,216,
+nnz = 117,047,296), FP64 CSR with int32 indices, x* uniform[-1, 1) from seed 0,
+b = A x*, x0 = 0, Jacobi-PCG to ||b - A x|| / ||b|| <= 1e-8.  One step = one
+whole solve (every phase of the hot path: SpMV + p.q, x/r update + r.z/r.r,
+p update, device-side convergence test, final fp64 true residual) through
+the C ABI.  The matrix (1.4 GB) and vectors exceed the 129 MB L2, so no
+explicit flush is needed between steps.
+
+Printed JSON line: value = solves per second over all ranks (inputs resident
+in HBM), ms_per_step = time to tolerance, e2e = the same through the host-buffer
+entry point (H2D of b and x0, D2H of x inside the timed region), roofline of the
+persistent solver kernel against the measured HBM copy bandwidth, and the CPU
+oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (builder, kwargs, precond, precision, tol, maxit, description)
+    "poisson3d_256": ("lap3d7", {"N": 256}, "jacobi", "fp64", 1e-8, 10000,
+                      "3-D 7-point Poisson 256^3, FP64 Jacobi-PCG to 1e-8"),
+    "poisson2d_64": ("lap2d", {"N": 64}, "none", "fp64", 1e-8, 1000,
+                     "2-D 5-point Poisson 64x64, FP64 CG to 1e-8"),
+    "diffusion27_160": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp32_ir",
+                        1e-10, 100000,
+                        "3-D 27-point lognormal diffusion 160^3, FP32 inner / FP64 refinement to 1e-10"),
+    "diffusion27_160_fp64": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp64",
+                             1e-10, 100000,
+                             "3-D 27-point lognormal diffusion 160^3, FP64 Jacobi-PCG to 1e-10"),
+}
+
+
+def bytes_per_iter(n, nnz, precond, precision):
+    """Modelled (algorithmic) HBM bytes of one CG iteration: the CSR stream plus
+    the vector streams of the three phases (SpMV + p.q, x/r update, p update)."""
+    if precision == "fp64":
+        return 12 * nnz + 4 * (n + 1) + (104 if precond == "jacobi" else 88) * n
+    return 8 * nnz + 4 * (n + 1) + (52 if precond == "jacobi" else 44) * n
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2608_09647_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the solver kernel from the committed ncu summary, if it
+    was taken from the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(workload)
+    if not d or d.get("kernel_sha") != kernel_source_sha():
+        return None
+    return d
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_matrix(workload):
+    import cgproblems as gen
+    builder, kw, *_ = WORKLOADS[workload]
+    return getattr(gen, builder)(**kw)
+
+
+def golden_iters(workload):
+    p = os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if workload in d:
+            return int(d[workload]["iters"])
+    return None
+
+
+def time_oracle_sample(A, b, precond, precision, tol, budget_s):
+    """Time the oracle on a bounded sample of the workload: Jacobi-PCG iterations on the full
+    matrix, as many as fit the budget.  Returns (seconds per iteration, iterations run)."""
+    import oracle
+    pc = 1 if precond == "jacobi" else 0
+    m = 2
+    while True:
+        t0 = time.perf_counter()
+        if precision == "fp64":
+            oracle.pcg(A, b, tol=0.0, maxit=m, precond=pc, max_restarts=0)
+        else:
+            oracle.pcg_ir(A, b, tol=0.0, tol_in=1e-30, maxit=m, max_outer=1, precond=pc)
+        dt = time.perf_counter() - t0
+        if dt >= budget_s / 3 or m >= 4096:
+            return dt / m, m
+        m = max(m * 2, int(m * (budget_s / 3) / max(dt, 1e-3)))
+
+
+def run_reference(args):
+    """The oracle as the reference arm: rank 0 times bounded samples on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    import cgproblems as gen
+    _, _, precond, precision, tol, maxit, desc = WORKLOADS[args.workload]
+    A = build_matrix(args.workload)
+    b = oracle.spmv(A, gen.xstar(A.n, 0))
+    iters = golden_iters(args.workload)
+    per_step_budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        time_oracle_sample(A, b, precond, precision, tol, per_step_budget)
+    samples = []
+    for _ in range(args.steps):
+        s, m = time_oracle_sample(A, b, precond, precision, tol, per_step_budget)
+        samples.append((s, m))
+    s_iter = statistics.median(s for s, _ in samples)
+    est_iters = iters if iters else None
+    solve_s = s_iter * est_iters if est_iters else None
+    value = 1.0 / solve_s if solve_s else None
+    sample = (f"{samples[0][1]} oracle {precision} {'Jacobi-' if precond == 'jacobi' else ''}PCG "
+              f"iterations on the full matrix per step, scaled to "
+              f"{est_iters if est_iters else '?'} iterations (oracle's own count to tol)")
+    line = {"impl": "reference", "metric": "PCG time to 1e-8 rel. residual (solves/s)",
+            "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": solve_s * 1e3 if solve_s else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": A.n, "nnz": A.nnz},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "s_per_iter": s_iter},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libcg", choices=["libcg", "reference"])
+    ap.add_argument("--workload", default="poisson3d_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle CPU time for the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import cgproblems as gen
+    import paper_2608_09647_gb300 as cg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    builder, kw, precond_s, precision_s, tol, maxit, desc = WORKLOADS[args.workload]
+    precond = cg.CG_PRECOND_JACOBI if precond_s == "jacobi" else cg.CG_PRECOND_NONE
+    precision = cg.CG_PREC_FP64 if precision_s == "fp64" else cg.CG_PREC_FP32_IR
+
+    # every rank solves its own copy of the system (replicas: weak scaling)
+    A = build_matrix(args.workload)
+    rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colind, A.vals))
+    h = cg.cg_create(A.n, rp, ci, va)
+    xs = torch.from_numpy(gen.xstar(A.n, 0)).to(dev)
+    b = torch.empty_like(xs)
+    assert cg.cg_spmv(h, xs, b) == cg.CG_OK        # b = A x* on the device
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+
+    def step():
+        x.zero_()
+        st, it, rel = cg.cg_solve(h, b, x, tol, maxit, precond, precision)
+        if st != cg.CG_OK:
+            raise RuntimeError(f"solve failed: {cg.status_string(st)} {cg.cg_last_error(h)}")
+        return it, rel, cg.cg_get_solve_info(h)
+
+    for _ in range(args.warmup):
+        step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    infos = []
+    barrier()
+    with ClockSampler(uuid) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            infos.append(step())
+        ev1.record()
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t_max = elapsed_ms
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * args.steps / (t_max / 1e3)
+
+    iters = [i for i, _, _ in infos]
+    relres = max(r for _, r, _ in infos)
+    kern_ms = sum(inf["kernel_ms"] for _, _, inf in infos)
+    kern_bytes = sum(inf["bytes_moved"] for _, _, inf in infos)
+    peak, peak_kind = load_peaks()
+    achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    bpi = bytes_per_iter(A.n, A.nnz, precond_s, precision_s)
+    tr = ncu_traffic(args.workload)
+    traffic = None
+    if tr:
+        traffic = int(tr["dram_bytes_per_iter"] * statistics.mean(iters))
+
+    # end to end through the host-buffer entry point
+    bh = torch.from_numpy(b.cpu().numpy()).pin_memory()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)   # warm the staging buffers
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh.zero_()
+        st, it, rel = cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)
+        if st != cg.CG_OK:
+            raise RuntimeError(f"host solve failed: {cg.status_string(st)}")
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        bo = oracle.spmv(A, gen.xstar(A.n, 0))
+        s_iter, m = time_oracle_sample(A, bo, precond_s, precision_s, tol, args.cpu_budget)
+        it_ref = golden_iters(args.workload) or int(statistics.median(iters))
+        solve_s = s_iter * it_ref
+        cpu = {"value": 1.0 / solve_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": (f"{m} oracle iterations of the same system on 1 host core "
+                          f"({s_iter * 1e3:.1f} ms/iter), scaled to {it_ref} iterations"),
+               "ms_per_solve": solve_s * 1e3}
+
+    cg.cg_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": "PCG time to 1e-8 rel. residual (solves/s)",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision_s == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": A.n, "nnz": A.nnz,
+                       "tol": tol, "iters": iters[0], "relres_true_max": relres,
+                       "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
+                       "grid_ctas": infos[0][2]["grid_ctas"]},
+            "iter_us": 1e3 * kern_ms / sum(iters),
+            "loop_gbs_model": achieved,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "pcg64_kernel<Jacobi>" if precision_s == "fp64" else "pcg_ir_kernel<Jacobi>",
+                         "bytes_per_iter_model": bpi, "peak_kind": peak_kind},
+            "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
+                    "h2d_bytes_per_step": 16 * A.n, "d2h_bytes_per_step": 8 * A.n},
+            "gpu_launches": args.steps,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

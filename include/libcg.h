@@ -1,0 +1,145 @@
+/*
+ * libcg — sparse (preconditioned) conjugate gradient on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the CG hot path of "A Preliminary Study on Simultaneous
+ * Coscheduling for Discrete GPU vs. Fused GPU" (ICPP Workshops '26), run
+ * entirely on the GPU (the paper's GPU-only split, g = 1).  The paper's
+ * problem statement (Sec. 3): solve A x = b for a sparse A that stays fixed
+ * during the solve, A held in CSR form (Sec. 3.2) with fp64 values, vectors
+ * and reductions (Sec. 3.1), each iteration = fused SpMV + p.q, fused x/r
+ * update + r.r, p update (Alg. 1, Sec. 3.3).
+ *
+ * Conventions for every call:
+ *  - Pointers named in the comments as "device" must point to memory of the
+ *    current CUDA device; "host" pointers to ordinary or pinned host memory.
+ *  - Matrix arrays are BORROWED: the caller keeps rowptr/colind/vals alive and
+ *    unchanged until cg_destroy.  Every other buffer the library needs is
+ *    allocated (cudaMalloc) by cg_create and freed by cg_destroy.
+ *  - Indices are int32 (0-based), values fp64; vectors are fp64 with 16-byte
+ *    aligned start addresses (any torch.empty/zeros tensor qualifies).
+ *  - Work is ordered on the handle's stream (cg_set_stream; default: the
+ *    legacy default stream).  cg_solve blocks until its result word is back
+ *    on the host; cg_spmv does not block.
+ *  - Every call returns a cg_status.  CG_NOT_CONVERGED is not an error: the
+ *    outputs are valid.  Negative values are errors; cg_last_error() gives a
+ *    one-line reason.  A handle is not thread-safe.
+ */
+#ifndef LIBCG_H
+#define LIBCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cg_handle cg_handle;
+
+typedef enum {
+  CG_OK = 0,
+  CG_NOT_CONVERGED = 1,   /* maxit reached (or restarts exhausted); x is the last iterate */
+  CG_ERR_INVALID = -1,    /* bad argument, malformed CSR, missing/non-positive diagonal */
+  CG_ERR_BREAKDOWN = -2,  /* p.q <= 0: A is not SPD on the Krylov space */
+  CG_ERR_NUMERIC = -3,    /* NaN or Inf in a reduction */
+  CG_ERR_TIMEOUT = -4,    /* a grid barrier of the persistent kernel gave up waiting */
+  CG_ERR_CUDA = -5,       /* a CUDA runtime call failed */
+  CG_ERR_OOM = -6         /* device or pinned-host allocation failed */
+} cg_status;
+
+typedef enum {
+  CG_PRECOND_NONE = 0,    /* plain CG, Alg. 1 */
+  CG_PRECOND_JACOBI = 1   /* z = D^-1 r, D = diag(A) (not in the paper) */
+} cg_precond;
+
+typedef enum {
+  CG_PREC_FP64 = 0,       /* every value, vector and reduction in fp64 (Sec. 3.1) */
+  CG_PREC_FP32_IR = 1     /* fp32 inner PCG, fp64 outer iterative refinement (not in the paper) */
+} cg_precision;
+
+typedef enum {
+  CG_OPT_MAX_RESTARTS = 0,        /* residual-replacement restarts after a false convergence (default 3) */
+  CG_OPT_BARRIER_TIMEOUT_MS = 1,  /* grid-barrier wait limit in ms (default 2000) */
+  CG_OPT_GRID_CTAS = 2,           /* persistent-kernel CTAs; 0 = choose automatically (default) */
+  CG_OPT_IR_TOL_INNER = 3,        /* inner relative tolerance of fp32 refinement (default 1e-4) */
+  CG_OPT_IR_MAX_OUTER = 4,        /* refinement steps cap (default 30) */
+  CG_OPT_DEBUG_SKIP_ARRIVAL = 5   /* fault injection: CTA 0 skips arrival at grid barrier #value
+                                     (1-based; 0 = off), so every wait runs into its limit */
+} cg_option;
+
+/* Statistics of the most recent cg_solve on a handle. */
+typedef struct {
+  int32_t status;         /* cg_status of the solve */
+  int32_t iters;          /* SpMVs in the CG loop (fp64) / total inner iterations (fp32 IR) */
+  int32_t restarts;       /* residual replacements (fp64) / refinement steps (fp32 IR) */
+  int32_t grid_ctas;      /* CTAs of the persistent launch */
+  double relres_true;     /* ||b - A x||_2 / ||b||_2 recomputed in fp64 from the final x */
+  double relres_rec;      /* the recursive residual's relative norm at exit */
+  double kernel_ms;       /* device time of the persistent launch (CUDA events) */
+  int64_t bytes_moved;    /* modelled HBM bytes of the launch (algorithmic count) */
+} cg_solve_info;
+
+/*
+ * Create a solver for the n x n CSR matrix (rowptr[n+1], colind[nnz],
+ * vals[nnz], all DEVICE pointers, nnz = rowptr[n]).  The CSR is validated
+ * (rowptr[0] = 0, non-decreasing, every colind in [0, n)); the diagonal is
+ * extracted for Jacobi (a row whose diagonal is absent or <= 0 only disables
+ * Jacobi).  The rows are cut into row blocks for the SpMV schedule.  On
+ * success *out owns all workspace; on failure *out = NULL and the status says
+ * why (message via cg_last_error(NULL)).  n = 0 is allowed.
+ */
+cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind,
+                    const double* vals, cg_handle** out);
+
+/* Order all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy default). */
+cg_status cg_set_stream(cg_handle* h, void* cuda_stream);
+
+/* Set a tuning/debug option (cg_option); returns CG_ERR_INVALID for unknown options or values. */
+cg_status cg_set_option(cg_handle* h, int32_t option, double value);
+
+/* y = A x (Sec. 3.1 SpMV), x and y DEVICE fp64 vectors of length n; y must not alias x. */
+cg_status cg_spmv(cg_handle* h, const double* x, double* y);
+
+/*
+ * Solve A x = b (Alg. 1).  b: DEVICE rhs; x: DEVICE, in = initial guess x0,
+ * out = solution.  Stops when ||r||_2 <= tol ||b||_2 on the recursive
+ * residual (tested before each SpMV, so iters counts SpMVs), then recomputes
+ * the true residual in fp64; if that misses tol, restarts from x (residual
+ * replacement) up to CG_OPT_MAX_RESTARTS times.  b = 0 gives x = 0, iters 0,
+ * relres 0.  The whole loop is one persistent kernel launch with no host
+ * round trip per iteration.  iters_out / relres_out (host, may be NULL)
+ * receive the iteration count and the fp64 true relative residual.
+ * Returns CG_OK, CG_NOT_CONVERGED or an error (x then holds the last iterate).
+ */
+cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                   int32_t precond, int32_t precision, int32_t* iters_out, double* relres_out);
+
+/*
+ * cg_solve with HOST buffers: b_host and x_host (x0 in, solution out) are
+ * copied to the device and back inside the call (pinned memory makes the
+ * copies asynchronous and fastest).  Same results and statuses as cg_solve.
+ */
+cg_status cg_solve_host(cg_handle* h, const double* b_host, double* x_host, double tol,
+                        int32_t maxit, int32_t precond, int32_t precision, int32_t* iters_out,
+                        double* relres_out);
+
+/* Statistics of the last solve on h (host struct). */
+cg_status cg_get_solve_info(const cg_handle* h, cg_solve_info* out);
+
+/* Matrix and schedule facts: n, nnz, row blocks, long rows, CTAs of the persistent kernel. */
+cg_status cg_get_matrix_info(const cg_handle* h, int64_t* n, int64_t* nnz, int64_t* row_blocks,
+                             int64_t* long_rows, int32_t* grid_ctas);
+
+/* Free every buffer owned by h (not the borrowed CSR).  NULL is a no-op. */
+void cg_destroy(cg_handle* h);
+
+/* Last error message of h, or of the calling thread's last failed cg_create when h is NULL. */
+const char* cg_last_error(const cg_handle* h);
+
+/* Static name of a status code. */
+const char* cg_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBCG_H */

@@ -1,0 +1,263 @@
+"""libcg Python binding: argument marshalling over the C ABI of ``include/libcg.h``.
+
+Every step of the solver runs in the CUDA kernels of ``libcg.so``; this module
+only passes device pointers of torch tensors, sizes and the current CUDA
+stream.  There is no CPU fallback: if ``libcg.so`` cannot be loaded, importing
+the functions raises.
+
+The functions keep the C names (``cg_create``, ``cg_spmv``, ``cg_solve`` ...).
+Paper anchors: CSR SpMV, Sec. 3.1; CG iteration, Alg. 1; fused kernels, Sec. 3.3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+from . import _build
+
+CG_OK, CG_NOT_CONVERGED = 0, 1
+CG_ERR_INVALID, CG_ERR_BREAKDOWN, CG_ERR_NUMERIC = -1, -2, -3
+CG_ERR_TIMEOUT, CG_ERR_CUDA, CG_ERR_OOM = -4, -5, -6
+CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+CG_PREC_FP64, CG_PREC_FP32_IR = 0, 1
+CG_OPT_MAX_RESTARTS, CG_OPT_BARRIER_TIMEOUT_MS, CG_OPT_GRID_CTAS = 0, 1, 2
+CG_OPT_IR_TOL_INNER, CG_OPT_IR_MAX_OUTER, CG_OPT_DEBUG_SKIP_ARRIVAL = 3, 4, 5
+
+# every symbol include/libcg.h declares
+EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
+           "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
+           "cg_last_error", "cg_status_string")
+
+
+class CGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("relres_true", ctypes.c_double), ("relres_rec", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("bytes_moved", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcg.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libcg.so not built at {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    pi32, pf64, pi64 = (ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_int64))
+    lib.cg_create.argtypes = [i64, P, P, P, ctypes.POINTER(P)]
+    lib.cg_set_stream.argtypes = [P, P]
+    lib.cg_set_option.argtypes = [P, i32, f64]
+    lib.cg_spmv.argtypes = [P, P, P]
+    lib.cg_solve.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
+    lib.cg_solve_host.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
+    lib.cg_get_solve_info.argtypes = [P, ctypes.POINTER(SolveInfo)]
+    lib.cg_get_matrix_info.argtypes = [P, pi64, pi64, pi64, pi64, pi32]
+    lib.cg_destroy.argtypes = [P]
+    lib.cg_destroy.restype = None
+    lib.cg_last_error.argtypes = [P]
+    lib.cg_last_error.restype = ctypes.c_char_p
+    lib.cg_status_string.argtypes = [i32]
+    lib.cg_status_string.restype = ctypes.c_char_p
+    for name in ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
+                 "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().cg_status_string(int(status)).decode()
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Handle:
+    """Owns a cg_handle; keeps the borrowed CSR tensors alive until destroyed."""
+
+    def __init__(self, ptr, n, keep):
+        self._ptr = ptr
+        self.n = n
+        self._keep = keep
+
+    @property
+    def ptr(self):
+        if self._ptr is None:
+            raise ValueError("handle already destroyed")
+        return self._ptr
+
+    def __del__(self):
+        try:
+            cg_destroy(self)
+        except Exception:
+            pass
+
+
+def cg_create(n: int, rowptr, colind, vals) -> Handle:
+    """Create a solver for the CSR matrix (device int32/int32/float64 tensors)."""
+    import torch
+    lib = load()
+    out = ctypes.c_void_p()
+    torch.cuda.current_stream().synchronize()
+    st = lib.cg_create(int(n), _dptr(rowptr, torch.int32, "rowptr"),
+                       _dptr(colind, torch.int32, "colind"), _dptr(vals, torch.float64, "vals"),
+                       ctypes.byref(out))
+    if st != CG_OK:
+        raise CGError(st, lib.cg_last_error(None).decode())
+    return Handle(out, int(n), (rowptr, colind, vals))
+
+
+def cg_last_error(h: Handle | None = None) -> str:
+    return load().cg_last_error(None if h is None else h.ptr).decode()
+
+
+def cg_set_stream(h: Handle, stream=None) -> int:
+    return load().cg_set_stream(h.ptr, _stream_ptr(stream))
+
+
+def cg_set_option(h: Handle, option: int, value: float) -> int:
+    return load().cg_set_option(h.ptr, int(option), float(value))
+
+
+def cg_spmv(h: Handle, x, y) -> int:
+    """y = A x on the current stream."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    return lib.cg_spmv(h.ptr, _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"))
+
+
+def cg_solve(h: Handle, b, x, tol: float = 1e-8, maxit: int = 1000,
+             precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64):
+    """Solve A x = b on the current stream; x holds x0 on entry.
+    Returns (status, iters, relres_true)."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.cg_solve(h.ptr, _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"),
+                      float(tol), int(maxit), int(precond), int(precision), ctypes.byref(it),
+                      ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def cg_solve_host(h: Handle, b_host, x_host, tol: float = 1e-8, maxit: int = 1000,
+                  precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64):
+    """cg_solve with host (preferably pinned) float64 tensors; copies happen inside
+    the call.  Returns (status, iters, relres_true)."""
+    import torch
+    for t, name in ((b_host, "b_host"), (x_host, "x_host")):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous host float64 tensor")
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = lib.cg_solve_host(h.ptr, ctypes.c_void_p(b_host.data_ptr()),
+                           ctypes.c_void_p(x_host.data_ptr()), float(tol), int(maxit),
+                           int(precond), int(precision), ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def cg_get_solve_info(h: Handle) -> dict:
+    info = SolveInfo()
+    st = load().cg_get_solve_info(h.ptr, ctypes.byref(info))
+    if st != CG_OK:
+        raise CGError(st, cg_last_error(h))
+    return info.as_dict()
+
+
+def cg_get_matrix_info(h: Handle) -> dict:
+    n, nnz, nrb, nlong = (ctypes.c_int64() for _ in range(4))
+    g = ctypes.c_int32()
+    load().cg_get_matrix_info(h.ptr, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(nrb),
+                              ctypes.byref(nlong), ctypes.byref(g))
+    return {"n": n.value, "nnz": nnz.value, "row_blocks": nrb.value, "long_rows": nlong.value,
+            "grid_ctas": g.value}
+
+
+def cg_destroy(h: Handle) -> None:
+    if h is not None and h._ptr is not None and _lib is not None:
+        _lib.cg_destroy(h._ptr)
+        h._ptr = None
+        h._keep = None
+
+
+@dataclass
+class Result:
+    status: int
+    iters: int
+    relres: float
+
+
+class Solver:
+    """Convenience wrapper: ``Solver(rowptr, colind, vals).solve(b, x)``."""
+
+    def __init__(self, rowptr, colind, vals):
+        self.n = rowptr.numel() - 1
+        self.h = cg_create(self.n, rowptr, colind, vals)
+
+    def spmv(self, x, y=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        st = cg_spmv(self.h, x, y)
+        if st != CG_OK:
+            raise CGError(st, cg_last_error(self.h))
+        return y
+
+    def solve(self, b, x=None, tol=1e-8, maxit=1000, precond=CG_PRECOND_JACOBI,
+              precision=CG_PREC_FP64, check=True) -> Result:
+        import torch
+        if x is None:
+            x = torch.zeros_like(b)
+        st, it, rel = cg_solve(self.h, b, x, tol, maxit, precond, precision)
+        if check and st < 0:
+            raise CGError(st, cg_last_error(self.h))
+        return Result(st, it, rel)
+
+    def set_option(self, option, value):
+        st = cg_set_option(self.h, option, value)
+        if st != CG_OK:
+            raise CGError(st, cg_last_error(self.h))
+
+    def info(self):
+        return cg_get_solve_info(self.h)
+
+    def close(self):
+        cg_destroy(self.h)

@@ -1,0 +1,149 @@
+// Device-side building blocks shared by the libcg kernels: bounded grid
+// barrier, fixed-order block and grid reductions, vector load helpers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cg {
+
+constexpr int kBlock = 256;          // threads per CTA of every libcg kernel
+constexpr int kWarps = kBlock / 32;
+
+// Device status words of one persistent launch (zeroed before each launch).
+struct DevState {
+  unsigned bar_count;    // arrivals at the current grid barrier
+  unsigned bar_gen;      // barrier generation, bumped by the last arriver
+  int abort;             // set by any CTA that gave up; every CTA then leaves
+  int status;            // cg_status of the solve
+  int iters;
+  int restarts;
+  int err_cta;           // CTA that first timed out (-1 none)
+  int err_barrier;       // barrier sequence number where it happened
+  double relres_true;
+  double relres_rec;
+};
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Grid-wide barrier for a co-resident (cooperatively launched) grid.  Every
+// wait is bounded: a CTA that waits longer than timeout_ns, or sees another
+// CTA's abort flag, records CG_ERR_TIMEOUT (-4) and returns false; the caller
+// must then leave the kernel.  `seq` numbers the barriers of the launch
+// (1-based) for the fault-injection hook: when skip_seq == seq, CTA 0 does not
+// arrive, so the barrier can never complete and every CTA's wait runs out.
+// With a single CTA this is a plain __syncthreads().
+__device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks, uint64_t timeout_ns,
+                                             unsigned seq, unsigned skip_seq) {
+  __shared__ int s_ok;
+  if (nblocks == 1) {
+    __syncthreads();
+    return true;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned gen = ld_acquire_u32(&st->bar_gen);
+    const bool skip = (skip_seq != 0u && seq == skip_seq && blockIdx.x == 0);
+    unsigned prev = skip ? 0u : atom_add_acq_rel_u32(&st->bar_count, 1u);
+    if (!skip && prev == nblocks - 1) {
+      atomicExch(&st->bar_count, 0u);
+      st_release_u32(&st->bar_gen, gen + 1u);
+    } else {
+      const uint64_t t0 = global_timer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if (ld_relaxed_s32(&st->abort) != 0) { ok = 0; break; }
+        if (((++spins) & 15u) == 0u && global_timer_ns() - t0 > timeout_ns) {
+          if (atomicCAS(&st->abort, 0, 1) == 0) {
+            st->err_cta = (int)blockIdx.x;
+            st->err_barrier = (int)seq;
+          }
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum of v over the CTA in a fixed order (warp xor-tree, then warp 0 over the
+// per-warp sums); the result is returned to every thread.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double s_red[NV][kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  }
+  __syncthreads();  // s_red may still be read from a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s_red[j][warp] = v[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s_red[j][w];
+    v[j] = t;
+  }
+}
+
+// Fixed-order sum of per-CTA partials part[j*G + c], c < G, for j < NV.  Every
+// CTA computes the identical value (same loads, same order), so decisions
+// made from it agree across the grid without another barrier.
+template <int NV>
+__device__ __forceinline__ void grid_sum(const double* part, unsigned G, double (&out)[NV]) {
+  __shared__ double s_out[NV];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = 0.0;
+      for (unsigned c = lane; c < G; c += 32) t += __ldcg(part + (size_t)j * G + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) s_out[j] = t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = s_out[j];
+  __syncthreads();
+}
+
+}  // namespace cg

@@ -1,0 +1,317 @@
+"""GPU parity: the CUDA path (through the C ABI) against the fp64 oracle on the same
+seeded inputs.
+
+Tolerances (derived from the arithmetic, stated here once):
+* SpMV: |y_gpu - y_oracle|_i <= 1e-12 * (|A| |x|)_i.  Stream row blocks sum in the
+  oracle's order and agree bit for bit; long rows use a tree order.
+* CG: same status; |iters_gpu - iters_oracle| <= max(3, 2% of iters_oracle) (reduction
+  order differs, Sec. 3.1 notes the effect); true relative residual of the GPU x,
+  recomputed by the oracle in fp64, <= tol; ||x_gpu - x_oracle|| / ||x_oracle|| <=
+  2 kappa tol where kappa is known, else 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import cgproblems as gen
+import oracle
+from helpers import adversarial, spd_from_pattern, to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2608_09647_gb300 as cg  # noqa: E402
+
+
+def iters_band(k):
+    return max(3, math.ceil(0.02 * k))
+
+
+def check_spmv(A, seed=1):
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    x = gen.xstar(A.n, seed)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    assert cg.cg_spmv(h, xd, yd) == cg.CG_OK
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    ref = oracle.spmv(A, x)
+    scale = np.abs(A.to_scipy()) @ np.abs(x)
+    err = np.abs(y - ref)
+    assert np.all(err <= 1e-12 * scale + 1e-300), f"max rel err {np.max(err / (scale + 1e-300))}"
+    cg.cg_destroy(h)
+    return y, ref
+
+
+# ---------------------------------------------------------------- a1: SpMV
+
+@pytest.mark.parametrize("A", [
+    gen.lap2d(64),                         # the 64 x 64 Poisson workload: 16 row blocks
+    gen.lap2d(37, 9, 0.01),                # ragged tail block
+    gen.lap3d7(23),                        # 12167 rows, ragged
+    gen.diff3d27(14, 1.0, 3),              # 27-point, 75-row blocks
+    gen.q1aniso(45, 1.5, 0.3, 0.05, 2),
+], ids=lambda A: A.name)
+def test_spmv_matches_oracle(A):
+    y, ref = check_spmv(A)
+    # stream row blocks reproduce the oracle's summation order exactly
+    assert np.array_equal(y, ref)
+
+
+@pytest.mark.parametrize("case", ["empty_rows", "long_rows", "huge_row", "tiny"])
+def test_spmv_adversarial_row_lengths(case):
+    if case == "empty_rows":
+        A = adversarial(3000, 1, empty_every=3)
+    elif case == "long_rows":   # rows longer than a row block's 2048 staged nonzeros
+        A = adversarial(6000, 2, long_rows=[(0, 2049), (17, 5000), (5999, 2500)])
+    elif case == "huge_row":    # one row touching every column
+        A = adversarial(20000, 3, long_rows=[(12345, 20000)])
+    else:
+        A = adversarial(1, 4, max_len=1)
+    check_spmv(A)
+
+
+def test_spmv_all_empty_rows():
+    n = 1000
+    A = gen.CSR(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0), "empty")
+    y, _ = check_spmv(A)
+    assert np.all(y == 0)
+
+
+# ---------------------------------------------------------------- a1-a5: solves
+
+def gpu_solve(A, b, tol, maxit, precond, precision=cg.CG_PREC_FP64, x0=None, h=None):
+    rp, ci, va = to_device(A)
+    own = h is None
+    if own:
+        h = cg.cg_create(A.n, rp, ci, va)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd) if x0 is None else torch.from_numpy(x0.copy()).cuda()
+    st, it, rel = cg.cg_solve(h, bd, xd, tol, maxit, precond, precision)
+    info = cg.cg_get_solve_info(h)
+    x = xd.cpu().numpy()
+    if own:
+        cg.cg_destroy(h)
+    return st, it, rel, x, info
+
+
+def compare_solve(A, b, tol, maxit, precond, kappa=None):
+    ref = oracle.pcg(A, b, tol=tol, maxit=maxit, precond=precond)
+    st, it, rel, x, info = gpu_solve(A, b, tol, maxit, precond)
+    assert st == ref.status, (st, ref.status, cg.cg_last_error())
+    assert abs(it - ref.iters) <= iters_band(ref.iters), (it, ref.iters)
+    rel_or = oracle.true_relres(A, b, x)
+    if st == cg.CG_OK:
+        assert rel_or <= tol * (1 + 1e-6)
+    assert abs(rel - rel_or) <= 1e-6 * rel_or + 1e-15
+    xerr = np.linalg.norm(x - ref.x) / np.linalg.norm(ref.x)
+    bound = 2 * kappa * tol if kappa else 1e-4
+    assert xerr <= bound, (xerr, bound)
+    return it, ref.iters, xerr, info
+
+
+def test_cg_poisson_64x64_unpreconditioned():
+    """The 64 x 64 Poisson workload: plain CG (Alg. 1), tol 1e-8, maxit 1000."""
+    A = gen.lap2d(64)
+    b = oracle.spmv(A, gen.xstar(A.n, 0))
+    kappa = 1.0 / math.tan(math.pi / 130) ** 2
+    it, it_or, xerr, _ = compare_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, kappa)
+    assert it <= 473  # Chebyshev bound
+
+
+@pytest.mark.parametrize("N", [20, 33])
+def test_jacobi_pcg_poisson_3d(N):
+    A = gen.lap3d7(N)
+    b = oracle.spmv(A, gen.xstar(A.n, 1))
+    kappa = 1.0 / math.tan(math.pi / (2 * (N + 1))) ** 2
+    compare_solve(A, b, 1e-8, 5000, cg.CG_PRECOND_JACOBI, kappa)
+
+
+def test_jacobi_pcg_variable_coefficient_27pt():
+    A = gen.diff3d27(16, 1.0, 5)
+    b = oracle.spmv(A, gen.xstar(A.n, 5))
+    compare_solve(A, b, 1e-10, 5000, cg.CG_PRECOND_JACOBI)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_jacobi_pcg_uneven_rows(seed):
+    A = spd_from_pattern(5000, seed, long_rows=[(10, 3000), (4000, 2100)])
+    b = oracle.spmv(A, gen.xstar(A.n, seed))
+    compare_solve(A, b, 1e-9, 2000, cg.CG_PRECOND_JACOBI)
+
+
+def test_anisotropic_batch_member():
+    A = gen.lap2d(70, 9, 2e-3)
+    b = oracle.spmv(A, gen.xstar(A.n, 9))
+    compare_solve(A, b, 1e-8, 5000, cg.CG_PRECOND_JACOBI)
+
+
+def test_solve_is_deterministic():
+    A = gen.lap3d7(24)
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    r1 = gpu_solve(A, b, 1e-8, 2000, cg.CG_PRECOND_JACOBI)
+    r2 = gpu_solve(A, b, 1e-8, 2000, cg.CG_PRECOND_JACOBI)
+    assert r1[1] == r2[1] and np.array_equal(r1[3], r2[3])
+
+
+def test_grid_size_does_not_change_the_answer_beyond_rounding():
+    A = gen.lap3d7(24)
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    outs = []
+    for g in (1, 3, 0):
+        assert cg.cg_set_option(h, cg.CG_OPT_GRID_CTAS, g) == cg.CG_OK
+        st, it, rel, x, info = gpu_solve(A, b, 1e-8, 2000, cg.CG_PRECOND_JACOBI, h=h)
+        assert st == cg.CG_OK and rel <= 1e-8
+        outs.append((it, x, info["grid_ctas"]))
+    assert outs[0][2] == 1 and outs[1][2] == 3
+    for it, x, _ in outs[1:]:
+        assert abs(it - outs[0][0]) <= 3
+        assert np.linalg.norm(x - outs[0][1]) <= 1e-5 * np.linalg.norm(outs[0][1])
+    cg.cg_destroy(h)
+
+
+# ---------------------------------------------------------------- mixed precision
+
+@pytest.mark.parametrize("tol_in", [1e-3, 1e-4])
+def test_fp32_refinement_reaches_fp64_tolerance(tol_in):
+    A = gen.diff3d27(14, 1.0, 7)
+    b = oracle.spmv(A, gen.xstar(A.n, 7))
+    ref = oracle.pcg_ir(A, b, tol=1e-10, tol_in=tol_in)
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_IR_TOL_INNER, tol_in) == cg.CG_OK
+    st, it, rel, x, info = gpu_solve(A, b, 1e-10, 100000, cg.CG_PRECOND_JACOBI,
+                                     cg.CG_PREC_FP32_IR, h=h)
+    cg.cg_destroy(h)
+    assert st == cg.CG_OK == ref.status
+    assert oracle.true_relres(A, b, x) <= 1e-10 * (1 + 1e-6)
+    assert abs(info["restarts"] - ref.restarts) <= 1
+    assert abs(it - ref.iters) <= max(5, math.ceil(0.1 * ref.iters)), (it, ref.iters)
+    fp64 = oracle.pcg(A, b, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(x - fp64.x) / np.linalg.norm(fp64.x) <= 1e-7
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_zero_rhs():
+    A = gen.lap2d(16)
+    st, it, rel, x, _ = gpu_solve(A, np.zeros(A.n), 1e-8, 100, cg.CG_PRECOND_JACOBI,
+                                  x0=np.ones(A.n))
+    assert st == cg.CG_OK and it == 0 and rel == 0.0 and np.all(x == 0)
+
+
+def test_exact_initial_guess():
+    A = gen.lap2d(16)
+    xs = gen.xstar(A.n, 3)
+    b = oracle.spmv(A, xs)
+    st, it, rel, x, _ = gpu_solve(A, b, 1e-8, 100, cg.CG_PRECOND_JACOBI, x0=xs)
+    assert st == cg.CG_OK and it == 0
+
+
+def test_maxit_not_converged_matches_oracle():
+    A = gen.lap2d(40)
+    b = oracle.spmv(A, gen.xstar(A.n, 1))
+    ref = oracle.pcg(A, b, tol=1e-12, maxit=25, precond=0)
+    st, it, rel, x, _ = gpu_solve(A, b, 1e-12, 25, cg.CG_PRECOND_NONE)
+    assert st == cg.CG_NOT_CONVERGED == ref.status and it == 25
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+
+
+def test_maxit_zero():
+    A = gen.lap2d(8)
+    b = oracle.spmv(A, gen.xstar(A.n, 1))
+    st, it, rel, x, _ = gpu_solve(A, b, 1e-8, 0, cg.CG_PRECOND_JACOBI)
+    assert st == cg.CG_NOT_CONVERGED and it == 0 and np.all(x == 0)
+
+
+def test_empty_matrix():
+    rp = torch.zeros(1, dtype=torch.int32, device="cuda")
+    h = cg.cg_create(0, rp, None, None)
+    st, it, rel = cg.cg_solve(h, None, None, 1e-8, 10, 0, 0)
+    assert st == cg.CG_OK and it == 0
+    cg.cg_destroy(h)
+
+
+def test_indefinite_matrix_breaks_down():
+    import scipy.sparse as sp
+    M = sp.diags([1.0, 2.0, -3.0, 4.0] * 50).tocsr()
+    A = gen.CSR(200, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data, "indef")
+    b = np.ones(200)
+    ref = oracle.pcg(A, b, tol=1e-10, maxit=50, precond=0)
+    st, *_ = gpu_solve(A, b, 1e-10, 50, cg.CG_PRECOND_NONE)
+    assert st == cg.CG_ERR_BREAKDOWN == ref.status
+
+
+def test_nan_rhs_is_numeric_error():
+    A = gen.lap2d(12)
+    b = np.ones(A.n)
+    b[7] = np.nan
+    st, *_ = gpu_solve(A, b, 1e-8, 50, cg.CG_PRECOND_JACOBI)
+    assert st == cg.CG_ERR_NUMERIC == oracle.pcg(A, b, tol=1e-8, maxit=50).status
+
+
+def test_invalid_column_index_rejected():
+    A = gen.lap2d(10)
+    ci = A.colind.copy()
+    ci[37] = A.n  # out of range
+    rp, _, va = to_device(A)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.n, rp, torch.from_numpy(ci).cuda(), va)
+    assert e.value.status == cg.CG_ERR_INVALID
+
+
+def test_decreasing_rowptr_rejected():
+    A = gen.lap2d(10)
+    rp = A.rowptr.copy()
+    rp[5], rp[6] = rp[6], rp[5]
+    _, ci, va = to_device(A)
+    with pytest.raises(cg.CGError) as e:
+        cg.cg_create(A.n, torch.from_numpy(rp).cuda(), ci, va)
+    assert e.value.status == cg.CG_ERR_INVALID
+
+
+def test_jacobi_needs_positive_diagonal():
+    import scipy.sparse as sp
+    M = sp.csr_matrix((np.array([2.0, 3.0]), np.array([0, 2], np.int32),
+                       np.array([0, 1, 1, 2], np.int32)), shape=(3, 3))
+    A = gen.CSR(3, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data, "nodiag")
+    st, *_ = gpu_solve(A, np.ones(3), 1e-8, 10, cg.CG_PRECOND_JACOBI)
+    assert st == cg.CG_ERR_INVALID
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    """Fault injection on the host's request: CTA 0 skips its arrival at the second grid
+    barrier, so every CTA's bounded wait runs out; the solve returns CG_ERR_TIMEOUT and
+    the next solve on the same handle works."""
+    A = gen.lap2d(64)
+    b = oracle.spmv(A, gen.xstar(A.n, 0))
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_get_matrix_info(h)["grid_ctas"] > 1
+    assert cg.cg_set_option(h, cg.CG_OPT_BARRIER_TIMEOUT_MS, 100) == cg.CG_OK
+    assert cg.cg_set_option(h, cg.CG_OPT_DEBUG_SKIP_ARRIVAL, 2) == cg.CG_OK
+    st, *_ = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
+    assert st == cg.CG_ERR_TIMEOUT
+    assert "timed out" in cg.cg_last_error(h)
+    assert cg.cg_set_option(h, cg.CG_OPT_DEBUG_SKIP_ARRIVAL, 0) == cg.CG_OK
+    st, it, rel, x, _ = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
+    assert st == cg.CG_OK and rel <= 1e-8
+    cg.cg_destroy(h)
+
+
+def test_host_buffer_entry_point_matches_device_entry_point():
+    A = gen.lap3d7(16)
+    b = oracle.spmv(A, gen.xstar(A.n, 4))
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    st, it, rel = cg.cg_solve_host(h, bh, xh, 1e-8, 2000, cg.CG_PRECOND_JACOBI, cg.CG_PREC_FP64)
+    st2, it2, rel2, x2, _ = gpu_solve(A, b, 1e-8, 2000, cg.CG_PRECOND_JACOBI, h=h)
+    assert st == st2 == cg.CG_OK and it == it2
+    assert np.array_equal(xh.numpy(), x2)
+    cg.cg_destroy(h)
