@@ -38,6 +38,8 @@ WORKLOADS = {
                       "3-D 7-point Poisson 256^3, FP64 Jacobi-PCG to 1e-8"),
     "poisson2d_64": ("lap2d", {"N": 64}, "none", "fp64", 1e-8, 1000,
                      "2-D 5-point Poisson 64x64, FP64 CG to 1e-8"),
+    "poisson3d_128": ("lap3d7", {"N": 128}, "jacobi", "fp64", 1e-8, 10000,
+                      "3-D 7-point Poisson 128^3, FP64 Jacobi-PCG to 1e-8 (profiling size)"),
     "diffusion27_160": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp32_ir",
                         1e-10, 100000,
                         "3-D 27-point lognormal diffusion 160^3, FP32 inner / FP64 refinement to 1e-10"),
@@ -225,6 +227,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle CPU time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -255,6 +259,8 @@ def main():
     A = build_matrix(args.workload)
     rp, ci, va = (torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colind, A.vals))
     h = cg.cg_create(A.n, rp, ci, va)
+    mode = {"auto": 0, "persistent": 1, "graph": 2, "unrolled": 3}[args.loop_mode]
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
     xs = torch.from_numpy(gen.xstar(A.n, 0)).to(dev)
     b = torch.empty_like(xs)
     assert cg.cg_spmv(h, xs, b) == cg.CG_OK        # b = A x* on the device
@@ -313,22 +319,26 @@ def main():
         traffic = int(tr["dram_bytes_per_iter"] * statistics.mean(iters))
 
     # end to end through the host-buffer entry point
-    bh = torch.from_numpy(b.cpu().numpy()).pin_memory()
-    xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
-    cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)   # warm the staging buffers
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        xh.zero_()
-        st, it, rel = cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)
-        if st != cg.CG_OK:
-            raise RuntimeError(f"host solve failed: {cg.status_string(st)}")
-    barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e = None
+    if not args.no_e2e:
+        bh = torch.from_numpy(b.cpu().numpy()).pin_memory()
+        xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+        cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)   # warm the staging buffers
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh.zero_()
+            st, it, rel = cg.cg_solve_host(h, bh, xh, tol, maxit, precond, precision)
+            if st != cg.CG_OK:
+                raise RuntimeError(f"host solve failed: {cg.status_string(st)}")
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
+               "h2d_bytes_per_step": 16 * A.n, "d2h_bytes_per_step": 8 * A.n}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -353,15 +363,14 @@ def main():
             "config": {"workload": args.workload, "description": desc, "n": A.n, "nnz": A.nnz,
                        "tol": tol, "iters": iters[0], "relres_true_max": relres,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
-                       "grid_ctas": infos[0][2]["grid_ctas"]},
+                       "grid_ctas": infos[0][2]["grid_ctas"], "loop_mode": args.loop_mode},
             "iter_us": 1e3 * kern_ms / sum(iters),
             "loop_gbs_model": achieved,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "pcg64_kernel<Jacobi>" if precision_s == "fp64" else "pcg_ir_kernel<Jacobi>",
                          "bytes_per_iter_model": bpi, "peak_kind": peak_kind},
-            "e2e": {"value": world * args.steps / e2e_s, "unit": "solves/s",
-                    "h2d_bytes_per_step": 16 * A.n, "d2h_bytes_per_step": 8 * A.n},
+            "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,

@@ -62,8 +62,12 @@ typedef enum {
   CG_OPT_GRID_CTAS = 2,           /* persistent-kernel CTAs; 0 = choose automatically (default) */
   CG_OPT_IR_TOL_INNER = 3,        /* inner relative tolerance of fp32 refinement (default 1e-4) */
   CG_OPT_IR_MAX_OUTER = 4,        /* refinement steps cap (default 30) */
-  CG_OPT_DEBUG_SKIP_ARRIVAL = 5   /* fault injection: CTA 0 skips arrival at grid barrier #value
+  CG_OPT_DEBUG_SKIP_ARRIVAL = 5,  /* fault injection: CTA 0 skips arrival at grid barrier #value
                                      (1-based; 0 = off), so every wait runs into its limit */
+  CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
+  CG_OPT_LOOP_MODE = 7            /* fp64 loop form: 0 auto (graph from 2^20 rows), 1 one persistent cooperative launch,
+                                     2 CUDA graph with a device-side WHILE node, 3 graphs of 8
+                                     unrolled iterations relaunched by the host until done */
 } cg_option;
 
 /* Statistics of the most recent cg_solve on a handle. */
@@ -75,7 +79,13 @@ typedef struct {
   double relres_true;     /* ||b - A x||_2 / ||b||_2 recomputed in fp64 from the final x */
   double relres_rec;      /* the recursive residual's relative norm at exit */
   double kernel_ms;       /* device time of the persistent launch (CUDA events) */
-  int64_t bytes_moved;    /* modelled HBM bytes of the launch (algorithmic count) */
+  int64_t bytes_moved;    /* modelled HBM bytes of the loop: iters x (12 nnz + 4(n+1) + 104 n)
+                             (Jacobi; 88 n without; fp32 refinement 8 nnz + 4(n+1) + 52/44 n) */
+  int64_t kernel_bytes_per_iter; /* bytes one iteration of this library's loop must move:
+                             its SELL-32 off-diagonal slices (12 B/entry fp64, 8 B fp32) plus
+                             88 n (Jacobi) / 80 n bytes of vectors (fp64; half that in fp32) */
+  double phase_ms[6];     /* with CG_OPT_PHASE_TIMERS: CTA 0 time in the SpMV, r-update and
+                             x/p-update phases, each followed by its grid-barrier wait */
 } cg_solve_info;
 
 /*

@@ -23,6 +23,7 @@ CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
 CG_PREC_FP64, CG_PREC_FP32_IR = 0, 1
 CG_OPT_MAX_RESTARTS, CG_OPT_BARRIER_TIMEOUT_MS, CG_OPT_GRID_CTAS = 0, 1, 2
 CG_OPT_IR_TOL_INNER, CG_OPT_IR_MAX_OUTER, CG_OPT_DEBUG_SKIP_ARRIVAL = 3, 4, 5
+CG_OPT_PHASE_TIMERS, CG_OPT_LOOP_MODE = 6, 7
 
 # every symbol include/libcg.h declares
 EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
@@ -40,10 +41,13 @@ class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("relres_true", ctypes.c_double), ("relres_rec", ctypes.c_double),
-                ("kernel_ms", ctypes.c_double), ("bytes_moved", ctypes.c_int64)]
+                ("kernel_ms", ctypes.c_double), ("bytes_moved", ctypes.c_int64),
+                ("kernel_bytes_per_iter", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
 
 
 _lib = None

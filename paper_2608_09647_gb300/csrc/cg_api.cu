@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "../../include/libcg.h"
-#include "cg_kernels.cuh"
+#include "cg_graph.cuh"
 
 using namespace cg;
 
@@ -21,68 +21,171 @@ namespace {
 thread_local std::string g_create_error;
 
 // Device checks of a CSR whose rowptr the host has already validated:
-// colind in [0, n); diagonal sum per row -> dinv (0 marks a row without a
-// positive diagonal).
+// colind in [0, n); per row the diagonal sum A_ii and the number of stored
+// diagonal entries; counters[1] counts rows without a positive diagonal.
 __global__ void validate_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                                 const int32_t* __restrict__ colind, const double* __restrict__ vals,
-                                double* dinv, unsigned long long* counters) {
+                                double* diag, int32_t* ndiag, unsigned long long* counters) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int a = rowptr[i], e = rowptr[i + 1];
     double d = 0.0;
-    bool found = false;
+    int found = 0;
     unsigned long long bad = 0;
     for (int k = a; k < e; ++k) {
       const int c = colind[k];
       if (c < 0 || (int64_t)c >= n) { ++bad; continue; }
-      if ((int64_t)c == i) { d += vals[k]; found = true; }
+      if ((int64_t)c == i) { d += vals[k]; ++found; }
     }
     if (bad) atomicAdd(&counters[0], bad);
-    if (found && d > 0.0) {
-      dinv[i] = 1.0 / d;
-    } else {
-      dinv[i] = 0.0;
-      atomicAdd(&counters[1], 1ull);
+    diag[i] = d;
+    ndiag[i] = found;
+    if (!(found && d > 0.0)) atomicAdd(&counters[1], 1ull);
+  }
+}
+
+// Diagonal vectors: sqrt(A_ii), 1/sqrt(A_ii) (Jacobi scaling) and fp32 copies.
+__global__ void diag_kernel(int64_t n, const double* __restrict__ diag, double* dsq, double* disq,
+                            float* diag32, float* disq32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = diag[i];
+    const double s = d > 0.0 ? sqrt(d) : 0.0;
+    const double si = d > 0.0 ? 1.0 / s : 0.0;
+    dsq[i] = s;
+    disq[i] = si;
+    diag32[i] = (float)d;
+    disq32[i] = (float)si;
+  }
+}
+
+// SELL-32 slices of the off-diagonal part (thread per row i): entries of a
+// short row go to column m of its slice in storage order, the rest of the
+// slice width is padding (column = i, value = 0); a long row (more than
+// kLongRow off-diagonal entries) gets padding only.  With SCALE the values
+// become A_ij / sqrt(A_ii A_jj) (the product of the two scales is formed
+// first, so A^ stays bitwise symmetric when A is).  col may be null (already
+// written by an earlier value variant).
+template <typename T, bool SCALE>
+__global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colind,
+                                 const double* __restrict__ vals,
+                                 const int32_t* __restrict__ ndiag,
+                                 const double* __restrict__ disq,
+                                 const int32_t* __restrict__ soff, int32_t* col, T* val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i >> 5, l = i & 31;
+    const int64_t base = (int64_t)soff[s] * 32 + l;
+    const int w = soff[s + 1] - soff[s];
+    const int len = rowptr[i + 1] - rowptr[i] - ndiag[i];
+    int m = 0;
+    if (len <= kLongRow) {
+      const double si = SCALE ? disq[i] : 1.0;
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int c = colind[k];
+        if ((int64_t)c == i) continue;
+        if (col) col[base + (int64_t)m * 32] = c;
+        val[base + (int64_t)m * 32] = (T)(SCALE ? vals[k] * (si * disq[c]) : vals[k]);
+        ++m;
+      }
+    }
+    for (; m < w; ++m) {
+      if (col) col[base + (int64_t)m * 32] = (int32_t)i;
+      val[base + (int64_t)m * 32] = T(0);
     }
   }
 }
 
-__global__ void to_float_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// Compact CSR of the long rows (thread per long row).
+template <typename T, bool SCALE>
+__global__ void fill_long_kernel(int32_t nlong, const int32_t* __restrict__ lrow,
+                                 const int32_t* __restrict__ lptr,
+                                 const int32_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ colind,
+                                 const double* __restrict__ vals,
+                                 const double* __restrict__ disq, int32_t* lcol, T* lval) {
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < nlong;
+       l += (int64_t)gridDim.x * blockDim.x) {
+    const int i = lrow[l];
+    int ko = lptr[l];
+    const double si = SCALE ? disq[i] : 1.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int c = colind[k];
+      if (c == i) continue;
+      if (lcol) lcol[ko] = c;
+      lval[ko] = (T)(SCALE ? vals[k] * (si * disq[c]) : vals[k]);
+      ++ko;
+    }
+  }
 }
 
 }  // namespace
 
+// Device memory owned by a handle.  The internal off-diagonal matrices and
+// work vectors are built on first use of a precision / preconditioner.
 struct cg_handle {
   int64_t n = 0, nnz = 0;
-  const int32_t* rowptr = nullptr;
+  const int32_t* rowptr = nullptr;  // borrowed caller CSR
   const int32_t* colind = nullptr;
   const double* vals = nullptr;
-  int32_t* rb = nullptr;       // row-block boundaries [nrb + 1]
+  int32_t* rb = nullptr;            // row blocks of the caller CSR
   int32_t nrb = 0;
   int64_t long_rows = 0;
-  double* dinv = nullptr;
+  std::vector<int32_t> host_rowptr;
+  // diagonal data
+  double* diag = nullptr;           // A_ii (sum of stored diagonal entries)
+  int32_t* ndiag = nullptr;         // diagonal entries per row
+  double *dsq = nullptr, *disq = nullptr;
+  float *diag32 = nullptr, *disq32 = nullptr;
   bool jacobi_ok = false;
-  float* vals32 = nullptr;     // refinement: fp32 values and work vectors (lazy)
-  float* dinv32 = nullptr;
-  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;
-  double *r = nullptr, *p = nullptr, *q = nullptr;
+  // off-diagonal loop matrix in SELL-32 form (+ compact CSR of long rows)
+  int32_t nslices = 0;
+  int32_t uniform_w = -1;           // every slice padded to this width (-1: variable)
+  int32_t* soff = nullptr;
+  uint32_t* lmask = nullptr;
+  int32_t* scol = nullptr;
+  int64_t sell_entries = 0;         // padded entries (multiple of 32)
+  int64_t nnz_od = 0;
+  int32_t nlong = 0;
+  int32_t *lrow = nullptr, *lptr = nullptr, *lcol = nullptr;
+  int64_t nnz_long = 0;
+  double* sval64[2] = {nullptr, nullptr};  // [precond]: unscaled / Jacobi-scaled
+  float* sval32[2] = {nullptr, nullptr};
+  double* lval64[2] = {nullptr, nullptr};
+  float* lval32[2] = {nullptr, nullptr};
+  bool scol_written = false;
+  // work vectors
+  double *r = nullptr, *p = nullptr, *q = nullptr, *xh = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xh32 = nullptr;
   double* part = nullptr;
   DevState* st = nullptr;
-  DevState* host_st = nullptr; // pinned
+  DevState* host_st = nullptr;      // pinned
   double *stage_b = nullptr, *stage_x = nullptr;  // device staging of cg_solve_host (lazy)
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int sm_count = 0;
-  int grid_max = 0;            // co-resident CTAs of the persistent kernels
-  int grid_opt = 0;            // CG_OPT_GRID_CTAS (0 = auto)
+  int grid_max = 0;                 // co-resident CTAs of the persistent kernels
+  int grid_opt = 0;                 // CG_OPT_GRID_CTAS (0 = auto)
   int max_restarts = 3;
   double timeout_ms = 2000.0;
   double tol_in = 1e-4;
   int max_outer = 30;
   unsigned skip_seq = 0;
+  int timers = 0;
+  int loop_mode = 0;                // CG_OPT_LOOP_MODE (0 auto, 1 persistent, 2 graph)
+  // graph form of the loop
+  int grid_graph = 0;               // CTAs of the graph-mode vector kernels
+  int grid_part = 0;                // partial-sum slots per kind (the largest grid of any loop kernel)
+  GState* gs = nullptr;
+  GState* host_gs = nullptr;        // pinned
+  cudaGraph_t graph = nullptr, graph_it = nullptr, graph_ep = nullptr;
+  cudaGraphExec_t gexec = nullptr, gexec_it = nullptr, gexec_ep = nullptr;
+  int gkey_unroll = -1;
+  const void* gkey_b = nullptr;     // the graph bakes in these solve arguments
+  const void* gkey_x = nullptr;
+  double gkey_tol = -1.0;
+  int gkey_maxit = -1, gkey_jac = -1;
   cg_solve_info last{};
   std::string err;
 };
@@ -108,10 +211,13 @@ cg_status cuda_fail(cg_handle* h, cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+unsigned grid_for(int64_t items) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 65535));
+}
+
 // Cut rows into row blocks: greedily extend a block while it stays within
 // kCap nonzeros and kBlock rows; a row longer than kCap gets a block alone.
-std::vector<int32_t> build_row_blocks(const std::vector<int32_t>& rowptr, int64_t n,
-                                      int64_t* long_rows) {
+std::vector<int32_t> build_row_blocks(const int32_t* rowptr, int64_t n, int64_t* long_rows) {
   std::vector<int32_t> rb;
   rb.reserve((size_t)(n / 64 + 2));
   rb.push_back(0);
@@ -153,33 +259,315 @@ int auto_grid(const cg_handle* h) {
   return (int)std::min<int64_t>(want, h->grid_max);
 }
 
-cg_status ensure_fp32(cg_handle* h) {
-  if (h->vals32) return CG_OK;
-  const size_t nv = (size_t)std::max<int64_t>(h->n, 1);
-  CG_CUDA(h, cudaMalloc(&h->vals32, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1)));
-  CG_CUDA(h, cudaMalloc(&h->dinv32, sizeof(float) * nv));
-  CG_CUDA(h, cudaMalloc(&h->r32, sizeof(float) * nv));
-  CG_CUDA(h, cudaMalloc(&h->p32, sizeof(float) * nv));
-  CG_CUDA(h, cudaMalloc(&h->q32, sizeof(float) * nv));
-  CG_CUDA(h, cudaMalloc(&h->d32, sizeof(float) * nv));
-  if (h->nnz > 0)
-    to_float_kernel<<<std::min<int64_t>((h->nnz + 255) / 256, 4096), 256, 0, h->stream>>>(
-        h->nnz, h->vals, h->vals32);
-  if (h->n > 0)
-    to_float_kernel<<<std::min<int64_t>((h->n + 255) / 256, 4096), 256, 0, h->stream>>>(
-        h->n, h->dinv, h->dinv32);
-  CG_CUDA(h, cudaGetLastError());
+// SELL-32 structure of the off-diagonal part (shared by every value
+// variant) and the diagonal vectors.
+cg_status ensure_offdiag(cg_handle* h) {
+  if (h->soff) return CG_OK;
+  const int64_t n = h->n;
+  std::vector<int32_t> nd((size_t)n);
+  if (n > 0) CG_CUDA(h, cudaMemcpy(nd.data(), h->ndiag, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost));
+  const std::vector<int32_t>& rp = h->host_rowptr;
+  const int64_t ns = (n + 31) / 32;
+  std::vector<int32_t> soff((size_t)ns + 1, 0);
+  std::vector<uint32_t> lmask((size_t)std::max<int64_t>(ns, 1), 0u);
+  std::vector<int32_t> lrow, lptr(1, 0);
+  std::vector<int32_t> width((size_t)std::max<int64_t>(ns, 1), 0);
+  int64_t sumw = 0, nnz_od = 0;
+  int maxw = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    int w = 0;
+    for (int64_t i = s * 32; i < std::min<int64_t>(n, s * 32 + 32); ++i) {
+      const int len = rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
+      nnz_od += len;
+      if (len > kLongRow) {
+        lmask[(size_t)s] |= 1u << (i & 31);
+        lrow.push_back((int32_t)i);
+        lptr.push_back(lptr.back() + len);
+      } else {
+        w = std::max(w, len);
+      }
+    }
+    width[(size_t)s] = w;
+    sumw += w;
+    maxw = std::max(maxw, w);
+  }
+  // uniform slices (offsets computed, not loaded) when that pads by <= 1/16
+  const bool uniform = lrow.empty() && ns > 0 && (int64_t)maxw * ns * 16 <= sumw * 17;
+  h->uniform_w = uniform ? maxw : -1;
+  int64_t off = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    off += uniform ? maxw : width[(size_t)s];
+    if (off >= INT32_MAX / 32) return fail(h, CG_ERR_INVALID, "cg_create: padded matrix too large");
+    soff[(size_t)s + 1] = (int32_t)off;
+  }
+  h->nslices = (int32_t)ns;
+  h->sell_entries = off * 32;
+  h->nnz_od = nnz_od;
+  h->nlong = (int32_t)lrow.size();
+  h->nnz_long = lptr.back();
+  const size_t nv = (size_t)std::max<int64_t>(n, 1);
+  CG_CUDA(h, cudaMalloc(&h->soff, sizeof(int32_t) * soff.size()));
+  CG_CUDA(h, cudaMemcpy(h->soff, soff.data(), sizeof(int32_t) * soff.size(), cudaMemcpyHostToDevice));
+  CG_CUDA(h, cudaMalloc(&h->lmask, sizeof(uint32_t) * lmask.size()));
+  CG_CUDA(h, cudaMemcpy(h->lmask, lmask.data(), sizeof(uint32_t) * lmask.size(), cudaMemcpyHostToDevice));
+  CG_CUDA(h, cudaMalloc(&h->scol, sizeof(int32_t) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
+  CG_CUDA(h, cudaMalloc(&h->lrow, sizeof(int32_t) * std::max<size_t>(lrow.size(), 1)));
+  CG_CUDA(h, cudaMalloc(&h->lptr, sizeof(int32_t) * lptr.size()));
+  CG_CUDA(h, cudaMalloc(&h->lcol, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz_long, 1)));
+  if (!lrow.empty())
+    CG_CUDA(h, cudaMemcpy(h->lrow, lrow.data(), sizeof(int32_t) * lrow.size(), cudaMemcpyHostToDevice));
+  CG_CUDA(h, cudaMemcpy(h->lptr, lptr.data(), sizeof(int32_t) * lptr.size(), cudaMemcpyHostToDevice));
+  CG_CUDA(h, cudaMalloc(&h->dsq, sizeof(double) * nv));
+  CG_CUDA(h, cudaMalloc(&h->disq, sizeof(double) * nv));
+  CG_CUDA(h, cudaMalloc(&h->diag32, sizeof(float) * nv));
+  CG_CUDA(h, cudaMalloc(&h->disq32, sizeof(float) * nv));
+  if (n > 0) {
+    diag_kernel<<<grid_for(n), 256>>>(n, h->diag, h->dsq, h->disq, h->diag32, h->disq32);
+    CG_CUDA(h, cudaGetLastError());
+    CG_CUDA(h, cudaDeviceSynchronize());
+  }
   return CG_OK;
 }
 
+// Loop-matrix values for (precision, precond), built on first use; the first
+// variant built also writes the shared column indices.
+template <typename T>
+cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
+  if (*sval) return CG_OK;
+  cg_status s = ensure_offdiag(h);
+  if (s != CG_OK) return s;
+  const bool write_col = !h->scol_written;
+  CG_CUDA(h, cudaMalloc(sval, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
+  CG_CUDA(h, cudaMalloc(lval, sizeof(T) * (size_t)std::max<int64_t>(h->nnz_long, 1)));
+  if (h->n > 0) {
+    int32_t* col = write_col ? h->scol : nullptr;
+    int32_t* lcol = write_col ? h->lcol : nullptr;
+    if (scale) {
+      fill_sell_kernel<T, true><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals,
+                                                         h->ndiag, h->disq, h->soff, col, *sval);
+      if (h->nlong)
+        fill_long_kernel<T, true><<<grid_for(h->nlong), 256>>>(h->nlong, h->lrow, h->lptr,
+                                                               h->rowptr, h->colind, h->vals,
+                                                               h->disq, lcol, *lval);
+    } else {
+      fill_sell_kernel<T, false><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals,
+                                                          h->ndiag, h->disq, h->soff, col, *sval);
+      if (h->nlong)
+        fill_long_kernel<T, false><<<grid_for(h->nlong), 256>>>(h->nlong, h->lrow, h->lptr,
+                                                                h->rowptr, h->colind, h->vals,
+                                                                h->disq, lcol, *lval);
+    }
+    CG_CUDA(h, cudaGetLastError());
+    CG_CUDA(h, cudaDeviceSynchronize());
+  }
+  h->scol_written = true;
+  return CG_OK;
+}
+
+template <typename T>
+cg_status ensure_vectors(cg_handle* h, T** r, T** p, T** q, T** xh) {
+  if (*r) return CG_OK;
+  const size_t nv = (size_t)std::max<int64_t>(h->n, 1);
+  CG_CUDA(h, cudaMalloc(r, sizeof(T) * nv));
+  CG_CUDA(h, cudaMalloc(p, sizeof(T) * nv));
+  CG_CUDA(h, cudaMalloc(q, sizeof(T) * nv));
+  CG_CUDA(h, cudaMalloc(xh, sizeof(T) * nv));
+  return CG_OK;
+}
+
+void destroy_graph(cudaGraphExec_t* e, cudaGraph_t* g) {
+  if (*e) { cudaGraphExecDestroy(*e); *e = nullptr; }
+  if (*g) { cudaGraphDestroy(*g); *g = nullptr; }
+}
+
 void free_all(cg_handle* h) {
-  void* dev[] = {h->rb, h->dinv, h->vals32, h->dinv32, h->r32,  h->p32,    h->q32, h->d32,
-                 h->r,  h->p,    h->q,      h->part,   h->st,   h->stage_b, h->stage_x};
+  void* dev[] = {h->rb,        h->diag,      h->ndiag,     h->dsq,       h->disq,
+                 h->diag32,    h->disq32,    h->soff,      h->lmask,     h->scol,
+                 h->lrow,      h->lptr,      h->lcol,      h->sval64[0], h->sval64[1],
+                 h->sval32[0], h->sval32[1], h->lval64[0], h->lval64[1], h->lval32[0],
+                 h->lval32[1], h->r,         h->p,         h->q,         h->xh,
+                 h->r32,       h->p32,       h->q32,       h->xh32,      h->part,
+                 h->st,        h->stage_b,   h->stage_x};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->host_st) cudaFreeHost(h->host_st);
+  if (h->host_gs) cudaFreeHost(h->host_gs);
+  if (h->gs) cudaFree(h->gs);
+  destroy_graph(&h->gexec, &h->graph);
+  destroy_graph(&h->gexec_it, &h->graph_it);
+  destroy_graph(&h->gexec_ep, &h->graph_ep);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+}
+
+// The graph-mode SpMV kernel for the loop matrix's slice layout.
+const void* spmv_kernel_for(int uw, bool jac) {
+  switch (uw) {
+    case 4: return jac ? (const void*)g_spmv<double, true, 4> : (const void*)g_spmv<double, false, 4>;
+    case 6: return jac ? (const void*)g_spmv<double, true, 6> : (const void*)g_spmv<double, false, 6>;
+    case 8: return jac ? (const void*)g_spmv<double, true, 8> : (const void*)g_spmv<double, false, 8>;
+    default: return jac ? (const void*)g_spmv<double, true, 0> : (const void*)g_spmv<double, false, 0>;
+  }
+}
+
+// Append a kernel node after `dep` (may be null) to graph g.
+template <typename... Args>
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn,
+                       unsigned grid, unsigned block, void** args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+// Build and instantiate the graph form of an fp64 solve for (b, x, tol, maxit,
+// precond).  unroll == 0: one graph [prologue, WHILE{3 phase kernels},
+// epilogue].  unroll > 0: three graphs (prologue, `unroll` iterations whose
+// kernels return at once after the loop has stopped, epilogue) that the host
+// launches in turn, reading the loop state after each iteration graph.
+cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll) {
+  destroy_graph(&h->gexec, &h->graph);
+  destroy_graph(&h->gexec_it, &h->graph_it);
+  destroy_graph(&h->gexec_ep, &h->graph_ep);
+  cudaGraph_t g;
+  CG_CUDA(h, cudaGraphCreate(&g, 0));
+  h->graph = g;
+  cudaGraphConditionalHandle ch = 0;
+  if (unroll == 0) CG_CUDA(h, cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
+  const void* f_spmv = spmv_kernel_for(h->uniform_w, jac);
+  const unsigned G = (unsigned)h->grid_graph;
+  const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count),
+                                                     h->grid_part));
+  GArgs ga{P, h->gs, ch, unroll == 0 ? 1 : 0, Gq, G};
+  Csr<double> A = P.A;
+  const double* x = P.x;
+  double* q = P.V64.q;
+  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  void* a_spmv[] = {&A, &x, &q};
+  void* a_ga[] = {&ga};
+  const void* f_r = jac ? (const void*)g_upd_r<double, true> : (const void*)g_upd_r<double, false>;
+  const void* f_xp = jac ? (const void*)g_upd_xp<double, true, false>
+                         : (const void*)g_upd_xp<double, false, false>;
+  const void* f_flush = jac ? (const void*)g_flush<double, true, false>
+                            : (const void*)g_flush<double, false, false>;
+  cudaGraphNode_t n, prev;
+  // prologue
+  CG_CUDA(h, add_kernel(g, &n, nullptr, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
+  prev = n;
+  CG_CUDA(h, add_kernel(g, &n, prev, jac ? (const void*)g_res64<true> : (const void*)g_res64<false>,
+                        G, kBlock, a_ga));
+  prev = n;
+  CG_CUDA(h, add_kernel(g, &n, prev, (const void*)g_start64, 1, 32, a_ga));
+  prev = n;
+  cudaGraph_t ep = g;
+  if (unroll == 0) {
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = ch;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    CG_CUDA(h, cudaGraphAddNode(&n, g, &prev, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaGraphNode_t b1, b2, b3;
+    CG_CUDA(h, add_kernel(body, &b1, nullptr, f_spmv, Gq, kBlock, a_ga));
+    CG_CUDA(h, add_kernel(body, &b2, b1, f_r, G, kBlock, a_ga));
+    CG_CUDA(h, add_kernel(body, &b3, b2, f_xp, G, kBlock, a_ga));
+    prev = n;
+  } else {
+    CG_CUDA(h, cudaGraphCreate(&h->graph_it, 0));
+    cudaGraphNode_t pi = nullptr, ci;
+    for (int u = 0; u < unroll; ++u) {
+      CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, f_spmv, Gq, kBlock, a_ga));
+      pi = ci;
+      CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, f_r, G, kBlock, a_ga));
+      pi = ci;
+      CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, f_xp, G, kBlock, a_ga));
+      pi = ci;
+    }
+    CG_CUDA(h, cudaGraphInstantiate(&h->gexec_it, h->graph_it, 0));
+    CG_CUDA(h, cudaGraphCreate(&h->graph_ep, 0));
+    ep = h->graph_ep;
+    prev = nullptr;
+  }
+  // epilogue: flush on breakdown, true residual, verdict
+  CG_CUDA(h, add_kernel(ep, &n, prev, f_flush, G, kBlock, a_ga));
+  prev = n;
+  CG_CUDA(h, add_kernel(ep, &n, prev, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
+  prev = n;
+  CG_CUDA(h, add_kernel(ep, &n, prev, (const void*)g_true, G, kBlock, a_ga));
+  prev = n;
+  CG_CUDA(h, add_kernel(ep, &n, prev, (const void*)g_final64, 1, 32, a_ga));
+  CG_CUDA(h, cudaGraphInstantiate(&h->gexec, g, 0));
+  if (unroll > 0) CG_CUDA(h, cudaGraphInstantiate(&h->gexec_ep, h->graph_ep, 0));
+  h->gkey_unroll = unroll;
+  h->gkey_b = P.b;
+  h->gkey_x = P.x;
+  h->gkey_tol = P.tol;
+  h->gkey_maxit = P.maxit;
+  h->gkey_jac = jac;
+  return CG_OK;
+}
+
+constexpr int64_t kGraphMinRows = 1 << 20;  // auto mode: graph loop from this many rows
+constexpr int kUnrollIters = 8;               // iterations per launch of the unrolled form
+
+// fp64 solve through the graph form of the loop; restarts (true residual
+// missing tol after the recursive test passed) relaunch the graph from x.
+cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll,
+                        int32_t* iters_out, double* relres_out) {
+  if (!h->gexec || h->gkey_b != P.b || h->gkey_x != P.x || h->gkey_tol != P.tol ||
+      h->gkey_maxit != P.maxit || h->gkey_jac != (int)jac || h->gkey_unroll != unroll) {
+    cg_status s = build_graph64(h, P, jac, unroll);
+    if (s != CG_OK) return s;
+  }
+  CG_CUDA(h, cudaMemsetAsync(h->gs, 0, sizeof(GState), h->stream));
+  CG_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  int restarts = 0, status;
+  for (;;) {
+    CG_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+    if (unroll > 0) {
+      for (;;) {  // iteration graphs until the loop state leaves kRunning
+        CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
+        CG_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (h->host_gs->status != kRunning) break;
+        CG_CUDA(h, cudaGraphLaunch(h->gexec_it, h->stream));
+      }
+      CG_CUDA(h, cudaGraphLaunch(h->gexec_ep, h->stream));
+    }
+    CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
+    CG_CUDA(h, cudaStreamSynchronize(h->stream));
+    status = h->host_gs->status;
+    if (status != kNeedRestart) break;
+    if (h->host_gs->k >= P.maxit || restarts >= P.max_restarts) {
+      status = kNotConverged;
+      break;
+    }
+    ++restarts;
+  }
+  CG_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  CG_CUDA(h, cudaEventSynchronize(h->ev1));
+  float ms = 0.0f;
+  CG_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  const GState& gs = *h->host_gs;
+  h->last.status = status;
+  h->last.iters = gs.k;
+  h->last.restarts = restarts;
+  h->last.grid_ctas = h->grid_graph;
+  h->last.relres_true = gs.relres_true;
+  h->last.relres_rec = gs.bb > 0.0 ? sqrt(gs.rr) / sqrt(gs.bb) : 0.0;
+  h->last.kernel_ms = ms;
+  const int64_t n = h->n, nnz = h->nnz;
+  h->last.bytes_moved = (12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n) * (int64_t)gs.k;
+  const int64_t ent = h->sell_entries + h->nnz_long;
+  h->last.kernel_bytes_per_iter = 12 * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n;
+  if (iters_out) *iters_out = gs.k;
+  if (relres_out) *relres_out = gs.relres_true;
+  if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
+  return (cg_status)status;
 }
 
 }  // namespace
@@ -227,25 +615,25 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "cg_create: device query"));
 
   // rowptr checks on the host (the row-block cut needs it there anyway)
-  std::vector<int32_t> hrp((size_t)n + 1);
+  h->host_rowptr.resize((size_t)n + 1);
+  std::vector<int32_t>& hrp = h->host_rowptr;
   e = cudaMemcpy(hrp.data(), rowptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "cg_create: rowptr copy"));
   if (hrp[0] != 0) return bail(fail(h, CG_ERR_INVALID, "cg_create: rowptr[0] != 0"));
   for (int64_t i = 0; i < n; ++i)
-    if (hrp[i + 1] < hrp[i]) return bail(fail(h, CG_ERR_INVALID, "cg_create: rowptr decreases at row " + std::to_string(i)));
-  h->nnz = hrp[n];
+    if (hrp[(size_t)i + 1] < hrp[(size_t)i])
+      return bail(fail(h, CG_ERR_INVALID, "cg_create: rowptr decreases at row " + std::to_string(i)));
+  h->nnz = hrp[(size_t)n];
   if (h->nnz > 0 && (!colind || !vals))
     return bail(fail(h, CG_ERR_INVALID, "cg_create: colind/vals NULL with nnz > 0"));
 
-  std::vector<int32_t> rb = build_row_blocks(hrp, n, &h->long_rows);
+  std::vector<int32_t> rb = build_row_blocks(hrp.data(), n, &h->long_rows);
   h->nrb = (int32_t)(rb.size() - 1);
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
   e = cudaMalloc(&h->rb, sizeof(int32_t) * rb.size());
   if (e == cudaSuccess) e = cudaMemcpy(h->rb, rb.data(), sizeof(int32_t) * rb.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&h->dinv, sizeof(double) * nv);
-  if (e == cudaSuccess) e = cudaMalloc(&h->r, sizeof(double) * nv);
-  if (e == cudaSuccess) e = cudaMalloc(&h->p, sizeof(double) * nv);
-  if (e == cudaSuccess) e = cudaMalloc(&h->q, sizeof(double) * nv);
+  if (e == cudaSuccess) e = cudaMalloc(&h->diag, sizeof(double) * nv);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ndiag, sizeof(int32_t) * nv);
   if (e == cudaSuccess) e = cudaMalloc(&h->st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaMallocHost(&h->host_st, sizeof(DevState));
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
@@ -257,7 +645,7 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   e = cudaMalloc(&cnt, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(cnt, 0, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess && n > 0) {
-    validate_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256>>>(n, rowptr, colind, vals, h->dinv, cnt);
+    validate_kernel<<<grid_for(n), 256>>>(n, rowptr, colind, vals, h->diag, h->ndiag, cnt);
     e = cudaGetLastError();
   }
   unsigned long long hc[2] = {0, 0};
@@ -269,13 +657,22 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   h->jacobi_ok = (hc[1] == 0);
 
   // persistent-kernel residency (the smallest over the kernels we may launch)
-  int g1 = max_coresident(pcg64_kernel<true>, h->sm_count);
-  int g2 = max_coresident(pcg64_kernel<false>, h->sm_count);
-  int g3 = max_coresident(pcg_ir_kernel<true>, h->sm_count);
-  int g4 = max_coresident(pcg_ir_kernel<false>, h->sm_count);
+  const int g1 = max_coresident(pcg64_kernel<true>, h->sm_count);
+  const int g2 = max_coresident(pcg64_kernel<false>, h->sm_count);
+  const int g3 = max_coresident(pcg_ir_kernel<true>, h->sm_count);
+  const int g4 = max_coresident(pcg_ir_kernel<false>, h->sm_count);
   h->grid_max = std::min(std::min(g1, g2), std::min(g3, g4));
-  if (h->grid_max <= 0) return bail(fail(h, CG_ERR_CUDA, "cg_create: occupancy query failed"));
-  e = cudaMalloc(&h->part, sizeof(double) * (size_t)kParts * (size_t)h->grid_max);
+  const int g5 = std::min(max_coresident(g_upd_r<double, true>, h->sm_count),
+                          max_coresident(g_upd_r<double, false>, h->sm_count));
+  const int g6 = std::min(max_coresident(g_upd_xp<double, true, false>, h->sm_count),
+                          max_coresident(g_res64<true>, h->sm_count));
+  h->grid_graph = std::min(g5, g6);
+  h->grid_part = 64 * h->sm_count;  // bounds every loop kernel's grid
+  if (h->grid_max <= 0 || h->grid_graph <= 0 || h->grid_max > h->grid_part || h->grid_graph > h->grid_part)
+    return bail(fail(h, CG_ERR_CUDA, "cg_create: occupancy query failed"));
+  e = cudaMalloc(&h->part, sizeof(double) * (size_t)kParts * (size_t)h->grid_part);
+  if (e == cudaSuccess) e = cudaMalloc(&h->gs, sizeof(GState));
+  if (e == cudaSuccess) e = cudaMallocHost(&h->host_gs, sizeof(GState));
   if (e != cudaSuccess) return bail(cuda_fail(h, e, "cg_create: partials"));
   *out = h;
   return CG_OK;
@@ -314,6 +711,14 @@ cg_status cg_set_option(cg_handle* h, int32_t option, double value) {
       if (!(value >= 0 && value < 4e9)) break;
       h->skip_seq = (unsigned)value;
       return CG_OK;
+    case CG_OPT_PHASE_TIMERS:
+      if (!(value == 0 || value == 1)) break;
+      h->timers = (int)value;
+      return CG_OK;
+    case CG_OPT_LOOP_MODE:
+      if (!(value == 0 || value == 1 || value == 2 || value == 3)) break;
+      h->loop_mode = (int)value;
+      return CG_OK;
     default:
       break;
   }
@@ -350,39 +755,48 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   if (!b || !x) return fail(h, CG_ERR_INVALID, "cg_solve: b or x is NULL");
   if (!aligned16(b) || !aligned16(x)) return fail(h, CG_ERR_INVALID, "cg_solve: b and x must be 16-byte aligned");
   if (b == x) return fail(h, CG_ERR_INVALID, "cg_solve: b and x alias");
-  if (precision == CG_PREC_FP32_IR) {
-    cg_status s = ensure_fp32(h);
-    if (s != CG_OK) return s;
-  }
+  const bool jac = precond == CG_PRECOND_JACOBI;
+  const bool fp64 = precision == CG_PREC_FP64;
+  cg_status s = ensure_offdiag(h);
+  if (s == CG_OK) s = ensure_vectors<double>(h, &h->r, &h->p, &h->q, &h->xh);
+  if (s == CG_OK && fp64) s = ensure_vals<double>(h, &h->sval64[jac], &h->lval64[jac], jac);
+  if (s == CG_OK && !fp64) s = ensure_vals<float>(h, &h->sval32[jac], &h->lval32[jac], jac);
+  if (s == CG_OK && !fp64) s = ensure_vectors<float>(h, &h->r32, &h->p32, &h->q32, &h->xh32);
+  if (s != CG_OK) return s;
+
   const int G = auto_grid(h);
   SolveParams P{};
   P.A = Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
-  P.A32 = Csr<float>{h->n, h->rowptr, h->colind, h->vals32, h->rb, h->nrb};
+  P.S64 = Sell<double>{h->n,      h->nslices,     h->uniform_w, h->soff, h->lmask, h->scol, h->sval64[jac],
+                       h->nlong,  h->lrow,        h->lptr, h->lcol,  h->lval64[jac],
+                       h->diag,   h->diag,        h->disq};
+  P.S32 = Sell<float>{h->n,      h->nslices,     h->uniform_w, h->soff, h->lmask, h->scol, h->sval32[jac],
+                      h->nlong,  h->lrow,        h->lptr, h->lcol,  h->lval32[jac],
+                      h->diag32, h->diag32,      h->disq32};
+  P.V64 = LoopVecs<double>{h->r, h->p, h->q, h->xh};
+  P.V32 = LoopVecs<float>{h->r32, h->p32, h->q32, h->xh32};
   P.b = b;
   P.x = x;
-  P.r = h->r;
-  P.p = h->p;
-  P.q = h->q;
-  P.dinv = h->dinv;
-  P.r32 = h->r32;
-  P.p32 = h->p32;
-  P.q32 = h->q32;
-  P.d32 = h->d32;
-  P.dinv32 = h->dinv32;
+  P.dsq = h->dsq;
+  P.disq = h->disq;
   P.part = h->part;
+  P.pstride = h->grid_part;
   P.st = h->st;
   P.tol = tol;
   P.tol_in = h->tol_in;
   P.maxit = maxit;
-  P.max_restarts = precision == CG_PREC_FP64 ? h->max_restarts : h->max_outer;
+  P.max_restarts = fp64 ? h->max_restarts : h->max_outer;
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
+  P.timers = h->timers;
+  const bool graph_mode = fp64 && (h->loop_mode >= 2 || (h->loop_mode == 0 && h->n >= kGraphMinRows));
+  if (graph_mode) return solve_graph64(h, P, jac, h->loop_mode == 3 ? kUnrollIters : 0, iters_out, relres_out);
   void* args[] = {&P};
   const void* fn;
-  if (precision == CG_PREC_FP64)
-    fn = precond == CG_PRECOND_JACOBI ? (const void*)pcg64_kernel<true> : (const void*)pcg64_kernel<false>;
+  if (fp64)
+    fn = jac ? (const void*)pcg64_kernel<true> : (const void*)pcg64_kernel<false>;
   else
-    fn = precond == CG_PRECOND_JACOBI ? (const void*)pcg_ir_kernel<true> : (const void*)pcg_ir_kernel<false>;
+    fn = jac ? (const void*)pcg_ir_kernel<true> : (const void*)pcg_ir_kernel<false>;
   CG_CUDA(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
   CG_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   CG_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), args, 0, h->stream));
@@ -391,26 +805,31 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   CG_CUDA(h, cudaStreamSynchronize(h->stream));
   float ms = 0.0f;
   CG_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-  const DevState& s = *h->host_st;
-  cg_status status = s.abort ? CG_ERR_TIMEOUT : (cg_status)s.status;
+  const DevState& ds = *h->host_st;
+  cg_status status = ds.abort ? CG_ERR_TIMEOUT : (cg_status)ds.status;
   h->last.status = status;
-  h->last.iters = s.iters;
-  h->last.restarts = s.restarts;
+  h->last.iters = ds.iters;
+  h->last.restarts = ds.restarts;
   h->last.grid_ctas = G;
-  h->last.relres_true = s.relres_true;
-  h->last.relres_rec = s.relres_rec;
+  h->last.relres_true = ds.relres_true;
+  h->last.relres_rec = ds.relres_rec;
   h->last.kernel_ms = ms;
-  // modelled bytes of the CG loop (Sec. 3.3 phases): matrix + the vector streams
+  // modelled bytes of the CG loop (three phases of Alg. 1 on the caller's CSR)
   const int64_t n = h->n, nnz = h->nnz;
-  const int64_t per_iter = precision == CG_PREC_FP64
-      ? 12 * nnz + 4 * (n + 1) + (precond == CG_PRECOND_JACOBI ? 104 : 88) * n
-      : 8 * nnz + 4 * (n + 1) + (precond == CG_PRECOND_JACOBI ? 52 : 44) * n;
-  h->last.bytes_moved = per_iter * (int64_t)s.iters;
-  if (iters_out) *iters_out = s.iters;
-  if (relres_out) *relres_out = s.relres_true;
+  const int64_t per_iter = fp64 ? 12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n
+                                : 8 * nnz + 4 * (n + 1) + (jac ? 52 : 44) * n;
+  h->last.bytes_moved = per_iter * (int64_t)ds.iters;
+  // bytes this kernel's loop must move per iteration: the SELL-32 slices
+  // (padding included), the long-row CSR and the vector streams
+  const int64_t ent = h->sell_entries + h->nnz_long;
+  h->last.kernel_bytes_per_iter = fp64 ? 12 * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n
+                                       : 8 * ent + 4 * (int64_t)h->nlong + (jac ? 44 : 40) * n;
+  for (int j = 0; j < 6; ++j) h->last.phase_ms[j] = ds.tphase[j] * 1e-6;
+  if (iters_out) *iters_out = ds.iters;
+  if (relres_out) *relres_out = ds.relres_true;
   if (status == CG_ERR_TIMEOUT)
-    return fail(h, status, "cg_solve: grid barrier " + std::to_string(s.err_barrier) +
-                               " timed out in CTA " + std::to_string(s.err_cta));
+    return fail(h, status, "cg_solve: a bounded wait gave up (barrier " + std::to_string(ds.err_barrier) +
+                               ", CTA " + std::to_string(ds.err_cta) + "); timed out");
   if (status < 0) return fail(h, status, std::string("cg_solve: ") + cg_status_string(status));
   return status;
 }

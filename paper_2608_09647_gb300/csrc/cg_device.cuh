@@ -22,6 +22,7 @@ struct DevState {
   int err_barrier;       // barrier sequence number where it happened
   double relres_true;
   double relres_rec;
+  unsigned long long tphase[6];  // CTA 0 time (ns): SpMV, wait, r update, wait, x/p update, wait
 };
 
 __device__ __forceinline__ uint64_t global_timer_ns() {

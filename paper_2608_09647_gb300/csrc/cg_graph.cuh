@@ -1,0 +1,239 @@
+// The CG loop as a CUDA graph with a device-controlled WHILE node (large
+// systems).  Each phase of an iteration is its own high-occupancy kernel; a
+// kernel boundary is the grid-wide barrier, the scalars are re-formed by every
+// CTA from the fixed-order partial sums of the previous kernel, and the last
+// CTA of the x/p pass stores the loop state and sets the loop condition.  The
+// host launches one graph per solve and reads one status word back.
+//
+//   prologue : q = A x | r = b - q, r^, p, x^, partials | start (1 CTA)
+//   WHILE    : q = A^ p, p.q | alpha, r^ -= alpha q, r.z, r.r | beta, x^/p
+//   epilogue : flush x on breakdown | q = A x | ||b - q||^2 | final (1 CTA)
+//
+// The phases are the same device functions as the persistent launch, so both
+// loop forms compute identical iterates for the same grid size.
+#pragma once
+
+#include "cg_kernels.cuh"
+
+namespace cg {
+
+constexpr int kRunning = 100;     // loop state status while iterating
+constexpr int kNeedRestart = 101; // recursive residual met tol, true residual did not
+
+// Loop state of a graph solve (device memory, zeroed before the first launch).
+struct GState {
+  double rho;          // r^.r^ of the current residual
+  double rr;           // r.r of the current residual
+  double bb;           // b.b
+  double stop_abs;     // tol ||b||
+  double relres_true;  // ||b - A x|| / ||b|| after the epilogue
+  int k;               // SpMVs so far (across restarts)
+  int k_start;         // k when this launch's loop started
+  int status;          // kRunning, cg status, or kNeedRestart
+  int started;         // 0 before the first prologue of a solve
+  unsigned ctr;        // arrivals of the current x/p pass (last-CTA election)
+  int pad;
+};
+
+struct GArgs {
+  SolveParams P;
+  GState* gs;
+  cudaGraphConditionalHandle h;
+  int use_cond;     // 0: unrolled form, the kernels of finished iterations return at once
+  unsigned G_spmv;  // CTAs of the SpMV kernel (its p.q partials)
+  unsigned G_upd;   // CTAs of the vector kernels (their partials)
+};
+
+__device__ __forceinline__ Grid graph_grid() { return Grid(nullptr, 0, 0); }
+
+template <typename T> __device__ __forceinline__ const Sell<T>& sell_of(const SolveParams& P);
+template <> __device__ __forceinline__ const Sell<double>& sell_of<double>(const SolveParams& P) { return P.S64; }
+template <> __device__ __forceinline__ const Sell<float>& sell_of<float>(const SolveParams& P) { return P.S32; }
+template <typename T> __device__ __forceinline__ const LoopVecs<T>& vecs_of(const SolveParams& P);
+template <> __device__ __forceinline__ const LoopVecs<double>& vecs_of<double>(const SolveParams& P) { return P.V64; }
+template <> __device__ __forceinline__ const LoopVecs<float>& vecs_of<float>(const SolveParams& P) { return P.V32; }
+
+// r = b - q (q = A x from the plain CSR kernel); r^ = D^-1/2 r, p = r^,
+// x^ = D^1/2 x; partials (r^.r^, r.r, b.b).
+template <bool JAC>
+__global__ void __launch_bounds__(kBlock) g_res64(GArgs a) {
+  const SolveParams& P = a.P;
+  Grid g = graph_grid();
+  const LoopVecs<double>& V = P.V64;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) {
+    const double bi = P.b[i];
+    const double ri = bi - V.q[i];
+    const double rh = JAC ? ri * __ldg(P.disq + i) : ri;
+    V.r[i] = rh;
+    V.p[i] = rh;
+    V.xh[i] = JAC ? P.x[i] * __ldg(P.dsq + i) : P.x[i];
+    v[0] += rh * rh;
+    v[1] += ri * ri;
+    v[2] += bi * bi;
+  }
+  publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+}
+
+// One CTA: loop state from the prologue partials; sets the WHILE condition.
+__global__ void g_start64(GArgs a) {
+  const unsigned G = a.G_upd;
+  double s[3];
+  grid_sum<3>(a.P.part + kSlotRes * (size_t)a.P.pstride, G, s);
+  if (threadIdx.x != 0) return;
+  GState* gs = a.gs;
+  if (!gs->started) {
+    gs->started = 1;
+    gs->bb = s[2];
+    gs->stop_abs = a.P.tol * sqrt(s[2]);
+    gs->k = 0;
+  }
+  gs->rho = s[0];
+  gs->rr = s[1];
+  gs->k_start = gs->k;
+  int status = kRunning;
+  if (gs->bb == 0.0) status = kOk;                          // b = 0: x = 0 (written by g_flush)
+  else if (sqrt(s[1]) <= gs->stop_abs) status = kOk;       // a4 before the first SpMV
+  else if (gs->k >= a.P.maxit) status = kNotConverged;
+  gs->status = status;
+  gs->ctr = 0;
+  if (a.use_cond) cudaGraphSetConditional(a.h, status == kRunning ? 1u : 0u);
+}
+
+// a1: q = A^ p, partial p.q.  W > 0: the matrix has uniform slices of width W
+// (chosen on the host, so each width gets its own register budget).
+template <typename T, bool JAC, int W>
+__global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
+  const SolveParams& P = a.P;
+  if (a.gs->status != kRunning) return;
+  Grid g = graph_grid();
+  const Sell<T>& S = sell_of<T>(P);
+  const LoopVecs<T>& V = vecs_of<T>(P);
+  double v[1];
+  if constexpr (W > 0) v[0] = spmv_phase_w<T, JAC, W>(S, V.p, V.q, g);
+  else v[0] = spmv_phase<T, JAC>(S, V.p, V.q, g);
+  publish<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g);
+}
+
+// a2: alpha = rho / p.q (breakdown / non-finite stop the loop); r^ -= alpha q;
+// partials (r^.r^, r.r).
+template <typename T, bool JAC>
+__global__ void __launch_bounds__(kBlock) g_upd_r(GArgs a) {
+  const SolveParams& P = a.P;
+  if (a.gs->status != kRunning) return;
+  Grid g = graph_grid();
+  const Sell<T>& S = sell_of<T>(P);
+  const LoopVecs<T>& V = vecs_of<T>(P);
+  double pq[1];
+  grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
+  const double rho = a.gs->rho;
+  if (!isfinite(pq[0]) || !isfinite(rho) || pq[0] <= 0.0) {
+    if (g.cta == 0 && threadIdx.x == 0)
+      a.gs->status = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : kBreakdown;
+    return;
+  }
+  const T alpha = (T)(rho / pq[0]);
+  double v[2] = {0.0, 0.0};
+  update_r_phase<T, JAC>(S, V, alpha, v[0], v[1], g);
+  publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
+}
+
+// a3 + a4: beta, convergence; x^ += alpha p and p = r^ + beta p, or on the
+// last iteration out = scale (x^ + alpha p) (OUT_ADD: out += ...).  The last
+// CTA to finish stores the loop state and sets the WHILE condition.
+template <typename T, bool JAC, bool OUT_ADD>
+__global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
+  const SolveParams& P = a.P;
+  Grid g = graph_grid();
+  const Sell<T>& S = sell_of<T>(P);
+  const LoopVecs<T>& V = vecs_of<T>(P);
+  GState* gs = a.gs;
+  if (!a.use_cond && gs->status != kRunning) return;  // unrolled form: loop already over
+  const bool failed = gs->status != kRunning;  // set by g_upd_r (breakdown / numeric)
+  double rho1 = 0.0, rr1 = 0.0;
+  bool done = true, conv = false;
+  const int k1 = gs->k + 1;
+  if (!failed) {
+    double pq[1], s2[2];
+    grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
+    grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, a.G_upd, s2);
+    const double rho = gs->rho;
+    const T alpha = (T)(rho / pq[0]);
+    const T beta = (T)(s2[0] / rho);
+    rho1 = s2[0];
+    rr1 = s2[1];
+    conv = sqrt(rr1) <= gs->stop_abs;
+    done = conv || k1 >= P.maxit;
+    double* out = P.x;
+    if (done) update_xp_phase<T, JAC, true, OUT_ADD>(S, V, alpha, beta, out, g);
+    else update_xp_phase<T, JAC, false, OUT_ADD>(S, V, alpha, beta, out, g);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&gs->ctr, 1u) == g.G - 1) {  // every CTA has read the state and finished
+      gs->ctr = 0;
+      if (!failed) {
+        gs->rho = rho1;
+        gs->rr = rr1;
+        gs->k = k1;
+        gs->status = done ? (conv ? kOk : kNotConverged) : kRunning;
+      }
+      __threadfence();
+      if (a.use_cond) cudaGraphSetConditional(a.h, (!failed && !done) ? 1u : 0u);
+    }
+  }
+}
+
+// After the loop: on breakdown / numeric error with iterations done, the
+// caller's x gets the last iterate; with b = 0 it gets 0.
+template <typename T, bool JAC, bool OUT_ADD>
+__global__ void __launch_bounds__(kBlock) g_flush(GArgs a) {
+  const SolveParams& P = a.P;
+  Grid g = graph_grid();
+  const Sell<T>& S = sell_of<T>(P);
+  const LoopVecs<T>& V = vecs_of<T>(P);
+  const GState* gs = a.gs;
+  if (gs->bb == 0.0) {
+    for (int64_t i = g.gtid; i < S.n; i += g.gstride) P.x[i] = 0.0;
+    return;
+  }
+  if (!(gs->status == kBreakdown || gs->status == kNumeric) || gs->k == gs->k_start) return;
+  for (int64_t i = g.gtid; i < S.n; i += g.gstride) {
+    const T xo = JAC ? V.xh[i] * __ldg(S.disq + i) : V.xh[i];
+    if (OUT_ADD) P.x[i] += (double)xo;
+    else P.x[i] = (double)xo;
+  }
+}
+
+// Partial ||b - q||^2 with q = A x (true residual, a5).
+__global__ void __launch_bounds__(kBlock) g_true(GArgs a) {
+  const SolveParams& P = a.P;
+  Grid g = graph_grid();
+  double v[1] = {0.0};
+  for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) {
+    const double ri = P.b[i] - P.V64.q[i];
+    v[0] += ri * ri;
+  }
+  publish<1>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+}
+
+// One CTA: the true relative residual and the solve's verdict.
+__global__ void g_final64(GArgs a) {
+  const unsigned G = a.G_upd;
+  double s[1];
+  grid_sum<1>(a.P.part + kSlotRes * (size_t)a.P.pstride, G, s);
+  if (threadIdx.x != 0) return;
+  GState* gs = a.gs;
+  if (gs->bb == 0.0) {
+    gs->relres_true = 0.0;
+    gs->status = kOk;
+    return;
+  }
+  const double rel = sqrt(s[0]) / sqrt(gs->bb);
+  gs->relres_true = rel;
+  if (!isfinite(rel)) gs->status = kNumeric;
+  else if (gs->status == kOk && rel > a.P.tol) gs->status = kNeedRestart;
+}
+
+}  // namespace cg

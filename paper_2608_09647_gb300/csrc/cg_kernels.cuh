@@ -1,22 +1,49 @@
 // Kernels of the CG hot path (one GPU, everything resident in HBM):
 //   a1  CSR SpMV q = A p fused with the p.q partial sum     (Alg. 1; Sec. 3.3 fused SpMV + dot)
-//   a2  alpha, x += alpha p, r -= alpha q, z = M^-1 r, r.z and r.r partials
+//   a2  alpha, r -= alpha q, r.z and r.r partials, x += alpha p
 //                                                          (Alg. 1; Sec. 3.3 fused update + r.r)
 //   a3  beta, p = z + beta p                               (Alg. 1)
 //   a4  convergence test on the device                     (Alg. 1, relative form)
 //   a5  true residual ||b - A x|| / ||b|| in fp64         (Sec. 3.1, recomputed residual)
-// The loop runs as one persistent cooperative launch: phases are separated by
-// bounded grid barriers and the scalars are formed redundantly in every CTA
-// from fixed-order sums of per-CTA partials, so there is no host round trip
-// per iteration and results are reproducible run to run.
+//
+// The loop runs as one persistent cooperative launch.  Phases are separated by
+// bounded grid barriers; every CTA forms the scalars redundantly from
+// fixed-order sums of per-CTA partials, so there is no host round trip per
+// iteration and reruns give identical results.
+//
+// GB300 design of one iteration:
+//  * Jacobi is applied as the symmetric scaling A^ = D^-1/2 A D^-1/2, which
+//    is algebraically the same iteration (x = D^-1/2 x^, r = D^1/2 r^,
+//    r.z = r^.r^, r.r = r^.D r^) and leaves A^ with a unit diagonal, so the
+//    loop streams no D^-1 vector and stores no diagonal entries.
+//  * Three streaming phases: [q = A^ p, p.q] | [r^ -= alpha q, r.z, r.r] |
+//    [x^ += alpha p, p = r^ + beta p]; the x update rides in the p pass, and
+//    on the last iteration that pass writes the caller's x directly.
+//    (Forming p on the fly inside the SpMV saves one pass and one barrier
+//    but doubles the gathered vectors; measured on GB300 that halves the
+//    SpMV's bandwidth, so the p update stays a pass of its own.)
+//  * The loop matrix is stored as SELL-32 (sliced ELLPACK, slice height 32 =
+//    one warp): the off-diagonal entries of 32 consecutive rows are laid out
+//    column-major per slice, so lane l of a warp owns row 32 s + l, every
+//    matrix load and most gathers are coalesced, the row sum stays in one
+//    register, and warps run with no shared memory and no CTA barrier.  The
+//    matrix is streamed with evict-first loads so the L2 keeps the vectors
+//    that the gathers reuse.  Rows longer than kLongRow entries leave the
+//    slices and are summed by a warp each from a compact CSR.
 #pragma once
 
 #include "cg_device.cuh"
 
 namespace cg {
 
-constexpr int kCap = 2048;                 // nonzeros staged per row block
-constexpr int kPerThread = kCap / kBlock;  // staged nonzeros per thread
+constexpr int kCap = 2048;                 // nonzeros of one caller-CSR row block
+constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
+constexpr int kLongRow = 128;              // off-diagonal entries above which a row leaves SELL
+constexpr int kUnroll = 8;                 // slice columns whose loads are issued together
+
+// --------------------------------------------------------------------------
+// Plain CSR (the caller's matrix): cg_spmv and the fp64 true residual
+// --------------------------------------------------------------------------
 
 // CSR matrix view plus its row-block schedule.  Row block b covers rows
 // [rb[b], rb[b+1]); it holds either <= kCap nonzeros and <= kBlock rows
@@ -33,29 +60,22 @@ struct Csr {
   int32_t nrb;
 };
 
-// One row block of y = A x.  Returns this thread's share of sum_i w_i y_i
-// (w may be null, then 0).  Stream blocks sum each row in storage order over
-// rounded products, which is the oracle's order, so fp64 results match it
-// bit for bit; long rows use a strided fused multiply-add and a tree.
+// One row block of y = A x.  Stream blocks sum each row in storage order over
+// rounded products, the oracle's order, so fp64 results match it bit for
+// bit; long rows use a strided fused multiply-add and a fixed tree.
 template <typename T>
-__device__ __forceinline__ double spmv_rowblock(const Csr<T>& A, const T* x, T* y, const T* w,
-                                                int b, T* s_prod) {
+__device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y, int b, T* s_prod) {
   const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
   const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
   const int nk = k1 - k0;
   const int t = threadIdx.x;
-  double dot = 0.0;
   if (nk > kCap) {  // long row (r1 == r0 + 1 by construction)
     T acc = T(0);
     for (int k = k0 + t; k < k1; k += kBlock) acc += __ldg(A.vals + k) * x[__ldg(A.colind + k)];
     double v[1] = {(double)acc};
-    block_sum<1>(v);  // fixed-order tree over the CTA
-    if (t == 0) {
-      const T s = (T)v[0];
-      y[r0] = s;
-      if (w) dot = (double)s * (double)w[r0];
-    }
-    return dot;
+    block_sum<1>(v);
+    if (t == 0) y[r0] = (T)v[0];
+    return;
   }
   T prod[kPerThread];
   int col[kPerThread];
@@ -84,47 +104,83 @@ __device__ __forceinline__ double spmv_rowblock(const Csr<T>& A, const T* x, T* 
     T s = T(0);
     for (int k = a; k < e; ++k) s += s_prod[k];
     y[i] = s;
-    if (w) dot = (double)s * (double)w[i];
   }
   __syncthreads();  // s_prod is reused by the next row block
-  return dot;
 }
 
-// Stand-alone y = A x over all row blocks (cg_spmv, and setup work).
+// Stand-alone y = A x over all row blocks (cg_spmv).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<T> A, const T* x, T* y) {
   __shared__ T s_prod[kCap];
-  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock<T>(A, x, y, nullptr, b, s_prod);
+  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock<T>(A, x, y, b, s_prod);
 }
 
-// ---------------------------------------------------------------------------
+// --------------------------------------------------------------------------
 // Persistent solver launch
-// ---------------------------------------------------------------------------
+// --------------------------------------------------------------------------
+
+// Off-diagonal part of the loop matrix (A^ with Jacobi, A without) in
+// SELL-32 form.  Slice s holds rows [32 s, 32 s + 32); its entries occupy
+// [soff[s], soff[s+1]) in units of 32 (column m of the slice is the 32
+// consecutive elements at (soff[s] + m) * 32; lane l = row 32 s + l).  Short
+// rows are padded to the slice width with (column = own row, value = 0).
+// Rows with more than kLongRow off-diagonal entries are marked in lmask and
+// kept in a compact CSR (lrow / lptr / lcol / lval) instead.
+template <typename T>
+struct Sell {
+  int64_t n;
+  int32_t nslices;
+  int32_t uw;  // >= 0: every slice has width uw and no row is long (soff, lmask unread)
+  const int32_t* __restrict__ soff;
+  const uint32_t* __restrict__ lmask;
+  const int32_t* __restrict__ col;
+  const T* __restrict__ val;
+  int32_t nlong;
+  const int32_t* __restrict__ lrow;
+  const int32_t* __restrict__ lptr;
+  const int32_t* __restrict__ lcol;
+  const T* __restrict__ lval;
+  const T* __restrict__ dg;    // diagonal of the loop matrix (unused with Jacobi: unit diagonal)
+  const T* __restrict__ dn;    // A_ii weights of the true residual norm (Jacobi)
+  const T* __restrict__ disq;  // 1/sqrt(A_ii) mapping x^ back to x (Jacobi)
+};
+
+// Work vectors of the loop on type T.
+template <typename T>
+struct LoopVecs {
+  T* r;       // r^ (scaled residual)
+  T* p;       // search direction
+  T* q;       // A^ p
+  T* xh;      // x^ (scaled iterate; the inner correction d^ when refining)
+};
 
 struct SolveParams {
-  Csr<double> A;          // fp64 matrix
-  Csr<float> A32;         // fp32 copy of the values (refinement only)
+  Csr<double> A;          // caller's fp64 matrix (true residual)
+  Sell<double> S64;       // fp64 loop matrix
+  Sell<float> S32;        // fp32 loop matrix (refinement)
+  LoopVecs<double> V64;
+  LoopVecs<float> V32;
   const double* b;
   double* x;
-  double *r, *p, *q;      // fp64 work vectors
-  const double* dinv;     // 1 / A_ii (Jacobi)
-  float *r32, *p32, *q32, *d32;
-  const float* dinv32;
-  double* part;           // per-CTA partials, kParts x G
+  const double* dsq;      // sqrt(A_ii) (Jacobi)
+  const double* disq;     // 1/sqrt(A_ii) (Jacobi)
+  double* part;           // per-CTA partials: kParts slots of pstride doubles
+  int pstride;            // slot stride (>= the grid of every loop kernel)
   DevState* st;
   double tol;             // outer relative tolerance
   double tol_in;          // inner tolerance (refinement)
-  int maxit;              // SpMV cap of the CG loop (total inner iterations for refinement)
-  int max_restarts;       // residual replacements (fp64) / refinement steps (refinement)
+  int maxit;              // SpMV cap (total inner iterations when refining)
+  int max_restarts;       // residual replacements (fp64) / refinement steps
   uint64_t timeout_ns;
   unsigned skip_seq;
+  int timers;             // accumulate CTA 0 phase times into st->tphase
 };
 
-// Partial-sum slots (each G doubles): 0 = p.q, 2/3 = r.z / r.r of the loop,
+// Partial-sum slots (each G doubles): 0 = p.q, 2/3 = the update phase,
 // 4..7 = the residual phase.  Disjoint slots mean a CTA never overwrites a
-// partial that a slower CTA has still to read.
+// partial that a slower CTA still has to read.
 constexpr int kParts = 8;
-constexpr int kSlotPQ = 0, kSlotRZ = 2, kSlotRes = 4;
+constexpr int kSlotPQ = 0, kSlotUpd = 2, kSlotRes = 4;
 
 // Grid coordinates and the barrier sequence of one persistent launch.
 struct Grid {
@@ -153,185 +209,363 @@ template <typename T> struct Vec;
 template <> struct Vec<double> { using type = double2; static constexpr int N = 2; };
 template <> struct Vec<float> { using type = float4; static constexpr int N = 4; };
 
-template <typename T>
-__device__ __forceinline__ T lane_of(const typename Vec<T>::type& v, int j);
-template <> __device__ __forceinline__ double lane_of<double>(const double2& v, int j) { return j == 0 ? v.x : v.y; }
-template <> __device__ __forceinline__ float lane_of<float>(const float4& v, int j) {
-  return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+template <typename T, typename VT>
+__device__ __forceinline__ T& lane(VT& v, int j) {
+  return reinterpret_cast<T*>(&v)[j];
 }
-template <typename T>
-__device__ __forceinline__ void set_lane(typename Vec<T>::type& v, int j, T a);
-template <> __device__ __forceinline__ void set_lane<double>(double2& v, int j, double a) {
-  if (j == 0) v.x = a; else v.y = a;
-}
-template <> __device__ __forceinline__ void set_lane<float>(float4& v, int j, float a) {
-  if (j == 0) v.x = a; else if (j == 1) v.y = a; else if (j == 2) v.z = a; else v.w = a;
-}
-
-// a2: x += alpha p; r -= alpha q; z = M^-1 r; partial (r.z, r.r).  16-byte
-// vector loads/stores over [0, n - n % VN), scalar tail after; every vector
-// starts 16-byte aligned.
-template <typename T, bool JAC>
-__device__ __forceinline__ void phase_update_xr(int64_t n, T* x, T* r, const T* p, const T* q,
-                                                const T* dinv, T alpha, double& rz, double& rr,
-                                                const Grid& g) {
-  using V = typename Vec<T>::type;
-  constexpr int VN = Vec<T>::N;
-  const int64_t nv = n / VN;
-  for (int64_t iv = g.gtid; iv < nv; iv += g.gstride) {
-    V xv = reinterpret_cast<V*>(x)[iv];
-    V rv = reinterpret_cast<V*>(r)[iv];
-    const V pv = reinterpret_cast<const V*>(p)[iv];
-    const V qv = reinterpret_cast<const V*>(q)[iv];
-    V dv;
-    if (JAC) dv = __ldg(reinterpret_cast<const V*>(dinv) + iv);
-#pragma unroll
-    for (int j = 0; j < VN; ++j) {
-      const T xi = lane_of<T>(xv, j) + alpha * lane_of<T>(pv, j);
-      const T ri = lane_of<T>(rv, j) - alpha * lane_of<T>(qv, j);
-      set_lane<T>(xv, j, xi);
-      set_lane<T>(rv, j, ri);
-      rr += (double)ri * (double)ri;
-      if (JAC) rz += (double)ri * (double)(ri * lane_of<T>(dv, j));
-    }
-    reinterpret_cast<V*>(x)[iv] = xv;
-    reinterpret_cast<V*>(r)[iv] = rv;
-  }
-  for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
-    const T xi = x[i] + alpha * p[i];
-    const T ri = r[i] - alpha * q[i];
-    x[i] = xi;
-    r[i] = ri;
-    rr += (double)ri * (double)ri;
-    if (JAC) rz += (double)ri * (double)(ri * __ldg(dinv + i));
-  }
-  if (!JAC) rz = rr;
-}
-
-// a3: p = z + beta p with z = M^-1 r.
-template <typename T, bool JAC>
-__device__ __forceinline__ void phase_update_p(int64_t n, const T* r, T* p, const T* dinv, T beta,
-                                               const Grid& g) {
-  using V = typename Vec<T>::type;
-  constexpr int VN = Vec<T>::N;
-  const int64_t nv = n / VN;
-  for (int64_t iv = g.gtid; iv < nv; iv += g.gstride) {
-    const V rv = reinterpret_cast<const V*>(r)[iv];
-    V pv = reinterpret_cast<V*>(p)[iv];
-    V dv;
-    if (JAC) dv = __ldg(reinterpret_cast<const V*>(dinv) + iv);
-#pragma unroll
-    for (int j = 0; j < VN; ++j) {
-      const T z = JAC ? lane_of<T>(rv, j) * lane_of<T>(dv, j) : lane_of<T>(rv, j);
-      set_lane<T>(pv, j, z + beta * lane_of<T>(pv, j));
-    }
-    reinterpret_cast<V*>(p)[iv] = pv;
-  }
-  for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
-    const T z = JAC ? r[i] * __ldg(dinv + i) : r[i];
-    p[i] = z + beta * p[i];
-  }
-}
-
-// a1 over the grid: q = A p, partial p.q (row blocks dealt round-robin to CTAs).
-template <typename T>
-__device__ __forceinline__ double phase_spmv(const Csr<T>& A, const T* p, T* q, const Grid& g,
-                                             T* s_prod) {
-  double pq = 0.0;
-  for (int b = (int)g.cta; b < A.nrb; b += (int)g.G) pq += spmv_rowblock<T>(A, p, q, p, b, s_prod);
-  return pq;
+template <typename T, typename VT>
+__device__ __forceinline__ T lane_c(const VT& v, int j) {
+  return reinterpret_cast<const T*>(&v)[j];
 }
 
 // Status codes shared with the host API (values of cg_status).
 constexpr int kOk = 0, kNotConverged = 1, kBreakdown = -2, kNumeric = -3, kTimeout = -4;
 
-// The CG loop of Alg. 1 on vectors of type T starting from r, p = M^-1 r,
-// rho = r.z, rr = r.r (given): iterate until sqrt(rr) <= stop_abs or maxit
-// SpMVs.  Returns kOk (recursive test met), kNotConverged (maxit), kBreakdown,
-// kNumeric or kTimeout; *iters is advanced by the SpMVs done; *rr_out holds
-// the last r.r.
+// CTA-local phase timer (CTA 0, thread 0, when enabled).
+struct PhaseClock {
+  bool on;
+  uint64_t t;
+  __device__ PhaseClock(bool enabled) : on(enabled && blockIdx.x == 0 && threadIdx.x == 0), t(0) {
+    if (on) t = global_timer_ns();
+  }
+  __device__ __forceinline__ void lap(DevState* st, int slot) {
+    if (on) {
+      const uint64_t now = global_timer_ns();
+      st->tphase[slot] += now - t;
+      t = now;
+    }
+  }
+};
+
+// Streaming (evict-first) loads for the matrix, read once per iteration.
+__device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+
+// a1 over the grid for uniform slices of compile-time width W (no long rows):
+// every load of a slice is issued at once and the register footprint is
+// exactly what W needs, which keeps occupancy high.
+template <typename T, bool JAC, int W>
+__device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __restrict__ p,
+                                               T* __restrict__ q, const Grid& g) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
+  const int Wt = (int)g.G * kWarps;
+  const int64_t n = S.n;
+  double dot = 0.0;
+  for (int s = gw; s < S.nslices; s += Wt) {
+    const int64_t i = (int64_t)s * 32 + lane;
+    const bool live = i < n;
+    T pi = T(0), dgi = T(1);
+    if (live) {
+      pi = p[i];
+      if (!JAC) dgi = __ldg(S.dg + i);
+    }
+    const int32_t* cp = S.col + (int64_t)s * (W * 32) + lane;
+    const T* vp = S.val + (int64_t)s * (W * 32) + lane;
+    int c[W];
+    T v[W], pc[W];
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+      c[m] = ld_stream(cp + m * 32);
+      v[m] = ld_stream(vp + m * 32);
+    }
+#pragma unroll
+    for (int m = 0; m < W; ++m) pc[m] = p[c[m]];
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < W; ++m) acc = fma(v[m], pc[m], acc);
+    if (live) {
+      const T qi = (JAC ? pi : dgi * pi) + acc;
+      q[i] = qi;
+      dot += (double)pi * (double)qi;
+    }
+  }
+  return dot;
+}
+
+// a1 over the grid: q = A^ p and this thread's share of p.q.  Warps take
+// slices round-robin; long rows are summed by a warp each.  Uniform slices of
+// width 4, 6 or 8 go to the specialised loop.
 template <typename T, bool JAC>
-__device__ int cg_loop(const Csr<T>& A, T* x, T* r, T* p, T* q, const T* dinv, double rho,
-                       double rr, double stop_abs, int maxit, int* iters, double* rr_out,
-                       double* part, Grid& g, T* s_prod) {
+__device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restrict__ p,
+                                             T* __restrict__ q, const Grid& g) {
+  if (S.uw == 4) return spmv_phase_w<T, JAC, 4>(S, p, q, g);
+  if (S.uw == 6) return spmv_phase_w<T, JAC, 6>(S, p, q, g);
+  if (S.uw == 8) return spmv_phase_w<T, JAC, 8>(S, p, q, g);
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
+  const int W = (int)g.G * kWarps;
+  const int64_t n = S.n;
+  double dot = 0.0;
+  for (int s = gw; s < S.nslices; s += W) {
+    const int64_t i = (int64_t)s * 32 + lane;
+    int o0, w;
+    uint32_t lm;
+    if (S.uw >= 0) {  // uniform slices: offsets are arithmetic, no metadata loads
+      o0 = s * S.uw;
+      w = S.uw;
+      lm = 0u;
+    } else {
+      o0 = __ldg(S.soff + s);
+      w = __ldg(S.soff + s + 1) - o0;
+      lm = __ldg(S.lmask + s);
+    }
+    T pi = T(0), dgi = T(1);
+    if (i < n) {
+      pi = p[i];
+      if (!JAC) dgi = __ldg(S.dg + i);
+    }
+    const int32_t* cp = S.col + (int64_t)o0 * 32 + lane;
+    const T* vp = S.val + (int64_t)o0 * 32 + lane;
+    T acc = T(0);
+    for (int m0 = 0; m0 < w; m0 += kUnroll) {
+      int c[kUnroll];
+      T v[kUnroll], pc[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (m0 + u < w) {
+          c[u] = ld_stream(cp + (m0 + u) * 32);
+          v[u] = ld_stream(vp + (m0 + u) * 32);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (m0 + u < w) pc[u] = p[c[u]];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (m0 + u < w) acc = fma(v[u], pc[u], acc);
+    }
+    if (i < n && !((lm >> lane) & 1u)) {
+      const T qi = (JAC ? pi : dgi * pi) + acc;
+      q[i] = qi;
+      dot += (double)pi * (double)qi;
+    }
+  }
+  // long rows: one warp per row, lanes stride, fixed xor tree
+  for (int l = gw; l < S.nlong; l += W) {
+    const int i = __ldg(S.lrow + l);
+    const int a = __ldg(S.lptr + l), e = __ldg(S.lptr + l + 1);
+    T acc = T(0);
+    for (int k = a + lane; k < e; k += 32) acc = fma(__ldg(S.lval + k), p[__ldg(S.lcol + k)], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const T pi = p[i];
+      const T qi = (JAC ? pi : __ldg(S.dg + i) * pi) + acc;
+      q[i] = qi;
+      dot += (double)pi * (double)qi;
+    }
+  }
+  return dot;
+}
+
+// a2 over the grid: r^ -= alpha q; rho = r^.r^ (= r.z); rr = r^.D r^ (= r.r,
+// Jacobi) or rho.  Two 16-byte vectors per thread per trip, loads first.
+template <typename T, bool JAC>
+__device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<T>& V, T alpha,
+                                               double& rho, double& rr, const Grid& g) {
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::N;
+  const int64_t n = S.n;
+  const int64_t nv = n / VN;
+  VT* r = reinterpret_cast<VT*>(V.r);
+  const VT* q = reinterpret_cast<const VT*>(V.q);
+  const VT* dn = reinterpret_cast<const VT*>(S.dn);
+  for (int64_t i0 = g.gtid; i0 < nv; i0 += 2 * g.gstride) {
+    const int64_t i1 = i0 + g.gstride;
+    const bool two = i1 < nv;
+    VT rv[2], qv[2], dv[2];
+    rv[0] = r[i0];
+    qv[0] = q[i0];
+    if (JAC) dv[0] = __ldg(dn + i0);
+    if (two) {
+      rv[1] = r[i1];
+      qv[1] = q[i1];
+      if (JAC) dv[1] = __ldg(dn + i1);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !two) break;
+#pragma unroll
+      for (int j = 0; j < VN; ++j) {
+        const T ri = fma(-alpha, lane_c<T>(qv[h], j), lane<T>(rv[h], j));
+        lane<T>(rv[h], j) = ri;
+        const double r2 = (double)ri * (double)ri;
+        rho += r2;
+        if (JAC) rr += (double)lane<T>(dv[h], j) * r2;
+      }
+    }
+    r[i0] = rv[0];
+    if (two) r[i1] = rv[1];
+  }
+  for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
+    const T ri = fma(-alpha, V.q[i], V.r[i]);
+    V.r[i] = ri;
+    const double r2 = (double)ri * (double)ri;
+    rho += r2;
+    if (JAC) rr += (double)__ldg(S.dn + i) * r2;
+  }
+  if (!JAC) rr = rho;
+}
+
+// a3 over the grid: x^ += alpha p; p = r^ + beta p.  On the last iteration
+// (FINAL) the p update is skipped and the caller's x is written instead:
+// out = scale (x^ + alpha p), or out += fl64(scale (x^ + alpha p)) (OUT_ADD).
+template <typename T, bool JAC, bool FINAL, bool OUT_ADD>
+__device__ __forceinline__ void update_xp_phase(const Sell<T>& S, const LoopVecs<T>& V, T alpha,
+                                                T beta, double* out, const Grid& g) {
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::N;
+  const int64_t n = S.n;
+  const int64_t nv = n / VN;
+  VT* x = reinterpret_cast<VT*>(V.xh);
+  VT* p = reinterpret_cast<VT*>(V.p);
+  const VT* r = reinterpret_cast<const VT*>(V.r);
+  const VT* sc = reinterpret_cast<const VT*>(S.disq);
+  for (int64_t iv = g.gtid; iv < nv; iv += g.gstride) {
+    VT xv = x[iv], pv = p[iv], rv, dv;
+    if (!FINAL) rv = r[iv];
+    if (FINAL && JAC) dv = __ldg(sc + iv);
+#pragma unroll
+    for (int j = 0; j < VN; ++j) {
+      const T pj = lane<T>(pv, j);
+      const T xj = fma(alpha, pj, lane<T>(xv, j));
+      if (FINAL) {
+        const T xo = JAC ? xj * lane<T>(dv, j) : xj;
+        if (OUT_ADD) out[iv * VN + j] += (double)xo;
+        else out[iv * VN + j] = (double)xo;
+      } else {
+        lane<T>(xv, j) = xj;
+        lane<T>(pv, j) = fma(beta, pj, lane_c<T>(rv, j));
+      }
+    }
+    if (!FINAL) {
+      x[iv] = xv;
+      p[iv] = pv;
+    }
+  }
+  for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
+    const T pj = V.p[i];
+    const T xj = fma(alpha, pj, V.xh[i]);
+    if (FINAL) {
+      const T xo = JAC ? xj * __ldg(S.disq + i) : xj;
+      if (OUT_ADD) out[i] += (double)xo;
+      else out[i] = (double)xo;
+    } else {
+      V.xh[i] = xj;
+      V.p[i] = fma(beta, pj, V.r[i]);
+    }
+  }
+}
+
+// The CG loop of Alg. 1 on the loop matrix from a (re)start state: r^ set,
+// p = r^, x^ set, rho = r^.r^, rr = the true-norm r.r.  Iterates until
+// sqrt(rr) <= stop_abs (kOk), maxit SpMVs (kNotConverged), breakdown /
+// non-finite (kBreakdown / kNumeric) or a barrier timeout (kTimeout); *iters
+// advances by the SpMVs done.  When an iteration ran, the caller's x is
+// written (out = scale x^, or out += fl64(scale x^) with OUT_ADD) before the
+// final grid barrier; otherwise out keeps its exact value.
+template <typename T, bool JAC, bool OUT_ADD>
+__device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, double rr,
+                       double stop_abs, int maxit, int* iters, double* rr_out, double* out,
+                       double* part, int pstride, Grid& g, PhaseClock& clk) {
   int k = *iters;
   int status = kNotConverged;
-  for (;;) {
-    if (sqrt(rr) <= stop_abs) { status = kOk; break; }  // a4: test before the SpMV
-    if (k >= maxit) break;
-    {  // a1
-      double v[1] = {phase_spmv<T>(A, p, q, g, s_prod)};
-      publish<1>(v, part + kSlotPQ * (size_t)g.G, g);
-    }
+  bool done = sqrt(rr) <= stop_abs || k >= maxit;  // a4: tested before every SpMV
+  if (sqrt(rr) <= stop_abs) status = kOk;
+  while (!done) {
+    // a1: q = A^ p; p.q
+    double v1[1] = {spmv_phase<T, JAC>(S, V.p, V.q, g)};
+    publish<1>(v1, part + kSlotPQ * (size_t)pstride, g);
+    clk.lap(g.st, 0);
     if (!g.sync()) { status = kTimeout; break; }
+    clk.lap(g.st, 1);
     double pq[1];
-    grid_sum<1>(part + kSlotPQ * (size_t)g.G, g.G, pq);
+    grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
     if (!isfinite(pq[0]) || !isfinite(rho)) { status = kNumeric; break; }
     if (pq[0] <= 0.0) { status = kBreakdown; break; }
     const T alpha = (T)(rho / pq[0]);
-    {  // a2
-      double v[2] = {0.0, 0.0};
-      phase_update_xr<T, JAC>(A.n, x, r, p, q, dinv, alpha, v[0], v[1], g);
-      publish<2>(v, part + kSlotRZ * (size_t)g.G, g);
-    }
+    // a2: r^ -= alpha q; r.z, r.r
+    double v2[2] = {0.0, 0.0};
+    update_r_phase<T, JAC>(S, V, alpha, v2[0], v2[1], g);
+    publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
+    clk.lap(g.st, 2);
     if (!g.sync()) { status = kTimeout; break; }
+    clk.lap(g.st, 3);
     double s2[2];
-    grid_sum<2>(part + kSlotRZ * (size_t)g.G, g.G, s2);
+    grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     const T beta = (T)(s2[0] / rho);
     rho = s2[0];
     rr = s2[1];
-    phase_update_p<T, JAC>(A.n, r, p, dinv, beta, g);  // a3
     ++k;
+    const bool conv = sqrt(rr) <= stop_abs;
+    done = conv || k >= maxit;
+    if (conv) status = kOk;
+    // a3: x^ += alpha p; p = r^ + beta p (last iteration: write the caller's x)
+    if (done) update_xp_phase<T, JAC, true, OUT_ADD>(S, V, alpha, beta, out, g);
+    else update_xp_phase<T, JAC, false, OUT_ADD>(S, V, alpha, beta, out, g);
+    clk.lap(g.st, 4);
     if (!g.sync()) { status = kTimeout; break; }
+    clk.lap(g.st, 5);
   }
   *iters = k;
   *rr_out = rr;
+  if (status == kNumeric || status == kBreakdown) {
+    // the caller's x gets the last iterate
+    for (int64_t i = g.gtid; i < S.n; i += g.gstride) {
+      const T xo = JAC ? V.xh[i] * __ldg(S.disq + i) : V.xh[i];
+      if (OUT_ADD) out[i] += (double)xo;
+      else out[i] = (double)xo;
+    }
+    if (!g.sync()) return kTimeout;
+  }
   return status;
 }
 
-// a5 and (re)start: q = A x; r = b - q; z = M^-1 r; p = z; returns (r.z, r.r, b.b)
-// grid sums.  Returns false on a barrier timeout.
-template <bool JAC>
-__device__ bool residual_phase64(const SolveParams& P, Grid& g, double* s_prod, double (&out)[3]) {
-  phase_spmv<double>(P.A, P.x, P.q, g, s_prod);
-  if (!g.sync()) return false;
-  double v[3] = {0.0, 0.0, 0.0};
-  const int64_t n = P.A.n;
-  for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    const double bi = P.b[i];
-    const double ri = bi - P.q[i];
-    const double zi = JAC ? ri * __ldg(P.dinv + i) : ri;
-    P.r[i] = ri;
-    P.p[i] = zi;
-    v[0] += ri * zi;
-    v[1] += ri * ri;
-    v[2] += bi * bi;
-  }
-  publish<3>(v, P.part + kSlotRes * (size_t)g.G, g);
-  if (!g.sync()) return false;
-  grid_sum<3>(P.part + kSlotRes * (size_t)g.G, g.G, out);
-  return true;
+// Caller's-matrix SpMV q = A x over the original row blocks (a5, restarts).
+__device__ __forceinline__ void spmv_orig(const Csr<double>& A, const double* x, double* q,
+                                          const Grid& g, double* s_prod) {
+  for (int b = (int)g.cta; b < A.nrb; b += (int)g.G) spmv_rowblock<double>(A, x, q, b, s_prod);
 }
 
 // fp64 (Jacobi-)PCG with true-residual check and residual-replacement
-// restarts (readings R1-R5 of the method; see the oracle's header).
+// restarts (readings R1-R5 of the method, see the oracle's header).
 template <bool JAC>
-__global__ void __launch_bounds__(kBlock) pcg64_kernel(SolveParams P) {
+__global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
   __shared__ double s_prod[kCap];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
+  PhaseClock clk(P.timers != 0);
+  const int64_t n = P.A.n;
+  const LoopVecs<double>& V = P.V64;
   int status = kNotConverged, k = 0, restarts = 0;
   double relres_true = 0.0, rr = 0.0, bb = 0.0;
   bool first = true;
   for (;;) {
+    // a5 / (re)start: r = b - A x; r^ = D^-1/2 r; x^ = D^1/2 x
+    spmv_orig(P.A, P.x, V.q, g, s_prod);
+    if (!g.sync()) { status = kTimeout; break; }
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = g.gtid; i < n; i += g.gstride) {
+      const double bi = P.b[i];
+      const double ri = bi - V.q[i];
+      const double rh = JAC ? ri * __ldg(P.disq + i) : ri;
+      V.r[i] = rh;
+      V.p[i] = rh;
+      V.xh[i] = JAC ? P.x[i] * __ldg(P.dsq + i) : P.x[i];
+      v[0] += rh * rh;
+      v[1] += ri * ri;
+      v[2] += bi * bi;
+    }
+    publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+    if (!g.sync()) { status = kTimeout; break; }
     double s3[3];
-    if (!residual_phase64<JAC>(P, g, s_prod, s3)) { status = kTimeout; break; }
+    grid_sum<3>(P.part + kSlotRes * (size_t)P.pstride, g.G, s3);
     if (first) {
       bb = s3[2];
       if (bb == 0.0) {  // b = 0: x = 0 solves it
-        for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) P.x[i] = 0.0;
+        for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] = 0.0;
         status = kOk;
-        relres_true = 0.0;
-        rr = 0.0;
         break;
       }
     } else {
@@ -341,19 +575,35 @@ __global__ void __launch_bounds__(kBlock) pcg64_kernel(SolveParams P) {
       if (k >= P.maxit || restarts >= P.max_restarts) { status = kNotConverged; break; }
       ++restarts;
     }
+    const bool was_first = first;
     first = false;
     rr = s3[1];
-    const int st = cg_loop<double, JAC>(P.A, P.x, P.r, P.p, P.q, P.dinv, s3[0], rr,
-                                         P.tol * sqrt(bb), P.maxit, &k, &rr, P.part, g, s_prod);
+    const int k_before = k;
+    const int st = cg_loop<double, JAC, false>(P.S64, V, s3[0], rr, P.tol * sqrt(bb), P.maxit,
+                                               &k, &rr, P.x, P.part, P.pstride, g, clk);
     if (st == kTimeout) { status = kTimeout; break; }
     if (st == kNumeric || st == kBreakdown) {
       status = st;
-      double s3e[3];
-      if (residual_phase64<JAC>(P, g, s_prod, s3e)) relres_true = sqrt(s3e[1]) / sqrt(bb);
-      else status = kTimeout;
+      spmv_orig(P.A, P.x, V.q, g, s_prod);  // report the true residual of the last iterate
+      if (!g.sync()) { status = kTimeout; break; }
+      double w[1] = {0.0};
+      for (int64_t i = g.gtid; i < n; i += g.gstride) {
+        const double ri = P.b[i] - V.q[i];
+        w[0] += ri * ri;
+      }
+      publish<1>(w, P.part + kSlotRes * (size_t)P.pstride, g);
+      if (!g.sync()) { status = kTimeout; break; }
+      double s1[1];
+      grid_sum<1>(P.part + kSlotRes * (size_t)P.pstride, g.G, s1);
+      relres_true = sqrt(s1[0]) / sqrt(bb);
       break;
     }
-    // st is kOk or kNotConverged: loop back to recompute the true residual
+    if (was_first && k == k_before && st == kOk) {  // x0 met tol: its true residual is s3[1]
+      relres_true = sqrt(s3[1]) / sqrt(bb);
+      status = kOk;
+      break;
+    }
+    // kOk or kNotConverged: loop back to recompute the true residual
   }
   // CTA 0 reports; a timeout anywhere is visible to the host through st->abort
   if (g.cta == 0 && threadIdx.x == 0) {
@@ -366,45 +616,45 @@ __global__ void __launch_bounds__(kBlock) pcg64_kernel(SolveParams P) {
 }
 
 // fp32-inner / fp64-outer iterative refinement (reading R6): the outer fp64
-// residual, solution update and convergence test, the inner fp32 Jacobi-PCG
-// with fp64-accumulated dot products, all in one persistent launch.
+// residual, solution update and convergence test, the inner fp32 (scaled
+// Jacobi) CG with fp64-accumulated dot products, all in one launch.
 template <bool JAC>
-__global__ void __launch_bounds__(kBlock) pcg_ir_kernel(SolveParams P) {
-  __shared__ double s_prod64[kCap];
-  float* s_prod32 = reinterpret_cast<float*>(s_prod64);
+__global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
+  __shared__ double s_prod[kCap];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
+  PhaseClock clk(P.timers != 0);
   const int64_t n = P.A.n;
+  const LoopVecs<float>& V = P.V32;
   int status = kNotConverged, inner = 0, outer = 0;
   double relres = 0.0, bb = 0.0, rr32 = 0.0;
   for (;;) {
-    // outer fp64 residual r = b - A x, fused with the inner start:
-    // r32 = fl32(r), d = 0, p32 = z32 = dinv32 r32
-    phase_spmv<double>(P.A, P.x, P.q, g, s_prod64);
+    // outer fp64 residual r = b - A x fused with the inner start:
+    // r^32 = fl32(D^-1/2 r), d^ = 0
+    spmv_orig(P.A, P.x, P.V64.q, g, s_prod);
     if (!g.sync()) { status = kTimeout; break; }
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = g.gtid; i < n; i += g.gstride) {
       const double bi = P.b[i];
-      const double ri = bi - P.q[i];
-      const float r32 = (float)ri;
-      const float z32 = JAC ? r32 * __ldg(P.dinv32 + i) : r32;
-      P.r32[i] = r32;
-      P.p32[i] = z32;
-      P.d32[i] = 0.0f;
+      const double ri = bi - P.V64.q[i];
+      const float rh = (float)(JAC ? ri * __ldg(P.disq + i) : ri);
+      V.r[i] = rh;
+      V.p[i] = rh;
+      V.xh[i] = 0.0f;
+      const double rh2 = (double)rh * (double)rh;
       v[0] += ri * ri;
       v[1] += bi * bi;
-      v[2] += (double)r32 * (double)z32;
-      v[3] += (double)r32 * (double)r32;
+      v[2] += rh2;
+      v[3] += JAC ? (double)__ldg(P.S32.dn + i) * rh2 : rh2;
     }
-    publish<4>(v, P.part + kSlotRes * (size_t)g.G, g);
+    publish<4>(v, P.part + kSlotRes * (size_t)P.pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
     double s4[4];
-    grid_sum<4>(P.part + kSlotRes * (size_t)g.G, g.G, s4);
+    grid_sum<4>(P.part + kSlotRes * (size_t)P.pstride, g.G, s4);
     if (outer == 0) {
       bb = s4[1];
       if (bb == 0.0) {
         for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] = 0.0;
         status = kOk;
-        relres = 0.0;
         break;
       }
     }
@@ -412,14 +662,10 @@ __global__ void __launch_bounds__(kBlock) pcg_ir_kernel(SolveParams P) {
     if (!isfinite(relres)) { status = kNumeric; break; }
     if (relres <= P.tol) { status = kOk; break; }
     if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
-    const int st = cg_loop<float, JAC>(P.A32, P.d32, P.r32, P.p32, P.q32, P.dinv32, s4[2], s4[3],
-                                        P.tol_in * sqrt(s4[3]), P.maxit, &inner, &rr32, P.part, g,
-                                        s_prod32);
+    const int st = cg_loop<float, JAC, true>(P.S32, V, s4[2], s4[3], P.tol_in * sqrt(s4[3]),
+                                             P.maxit, &inner, &rr32, P.x, P.part, P.pstride, g, clk);
     if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
-    // x += fl64(d); a barrier before the next SpMV reads x at neighbours
-    for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)P.d32[i];
     ++outer;
-    if (!g.sync()) { status = kTimeout; break; }
   }
   if (g.cta == 0 && threadIdx.x == 0) {
     P.st->status = status;

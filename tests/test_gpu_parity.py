@@ -315,3 +315,107 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     assert st == st2 == cg.CG_OK and it == it2
     assert np.array_equal(xh.numpy(), x2)
     cg.cg_destroy(h)
+
+
+def test_fp32_refinement_unpreconditioned():
+    A = gen.lap2d(48, 9, 0.05)
+    b = oracle.spmv(A, gen.xstar(A.n, 11))
+    ref = oracle.pcg_ir(A, b, tol=1e-10, tol_in=1e-4, precond=0)
+    st, it, rel, x, info = gpu_solve(A, b, 1e-10, 100000, cg.CG_PRECOND_NONE, cg.CG_PREC_FP32_IR)
+    assert st == cg.CG_OK == ref.status
+    assert oracle.true_relres(A, b, x) <= 1e-10 * (1 + 1e-6)
+    assert abs(info["restarts"] - ref.restarts) <= 1
+    assert abs(it - ref.iters) <= max(5, math.ceil(0.1 * ref.iters)), (it, ref.iters)
+
+
+def test_phase_timers_report_time_per_phase():
+    A = gen.lap3d7(32)
+    b = oracle.spmv(A, gen.xstar(A.n, 1))
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_PHASE_TIMERS, 1) == cg.CG_OK
+    st, it, rel, x, info = gpu_solve(A, b, 1e-8, 2000, cg.CG_PRECOND_JACOBI, h=h)
+    cg.cg_destroy(h)
+    assert st == cg.CG_OK
+    ph = info["phase_ms"]
+    assert all(t >= 0 for t in ph) and ph[0] > 0 and ph[2] > 0
+    assert sum(ph) <= info["kernel_ms"] * 1.01
+    assert info["kernel_bytes_per_iter"] > 0
+
+
+# ---------------------------------------------------------------- loop forms
+
+def solve_mode(A, b, tol, maxit, precond, mode, x0=None, max_restarts=None):
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
+    if max_restarts is not None:
+        assert cg.cg_set_option(h, cg.CG_OPT_MAX_RESTARTS, max_restarts) == cg.CG_OK
+    out = gpu_solve(A, b, tol, maxit, precond, x0=x0, h=h)
+    cg.cg_destroy(h)
+    return out
+
+
+GRAPH_CASES = [
+    ("lap2d64_none", lambda: gen.lap2d(64), 0, 1e-8, 1000),
+    ("lap3d7_20_jac", lambda: gen.lap3d7(20), 1, 1e-8, 2000),
+    ("diff27_12_jac", lambda: gen.diff3d27(12, 1.0, 4), 1, 1e-10, 5000),
+    ("uneven_jac", lambda: spd_from_pattern(4000, 3, long_rows=[(5, 2500), (100, 300)]), 1, 1e-9, 3000),
+    ("q1_none", lambda: gen.q1aniso(40, 1.5, 0.7, 0.03, 3), 0, 1e-8, 5000),
+]
+
+
+@pytest.mark.parametrize("name,make,precond,tol,maxit", GRAPH_CASES, ids=[c[0] for c in GRAPH_CASES])
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+def test_loop_forms_match_oracle(name, make, precond, tol, maxit, mode):
+    A = make()
+    b = oracle.spmv(A, gen.xstar(A.n, 6))
+    ref = oracle.pcg(A, b, tol=tol, maxit=maxit, precond=precond)
+    st, it, rel, x, info = solve_mode(A, b, tol, maxit, precond, mode)
+    assert st == ref.status == cg.CG_OK, cg.cg_last_error()
+    assert abs(it - ref.iters) <= iters_band(ref.iters), (it, ref.iters)
+    rel_or = oracle.true_relres(A, b, x)
+    assert rel_or <= tol * (1 + 1e-6)
+    assert abs(rel - rel_or) <= 1e-6 * rel_or + 1e-15
+    assert np.linalg.norm(x - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+def test_loop_form_edge_cases(mode):
+    A = gen.lap2d(24)
+    xs = gen.xstar(A.n, 3)
+    b = oracle.spmv(A, xs)
+    st, it, rel, x, _ = solve_mode(A, np.zeros(A.n), 1e-8, 100, 1, mode, x0=np.ones(A.n))
+    assert st == cg.CG_OK and it == 0 and rel == 0.0 and np.all(x == 0)
+    st, it, rel, x, _ = solve_mode(A, b, 1e-8, 100, 1, mode, x0=xs)
+    assert st == cg.CG_OK and it == 0 and np.array_equal(x, xs)
+    ref = oracle.pcg(A, b, tol=1e-12, maxit=20, precond=0)
+    st, it, rel, x, _ = solve_mode(A, b, 1e-12, 20, 0, mode)
+    assert st == cg.CG_NOT_CONVERGED and it == 20
+    assert np.linalg.norm(x - ref.x) <= 1e-10 * np.linalg.norm(ref.x)
+    st, it, rel, x, _ = solve_mode(A, b, 1e-8, 0, 1, mode)
+    assert st == cg.CG_NOT_CONVERGED and it == 0 and np.all(x == 0)
+    import scipy.sparse as sp
+    M = sp.diags([1.0, 2.0, -3.0, 4.0] * 50).tocsr()
+    Ai = gen.CSR(200, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data, "indef")
+    st, *_ = solve_mode(Ai, np.ones(200), 1e-10, 50, 0, mode)
+    assert st == cg.CG_ERR_BREAKDOWN
+    bn = b.copy()
+    bn[7] = np.nan
+    st, *_ = solve_mode(A, bn, 1e-8, 50, 1, mode)
+    assert st == cg.CG_ERR_NUMERIC
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+def test_residual_replacement_restarts_match_oracle(mode):
+    """A tolerance below what fp64 can attain: the recursive residual passes while the
+    true residual stagnates, so the solve restarts from x (reading R3) until the restarts
+    run out; the oracle takes the same path."""
+    A = gen.diff3d27(10, 1.0, 8)
+    b = oracle.spmv(A, gen.xstar(A.n, 8))
+    tol, maxit = 1e-17, 3000
+    ref = oracle.pcg(A, b, tol=tol, maxit=maxit, precond=1, max_restarts=2)
+    st, it, rel, x, info = solve_mode(A, b, tol, maxit, 1, mode, max_restarts=2)
+    assert st == ref.status == cg.CG_NOT_CONVERGED
+    assert info["restarts"] == ref.restarts
+    assert rel <= 1e-12
