@@ -14,7 +14,7 @@ entry point (H2D of b and x0, D2H of x inside the timed region), roofline of the
 persistent solver kernel against the measured HBM copy bandwidth, and the CPU
 oracle timed on a bounded sample.
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the CPU oracle (the reference arm: the paper ships no code) on a
 bounded sample of the same workload.
 """
 from __future__ import annotations

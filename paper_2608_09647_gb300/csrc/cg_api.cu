@@ -493,7 +493,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
     ep = h->graph_ep;
     prev = nullptr;
   }
-  // epilogue: flush on breakdown, true residual, verdict
+  // epilogue: flush on breakdown, true residual, final status
   CG_CUDA(h, add_kernel(ep, &n, prev, f_flush, G, kBlock, a_ga));
   prev = n;
   CG_CUDA(h, add_kernel(ep, &n, prev, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));

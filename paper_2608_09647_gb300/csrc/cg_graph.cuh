@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) g_true(GArgs a) {
   publish<1>(v, P.part + kSlotRes * (size_t)P.pstride, g);
 }
 
-// One CTA: the true relative residual and the solve's verdict.
+// One CTA: the true relative residual and the solve's final status.
 __global__ void g_final64(GArgs a) {
   const unsigned G = a.G_upd;
   double s[1];
