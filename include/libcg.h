@@ -148,6 +148,44 @@ const char* cg_last_error(const cg_handle* h);
 /* Static name of a status code. */
 const char* cg_status_string(int32_t status);
 
+/* Largest n that cg_solve_noalloc accepts: its scratch is four device vectors
+ * of this many doubles plus a result block (2 MiB per GPU). */
+#define CG_NOALLOC_MAX_ROWS 65536
+
+/*
+ * Allocation-free (Jacobi-)CG for small systems.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory: a
+ * plugin or operator inside a framework that owns all device memory through
+ * its own pool, code that may not hold device allocations of its own, or a
+ * latency-critical loop where a cudaMalloc could synchronise the device.
+ *
+ * It needs no handle and calls no cudaMalloc/cudaFree: the scratch vectors
+ * live in one file-scope __device__ array that every GPU loading this library
+ * keeps until the process exits.  n <= CG_NOALLOC_MAX_ROWS; rowptr[n+1],
+ * colind[nnz], vals[nnz], b[n] and x[n] are DEVICE pointers (x: x0 in,
+ * solution out); cuda_stream is a cudaStream_t (NULL = legacy default);
+ * iters_out / relres_out are host pointers and may be NULL.  The solve follows
+ * cg_solve's rules (relative test before each SpMV, fp64 true residual, up to
+ * 3 residual-replacement restarts) but runs in a single CTA, so it suits small
+ * systems only.  It blocks until the result is on the host.
+ *
+ * Errors: CG_ERR_INVALID when n exceeds CG_NOALLOC_MAX_ROWS, a size or
+ * pointer is bad, the CSR is malformed (checked on the device: rowptr[0] = 0,
+ * rowptr[n] = nnz, non-decreasing, colind in [0, n)) or Jacobi meets a row
+ * without a positive diagonal; CG_ERR_CUDA when a CUDA call fails; otherwise
+ * the statuses of cg_solve.
+ *
+ * All calls on a device share the scratch array, which keeps the last call's
+ * contents (the kernel initialises what it reads): calls that may overlap on
+ * the GPU (other streams or host threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address
+ * with that device current, so make that first call before any stream capture.
+ */
+cg_status cg_solve_noalloc(int64_t n, int64_t nnz, const int32_t* rowptr, const int32_t* colind,
+                           const double* vals, const double* b, double* x, double tol,
+                           int32_t maxit, int32_t precond, void* cuda_stream,
+                           int32_t* iters_out, double* relres_out);
+
 #ifdef __cplusplus
 }
 #endif

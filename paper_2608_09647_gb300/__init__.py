@@ -28,7 +28,8 @@ CG_OPT_PHASE_TIMERS, CG_OPT_LOOP_MODE = 6, 7
 # every symbol include/libcg.h declares
 EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
            "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
-           "cg_last_error", "cg_status_string")
+           "cg_last_error", "cg_status_string", "cg_solve_noalloc")
+CG_NOALLOC_MAX_ROWS = 65536
 
 
 class CGError(RuntimeError):
@@ -84,6 +85,8 @@ def load(build_if_missing: bool = True):
     lib.cg_last_error.restype = ctypes.c_char_p
     lib.cg_status_string.argtypes = [i32]
     lib.cg_status_string.restype = ctypes.c_char_p
+    lib.cg_solve_noalloc.argtypes = [i64, i64, P, P, P, P, P, f64, i32, i32, P, pi32, pf64]
+    lib.cg_solve_noalloc.restype = ctypes.c_int
     for name in ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
                  "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info"):
         getattr(lib, name).restype = ctypes.c_int
@@ -195,6 +198,24 @@ def cg_solve_host(h: Handle, b_host, x_host, tol: float = 1e-8, maxit: int = 100
     st = lib.cg_solve_host(h.ptr, ctypes.c_void_p(b_host.data_ptr()),
                            ctypes.c_void_p(x_host.data_ptr()), float(tol), int(maxit),
                            int(precond), int(precision), ctypes.byref(it), ctypes.byref(rel))
+    return st, it.value, rel.value
+
+
+def cg_solve_noalloc(rowptr, colind, vals, b, x, tol: float = 1e-8, maxit: int = 1000,
+                     precond: int = CG_PRECOND_JACOBI):
+    """Handle-free solve that allocates no device memory (for callers that cannot call
+    cudaMalloc); n <= CG_NOALLOC_MAX_ROWS, single CTA, so small systems only.  Runs on
+    the current stream; x holds x0 on entry.  Returns (status, iters, relres_true)."""
+    import torch
+    n = rowptr.numel() - 1
+    it = ctypes.c_int32(0)
+    rel = ctypes.c_double(0.0)
+    st = load().cg_solve_noalloc(n, colind.numel() if colind is not None else 0,
+                                 _dptr(rowptr, torch.int32, "rowptr"),
+                                 _dptr(colind, torch.int32, "colind"),
+                                 _dptr(vals, torch.float64, "vals"), _dptr(b, torch.float64, "b"),
+                                 _dptr(x, torch.float64, "x"), float(tol), int(maxit),
+                                 int(precond), _stream_ptr(), ctypes.byref(it), ctypes.byref(rel))
     return st, it.value, rel.value
 
 
