@@ -310,9 +310,13 @@ def main():
     relres = max(r for _, r, _ in infos)
     kern_ms = sum(inf["kernel_ms"] for _, _, inf in infos)
     kern_bytes = sum(inf["bytes_moved"] for _, _, inf in infos)
+    own_bytes = sum(inf["kernel_bytes_per_iter"] * inf["iters"] for _, _, inf in infos)
     peak, peak_kind = load_peaks()
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    achieved_own = own_bytes / (kern_ms / 1e3) / 1e9
     bpi = bytes_per_iter(A.n, A.nnz, precond_s, precision_s)
+    form = {1: "persistent", 2: "graph", 3: "unrolled"}.get(infos[0][2]["loop_form"], "?")
+    launches = sum(inf["kernel_launches"] for _, _, inf in infos)
     tr = ncu_traffic(args.workload)
     traffic = None
     if tr:
@@ -368,10 +372,14 @@ def main():
             "loop_gbs_model": achieved,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "pcg64_kernel<Jacobi>" if precision_s == "fp64" else "pcg_ir_kernel<Jacobi>",
-                         "bytes_per_iter_model": bpi, "peak_kind": peak_kind},
+                         "timed_unit": ("the CG loop of one solve: the persistent kernel" if form == "persistent"
+                                        else "the CG loop of one solve: graph of SpMV, r-update and x/p-update kernels"),
+                         "loop_form": form,
+                         "bytes_per_iter_model": bpi, "peak_kind": peak_kind,
+                         "kernel_bytes_per_iter": infos[0][2]["kernel_bytes_per_iter"],
+                         "achieved_kernel_bytes": achieved_own, "frac_kernel_bytes": achieved_own / peak},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": launches,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
         }

@@ -86,6 +86,8 @@ typedef struct {
                              88 n (Jacobi) / 80 n bytes of vectors (fp64; half that in fp32) */
   double phase_ms[6];     /* with CG_OPT_PHASE_TIMERS: CTA 0 time in the SpMV, r-update and
                              x/p-update phases, each followed by its grid-barrier wait */
+  int32_t loop_form;      /* CG_OPT_LOOP_MODE form that ran: 1 persistent, 2 graph WHILE, 3 unrolled */
+  int32_t kernel_launches;/* kernels of this library launched by the solve */
 } cg_solve_info;
 
 /*

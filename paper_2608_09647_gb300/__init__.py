@@ -43,7 +43,8 @@ class SolveInfo(ctypes.Structure):
                 ("restarts", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
                 ("relres_true", ctypes.c_double), ("relres_rec", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("bytes_moved", ctypes.c_int64),
-                ("kernel_bytes_per_iter", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6)]
+                ("kernel_bytes_per_iter", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6),
+                ("loop_form", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -442,7 +442,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   const unsigned G = (unsigned)h->grid_graph;
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count),
                                                      h->grid_part));
-  GArgs ga{P, h->gs, ch, unroll == 0 ? 1 : 0, Gq, G};
+  GArgs ga{P, h->gs, ch, Gq, G};
   Csr<double> A = P.A;
   const double* x = P.x;
   double* q = P.V64.q;
@@ -450,8 +450,11 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   void* a_spmv[] = {&A, &x, &q};
   void* a_ga[] = {&ga};
   const void* f_r = jac ? (const void*)g_upd_r<double, true> : (const void*)g_upd_r<double, false>;
-  const void* f_xp = jac ? (const void*)g_upd_xp<double, true, false>
-                         : (const void*)g_upd_xp<double, false, false>;
+  const void* f_xp =
+      unroll == 0 ? (jac ? (const void*)g_upd_xp<double, true, false, true>
+                         : (const void*)g_upd_xp<double, false, false, true>)
+                  : (jac ? (const void*)g_upd_xp<double, true, false, false>
+                         : (const void*)g_upd_xp<double, false, false, false>);
   const void* f_flush = jac ? (const void*)g_flush<double, true, false>
                             : (const void*)g_flush<double, false, false>;
   cudaGraphNode_t n, prev;
@@ -461,7 +464,9 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   CG_CUDA(h, add_kernel(g, &n, prev, jac ? (const void*)g_res64<true> : (const void*)g_res64<false>,
                         G, kBlock, a_ga));
   prev = n;
-  CG_CUDA(h, add_kernel(g, &n, prev, (const void*)g_start64, 1, 32, a_ga));
+  CG_CUDA(h, add_kernel(g, &n, prev,
+                        unroll == 0 ? (const void*)g_start64<true> : (const void*)g_start64<false>,
+                        1, 32, a_ga));
   prev = n;
   cudaGraph_t ep = g;
   if (unroll == 0) {
@@ -527,20 +532,26 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   CG_CUDA(h, cudaMemsetAsync(h->gs, 0, sizeof(GState), h->stream));
   CG_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   int restarts = 0, status;
+  int64_t launches = 0;
+  int k_prev = 0;
   for (;;) {
     CG_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+    launches += 7;  // prologue 3 + epilogue 4
     if (unroll > 0) {
       for (;;) {  // iteration graphs until the loop state leaves kRunning
         CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
         CG_CUDA(h, cudaStreamSynchronize(h->stream));
         if (h->host_gs->status != kRunning) break;
         CG_CUDA(h, cudaGraphLaunch(h->gexec_it, h->stream));
+        launches += 3 * unroll;
       }
       CG_CUDA(h, cudaGraphLaunch(h->gexec_ep, h->stream));
     }
     CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
     CG_CUDA(h, cudaStreamSynchronize(h->stream));
     status = h->host_gs->status;
+    if (unroll == 0) launches += 3 * (int64_t)(h->host_gs->k - k_prev);
+    k_prev = h->host_gs->k;
     if (status != kNeedRestart) break;
     if (h->host_gs->k >= P.maxit || restarts >= P.max_restarts) {
       status = kNotConverged;
@@ -560,6 +571,8 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   h->last.relres_true = gs.relres_true;
   h->last.relres_rec = gs.bb > 0.0 ? sqrt(gs.rr) / sqrt(gs.bb) : 0.0;
   h->last.kernel_ms = ms;
+  h->last.loop_form = unroll > 0 ? 3 : 2;
+  h->last.kernel_launches = (int32_t)std::min<int64_t>(launches, INT32_MAX);
   const int64_t n = h->n, nnz = h->nnz;
   h->last.bytes_moved = (12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n) * (int64_t)gs.k;
   const int64_t ent = h->sell_entries + h->nnz_long;
@@ -664,7 +677,7 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   h->grid_max = std::min(std::min(g1, g2), std::min(g3, g4));
   const int g5 = std::min(max_coresident(g_upd_r<double, true>, h->sm_count),
                           max_coresident(g_upd_r<double, false>, h->sm_count));
-  const int g6 = std::min(max_coresident(g_upd_xp<double, true, false>, h->sm_count),
+  const int g6 = std::min(max_coresident(g_upd_xp<double, true, false, true>, h->sm_count),
                           max_coresident(g_res64<true>, h->sm_count));
   h->grid_graph = std::min(g5, g6);
   h->grid_part = 64 * h->sm_count;  // bounds every loop kernel's grid
@@ -814,6 +827,8 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   h->last.relres_true = ds.relres_true;
   h->last.relres_rec = ds.relres_rec;
   h->last.kernel_ms = ms;
+  h->last.loop_form = 1;
+  h->last.kernel_launches = 1;
   // modelled bytes of the CG loop (three phases of Alg. 1 on the caller's CSR)
   const int64_t n = h->n, nnz = h->nnz;
   const int64_t per_iter = fp64 ? 12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n

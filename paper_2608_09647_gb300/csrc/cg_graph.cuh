@@ -39,7 +39,6 @@ struct GArgs {
   SolveParams P;
   GState* gs;
   cudaGraphConditionalHandle h;
-  int use_cond;     // 0: unrolled form, the kernels of finished iterations return at once
   unsigned G_spmv;  // CTAs of the SpMV kernel (its p.q partials)
   unsigned G_upd;   // CTAs of the vector kernels (their partials)
 };
@@ -75,7 +74,9 @@ __global__ void __launch_bounds__(kBlock) g_res64(GArgs a) {
   publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
 }
 
-// One CTA: loop state from the prologue partials; sets the WHILE condition.
+// One CTA: loop state from the prologue partials; sets the WHILE condition
+// (COND; the unrolled form compiles no device-side graph call).
+template <bool COND>
 __global__ void g_start64(GArgs a) {
   const unsigned G = a.G_upd;
   double s[3];
@@ -97,7 +98,7 @@ __global__ void g_start64(GArgs a) {
   else if (gs->k >= a.P.maxit) status = kNotConverged;
   gs->status = status;
   gs->ctr = 0;
-  if (a.use_cond) cudaGraphSetConditional(a.h, status == kRunning ? 1u : 0u);
+  if constexpr (COND) cudaGraphSetConditional(a.h, status == kRunning ? 1u : 0u);
 }
 
 // a1: q = A^ p, partial p.q.  W > 0: the matrix has uniform slices of width W
@@ -141,14 +142,14 @@ __global__ void __launch_bounds__(kBlock) g_upd_r(GArgs a) {
 // a3 + a4: beta, convergence; x^ += alpha p and p = r^ + beta p, or on the
 // last iteration out = scale (x^ + alpha p) (OUT_ADD: out += ...).  The last
 // CTA to finish stores the loop state and sets the WHILE condition.
-template <typename T, bool JAC, bool OUT_ADD>
+template <typename T, bool JAC, bool OUT_ADD, bool COND>
 __global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
   const SolveParams& P = a.P;
   Grid g = graph_grid();
   const Sell<T>& S = sell_of<T>(P);
   const LoopVecs<T>& V = vecs_of<T>(P);
   GState* gs = a.gs;
-  if (!a.use_cond && gs->status != kRunning) return;  // unrolled form: loop already over
+  if (!COND && gs->status != kRunning) return;  // unrolled form: loop already over
   const bool failed = gs->status != kRunning;  // set by g_upd_r (breakdown / numeric)
   double rho1 = 0.0, rr1 = 0.0;
   bool done = true, conv = false;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
         gs->status = done ? (conv ? kOk : kNotConverged) : kRunning;
       }
       __threadfence();
-      if (a.use_cond) cudaGraphSetConditional(a.h, (!failed && !done) ? 1u : 0u);
+      if constexpr (COND) cudaGraphSetConditional(a.h, (!failed && !done) ? 1u : 0u);
     }
   }
 }
