@@ -97,6 +97,57 @@ __global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
+// Distinct off-diagonal offsets j - i into a 64-slot open-addressing table
+// (kOffEmpty marks a free slot); *overflow is set when they do not fit.
+constexpr int kOffSlots = 64;
+constexpr int kOffEmpty = INT32_MIN;
+__global__ void offsets_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ colind, int* table, int* overflow) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int64_t c = colind[k];
+      if (c == i) continue;
+      const int d = (int)(c - i);
+      unsigned h = ((unsigned)d * 2654435761u) >> 26;  // 6 bits
+      int t = 0;
+      for (; t < kOffSlots; ++t, h = (h + 1) & (kOffSlots - 1)) {
+        const int v = *((volatile int*)&table[h]);
+        if (v == d) break;
+        if (v == kOffEmpty) {
+          const int old = atomicCAS(&table[h], kOffEmpty, d);
+          if (old == kOffEmpty || old == d) break;
+        }
+      }
+      if (t == kOffSlots) atomicExch(overflow, 1);
+    }
+  }
+}
+
+// Sliced-diagonal values (thread per row): slot m of row i holds the sum of
+// the row's entries in column i + delta[m] (0 where there is none); with
+// SCALE the Jacobi scaling A_ij / sqrt(A_ii A_jj).  The array is zeroed
+// before, so lanes past n stay 0.
+template <typename T, bool SCALE>
+__global__ void fill_dia_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                const int32_t* __restrict__ colind,
+                                const double* __restrict__ vals,
+                                const double* __restrict__ disq, int ndiag,
+                                const int32_t* __restrict__ delta, T* val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = (i >> 5) * ndiag * 32 + (i & 31);
+    const double si = SCALE ? disq[i] : 1.0;
+    for (int m = 0; m < ndiag; ++m) {
+      const int64_t target = i + delta[m];
+      double v = 0.0;
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+        if ((int64_t)colind[k] == target) v += SCALE ? vals[k] * (si * disq[target]) : vals[k];
+      val[base + (int64_t)m * 32] = (T)v;
+    }
+  }
+}
+
 // Compact CSR of the long rows (thread per long row).
 template <typename T, bool SCALE>
 __global__ void fill_long_kernel(int32_t nlong, const int32_t* __restrict__ lrow,
@@ -142,6 +193,9 @@ struct cg_handle {
   // off-diagonal loop matrix in SELL-32 form (+ compact CSR of long rows)
   int32_t nslices = 0;
   int32_t uniform_w = -1;           // every slice padded to this width (-1: variable)
+  int32_t dia = 0;                  // sliced-diagonal layout (no column array)
+  int32_t delta[kMaxDiag] = {};     // its diagonal offsets, ascending
+  int32_t* delta_dev = nullptr;
   int32_t* soff = nullptr;
   uint32_t* lmask = nullptr;
   int32_t* scol = nullptr;
@@ -268,6 +322,59 @@ cg_status ensure_offdiag(cg_handle* h) {
   if (n > 0) CG_CUDA(h, cudaMemcpy(nd.data(), h->ndiag, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost));
   const std::vector<int32_t>& rp = h->host_rowptr;
   const int64_t ns = (n + 31) / 32;
+  // sliced-diagonal layout when the off-diagonal part lies on <= kMaxDiag
+  // diagonals that are at least 90 % full
+  int64_t nnz_od_all = 0;
+  for (int64_t i = 0; i < n; ++i) nnz_od_all += rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
+  if (n > 0 && nnz_od_all > 0) {
+    int* tab = nullptr;
+    CG_CUDA(h, cudaMalloc(&tab, sizeof(int) * (kOffSlots + 1)));
+    std::vector<int> ht(kOffSlots + 1, kOffEmpty);
+    ht[kOffSlots] = 0;
+    cudaError_t e = cudaMemcpy(tab, ht.data(), sizeof(int) * (kOffSlots + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      offsets_kernel<<<grid_for(n), 256>>>(n, h->rowptr, h->colind, tab, tab + kOffSlots);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ht.data(), tab, sizeof(int) * (kOffSlots + 1), cudaMemcpyDeviceToHost);
+    cudaFree(tab);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cg_create: diagonal offsets");
+    std::vector<int32_t> offs;
+    for (int t = 0; t < kOffSlots; ++t)
+      if (ht[(size_t)t] != kOffEmpty) offs.push_back(ht[(size_t)t]);
+    std::sort(offs.begin(), offs.end());
+    const int nd_ = (int)offs.size();
+    if (!ht[kOffSlots] && nd_ > 0 && nd_ <= kMaxDiag && nnz_od_all * 10 >= (int64_t)nd_ * n * 9) {
+      h->dia = 1;
+      h->uniform_w = nd_;
+      for (int m = 0; m < nd_; ++m) h->delta[m] = offs[(size_t)m];
+      h->nslices = (int32_t)ns;
+      h->sell_entries = ns * 32 * nd_;
+      h->nnz_od = nnz_od_all;
+      h->nlong = 0;
+      h->nnz_long = 0;
+      std::vector<int32_t> soff((size_t)ns + 1);
+      for (int64_t s2 = 0; s2 <= ns; ++s2) soff[(size_t)s2] = (int32_t)(s2 * nd_);
+      std::vector<uint32_t> lmask((size_t)std::max<int64_t>(ns, 1), 0u);
+      CG_CUDA(h, cudaMalloc(&h->soff, sizeof(int32_t) * soff.size()));
+      CG_CUDA(h, cudaMemcpy(h->soff, soff.data(), sizeof(int32_t) * soff.size(), cudaMemcpyHostToDevice));
+      CG_CUDA(h, cudaMalloc(&h->lmask, sizeof(uint32_t) * lmask.size()));
+      CG_CUDA(h, cudaMemcpy(h->lmask, lmask.data(), sizeof(uint32_t) * lmask.size(), cudaMemcpyHostToDevice));
+      CG_CUDA(h, cudaMalloc(&h->delta_dev, sizeof(int32_t) * kMaxDiag));
+      CG_CUDA(h, cudaMemcpy(h->delta_dev, h->delta, sizeof(int32_t) * kMaxDiag, cudaMemcpyHostToDevice));
+      CG_CUDA(h, cudaMalloc(&h->lptr, sizeof(int32_t)));
+      CG_CUDA(h, cudaMemset(h->lptr, 0, sizeof(int32_t)));
+      const size_t nv = (size_t)std::max<int64_t>(n, 1);
+      CG_CUDA(h, cudaMalloc(&h->dsq, sizeof(double) * nv));
+      CG_CUDA(h, cudaMalloc(&h->disq, sizeof(double) * nv));
+      CG_CUDA(h, cudaMalloc(&h->diag32, sizeof(float) * nv));
+      CG_CUDA(h, cudaMalloc(&h->disq32, sizeof(float) * nv));
+      diag_kernel<<<grid_for(n), 256>>>(n, h->diag, h->dsq, h->disq, h->diag32, h->disq32);
+      CG_CUDA(h, cudaGetLastError());
+      CG_CUDA(h, cudaDeviceSynchronize());
+      return CG_OK;
+    }
+  }
   std::vector<int32_t> soff((size_t)ns + 1, 0);
   std::vector<uint32_t> lmask((size_t)std::max<int64_t>(ns, 1), 0u);
   std::vector<int32_t> lrow, lptr(1, 0);
@@ -339,6 +446,18 @@ cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
   const bool write_col = !h->scol_written;
   CG_CUDA(h, cudaMalloc(sval, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
   CG_CUDA(h, cudaMalloc(lval, sizeof(T) * (size_t)std::max<int64_t>(h->nnz_long, 1)));
+  if (h->dia) {
+    CG_CUDA(h, cudaMemset(*sval, 0, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
+    if (scale)
+      fill_dia_kernel<T, true><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq,
+                                                        h->uniform_w, h->delta_dev, *sval);
+    else
+      fill_dia_kernel<T, false><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq,
+                                                         h->uniform_w, h->delta_dev, *sval);
+    CG_CUDA(h, cudaGetLastError());
+    CG_CUDA(h, cudaDeviceSynchronize());
+    return CG_OK;
+  }
   if (h->n > 0) {
     int32_t* col = write_col ? h->scol : nullptr;
     int32_t* lcol = write_col ? h->lcol : nullptr;
@@ -365,6 +484,29 @@ cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
 }
 
 template <typename T>
+Sell<T> make_sell(const cg_handle* h, const T* val, const T* lval, const T* diag, const T* disq) {
+  Sell<T> S{};
+  S.n = h->n;
+  S.nslices = h->nslices;
+  S.uw = h->uniform_w;
+  S.dia = h->dia;
+  for (int m = 0; m < kMaxDiag; ++m) S.delta[m] = h->delta[m];
+  S.soff = h->soff;
+  S.lmask = h->lmask;
+  S.col = h->scol;
+  S.val = val;
+  S.nlong = h->nlong;
+  S.lrow = h->lrow;
+  S.lptr = h->lptr;
+  S.lcol = h->lcol;
+  S.lval = lval;
+  S.dg = diag;
+  S.dn = diag;
+  S.disq = disq;
+  return S;
+}
+
+template <typename T>
 cg_status ensure_vectors(cg_handle* h, T** r, T** p, T** q, T** xh) {
   if (*r) return CG_OK;
   const size_t nv = (size_t)std::max<int64_t>(h->n, 1);
@@ -381,7 +523,7 @@ void destroy_graph(cudaGraphExec_t* e, cudaGraph_t* g) {
 }
 
 void free_all(cg_handle* h) {
-  void* dev[] = {h->rb,        h->diag,      h->ndiag,     h->dsq,       h->disq,
+  void* dev[] = {h->rb,        h->diag,      h->ndiag,     h->dsq,       h->disq,       h->delta_dev,
                  h->diag32,    h->disq32,    h->soff,      h->lmask,     h->scol,
                  h->lrow,      h->lptr,      h->lcol,      h->sval64[0], h->sval64[1],
                  h->sval32[0], h->sval32[1], h->lval64[0], h->lval64[1], h->lval32[0],
@@ -401,13 +543,18 @@ void free_all(cg_handle* h) {
 }
 
 // The graph-mode SpMV kernel for the loop matrix's slice layout.
-const void* spmv_kernel_for(int uw, bool jac) {
+template <bool JAC, bool DIA>
+const void* spmv_kernel_w(int uw) {
   switch (uw) {
-    case 4: return jac ? (const void*)g_spmv<double, true, 4> : (const void*)g_spmv<double, false, 4>;
-    case 6: return jac ? (const void*)g_spmv<double, true, 6> : (const void*)g_spmv<double, false, 6>;
-    case 8: return jac ? (const void*)g_spmv<double, true, 8> : (const void*)g_spmv<double, false, 8>;
-    default: return jac ? (const void*)g_spmv<double, true, 0> : (const void*)g_spmv<double, false, 0>;
+    case 4: return (const void*)g_spmv<double, JAC, 4, DIA>;
+    case 6: return (const void*)g_spmv<double, JAC, 6, DIA>;
+    case 8: return (const void*)g_spmv<double, JAC, 8, DIA>;
+    default: return (const void*)g_spmv<double, JAC, 0, false>;
   }
+}
+const void* spmv_kernel_for(int uw, bool dia, bool jac) {
+  if (jac) return dia ? spmv_kernel_w<true, true>(uw) : spmv_kernel_w<true, false>(uw);
+  return dia ? spmv_kernel_w<false, true>(uw) : spmv_kernel_w<false, false>(uw);
 }
 
 // Append a kernel node after `dep` (may be null) to graph g.
@@ -438,7 +585,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   h->graph = g;
   cudaGraphConditionalHandle ch = 0;
   if (unroll == 0) CG_CUDA(h, cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
-  const void* f_spmv = spmv_kernel_for(h->uniform_w, jac);
+  const void* f_spmv = spmv_kernel_for(h->uniform_w, h->dia != 0, jac);
   const unsigned G = (unsigned)h->grid_graph;
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count),
                                                      h->grid_part));
@@ -576,7 +723,7 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   const int64_t n = h->n, nnz = h->nnz;
   h->last.bytes_moved = (12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n) * (int64_t)gs.k;
   const int64_t ent = h->sell_entries + h->nnz_long;
-  h->last.kernel_bytes_per_iter = 12 * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n;
+  h->last.kernel_bytes_per_iter = (h->dia ? 8 : 12) * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n;
   if (iters_out) *iters_out = gs.k;
   if (relres_out) *relres_out = gs.relres_true;
   if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
@@ -780,12 +927,8 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   const int G = auto_grid(h);
   SolveParams P{};
   P.A = Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
-  P.S64 = Sell<double>{h->n,      h->nslices,     h->uniform_w, h->soff, h->lmask, h->scol, h->sval64[jac],
-                       h->nlong,  h->lrow,        h->lptr, h->lcol,  h->lval64[jac],
-                       h->diag,   h->diag,        h->disq};
-  P.S32 = Sell<float>{h->n,      h->nslices,     h->uniform_w, h->soff, h->lmask, h->scol, h->sval32[jac],
-                      h->nlong,  h->lrow,        h->lptr, h->lcol,  h->lval32[jac],
-                      h->diag32, h->diag32,      h->disq32};
+  P.S64 = make_sell<double>(h, h->sval64[jac], h->lval64[jac], h->diag, h->disq);
+  P.S32 = make_sell<float>(h, h->sval32[jac], h->lval32[jac], h->diag32, h->disq32);
   P.V64 = LoopVecs<double>{h->r, h->p, h->q, h->xh};
   P.V32 = LoopVecs<float>{h->r32, h->p32, h->q32, h->xh32};
   P.b = b;
@@ -837,8 +980,9 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   // bytes this kernel's loop must move per iteration: the SELL-32 slices
   // (padding included), the long-row CSR and the vector streams
   const int64_t ent = h->sell_entries + h->nnz_long;
-  h->last.kernel_bytes_per_iter = fp64 ? 12 * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n
-                                       : 8 * ent + 4 * (int64_t)h->nlong + (jac ? 44 : 40) * n;
+  const int64_t cb = h->dia ? 0 : 4;  // column bytes per entry
+  h->last.kernel_bytes_per_iter = fp64 ? (8 + cb) * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n
+                                       : (4 + cb) * ent + 4 * (int64_t)h->nlong + (jac ? 44 : 40) * n;
   for (int j = 0; j < 6; ++j) h->last.phase_ms[j] = ds.tphase[j] * 1e-6;
   if (iters_out) *iters_out = ds.iters;
   if (relres_out) *relres_out = ds.relres_true;

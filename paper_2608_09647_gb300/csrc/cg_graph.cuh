@@ -103,7 +103,7 @@ __global__ void g_start64(GArgs a) {
 
 // a1: q = A^ p, partial p.q.  W > 0: the matrix has uniform slices of width W
 // (chosen on the host, so each width gets its own register budget).
-template <typename T, bool JAC, int W>
+template <typename T, bool JAC, int W, bool DIA>
 __global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
   const SolveParams& P = a.P;
   if (a.gs->status != kRunning) return;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
   const Sell<T>& S = sell_of<T>(P);
   const LoopVecs<T>& V = vecs_of<T>(P);
   double v[1];
-  if constexpr (W > 0) v[0] = spmv_phase_w<T, JAC, W>(S, V.p, V.q, g);
+  if constexpr (W > 0) v[0] = spmv_phase_w<T, JAC, W, DIA>(S, V.p, V.q, g);
   else v[0] = spmv_phase<T, JAC>(S, V.p, V.q, g);
   publish<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g);
 }

@@ -40,6 +40,7 @@ constexpr int kCap = 2048;                 // nonzeros of one caller-CSR row blo
 constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
 constexpr int kLongRow = 128;              // off-diagonal entries above which a row leaves SELL
 constexpr int kUnroll = 8;                 // slice columns whose loads are issued together
+constexpr int kMaxDiag = 32;               // most distinct offsets of the diagonal (DIA) layout
 
 // --------------------------------------------------------------------------
 // Plain CSR (the caller's matrix): cg_spmv and the fp64 true residual
@@ -120,7 +121,11 @@ __global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<T> A, const T* x, T* y
 // --------------------------------------------------------------------------
 
 // Off-diagonal part of the loop matrix (A^ with Jacobi, A without) in
-// SELL-32 form.  Slice s holds rows [32 s, 32 s + 32); its entries occupy
+// SELL-32 form, or in its sliced-diagonal special case (dia != 0): when every
+// off-diagonal entry lies on one of ndiag <= kMaxDiag diagonals j - i = delta[m]
+// and few slots are empty, slice column m holds diagonal m, the column index
+// of row i is i + delta[m] (clamped into range for the zero-valued slots) and
+// no column array is stored.  Otherwise:  Slice s holds rows [32 s, 32 s + 32); its entries occupy
 // [soff[s], soff[s+1]) in units of 32 (column m of the slice is the 32
 // consecutive elements at (soff[s] + m) * 32; lane l = row 32 s + l).  Short
 // rows are padded to the slice width with (column = own row, value = 0).
@@ -131,6 +136,8 @@ struct Sell {
   int64_t n;
   int32_t nslices;
   int32_t uw;  // >= 0: every slice has width uw and no row is long (soff, lmask unread)
+  int32_t dia;                // 1: sliced-diagonal layout, width uw = number of diagonals
+  int32_t delta[kMaxDiag];    // diagonal offsets (dia only)
   const int32_t* __restrict__ soff;
   const uint32_t* __restrict__ lmask;
   const int32_t* __restrict__ col;
@@ -244,8 +251,10 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 
 // a1 over the grid for uniform slices of compile-time width W (no long rows):
 // every load of a slice is issued at once and the register footprint is
-// exactly what W needs, which keeps occupancy high.
-template <typename T, bool JAC, int W>
+// exactly what W needs, which keeps occupancy high.  DIA: the column of slot m
+// is computed from delta[m] instead of loaded.  The diagonal term starts the
+// fused multiply-add chain, so each row costs W + 1 fp64 FMAs with the p.q term.
+template <typename T, bool JAC, int W, bool DIA>
 __device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __restrict__ p,
                                                T* __restrict__ q, const Grid& g) {
   const int lane = threadIdx.x & 31;
@@ -261,24 +270,73 @@ __device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __rest
       pi = p[i];
       if (!JAC) dgi = __ldg(S.dg + i);
     }
-    const int32_t* cp = S.col + (int64_t)s * (W * 32) + lane;
     const T* vp = S.val + (int64_t)s * (W * 32) + lane;
     int c[W];
     T v[W], pc[W];
 #pragma unroll
     for (int m = 0; m < W; ++m) {
-      c[m] = ld_stream(cp + m * 32);
       v[m] = ld_stream(vp + m * 32);
+      if (DIA) {
+        const int64_t cc = i + S.delta[m];
+        c[m] = (int)(cc < 0 ? 0 : (cc >= n ? n - 1 : cc));
+      } else {
+        c[m] = ld_stream(S.col + (int64_t)s * (W * 32) + lane + m * 32);
+      }
     }
 #pragma unroll
     for (int m = 0; m < W; ++m) pc[m] = p[c[m]];
-    T acc = T(0);
+    T acc = JAC ? pi : dgi * pi;
 #pragma unroll
     for (int m = 0; m < W; ++m) acc = fma(v[m], pc[m], acc);
     if (live) {
-      const T qi = (JAC ? pi : dgi * pi) + acc;
-      q[i] = qi;
-      dot += (double)pi * (double)qi;
+      q[i] = acc;
+      dot = fma((double)pi, (double)acc, dot);
+    }
+  }
+  return dot;
+}
+
+// Sliced-diagonal layout of any width up to kMaxDiag (loads in groups of kUnroll).
+template <typename T, bool JAC>
+__device__ __forceinline__ double spmv_phase_dia(const Sell<T>& S, const T* __restrict__ p,
+                                                 T* __restrict__ q, const Grid& g) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
+  const int Wt = (int)g.G * kWarps;
+  const int64_t n = S.n;
+  const int w = S.uw;
+  double dot = 0.0;
+  for (int s = gw; s < S.nslices; s += Wt) {
+    const int64_t i = (int64_t)s * 32 + lane;
+    const bool live = i < n;
+    T pi = T(0), dgi = T(1);
+    if (live) {
+      pi = p[i];
+      if (!JAC) dgi = __ldg(S.dg + i);
+    }
+    const T* vp = S.val + (int64_t)s * w * 32 + lane;
+    T acc = JAC ? pi : dgi * pi;
+    for (int m0 = 0; m0 < w; m0 += kUnroll) {
+      int c[kUnroll];
+      T v[kUnroll], pc[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (m0 + u < w) {
+          v[u] = ld_stream(vp + (m0 + u) * 32);
+          const int64_t cc = i + S.delta[m0 + u];
+          c[u] = (int)(cc < 0 ? 0 : (cc >= n ? n - 1 : cc));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (m0 + u < w) pc[u] = p[c[u]];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (m0 + u < w) acc = fma(v[u], pc[u], acc);
+    }
+    if (live) {
+      q[i] = acc;
+      dot = fma((double)pi, (double)acc, dot);
     }
   }
   return dot;
@@ -290,9 +348,15 @@ __device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __rest
 template <typename T, bool JAC>
 __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restrict__ p,
                                              T* __restrict__ q, const Grid& g) {
-  if (S.uw == 4) return spmv_phase_w<T, JAC, 4>(S, p, q, g);
-  if (S.uw == 6) return spmv_phase_w<T, JAC, 6>(S, p, q, g);
-  if (S.uw == 8) return spmv_phase_w<T, JAC, 8>(S, p, q, g);
+  if (S.dia) {
+    if (S.uw == 4) return spmv_phase_w<T, JAC, 4, true>(S, p, q, g);
+    if (S.uw == 6) return spmv_phase_w<T, JAC, 6, true>(S, p, q, g);
+    if (S.uw == 8) return spmv_phase_w<T, JAC, 8, true>(S, p, q, g);
+    return spmv_phase_dia<T, JAC>(S, p, q, g);
+  }
+  if (S.uw == 4) return spmv_phase_w<T, JAC, 4, false>(S, p, q, g);
+  if (S.uw == 6) return spmv_phase_w<T, JAC, 6, false>(S, p, q, g);
+  if (S.uw == 8) return spmv_phase_w<T, JAC, 8, false>(S, p, q, g);
   const int lane = threadIdx.x & 31;
   const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
   const int W = (int)g.G * kWarps;
@@ -318,7 +382,7 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
     }
     const int32_t* cp = S.col + (int64_t)o0 * 32 + lane;
     const T* vp = S.val + (int64_t)o0 * 32 + lane;
-    T acc = T(0);
+    T acc = JAC ? pi : dgi * pi;
     for (int m0 = 0; m0 < w; m0 += kUnroll) {
       int c[kUnroll];
       T v[kUnroll], pc[kUnroll];
@@ -337,9 +401,8 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
         if (m0 + u < w) acc = fma(v[u], pc[u], acc);
     }
     if (i < n && !((lm >> lane) & 1u)) {
-      const T qi = (JAC ? pi : dgi * pi) + acc;
-      q[i] = qi;
-      dot += (double)pi * (double)qi;
+      q[i] = acc;
+      dot = fma((double)pi, (double)acc, dot);
     }
   }
   // long rows: one warp per row, lanes stride, fixed xor tree
@@ -391,9 +454,8 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
       for (int j = 0; j < VN; ++j) {
         const T ri = fma(-alpha, lane_c<T>(qv[h], j), lane<T>(rv[h], j));
         lane<T>(rv[h], j) = ri;
-        const double r2 = (double)ri * (double)ri;
-        rho += r2;
-        if (JAC) rr += (double)lane<T>(dv[h], j) * r2;
+        rho = fma((double)ri, (double)ri, rho);
+        if (JAC) rr = fma((double)lane<T>(dv[h], j) * (double)ri, (double)ri, rr);
       }
     }
     r[i0] = rv[0];
@@ -402,9 +464,8 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
   for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
     const T ri = fma(-alpha, V.q[i], V.r[i]);
     V.r[i] = ri;
-    const double r2 = (double)ri * (double)ri;
-    rho += r2;
-    if (JAC) rr += (double)__ldg(S.dn + i) * r2;
+    rho = fma((double)ri, (double)ri, rho);
+    if (JAC) rr = fma((double)__ldg(S.dn + i) * (double)ri, (double)ri, rr);
   }
   if (!JAC) rr = rho;
 }

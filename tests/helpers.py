@@ -55,3 +55,26 @@ def spd_from_pattern(n, seed, long_rows=(), max_len=8):
     M.sort_indices()
     return gen.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
                    M.data.astype(np.float64), f"spd_pattern_n{n}_s{seed}")
+
+
+def random_graph_spd(n, seed, matchings=2):
+    """SPD graph Laplacian + I of the union of `matchings` random perfect matchings:
+    every row has at most 2*matchings off-diagonal entries at random columns, so the
+    loop matrix takes the uniform-width slice layout without the diagonal layout."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for _ in range(matchings):
+        perm = rng.permutation(n)
+        a, b = perm[0::2], perm[1::2]
+        rows += list(a) + list(b)
+        cols += list(b) + list(a)
+    W = sp.coo_matrix((rng.uniform(0.5, 1.5, len(rows)), (rows, cols)), shape=(n, n)).tocsr()
+    W = (W + W.T) * 0.5
+    W.setdiag(0)
+    W.eliminate_zeros()
+    d = np.asarray(W.sum(axis=1)).ravel() + 1.0
+    M = (sp.diags(d) - W).tocsr()
+    M.sort_indices()
+    return gen.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                   M.data.astype(np.float64), f"graph_spd_n{n}_s{seed}")

@@ -16,7 +16,7 @@ import pytest
 
 import cgproblems as gen
 import oracle
-from helpers import adversarial, spd_from_pattern, to_device
+from helpers import adversarial, random_graph_spd, spd_from_pattern, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -362,6 +362,9 @@ GRAPH_CASES = [
     ("diff27_12_jac", lambda: gen.diff3d27(12, 1.0, 4), 1, 1e-10, 5000),
     ("uneven_jac", lambda: spd_from_pattern(4000, 3, long_rows=[(5, 2500), (100, 300)]), 1, 1e-9, 3000),
     ("q1_none", lambda: gen.q1aniso(40, 1.5, 0.7, 0.03, 3), 0, 1e-8, 5000),
+    ("graph_uniform_jac", lambda: random_graph_spd(6000, 2, 4), 1, 1e-10, 3000),
+    ("graph_uniform_none", lambda: random_graph_spd(5000, 5, 3), 0, 1e-10, 3000),
+    ("diff27_40_jac", lambda: gen.diff3d27(40, 1.0, 2), 1, 1e-8, 5000),
 ]
 
 
