@@ -97,6 +97,20 @@ __global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
   }
 }
 
+// Range of a positive diagonal: min / max of the IEEE bit patterns, which
+// order like the values for positive doubles.
+__global__ void diag_range_kernel(int64_t n, const double* __restrict__ d, unsigned long long* mm) {
+  unsigned long long lo = ~0ull, hi = 0ull;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d[i]);
+    lo = b < lo ? b : lo;
+    hi = b > hi ? b : hi;
+  }
+  atomicMin(&mm[0], lo);
+  atomicMax(&mm[1], hi);
+}
+
 // Distinct off-diagonal offsets j - i into a 64-slot open-addressing table
 // (kOffEmpty marks a free slot); *overflow is set when they do not fit.
 constexpr int kOffSlots = 64;
@@ -194,6 +208,7 @@ struct cg_handle {
   int32_t nslices = 0;
   int32_t uniform_w = -1;           // every slice padded to this width (-1: variable)
   int32_t dia = 0;                  // sliced-diagonal layout (no column array)
+  double dmin = 1.0, dmax = 1.0;    // range of A_ii (Jacobi)
   int32_t delta[kMaxDiag] = {};     // its diagonal offsets, ascending
   int32_t* delta_dev = nullptr;
   int32_t* soff = nullptr;
@@ -503,6 +518,8 @@ Sell<T> make_sell(const cg_handle* h, const T* val, const T* lval, const T* diag
   S.dg = diag;
   S.dn = diag;
   S.disq = disq;
+  S.dmin = h->dmin;
+  S.dmax = h->dmax;
   return S;
 }
 
@@ -604,6 +621,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
                          : (const void*)g_upd_xp<double, false, false, false>);
   const void* f_flush = jac ? (const void*)g_flush<double, true, false>
                             : (const void*)g_flush<double, false, false>;
+  const bool with_rr = jac && h->dmin != h->dmax;  // r.r fallback kernel needed
   cudaGraphNode_t n, prev;
   // prologue
   CG_CUDA(h, add_kernel(g, &n, nullptr, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
@@ -627,6 +645,10 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
     cudaGraphNode_t b1, b2, b3;
     CG_CUDA(h, add_kernel(body, &b1, nullptr, f_spmv, Gq, kBlock, a_ga));
     CG_CUDA(h, add_kernel(body, &b2, b1, f_r, G, kBlock, a_ga));
+    if (with_rr) {
+      CG_CUDA(h, add_kernel(body, &b3, b2, (const void*)g_rr<double>, G, kBlock, a_ga));
+      b2 = b3;
+    }
     CG_CUDA(h, add_kernel(body, &b3, b2, f_xp, G, kBlock, a_ga));
     prev = n;
   } else {
@@ -637,6 +659,10 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
       pi = ci;
       CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, f_r, G, kBlock, a_ga));
       pi = ci;
+      if (with_rr) {
+        CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, (const void*)g_rr<double>, G, kBlock, a_ga));
+        pi = ci;
+      }
       CG_CUDA(h, add_kernel(h->graph_it, &ci, pi, f_xp, G, kBlock, a_ga));
       pi = ci;
     }
@@ -690,14 +716,14 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
         CG_CUDA(h, cudaStreamSynchronize(h->stream));
         if (h->host_gs->status != kRunning) break;
         CG_CUDA(h, cudaGraphLaunch(h->gexec_it, h->stream));
-        launches += 3 * unroll;
+        launches += (jac && h->dmin != h->dmax ? 4 : 3) * unroll;
       }
       CG_CUDA(h, cudaGraphLaunch(h->gexec_ep, h->stream));
     }
     CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
     CG_CUDA(h, cudaStreamSynchronize(h->stream));
     status = h->host_gs->status;
-    if (unroll == 0) launches += 3 * (int64_t)(h->host_gs->k - k_prev);
+    if (unroll == 0) launches += (jac && h->dmin != h->dmax ? 4 : 3) * (int64_t)(h->host_gs->k - k_prev);
     k_prev = h->host_gs->k;
     if (status != kNeedRestart) break;
     if (h->host_gs->k >= P.maxit || restarts >= P.max_restarts) {
@@ -723,7 +749,8 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   const int64_t n = h->n, nnz = h->nnz;
   h->last.bytes_moved = (12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n) * (int64_t)gs.k;
   const int64_t ent = h->sell_entries + h->nnz_long;
-  h->last.kernel_bytes_per_iter = (h->dia ? 8 : 12) * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n;
+  h->last.kernel_bytes_per_iter = (h->dia ? 8 : 12) * ent + 4 * (int64_t)h->nlong + 80 * n +
+                                  (jac && h->dmin != h->dmax ? 8 : 0) * n;
   if (iters_out) *iters_out = gs.k;
   if (relres_out) *relres_out = gs.relres_true;
   if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
@@ -815,6 +842,21 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   if (hc[0] != 0)
     return bail(fail(h, CG_ERR_INVALID, "cg_create: " + std::to_string(hc[0]) + " column indices outside [0, n)"));
   h->jacobi_ok = (hc[1] == 0);
+  if (h->jacobi_ok && n > 0) {
+    unsigned long long* mm = nullptr;
+    unsigned long long hmm[2] = {~0ull, 0ull};
+    e = cudaMalloc(&mm, sizeof(hmm));
+    if (e == cudaSuccess) e = cudaMemcpy(mm, hmm, sizeof(hmm), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      diag_range_kernel<<<std::min<unsigned>(grid_for(n), 1024u), 256>>>(n, h->diag, mm);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(hmm, mm, sizeof(hmm), cudaMemcpyDeviceToHost);
+    if (mm) cudaFree(mm);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cg_create: diagonal range"));
+    std::memcpy(&h->dmin, &hmm[0], sizeof(double));
+    std::memcpy(&h->dmax, &hmm[1], sizeof(double));
+  }
 
   // persistent-kernel residency (the smallest over the kernels we may launch)
   const int g1 = max_coresident(pcg64_kernel<true>, h->sm_count);
@@ -981,8 +1023,9 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   // (padding included), the long-row CSR and the vector streams
   const int64_t ent = h->sell_entries + h->nnz_long;
   const int64_t cb = h->dia ? 0 : 4;  // column bytes per entry
-  h->last.kernel_bytes_per_iter = fp64 ? (8 + cb) * ent + 4 * (int64_t)h->nlong + (jac ? 88 : 80) * n
-                                       : (4 + cb) * ent + 4 * (int64_t)h->nlong + (jac ? 44 : 40) * n;
+  const int64_t vb = 80 + (jac && h->dmin != h->dmax ? 8 : 0);  // vector bytes per row (fp64)
+  h->last.kernel_bytes_per_iter = fp64 ? (8 + cb) * ent + 4 * (int64_t)h->nlong + vb * n
+                                       : (4 + cb) * ent + 4 * (int64_t)h->nlong + vb / 2 * n;
   for (int j = 0; j < 6; ++j) h->last.phase_ms[j] = ds.tphase[j] * 1e-6;
   if (iters_out) *iters_out = ds.iters;
   if (relres_out) *relres_out = ds.relres_true;

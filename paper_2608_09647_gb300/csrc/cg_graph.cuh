@@ -134,9 +134,27 @@ __global__ void __launch_bounds__(kBlock) g_upd_r(GArgs a) {
     return;
   }
   const T alpha = (T)(rho / pq[0]);
+  const bool want_rr = JAC && rr_wanted(S, rho, a.gs->stop_abs * a.gs->stop_abs);
   double v[2] = {0.0, 0.0};
-  update_r_phase<T, JAC>(S, V, alpha, v[0], v[1], g);
+  update_r_phase<T, JAC>(S, V, alpha, want_rr, v[0], v[1], g);
   publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
+}
+
+// Jacobi with a varying diagonal only: when r.r was skipped and the new rho
+// falls into the band where it does not decide the test, compute r.r.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) g_rr(GArgs a) {
+  const SolveParams& P = a.P;
+  if (a.gs->status != kRunning) return;
+  Grid g = graph_grid();
+  const Sell<T>& S = sell_of<T>(P);
+  const double stop2 = a.gs->stop_abs * a.gs->stop_abs;
+  if (rr_wanted(S, a.gs->rho, stop2)) return;
+  double s2[2], rr;
+  grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, a.G_upd, s2);
+  if (rr_bound_test(S, s2[0], stop2, &rr) >= 0) return;
+  double v[1] = {rr_phase<T>(S, vecs_of<T>(P), g)};
+  publish<1>(v, P.part + kSlotRr * (size_t)P.pstride, g);
 }
 
 // a3 + a4: beta, convergence; x^ += alpha p and p = r^ + beta p, or on the
@@ -163,6 +181,12 @@ __global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
     const T beta = (T)(s2[0] / rho);
     rho1 = s2[0];
     rr1 = s2[1];
+    const double stop2 = gs->stop_abs * gs->stop_abs;
+    if (JAC && !rr_wanted(S, rho, stop2) && rr_bound_test(S, rho1, stop2, &rr1) < 0) {
+      double v3[1];  // written by g_rr
+      grid_sum<1>(P.part + kSlotRr * (size_t)P.pstride, a.G_upd, v3);
+      rr1 = v3[0];
+    }
     conv = sqrt(rr1) <= gs->stop_abs;
     done = conv || k1 >= P.maxit;
     double* out = P.x;

@@ -150,7 +150,31 @@ struct Sell {
   const T* __restrict__ dg;    // diagonal of the loop matrix (unused with Jacobi: unit diagonal)
   const T* __restrict__ dn;    // A_ii weights of the true residual norm (Jacobi)
   const T* __restrict__ disq;  // 1/sqrt(A_ii) mapping x^ back to x (Jacobi)
+  double dmin, dmax;           // range of A_ii (Jacobi): dmin r^.r^ <= r.r <= dmax r^.r^
 };
+
+// With Jacobi the stopping test needs r.r = r^.D r^, two more fp64 operations
+// and one more vector per row.  Since dmin rho <= r.r <= dmax rho, the test is
+// decided by rho alone except in the band stop^2 / dmax < rho <= stop^2 / dmin
+// (empty when the diagonal is constant).  The r update computes r.r only once
+// dmin rho comes within kRrMargin of stop^2; if rho jumps into the band before
+// that, one extra pass computes r.r, so the test stays exact.
+constexpr double kRrMargin = 64.0;
+
+template <typename T>
+__device__ __forceinline__ bool rr_wanted(const Sell<T>& S, double rho, double stop2) {
+  return S.dmin != S.dmax && S.dmin * rho <= kRrMargin * stop2;
+}
+
+// Decide sqrt(r.r) <= stop from rho: 1 converged, 0 not converged, -1 unknown.
+// *rr gets dmax rho (exact for a constant diagonal).
+template <typename T>
+__device__ __forceinline__ int rr_bound_test(const Sell<T>& S, double rho, double stop2, double* rr) {
+  *rr = S.dmax * rho;
+  if (S.dmax * rho <= stop2) return 1;
+  if (S.dmin * rho > stop2) return 0;
+  return -1;
+}
 
 // Work vectors of the loop on type T.
 template <typename T>
@@ -183,11 +207,11 @@ struct SolveParams {
   int timers;             // accumulate CTA 0 phase times into st->tphase
 };
 
-// Partial-sum slots (each G doubles): 0 = p.q, 2/3 = the update phase,
-// 4..7 = the residual phase.  Disjoint slots mean a CTA never overwrites a
+// Partial-sum slots (each G doubles): 0 = p.q, 1 = r.r fallback, 2/3 = the
+// update phase, 4..7 = the residual phase.  Disjoint slots mean a CTA never overwrites a
 // partial that a slower CTA still has to read.
 constexpr int kParts = 8;
-constexpr int kSlotPQ = 0, kSlotUpd = 2, kSlotRes = 4;
+constexpr int kSlotPQ = 0, kSlotRr = 1, kSlotUpd = 2, kSlotRes = 4;
 
 // Grid coordinates and the barrier sequence of one persistent launch.
 struct Grid {
@@ -427,7 +451,8 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
 // Jacobi) or rho.  Two 16-byte vectors per thread per trip, loads first.
 template <typename T, bool JAC>
 __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<T>& V, T alpha,
-                                               double& rho, double& rr, const Grid& g) {
+                                               bool want_rr, double& rho, double& rr,
+                                               const Grid& g) {
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::N;
   const int64_t n = S.n;
@@ -435,17 +460,18 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
   VT* r = reinterpret_cast<VT*>(V.r);
   const VT* q = reinterpret_cast<const VT*>(V.q);
   const VT* dn = reinterpret_cast<const VT*>(S.dn);
+  const bool with_rr = JAC && want_rr;
   for (int64_t i0 = g.gtid; i0 < nv; i0 += 2 * g.gstride) {
     const int64_t i1 = i0 + g.gstride;
     const bool two = i1 < nv;
     VT rv[2], qv[2], dv[2];
     rv[0] = r[i0];
     qv[0] = q[i0];
-    if (JAC) dv[0] = __ldg(dn + i0);
+    if (with_rr) dv[0] = __ldg(dn + i0);
     if (two) {
       rv[1] = r[i1];
       qv[1] = q[i1];
-      if (JAC) dv[1] = __ldg(dn + i1);
+      if (with_rr) dv[1] = __ldg(dn + i1);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -455,7 +481,7 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
         const T ri = fma(-alpha, lane_c<T>(qv[h], j), lane<T>(rv[h], j));
         lane<T>(rv[h], j) = ri;
         rho = fma((double)ri, (double)ri, rho);
-        if (JAC) rr = fma((double)lane<T>(dv[h], j) * (double)ri, (double)ri, rr);
+        if (with_rr) rr = fma((double)lane<T>(dv[h], j) * (double)ri, (double)ri, rr);
       }
     }
     r[i0] = rv[0];
@@ -465,9 +491,20 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
     const T ri = fma(-alpha, V.q[i], V.r[i]);
     V.r[i] = ri;
     rho = fma((double)ri, (double)ri, rho);
-    if (JAC) rr = fma((double)__ldg(S.dn + i) * (double)ri, (double)ri, rr);
+    if (with_rr) rr = fma((double)__ldg(S.dn + i) * (double)ri, (double)ri, rr);
   }
   if (!JAC) rr = rho;
+}
+
+// r.r = r^.D r^ from the current r^ (the exact-test fallback).
+template <typename T>
+__device__ __forceinline__ double rr_phase(const Sell<T>& S, const LoopVecs<T>& V, const Grid& g) {
+  double rr = 0.0;
+  for (int64_t i = g.gtid; i < S.n; i += g.gstride) {
+    const double ri = (double)V.r[i];
+    rr = fma((double)__ldg(S.dn + i) * ri, ri, rr);
+  }
+  return rr;
 }
 
 // a3 over the grid: x^ += alpha p; p = r^ + beta p.  On the last iteration
@@ -547,9 +584,10 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     if (!isfinite(pq[0]) || !isfinite(rho)) { status = kNumeric; break; }
     if (pq[0] <= 0.0) { status = kBreakdown; break; }
     const T alpha = (T)(rho / pq[0]);
-    // a2: r^ -= alpha q; r.z, r.r
+    // a2: r^ -= alpha q; r.z, r.r (r.r only when the test needs it)
+    const bool want_rr = JAC && rr_wanted(S, rho, stop_abs * stop_abs);
     double v2[2] = {0.0, 0.0};
-    update_r_phase<T, JAC>(S, V, alpha, v2[0], v2[1], g);
+    update_r_phase<T, JAC>(S, V, alpha, want_rr, v2[0], v2[1], g);
     publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
     clk.lap(g.st, 2);
     if (!g.sync()) { status = kTimeout; break; }
@@ -559,6 +597,13 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     const T beta = (T)(s2[0] / rho);
     rho = s2[0];
     rr = s2[1];
+    if (JAC && !want_rr && rr_bound_test(S, rho, stop_abs * stop_abs, &rr) < 0) {
+      double v3[1] = {rr_phase<T>(S, V, g)};  // rho fell into the band early: exact r.r
+      publish<1>(v3, part + kSlotRr * (size_t)pstride, g);
+      if (!g.sync()) { status = kTimeout; break; }
+      grid_sum<1>(part + kSlotRr * (size_t)pstride, g.G, v3);
+      rr = v3[0];
+    }
     ++k;
     const bool conv = sqrt(rr) <= stop_abs;
     done = conv || k >= maxit;
