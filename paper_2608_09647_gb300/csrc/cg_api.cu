@@ -255,6 +255,8 @@ struct cg_handle {
   const void* gkey_x = nullptr;
   double gkey_tol = -1.0;
   int gkey_maxit = -1, gkey_jac = -1;
+  double gkey_tol_in = -1.0;
+  int gkey_outer = -1;
   cg_solve_info last{};
   std::string err;
 };
@@ -560,18 +562,20 @@ void free_all(cg_handle* h) {
 }
 
 // The graph-mode SpMV kernel for the loop matrix's slice layout.
-template <bool JAC, bool DIA>
+template <typename T, bool JAC, bool DIA>
 const void* spmv_kernel_w(int uw) {
   switch (uw) {
-    case 4: return (const void*)g_spmv<double, JAC, 4, DIA>;
-    case 6: return (const void*)g_spmv<double, JAC, 6, DIA>;
-    case 8: return (const void*)g_spmv<double, JAC, 8, DIA>;
-    default: return (const void*)g_spmv<double, JAC, 0, false>;
+    case 4: return (const void*)g_spmv<T, JAC, 4, DIA>;
+    case 6: return (const void*)g_spmv<T, JAC, 6, DIA>;
+    case 8: return (const void*)g_spmv<T, JAC, 8, DIA>;
+    case 26: return DIA ? (const void*)g_spmv<T, JAC, 26, true> : (const void*)g_spmv<T, JAC, 0, false>;
+    default: return (const void*)g_spmv<T, JAC, 0, false>;
   }
 }
+template <typename T>
 const void* spmv_kernel_for(int uw, bool dia, bool jac) {
-  if (jac) return dia ? spmv_kernel_w<true, true>(uw) : spmv_kernel_w<true, false>(uw);
-  return dia ? spmv_kernel_w<false, true>(uw) : spmv_kernel_w<false, false>(uw);
+  if (jac) return dia ? spmv_kernel_w<T, true, true>(uw) : spmv_kernel_w<T, true, false>(uw);
+  return dia ? spmv_kernel_w<T, false, true>(uw) : spmv_kernel_w<T, false, false>(uw);
 }
 
 // Append a kernel node after `dep` (may be null) to graph g.
@@ -602,11 +606,11 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   h->graph = g;
   cudaGraphConditionalHandle ch = 0;
   if (unroll == 0) CG_CUDA(h, cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
-  const void* f_spmv = spmv_kernel_for(h->uniform_w, h->dia != 0, jac);
+  const void* f_spmv = spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac);
   const unsigned G = (unsigned)h->grid_graph;
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count),
                                                      h->grid_part));
-  GArgs ga{P, h->gs, ch, Gq, G};
+  GArgs ga{P, h->gs, ch, 0, Gq, G};
   Csr<double> A = P.A;
   const double* x = P.x;
   double* q = P.V64.q;
@@ -757,6 +761,116 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   return (cg_status)status;
 }
 
+// Build the graph form of an fp32-inner / fp64-outer refinement solve.
+cg_status build_graph_ir(cg_handle* h, const SolveParams& P, bool jac) {
+  destroy_graph(&h->gexec, &h->graph);
+  destroy_graph(&h->gexec_it, &h->graph_it);
+  destroy_graph(&h->gexec_ep, &h->graph_ep);
+  cudaGraph_t g;
+  CG_CUDA(h, cudaGraphCreate(&g, 0));
+  h->graph = g;
+  cudaGraphConditionalHandle outer_h, inner_h;
+  CG_CUDA(h, cudaGraphConditionalHandleCreate(&outer_h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams op{};
+  op.type = cudaGraphNodeTypeConditional;
+  op.conditional.handle = outer_h;
+  op.conditional.type = cudaGraphCondTypeWhile;
+  op.conditional.size = 1;
+  cudaGraphNode_t on;
+  CG_CUDA(h, cudaGraphAddNode(&on, g, nullptr, nullptr, 0, &op));
+  cudaGraph_t ob = op.conditional.phGraph_out[0];
+  CG_CUDA(h, cudaGraphConditionalHandleCreate(&inner_h, ob, 0, cudaGraphCondAssignDefault));
+  const void* f_spmv = spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac);
+  const unsigned G = (unsigned)h->grid_graph;
+  const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count), h->grid_part));
+  GArgs ga{P, h->gs, inner_h, outer_h, Gq, G};
+  Csr<double> A = P.A;
+  const double* x = P.x;
+  double* q = P.V64.q;
+  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  void* a_spmv[] = {&A, &x, &q};
+  void* a_ga[] = {&ga};
+  const bool with_rr = jac && h->dmin != h->dmax;
+  cudaGraphNode_t n, prev;
+  CG_CUDA(h, add_kernel(ob, &n, nullptr, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
+  prev = n;
+  CG_CUDA(h, add_kernel(ob, &n, prev, jac ? (const void*)g_res_ir<true> : (const void*)g_res_ir<false>,
+                        G, kBlock, a_ga));
+  prev = n;
+  CG_CUDA(h, add_kernel(ob, &n, prev, (const void*)g_start_ir<true>, 1, 32, a_ga));
+  prev = n;
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = inner_h;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  CG_CUDA(h, cudaGraphAddNode(&n, ob, &prev, nullptr, 1, &ip));
+  cudaGraph_t ib = ip.conditional.phGraph_out[0];
+  cudaGraphNode_t b1, b2, b3;
+  CG_CUDA(h, add_kernel(ib, &b1, nullptr, f_spmv, Gq, kBlock, a_ga));
+  CG_CUDA(h, add_kernel(ib, &b2, b1, jac ? (const void*)g_upd_r<float, true> : (const void*)g_upd_r<float, false>,
+                        G, kBlock, a_ga));
+  if (with_rr) {
+    CG_CUDA(h, add_kernel(ib, &b3, b2, (const void*)g_rr<float>, G, kBlock, a_ga));
+    b2 = b3;
+  }
+  CG_CUDA(h, add_kernel(ib, &b3, b2,
+                        jac ? (const void*)g_upd_xp<float, true, true, true>
+                            : (const void*)g_upd_xp<float, false, true, true>,
+                        G, kBlock, a_ga));
+  CG_CUDA(h, add_kernel(g, &n, on, (const void*)g_flush_ir, G, kBlock, a_ga));
+  CG_CUDA(h, cudaGraphInstantiate(&h->gexec, g, 0));
+  h->gkey_unroll = -2;  // marks the refinement graph
+  h->gkey_b = P.b;
+  h->gkey_x = P.x;
+  h->gkey_tol = P.tol;
+  h->gkey_maxit = P.maxit;
+  h->gkey_jac = jac;
+  h->gkey_tol_in = P.tol_in;
+  h->gkey_outer = P.max_restarts;
+  return CG_OK;
+}
+
+cg_status solve_graph_ir(cg_handle* h, const SolveParams& P, bool jac, int32_t* iters_out,
+                         double* relres_out) {
+  if (!h->gexec || h->gkey_unroll != -2 || h->gkey_b != P.b || h->gkey_x != P.x ||
+      h->gkey_tol != P.tol || h->gkey_maxit != P.maxit || h->gkey_jac != (int)jac ||
+      h->gkey_tol_in != P.tol_in || h->gkey_outer != P.max_restarts) {
+    cg_status s = build_graph_ir(h, P, jac);
+    if (s != CG_OK) return s;
+  }
+  CG_CUDA(h, cudaMemsetAsync(h->gs, 0, sizeof(GState), h->stream));
+  CG_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  CG_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+  CG_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  CG_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
+  CG_CUDA(h, cudaStreamSynchronize(h->stream));
+  float ms = 0.0f;
+  CG_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  const GState& gs = *h->host_gs;
+  const int status = gs.status;
+  const int64_t n = h->n, nnz = h->nnz;
+  h->last.status = status;
+  h->last.iters = gs.k;
+  h->last.restarts = gs.outer;
+  h->last.grid_ctas = h->grid_graph;
+  h->last.relres_true = gs.relres_true;
+  h->last.relres_rec = gs.relres_true;
+  h->last.kernel_ms = ms;
+  h->last.loop_form = 2;
+  const bool with_rr = jac && h->dmin != h->dmax;
+  h->last.kernel_launches = (int32_t)std::min<int64_t>(
+      3 * (int64_t)(gs.outer + 1) + (with_rr ? 4 : 3) * (int64_t)gs.k + 1, INT32_MAX);
+  h->last.bytes_moved = (8 * nnz + 4 * (n + 1) + (jac ? 52 : 44) * n) * (int64_t)gs.k;
+  const int64_t ent = h->sell_entries + h->nnz_long;
+  const int64_t cb = h->dia ? 0 : 4;
+  h->last.kernel_bytes_per_iter = (4 + cb) * ent + 4 * (int64_t)h->nlong + (with_rr ? 44 : 40) * n;
+  if (iters_out) *iters_out = gs.k;
+  if (relres_out) *relres_out = gs.relres_true;
+  if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
+  return (cg_status)status;
+}
+
 }  // namespace
 
 extern "C" {
@@ -864,8 +978,9 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   const int g3 = max_coresident(pcg_ir_kernel<true>, h->sm_count);
   const int g4 = max_coresident(pcg_ir_kernel<false>, h->sm_count);
   h->grid_max = std::min(std::min(g1, g2), std::min(g3, g4));
-  const int g5 = std::min(max_coresident(g_upd_r<double, true>, h->sm_count),
-                          max_coresident(g_upd_r<double, false>, h->sm_count));
+  const int g5 = std::min(std::min(max_coresident(g_upd_r<double, true>, h->sm_count),
+                                   max_coresident(g_upd_r<double, false>, h->sm_count)),
+                          max_coresident(g_upd_xp<float, true, true, true>, h->sm_count));
   const int g6 = std::min(max_coresident(g_upd_xp<double, true, false, true>, h->sm_count),
                           max_coresident(g_res64<true>, h->sm_count));
   h->grid_graph = std::min(g5, g6);
@@ -987,8 +1102,12 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
   P.timers = h->timers;
-  const bool graph_mode = fp64 && (h->loop_mode >= 2 || (h->loop_mode == 0 && h->n >= kGraphMinRows));
-  if (graph_mode) return solve_graph64(h, P, jac, h->loop_mode == 3 ? kUnrollIters : 0, iters_out, relres_out);
+  // auto: fp64 takes the graph form from kGraphMinRows rows; the refinement's
+  // fp32 vector passes are short, so it stays in the persistent form
+  const bool graph_mode = h->loop_mode >= 2 || (h->loop_mode == 0 && fp64 && h->n >= kGraphMinRows);
+  if (graph_mode && fp64)
+    return solve_graph64(h, P, jac, h->loop_mode == 3 ? kUnrollIters : 0, iters_out, relres_out);
+  if (graph_mode) return solve_graph_ir(h, P, jac, iters_out, relres_out);
   void* args[] = {&P};
   const void* fn;
   if (fp64)

@@ -32,13 +32,14 @@ struct GState {
   int status;          // kRunning, cg status, or kNeedRestart
   int started;         // 0 before the first prologue of a solve
   unsigned ctr;        // arrivals of the current x/p pass (last-CTA election)
-  int pad;
+  int outer;           // refinement: inner solves started
 };
 
 struct GArgs {
   SolveParams P;
   GState* gs;
-  cudaGraphConditionalHandle h;
+  cudaGraphConditionalHandle h;   // the CG loop's WHILE node
+  cudaGraphConditionalHandle h2;  // refinement: the outer WHILE node
   unsigned G_spmv;  // CTAs of the SpMV kernel (its p.q partials)
   unsigned G_upd;   // CTAs of the vector kernels (their partials)
 };
@@ -259,6 +260,93 @@ __global__ void g_final64(GArgs a) {
   gs->relres_true = rel;
   if (!isfinite(rel)) gs->status = kNumeric;
   else if (gs->status == kOk && rel > a.P.tol) gs->status = kNeedRestart;
+}
+
+// ---------------------------------------------------------------------------
+// fp32-inner / fp64-outer refinement (reading R6) as nested WHILE nodes:
+//   outer WHILE { q = A x | r = b - q, r^32, p32, d^ = 0, partials | start (1 CTA) |
+//                 inner WHILE { SpMV32 | r update | [r.r] | x/p update, x64 += d } }
+// The outer condition starts at 1; the start kernel clears it once the fp64
+// residual meets tol (or a limit or an error ends the solve), and sets the
+// inner condition for the inner solve it prepares.
+// ---------------------------------------------------------------------------
+
+template <bool JAC>
+__global__ void __launch_bounds__(kBlock) g_res_ir(GArgs a) {
+  const SolveParams& P = a.P;
+  Grid g = graph_grid();
+  const LoopVecs<float>& V = P.V32;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) {
+    const double bi = P.b[i];
+    const double ri = bi - P.V64.q[i];
+    const float rh = (float)(JAC ? ri * __ldg(P.disq + i) : ri);
+    V.r[i] = rh;
+    V.p[i] = rh;
+    V.xh[i] = 0.0f;
+    const double rh2 = (double)rh * (double)rh;
+    v[0] += ri * ri;
+    v[1] += bi * bi;
+    v[2] += rh2;
+    v[3] += JAC ? (double)__ldg(P.S32.dn + i) * rh2 : rh2;
+  }
+  publish<4>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+}
+
+// One CTA: fp64 residual test, limits, and the start state of the next inner solve.
+template <bool COND>
+__global__ void g_start_ir(GArgs a) {
+  double s[4];
+  grid_sum<4>(a.P.part + kSlotRes * (size_t)a.P.pstride, a.G_upd, s);
+  if (threadIdx.x != 0) return;
+  GState* gs = a.gs;
+  if (!gs->started) {
+    gs->started = 1;
+    gs->bb = s[1];
+    gs->k = 0;
+    gs->outer = 0;
+    gs->status = kRunning;
+  }
+  const double rel = gs->bb > 0.0 ? sqrt(s[0]) / sqrt(gs->bb) : 0.0;
+  gs->relres_true = rel;
+  gs->rr = s[0];
+  bool stop = true;
+  int status = gs->status;
+  if (status == kBreakdown || status == kNumeric) {
+    // the previous inner solve failed; x keeps the last good iterate
+  } else if (gs->bb == 0.0) {
+    status = kOk;  // x = 0, written after the loop
+  } else if (!isfinite(rel)) {
+    status = kNumeric;
+  } else if (rel <= a.P.tol) {
+    status = kOk;
+  } else if (gs->outer >= a.P.max_restarts || gs->k >= a.P.maxit) {
+    status = kNotConverged;
+  } else {
+    stop = false;
+  }
+  bool inner = false;
+  if (!stop) {
+    gs->rho = s[2];
+    gs->stop_abs = a.P.tol_in * sqrt(s[3]);
+    gs->k_start = gs->k;
+    gs->outer += 1;
+    gs->ctr = 0;
+    status = kRunning;
+    inner = !(sqrt(s[3]) <= gs->stop_abs);  // r32 = 0 only if tol_in >= 1
+  }
+  gs->status = status;
+  if constexpr (COND) {
+    cudaGraphSetConditional(a.h2, stop ? 0u : 1u);
+    cudaGraphSetConditional(a.h, inner ? 1u : 0u);
+  }
+}
+
+// After the outer loop: b = 0 gives x = 0.
+__global__ void __launch_bounds__(kBlock) g_flush_ir(GArgs a) {
+  if (a.gs->bb != 0.0) return;
+  Grid g = graph_grid();
+  for (int64_t i = g.gtid; i < a.P.A.n; i += g.gstride) a.P.x[i] = 0.0;
 }
 
 }  // namespace cg

@@ -249,6 +249,28 @@ __device__ __forceinline__ T lane_c(const VT& v, int j) {
   return reinterpret_cast<const T*>(&v)[j];
 }
 
+// Per-thread dot-product accumulator.  fp64: fused multiply-add.  fp32 (the
+// refinement's inner solve): fp32 products summed with Kahan compensation, so
+// the per-thread partial is accurate to about one fp32 rounding without any
+// fp64 instruction (GB300 issues 64 fp32 FMAs per fp64 FMA); partials are
+// combined in fp64 across threads and CTAs.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float y = __fmul_rn(a, b) - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
 // Status codes shared with the host API (values of cg_status).
 constexpr int kOk = 0, kNotConverged = 1, kBreakdown = -2, kNumeric = -3, kTimeout = -4;
 
@@ -278,46 +300,65 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 // exactly what W needs, which keeps occupancy high.  DIA: the column of slot m
 // is computed from delta[m] instead of loaded.  The diagonal term starts the
 // fused multiply-add chain, so each row costs W + 1 fp64 FMAs with the p.q term.
+// One slice's off-diagonal sum for uniform width W: loads of a chunk of CH
+// columns are issued together, then the multiply-adds.  DIA: the column of
+// slot m is i + delta[m], clamped into [0, n) with two 32-bit min/max (only
+// zero-valued slots of the first and last slices ever need the clamp).
+template <typename T, int W, bool DIA>
+__device__ __forceinline__ T slice_sum(const Sell<T>& S, const T* __restrict__ p, int64_t s,
+                                       int i32, int lane, T acc) {
+  constexpr int CH = W > 16 ? (W + 1) / 2 : W;
+  const T* vp = S.val + s * (W * 32) + lane;
+  const int nm1 = (int)S.n - 1;
+#pragma unroll
+  for (int m0 = 0; m0 < W; m0 += CH) {
+    T v[CH], pc[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int m = m0 + u;
+      if (m < W) {
+        v[u] = ld_stream(vp + m * 32);
+        const int c = DIA ? min(max(i32 + S.delta[m], 0), nm1)
+                          : ld_stream(S.col + s * (W * 32) + lane + m * 32);
+        pc[u] = p[c];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (m0 + u < W) acc = fma(v[u], pc[u], acc);
+  }
+  return acc;
+}
+
+// a1 over the grid for uniform slices of compile-time width W (no long rows).
+// Warps take slices round-robin, so at any moment the grid works on one
+// contiguous band of rows and the neighbours' lines are shared through L2.
+// The diagonal term starts the fused multiply-add chain: W + 1 FMAs per row
+// with the p.q term.
 template <typename T, bool JAC, int W, bool DIA>
 __device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __restrict__ p,
                                                T* __restrict__ q, const Grid& g) {
   const int lane = threadIdx.x & 31;
   const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
   const int Wt = (int)g.G * kWarps;
-  const int64_t n = S.n;
-  double dot = 0.0;
+  const int n = (int)S.n;
+  Acc<T> dot;
   for (int s = gw; s < S.nslices; s += Wt) {
-    const int64_t i = (int64_t)s * 32 + lane;
+    const int i = s * 32 + lane;
     const bool live = i < n;
     T pi = T(0), dgi = T(1);
     if (live) {
       pi = p[i];
       if (!JAC) dgi = __ldg(S.dg + i);
     }
-    const T* vp = S.val + (int64_t)s * (W * 32) + lane;
-    int c[W];
-    T v[W], pc[W];
-#pragma unroll
-    for (int m = 0; m < W; ++m) {
-      v[m] = ld_stream(vp + m * 32);
-      if (DIA) {
-        const int64_t cc = i + S.delta[m];
-        c[m] = (int)(cc < 0 ? 0 : (cc >= n ? n - 1 : cc));
-      } else {
-        c[m] = ld_stream(S.col + (int64_t)s * (W * 32) + lane + m * 32);
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < W; ++m) pc[m] = p[c[m]];
     T acc = JAC ? pi : dgi * pi;
-#pragma unroll
-    for (int m = 0; m < W; ++m) acc = fma(v[m], pc[m], acc);
+    acc = slice_sum<T, W, DIA>(S, p, s, i, lane, acc);
     if (live) {
       q[i] = acc;
-      dot = fma((double)pi, (double)acc, dot);
+      dot.add(pi, acc);
     }
   }
-  return dot;
+  return dot.get();
 }
 
 // Sliced-diagonal layout of any width up to kMaxDiag (loads in groups of kUnroll).
@@ -329,7 +370,7 @@ __device__ __forceinline__ double spmv_phase_dia(const Sell<T>& S, const T* __re
   const int Wt = (int)g.G * kWarps;
   const int64_t n = S.n;
   const int w = S.uw;
-  double dot = 0.0;
+  Acc<T> dot;
   for (int s = gw; s < S.nslices; s += Wt) {
     const int64_t i = (int64_t)s * 32 + lane;
     const bool live = i < n;
@@ -339,31 +380,34 @@ __device__ __forceinline__ double spmv_phase_dia(const Sell<T>& S, const T* __re
       if (!JAC) dgi = __ldg(S.dg + i);
     }
     const T* vp = S.val + (int64_t)s * w * 32 + lane;
+    const int64_t r0 = (int64_t)s * 32;
+    const bool inner = r0 + S.delta[0] >= 0 && r0 + 31 + S.delta[w - 1] < n;
+    const T* pb = p + i;
     T acc = JAC ? pi : dgi * pi;
     for (int m0 = 0; m0 < w; m0 += kUnroll) {
-      int c[kUnroll];
       T v[kUnroll], pc[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
         if (m0 + u < w) {
           v[u] = ld_stream(vp + (m0 + u) * 32);
-          const int64_t cc = i + S.delta[m0 + u];
-          c[u] = (int)(cc < 0 ? 0 : (cc >= n ? n - 1 : cc));
+          if (inner) {
+            pc[u] = pb[S.delta[m0 + u]];
+          } else {
+            const int64_t cc = i + S.delta[m0 + u];
+            pc[u] = p[cc < 0 ? 0 : (cc >= n ? n - 1 : cc)];
+          }
         }
       }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
-        if (m0 + u < w) pc[u] = p[c[u]];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u)
         if (m0 + u < w) acc = fma(v[u], pc[u], acc);
     }
     if (live) {
       q[i] = acc;
-      dot = fma((double)pi, (double)acc, dot);
+      dot.add(pi, acc);
     }
   }
-  return dot;
+  return dot.get();
 }
 
 // a1 over the grid: q = A^ p and this thread's share of p.q.  Warps take
@@ -376,6 +420,7 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
     if (S.uw == 4) return spmv_phase_w<T, JAC, 4, true>(S, p, q, g);
     if (S.uw == 6) return spmv_phase_w<T, JAC, 6, true>(S, p, q, g);
     if (S.uw == 8) return spmv_phase_w<T, JAC, 8, true>(S, p, q, g);
+    if (S.uw == 26) return spmv_phase_w<T, JAC, 26, true>(S, p, q, g);
     return spmv_phase_dia<T, JAC>(S, p, q, g);
   }
   if (S.uw == 4) return spmv_phase_w<T, JAC, 4, false>(S, p, q, g);
@@ -385,7 +430,7 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
   const int gw = (int)g.cta * kWarps + (int)(threadIdx.x >> 5);
   const int W = (int)g.G * kWarps;
   const int64_t n = S.n;
-  double dot = 0.0;
+  Acc<T> dot;
   for (int s = gw; s < S.nslices; s += W) {
     const int64_t i = (int64_t)s * 32 + lane;
     int o0, w;
@@ -426,7 +471,7 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
     }
     if (i < n && !((lm >> lane) & 1u)) {
       q[i] = acc;
-      dot = fma((double)pi, (double)acc, dot);
+      dot.add(pi, acc);
     }
   }
   // long rows: one warp per row, lanes stride, fixed xor tree
@@ -441,10 +486,10 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
       const T pi = p[i];
       const T qi = (JAC ? pi : __ldg(S.dg + i) * pi) + acc;
       q[i] = qi;
-      dot += (double)pi * (double)qi;
+      dot.add(pi, qi);
     }
   }
-  return dot;
+  return dot.get();
 }
 
 // a2 over the grid: r^ -= alpha q; rho = r^.r^ (= r.z); rr = r^.D r^ (= r.r,
@@ -461,6 +506,7 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
   const VT* q = reinterpret_cast<const VT*>(V.q);
   const VT* dn = reinterpret_cast<const VT*>(S.dn);
   const bool with_rr = JAC && want_rr;
+  Acc<T> a_rho, a_rr;
   for (int64_t i0 = g.gtid; i0 < nv; i0 += 2 * g.gstride) {
     const int64_t i1 = i0 + g.gstride;
     const bool two = i1 < nv;
@@ -480,8 +526,8 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
       for (int j = 0; j < VN; ++j) {
         const T ri = fma(-alpha, lane_c<T>(qv[h], j), lane<T>(rv[h], j));
         lane<T>(rv[h], j) = ri;
-        rho = fma((double)ri, (double)ri, rho);
-        if (with_rr) rr = fma((double)lane<T>(dv[h], j) * (double)ri, (double)ri, rr);
+        a_rho.add(ri, ri);
+        if (with_rr) a_rr.add(lane<T>(dv[h], j) * ri, ri);
       }
     }
     r[i0] = rv[0];
@@ -490,21 +536,23 @@ __device__ __forceinline__ void update_r_phase(const Sell<T>& S, const LoopVecs<
   for (int64_t i = nv * VN + g.gtid; i < n; i += g.gstride) {
     const T ri = fma(-alpha, V.q[i], V.r[i]);
     V.r[i] = ri;
-    rho = fma((double)ri, (double)ri, rho);
-    if (with_rr) rr = fma((double)__ldg(S.dn + i) * (double)ri, (double)ri, rr);
+    a_rho.add(ri, ri);
+    if (with_rr) a_rr.add(__ldg(S.dn + i) * ri, ri);
   }
+  rho += a_rho.get();
+  rr += a_rr.get();
   if (!JAC) rr = rho;
 }
 
 // r.r = r^.D r^ from the current r^ (the exact-test fallback).
 template <typename T>
 __device__ __forceinline__ double rr_phase(const Sell<T>& S, const LoopVecs<T>& V, const Grid& g) {
-  double rr = 0.0;
+  Acc<T> rr;
   for (int64_t i = g.gtid; i < S.n; i += g.gstride) {
-    const double ri = (double)V.r[i];
-    rr = fma((double)__ldg(S.dn + i) * ri, ri, rr);
+    const T ri = V.r[i];
+    rr.add(__ldg(S.dn + i) * ri, ri);
   }
-  return rr;
+  return rr.get();
 }
 
 // a3 over the grid: x^ += alpha p; p = r^ + beta p.  On the last iteration

@@ -176,13 +176,15 @@ def test_grid_size_does_not_change_the_answer_beyond_rounding():
 
 # ---------------------------------------------------------------- mixed precision
 
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "graph"])
 @pytest.mark.parametrize("tol_in", [1e-3, 1e-4])
-def test_fp32_refinement_reaches_fp64_tolerance(tol_in):
+def test_fp32_refinement_reaches_fp64_tolerance(tol_in, mode):
     A = gen.diff3d27(14, 1.0, 7)
     b = oracle.spmv(A, gen.xstar(A.n, 7))
     ref = oracle.pcg_ir(A, b, tol=1e-10, tol_in=tol_in)
     rp, ci, va = to_device(A)
     h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
     assert cg.cg_set_option(h, cg.CG_OPT_IR_TOL_INNER, tol_in) == cg.CG_OK
     st, it, rel, x, info = gpu_solve(A, b, 1e-10, 100000, cg.CG_PRECOND_JACOBI,
                                      cg.CG_PREC_FP32_IR, h=h)
@@ -317,11 +319,17 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     cg.cg_destroy(h)
 
 
-def test_fp32_refinement_unpreconditioned():
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "graph"])
+def test_fp32_refinement_unpreconditioned(mode):
     A = gen.lap2d(48, 9, 0.05)
     b = oracle.spmv(A, gen.xstar(A.n, 11))
     ref = oracle.pcg_ir(A, b, tol=1e-10, tol_in=1e-4, precond=0)
-    st, it, rel, x, info = gpu_solve(A, b, 1e-10, 100000, cg.CG_PRECOND_NONE, cg.CG_PREC_FP32_IR)
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
+    st, it, rel, x, info = gpu_solve(A, b, 1e-10, 100000, cg.CG_PRECOND_NONE, cg.CG_PREC_FP32_IR,
+                                     h=h)
+    cg.cg_destroy(h)
     assert st == cg.CG_OK == ref.status
     assert oracle.true_relres(A, b, x) <= 1e-10 * (1 + 1e-6)
     assert abs(info["restarts"] - ref.restarts) <= 1
@@ -422,3 +430,28 @@ def test_residual_replacement_restarts_match_oracle(mode):
     assert st == ref.status == cg.CG_NOT_CONVERGED
     assert info["restarts"] == ref.restarts
     assert rel <= 1e-12
+
+
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "graph"])
+def test_fp32_refinement_edge_cases(mode):
+    A = spd_from_pattern(3000, 4, long_rows=[(7, 2200)])   # variable diagonal, long row
+    b = oracle.spmv(A, gen.xstar(A.n, 4))
+
+    def run(bb, maxit, tol=1e-10, x0=None):
+        rp, ci, va = to_device(A)
+        h = cg.cg_create(A.n, rp, ci, va)
+        assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
+        out = gpu_solve(A, bb, tol, maxit, cg.CG_PRECOND_JACOBI, cg.CG_PREC_FP32_IR, x0=x0, h=h)
+        cg.cg_destroy(h)
+        return out
+
+    st, it, rel, x, info = run(np.zeros(A.n), 1000, x0=np.ones(A.n))
+    assert st == cg.CG_OK and it == 0 and np.all(x == 0)
+    ref = oracle.pcg_ir(A, b, tol=1e-10, tol_in=1e-4)
+    st, it, rel, x, info = run(b, 100000)
+    assert st == cg.CG_OK == ref.status
+    assert oracle.true_relres(A, b, x) <= 1e-10 * (1 + 1e-6)
+    assert abs(it - ref.iters) <= max(5, math.ceil(0.1 * ref.iters)), (it, ref.iters)
+    st, it, rel, x, info = run(b, 3)                        # inner budget of 3 iterations
+    assert st == cg.CG_NOT_CONVERGED and it == 3
+    assert abs(rel - oracle.true_relres(A, b, x)) <= 1e-6 * rel
