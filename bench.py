@@ -46,7 +46,11 @@ WORKLOADS = {
     "diffusion27_160_fp64": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp64",
                              1e-10, 100000,
                              "3-D 27-point lognormal diffusion 160^3, FP64 Jacobi-PCG to 1e-10"),
+    "batch512": ("batch", {"count": 512, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
+                 "512 systems in one launch: 2-D 5-/9-point anisotropic Laplacians, side uniform "
+                 "in [32, 512], eps log-uniform in [1e-3, 1]; FP64 Jacobi-PCG to 1e-8 each"),
 }
+BATCH_GOLDEN = os.path.join(ROOT, "tests", "golden", "batch512_oracle.json")
 
 
 def bytes_per_iter(n, nnz, precond, precision):
@@ -186,11 +190,39 @@ def run_reference(args):
         return
     import oracle
     import cgproblems as gen
-    _, _, precond, precision, tol, maxit, desc = WORKLOADS[args.workload]
+    builder, _, precond, precision, tol, maxit, desc = WORKLOADS[args.workload]
+    per_step_budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    if builder == "batch":
+        _, systems = batch_systems(args.workload)
+        gold = batch_golden_iters(len(systems))
+        if gold is None:
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "no golden oracle iteration counts for the batch (tests/golden)"}))
+            return
+        for _ in range(args.warmup):
+            time_oracle_batch_sample(systems, gold, per_step_budget)
+        times = []
+        for _ in range(args.steps):
+            t, sample = time_oracle_batch_sample(systems, gold, per_step_budget)
+            times.append(t)
+        solve_s = statistics.median(times)
+        value = 1.0 / solve_s
+        line = {"impl": "reference",
+                "metric": "batched PCG time to 1e-8 rel. residual, all systems (batches/s)",
+                "value": value, "unit": "batches/s", "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "description": desc, "systems": len(systems),
+                           "rows": int(sum(A.n for A in systems))},
+                "cpu_baseline": {"value": value, "unit": "batches/s", "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "batches/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     A = build_matrix(args.workload)
     b = oracle.spmv(A, gen.xstar(A.n, 0))
     iters = golden_iters(args.workload)
-    per_step_budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         time_oracle_sample(A, b, precond, precision, tol, per_step_budget)
     samples = []
@@ -215,6 +247,184 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_systems(workload):
+    import cgproblems as gen
+    kw = WORKLOADS[workload][1]
+    params = gen.batch_members(kw["count"], kw["seed"])
+    return params, [gen.lap2d(side, pts, eps) for side, pts, eps in params]
+
+
+def batch_golden_iters(count):
+    """The oracle's own iteration count of every batch member (committed golden file)."""
+    if not os.path.exists(BATCH_GOLDEN):
+        return None
+    d = json.load(open(BATCH_GOLDEN))
+    if d.get("count") != count:
+        return None
+    return [m["iters"] for m in d["members"]]
+
+
+def time_oracle_batch_sample(systems, iters, budget_s):
+    """Time the oracle on a bounded sample of a batch: fixed Jacobi-PCG iterations on a few
+    members spread over the size range; seconds per (row x iteration) from the sample,
+    scaled to sum_i n_i k_i.  Returns (seconds per batch solve, sample description)."""
+    import numpy as np
+    import oracle
+    import cgproblems as gen
+    order = sorted(range(len(systems)), key=lambda i: systems[i].n)
+    picks = [order[int(q * (len(order) - 1))] for q in (0.0, 0.25, 0.5, 0.75, 1.0)]
+    rows_iters, secs, m = 0, 0.0, 4
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s / 2:
+        for i in picks:
+            A = systems[i]
+            b = oracle.spmv(A, gen.xstar(A.n, i))
+            t0 = time.perf_counter()
+            oracle.pcg(A, b, tol=0.0, maxit=m, precond=1, max_restarts=0)
+            secs += time.perf_counter() - t0
+            rows_iters += A.n * m
+        m *= 2
+    per = secs / rows_iters
+    total = sum(A.n * k for A, k in zip(systems, iters))
+    desc = (f"oracle Jacobi-PCG iterations on members {picks} (n = "
+            f"{[systems[i].n for i in picks]}), {rows_iters} row-iterations in {secs:.1f} s on 1 core, "
+            f"scaled to sum_i n_i k_i = {total}")
+    return per * total, desc
+
+
+def run_batch(args, world, rank, dev, torch, cg):
+    """The batched workload: every system of the batch in one cg_solve_batch per step."""
+    import numpy as np
+    import torch.distributed as dist
+    _, kw, precond_s, precision_s, tol, maxit, desc = WORKLOADS[args.workload]
+    precond = cg.CG_PRECOND_JACOBI if precond_s == "jacobi" else cg.CG_PRECOND_NONE
+    params, systems = batch_systems(args.workload)
+    import cgproblems as gen
+    ns = [A.n for A in systems]
+    off = np.concatenate([[0], np.cumsum(ns)])
+    ntot = int(off[-1])
+    # one flat buffer per vector kind; member i is a view (x is reset by one fill per step)
+    b_flat = torch.empty(ntot, dtype=torch.float64, device=dev)
+    x_flat = torch.zeros(ntot, dtype=torch.float64, device=dev)
+    for i, A in enumerate(systems):
+        bi = A.to_scipy() @ gen.xstar(A.n, i)  # b = A x* (scipy, input preparation)
+        b_flat[off[i]:off[i + 1]].copy_(torch.from_numpy(bi))
+    bs = [b_flat[off[i]:off[i + 1]] for i in range(len(systems))]
+    xs = [x_flat[off[i]:off[i + 1]] for i in range(len(systems))]
+    dev_csr = [tuple(torch.from_numpy(a).to(dev) for a in (A.rowptr, A.colind, A.vals)) for A in systems]
+    h = cg.cg_batch_create([c[0] for c in dev_csr], [c[1] for c in dev_csr], [c[2] for c in dev_csr])
+    if args.loop_mode in ("persistent", "graph"):
+        assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, 1 if args.loop_mode == "persistent" else 2) == cg.CG_OK
+    torch.cuda.synchronize()
+
+    def step():
+        x_flat.zero_()
+        st, its, rels = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond)
+        if st != cg.CG_OK:
+            raise RuntimeError(f"batch solve failed: {cg.status_string(st)} {cg.cg_last_error(h)}")
+        return its, rels, cg.cg_get_solve_info(h)
+
+    for _ in range(args.warmup):
+        step()
+    tuning = cg.cg_batch_get_tuning(h, precond)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    infos = []
+    barrier()
+    with ClockSampler(uuid) as clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            infos.append(step())
+        ev1.record()
+        barrier()
+    t_max = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([t_max], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_per_step = t_max / args.steps
+    value = world * args.steps / (t_max / 1e3)
+    its = infos[0][0]
+    relres = max(max(r) for _, r, _ in infos)
+    kern_ms = sum(inf["kernel_ms"] for _, _, inf in infos)
+    kern_bytes = sum(inf["bytes_moved"] for _, _, inf in infos)
+    peak, peak_kind = load_peaks()
+    achieved = kern_bytes / (kern_ms / 1e3) / 1e9
+    launches = sum(inf["kernel_launches"] for _, _, inf in infos)
+    form = {1: "persistent", 2: "graph"}.get(infos[0][2]["loop_form"], "?")
+
+    e2e = None
+    if not args.no_e2e:
+        bh = b_flat.cpu().pin_memory()
+        x0h = torch.zeros(ntot, dtype=torch.float64).pin_memory()
+        xh = torch.empty(ntot, dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b_flat.copy_(bh, non_blocking=True)
+            x_flat.copy_(x0h, non_blocking=True)
+            st, _, _ = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond)
+            if st != cg.CG_OK:
+                raise RuntimeError(f"batch solve failed: {cg.status_string(st)}")
+            xh.copy_(x_flat, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * args.steps / e2e_s, "unit": "batches/s",
+               "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gold = batch_golden_iters(len(systems))
+        k_used = gold if gold else its
+        solve_s, sample = time_oracle_batch_sample(systems, k_used, args.cpu_budget)
+        sample += " (oracle's own counts)" if gold else " (this run's counts: no golden file)"
+        cpu = {"value": 1.0 / solve_s, "unit": "batches/s", "cores": 1, "kind": "oracle",
+               "sample": sample, "ms_per_batch": solve_s * 1e3}
+    cg.cg_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": "batched PCG time to 1e-8 rel. residual, all systems (batches/s)",
+            "value": value, "unit": "batches/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "systems": len(systems),
+                       "rows": ntot, "nnz": int(sum(A.nnz for A in systems)), "tol": tol,
+                       "iters_max": max(its), "iters_sum": int(sum(its)),
+                       "relres_true_max": relres, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "grid_ctas": infos[0][2]["grid_ctas"], "autotuner": tuning,
+                       "loop_mode": args.loop_mode},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "timed_unit": "one batched solve: the persistent batch kernel (whole launch)",
+                         "loop_form": form,
+                         "bytes_model": "sum over systems of iters x (12 nnz + 4 (n+1) + 104 n)"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def main():
@@ -252,6 +462,9 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     builder, kw, precond_s, precision_s, tol, maxit, desc = WORKLOADS[args.workload]
+    if builder == "batch":
+        run_batch(args, world, rank, dev, torch, cg)
+        return
     precond = cg.CG_PRECOND_JACOBI if precond_s == "jacobi" else cg.CG_PRECOND_NONE
     precision = cg.CG_PREC_FP64 if precision_s == "fp64" else cg.CG_PREC_FP32_IR
 

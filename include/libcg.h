@@ -151,6 +151,62 @@ const char* cg_last_error(const cg_handle* h);
 /* Static name of a status code. */
 const char* cg_status_string(int32_t status);
 
+/* Most systems in one batch handle. */
+#define CG_BATCH_MAX_SYSTEMS 4096
+
+/*
+ * Create a solver for nsys independent systems (1 <= nsys <=
+ * CG_BATCH_MAX_SYSTEMS) of uneven size, all solved by one launch.  n[s]
+ * (host array, each >= 1) is the order of system s; rowptr[s], colind[s] and
+ * vals[s] (host arrays of DEVICE pointers) its CSR, validated as in
+ * cg_create and borrowed until cg_destroy.  The handle concatenates the
+ * systems into one block-diagonal matrix in 256-row tiles (so it holds a
+ * second copy of all matrices) and serves cg_solve_batch,
+ * cg_batch_get_system, cg_batch_get_tuning, cg_set_stream, cg_set_option,
+ * cg_get_solve_info, cg_last_error and cg_destroy; the single-system calls
+ * return CG_ERR_INVALID on it.  On failure *out = NULL and
+ * cg_last_error(NULL) names the system at fault.
+ */
+cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* rowptr,
+                          const int32_t* const* colind, const double* const* vals,
+                          cg_handle** out);
+
+/*
+ * Solve every system of a batch handle, each exactly as cg_solve would in
+ * fp64 (Alg. 1 with the same stopping rule, fp64 true-residual test and
+ * restarts; precision must be CG_PREC_FP64).  b[s] and x[s] (host arrays of
+ * DEVICE pointers, length n[s]) are system s's rhs and initial guess /
+ * solution.  One persistent cooperative kernel, captured with its gather and
+ * scatter kernels in a CUDA graph (CG_OPT_LOOP_MODE 1: direct launch),
+ * iterates all systems; a converged system drops out of the tile schedule.
+ * The kernel variant (registers budgeted for 2, 3 or 4 resident CTAs per
+ * SM) and grid size come from an autotuner that times short trial solves of
+ * these systems at the first solve of each preconditioner (x is not touched
+ * by the trials; the choice is kept in the handle); CG_OPT_GRID_CTAS > 0
+ * forces the grid instead.  iters[s] and relres[s] (host,
+ * may be NULL) receive each system's iterations and fp64 true relative
+ * residual.  Returns the most severe error of any system, else
+ * CG_NOT_CONVERGED if any system missed tol, else CG_OK; per-system results
+ * via cg_batch_get_system.  cg_get_solve_info reports the largest iteration
+ * count and residual, the grid, the device time and the modelled bytes
+ * summed over systems.
+ */
+cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x, double tol,
+                         int32_t maxit, int32_t precond, int32_t precision, int32_t* iters,
+                         double* relres);
+
+/* Result of system s (0 <= s < nsys) of the last cg_solve_batch: status, iterations,
+ * restarts and fp64 true relative residual (each pointer may be NULL). */
+cg_status cg_batch_get_system(const cg_handle* h, int32_t s, int32_t* status, int32_t* iters,
+                              int32_t* restarts, double* relres);
+
+/* The autotuner's record for a preconditioner: *count candidates (kernel
+ * variant = resident CTAs per SM its registers are budgeted for, grid size)
+ * with their trial times in ms (arrays of at least 8 entries, may be NULL),
+ * and the index of the chosen candidate (-1 before the first autotuned solve). */
+cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* count, int32_t* grids,
+                              int32_t* ctas_per_sm, float* ms, int32_t* chosen);
+
 /* Largest n that cg_solve_noalloc accepts: its scratch is four device vectors
  * of this many doubles plus a result block (2 MiB per GPU). */
 #define CG_NOALLOC_MAX_ROWS 65536

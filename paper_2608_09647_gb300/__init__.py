@@ -28,8 +28,10 @@ CG_OPT_PHASE_TIMERS, CG_OPT_LOOP_MODE = 6, 7
 # every symbol include/libcg.h declares
 EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
            "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
-           "cg_last_error", "cg_status_string", "cg_solve_noalloc")
+           "cg_last_error", "cg_status_string", "cg_solve_noalloc", "cg_batch_create",
+           "cg_solve_batch", "cg_batch_get_system", "cg_batch_get_tuning")
 CG_NOALLOC_MAX_ROWS = 65536
+CG_BATCH_MAX_SYSTEMS = 4096
 
 
 class CGError(RuntimeError):
@@ -88,6 +90,10 @@ def load(build_if_missing: bool = True):
     lib.cg_status_string.restype = ctypes.c_char_p
     lib.cg_solve_noalloc.argtypes = [i64, i64, P, P, P, P, P, f64, i32, i32, P, pi32, pf64]
     lib.cg_solve_noalloc.restype = ctypes.c_int
+    lib.cg_batch_create.argtypes = [i32, pi64, P, P, P, ctypes.POINTER(P)]
+    lib.cg_solve_batch.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
+    lib.cg_batch_get_system.argtypes = [P, i32, pi32, pi32, pi32, pf64]
+    lib.cg_batch_get_tuning.argtypes = [P, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
     for name in ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
                  "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info"):
         getattr(lib, name).restype = ctypes.c_int
@@ -242,6 +248,75 @@ def cg_destroy(h: Handle) -> None:
         _lib.cg_destroy(h._ptr)
         h._ptr = None
         h._keep = None
+
+
+def _ptr_array(tensors, dtype, name):
+    arr = (ctypes.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = _dptr(t, dtype, f"{name}[{i}]").value
+    return arr
+
+
+def cg_batch_create(rowptrs, colinds, valss) -> Handle:
+    """Create a batch solver for len(rowptrs) systems (lists of device int32 / int32 /
+    float64 tensors, one CSR per system)."""
+    import torch
+    lib = load()
+    ns = len(rowptrs)
+    if not (len(colinds) == ns and len(valss) == ns):
+        raise ValueError("cg_batch_create: rowptrs, colinds and valss differ in length")
+    nrows = (ctypes.c_int64 * max(ns, 1))(*[int(r.numel()) - 1 for r in rowptrs])
+    rp = _ptr_array(rowptrs, torch.int32, "rowptr")
+    ci = _ptr_array(colinds, torch.int32, "colind")
+    va = _ptr_array(valss, torch.float64, "vals")
+    out = ctypes.c_void_p()
+    torch.cuda.current_stream().synchronize()
+    st = lib.cg_batch_create(ns, nrows, rp, ci, va, ctypes.byref(out))
+    if st != CG_OK:
+        raise CGError(st, lib.cg_last_error(None).decode())
+    return Handle(out, sum(int(r.numel()) - 1 for r in rowptrs),
+                  (list(rowptrs), list(colinds), list(valss)))
+
+
+def cg_solve_batch(h: Handle, bs, xs, tol: float = 1e-8, maxit: int = 1000,
+                   precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64):
+    """Solve every system of a batch handle on the current stream; xs hold the initial
+    guesses on entry.  Returns (status, iters list, relres list)."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    ns = len(bs)
+    if len(xs) != ns:
+        raise ValueError("cg_solve_batch: bs and xs differ in length")
+    its = (ctypes.c_int32 * max(ns, 1))()
+    rels = (ctypes.c_double * max(ns, 1))()
+    st = lib.cg_solve_batch(h.ptr, _ptr_array(bs, torch.float64, "b"), _ptr_array(xs, torch.float64, "x"),
+                            float(tol), int(maxit), int(precond), int(precision), its, rels)
+    return st, list(its)[:ns], list(rels)[:ns]
+
+
+def cg_batch_get_system(h: Handle, s: int) -> dict:
+    st, it, rs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rel = ctypes.c_double()
+    r = load().cg_batch_get_system(h.ptr, int(s), ctypes.byref(st), ctypes.byref(it), ctypes.byref(rs),
+                                   ctypes.byref(rel))
+    if r != CG_OK:
+        raise CGError(r, cg_last_error(h))
+    return {"status": st.value, "iters": it.value, "restarts": rs.value, "relres": rel.value}
+
+
+def cg_batch_get_tuning(h: Handle, precond: int = CG_PRECOND_JACOBI) -> dict:
+    cnt, chosen = ctypes.c_int32(), ctypes.c_int32()
+    grids = (ctypes.c_int32 * 8)()
+    per_sm = (ctypes.c_int32 * 8)()
+    ms = (ctypes.c_float * 8)()
+    r = load().cg_batch_get_tuning(h.ptr, int(precond), ctypes.byref(cnt), grids, per_sm, ms,
+                                   ctypes.byref(chosen))
+    if r != CG_OK:
+        raise CGError(r, cg_last_error(h))
+    k = cnt.value
+    return {"grids": list(grids)[:k], "ctas_per_sm": list(per_sm)[:k], "ms": list(ms)[:k],
+            "chosen": chosen.value}
 
 
 @dataclass

@@ -13,12 +13,19 @@
 
 #include "../../include/libcg.h"
 #include "cg_graph.cuh"
+#include "cg_handle.cuh"
 
 using namespace cg;
 
 namespace {
 
 thread_local std::string g_create_error;
+
+}  // namespace
+
+void cgi::set_create_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
 
 // Device checks of a CSR whose rowptr the host has already validated:
 // colind in [0, n); per row the diagonal sum A_ii and the number of stored
@@ -186,80 +193,6 @@ __global__ void fill_long_kernel(int32_t nlong, const int32_t* __restrict__ lrow
 }
 
 }  // namespace
-
-// Device memory owned by a handle.  The internal off-diagonal matrices and
-// work vectors are built on first use of a precision / preconditioner.
-struct cg_handle {
-  int64_t n = 0, nnz = 0;
-  const int32_t* rowptr = nullptr;  // borrowed caller CSR
-  const int32_t* colind = nullptr;
-  const double* vals = nullptr;
-  int32_t* rb = nullptr;            // row blocks of the caller CSR
-  int32_t nrb = 0;
-  int64_t long_rows = 0;
-  std::vector<int32_t> host_rowptr;
-  // diagonal data
-  double* diag = nullptr;           // A_ii (sum of stored diagonal entries)
-  int32_t* ndiag = nullptr;         // diagonal entries per row
-  double *dsq = nullptr, *disq = nullptr;
-  float *diag32 = nullptr, *disq32 = nullptr;
-  bool jacobi_ok = false;
-  // off-diagonal loop matrix in SELL-32 form (+ compact CSR of long rows)
-  int32_t nslices = 0;
-  int32_t uniform_w = -1;           // every slice padded to this width (-1: variable)
-  int32_t dia = 0;                  // sliced-diagonal layout (no column array)
-  double dmin = 1.0, dmax = 1.0;    // range of A_ii (Jacobi)
-  int32_t delta[kMaxDiag] = {};     // its diagonal offsets, ascending
-  int32_t* delta_dev = nullptr;
-  int32_t* soff = nullptr;
-  uint32_t* lmask = nullptr;
-  int32_t* scol = nullptr;
-  int64_t sell_entries = 0;         // padded entries (multiple of 32)
-  int64_t nnz_od = 0;
-  int32_t nlong = 0;
-  int32_t *lrow = nullptr, *lptr = nullptr, *lcol = nullptr;
-  int64_t nnz_long = 0;
-  double* sval64[2] = {nullptr, nullptr};  // [precond]: unscaled / Jacobi-scaled
-  float* sval32[2] = {nullptr, nullptr};
-  double* lval64[2] = {nullptr, nullptr};
-  float* lval32[2] = {nullptr, nullptr};
-  bool scol_written = false;
-  // work vectors
-  double *r = nullptr, *p = nullptr, *q = nullptr, *xh = nullptr;
-  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *xh32 = nullptr;
-  double* part = nullptr;
-  DevState* st = nullptr;
-  DevState* host_st = nullptr;      // pinned
-  double *stage_b = nullptr, *stage_x = nullptr;  // device staging of cg_solve_host (lazy)
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int sm_count = 0;
-  int grid_max = 0;                 // co-resident CTAs of the persistent kernels
-  int grid_opt = 0;                 // CG_OPT_GRID_CTAS (0 = auto)
-  int max_restarts = 3;
-  double timeout_ms = 2000.0;
-  double tol_in = 1e-4;
-  int max_outer = 30;
-  unsigned skip_seq = 0;
-  int timers = 0;
-  int loop_mode = 0;                // CG_OPT_LOOP_MODE (0 auto, 1 persistent, 2 graph)
-  // graph form of the loop
-  int grid_graph = 0;               // CTAs of the graph-mode vector kernels
-  int grid_part = 0;                // partial-sum slots per kind (the largest grid of any loop kernel)
-  GState* gs = nullptr;
-  GState* host_gs = nullptr;        // pinned
-  cudaGraph_t graph = nullptr, graph_it = nullptr, graph_ep = nullptr;
-  cudaGraphExec_t gexec = nullptr, gexec_it = nullptr, gexec_ep = nullptr;
-  int gkey_unroll = -1;
-  const void* gkey_b = nullptr;     // the graph bakes in these solve arguments
-  const void* gkey_x = nullptr;
-  double gkey_tol = -1.0;
-  int gkey_maxit = -1, gkey_jac = -1;
-  double gkey_tol_in = -1.0;
-  int gkey_outer = -1;
-  cg_solve_info last{};
-  std::string err;
-};
 
 namespace {
 
@@ -542,6 +475,7 @@ void destroy_graph(cudaGraphExec_t* e, cudaGraph_t* g) {
 }
 
 void free_all(cg_handle* h) {
+  if (h->batch) cgi::batch_free(h->batch);
   void* dev[] = {h->rb,        h->diag,      h->ndiag,     h->dsq,       h->disq,       h->delta_dev,
                  h->diag32,    h->disq32,    h->soff,      h->lmask,     h->scol,
                  h->lrow,      h->lptr,      h->lcol,      h->sval64[0], h->sval64[1],
@@ -1044,6 +978,7 @@ cg_status cg_set_option(cg_handle* h, int32_t option, double value) {
 
 cg_status cg_spmv(cg_handle* h, const double* x, double* y) {
   if (!h) return CG_ERR_INVALID;
+  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_spmv: batch handle (use cg_solve_batch)");
   if (h->n == 0) return CG_OK;
   if (!x || !y || x == y) return fail(h, CG_ERR_INVALID, "cg_spmv: x/y NULL or aliased");
   Csr<double> A{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
@@ -1056,6 +991,7 @@ cg_status cg_spmv(cg_handle* h, const double* x, double* y) {
 cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t maxit,
                    int32_t precond, int32_t precision, int32_t* iters_out, double* relres_out) {
   if (!h) return CG_ERR_INVALID;
+  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_solve: batch handle (use cg_solve_batch)");
   h->last = cg_solve_info{};
   if (!(tol >= 0.0) || maxit < 0) return fail(h, CG_ERR_INVALID, "cg_solve: tol < 0 or maxit < 0");
   if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)

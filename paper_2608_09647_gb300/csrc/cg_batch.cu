@@ -1,0 +1,1002 @@
+// Batched solves: up to CG_BATCH_MAX_SYSTEMS independent SPD systems of
+// uneven size in one persistent cooperative launch, captured in a CUDA graph.
+// Each system follows the single-system method of cg_solve (CG / Jacobi-PCG
+// of Sec. 3 with its stopping rule, true-residual check and restarts); only
+// the schedule is shared.
+//
+// Layout.  The systems are concatenated into one block-diagonal loop matrix
+// in SELL-32 form (32-row slices stored column-major, the diagonal held apart
+// as a vector; with Jacobi the matrix is the scaled D^-1/2 A D^-1/2 of unit
+// diagonal).  Every system is padded to whole 256-row tiles (padding rows are
+// identity rows with b = x = 0), so no tile spans two systems.  One tile is
+// one CTA's unit of work: 8 warps, one slice each, lane = row.
+//
+// Schedule.  Rounds of four phases separated by bounded grid barriers:
+//   R  r = b - A x for the systems that need it (start, after their loop,
+//      restarts): the fp64 true-residual test and the start of a loop;
+//   A  q = A p and p.q, alpha;
+//   B  r -= alpha q, r.r and r.D r, beta and the recursive stopping test;
+//   C  x += alpha p, p = r + beta p.
+// A system's stage says which phases it takes part in: 0 residual pending,
+// 1 iterating, 2 done, 3 last x update pending (C, then R).  At the start of
+// each phase every CTA scans the stages, forms the prefix sum of the tiles of
+// the systems in that phase in shared memory and deals those tiles
+// round-robin, so finished systems cost nothing.  A system's sums are formed
+// by the CTA that completes its last tile of the phase, over the tiles'
+// partials in tile order, so they do not depend on the schedule.  A stage
+// change made during a phase carries that phase's number; a CTA that reads
+// the word in the same phase takes the stage from before the change, so all
+// CTAs deal the same tile list.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cg_handle.cuh"
+
+using namespace cg;
+
+namespace {
+
+constexpr int kTile = kBlock;        // rows per tile (kWarps slices)
+constexpr int kMaxBatch = CG_BATCH_MAX_SYSTEMS;
+constexpr int kNP = 4;               // partial sums per slice
+constexpr int kStRunning = 100;      // status of a system still being solved
+constexpr int kMaxCand = 8;          // autotuner candidates
+
+// stage masks of the phases
+constexpr unsigned kMaskR = (1u << 0) | (1u << 3);
+constexpr unsigned kMaskAB = 1u << 1;
+constexpr unsigned kMaskC = (1u << 1) | (1u << 3);
+constexpr unsigned kMaskAlive = (1u << 0) | (1u << 1) | (1u << 3);
+
+struct BatchParams {
+  int nsys;
+  const int32_t* __restrict__ tstart;  // first tile of each system
+  const int32_t* __restrict__ ntile;   // tiles of each system
+  const int32_t* __restrict__ soff;    // slice offsets (units of 32 entries)
+  const int32_t* __restrict__ col;     // global (concatenated) column of each entry
+  const double* __restrict__ val;
+  const double* __restrict__ dg;       // A_ii, 1 on padding rows
+  double *r, *p, *q, *xh;
+  const double* __restrict__ bh;
+  double *rho, *rr, *bb, *alpha, *beta, *relres;
+  int *k, *restarts, *status, *zero;
+  unsigned long long* sstate;          // phase << 16 | stage before << 8 | stage after
+  unsigned* cnt;                       // tiles of the system finished in this phase
+  double* tpart;                       // kNP partials per slice
+  double tol;
+  int maxit, max_restarts;
+  DevState* st;
+  uint64_t timeout_ns;
+  unsigned skip_seq;
+};
+
+__device__ __forceinline__ int eff_stage(unsigned long long w, unsigned seq) {
+  return ((unsigned)(w >> 16) == seq) ? (int)((w >> 8) & 0xff) : (int)(w & 0xff);
+}
+
+// Exclusive prefix sum (in s_pref) of the tiles of the systems whose stage,
+// as seen in phase seq, is in `mask`; returns their total.  *alive gets
+// whether any system is still unfinished.
+__device__ int build_tiles(const BatchParams& P, unsigned mask, unsigned seq, int* s_pref, int* s_scan,
+                           bool* alive) {
+  const int t = threadIdx.x;
+  const int per = (P.nsys + kBlock - 1) / kBlock;
+  const int s0 = min(P.nsys, t * per), s1 = min(P.nsys, s0 + per);
+  int c = 0, live = 0;
+  for (int s = s0; s < s1; ++s) {
+    const unsigned sbit = 1u << eff_stage(__ldcg(P.sstate + s), seq);
+    const int cs = (sbit & mask) ? P.ntile[s] : 0;
+    live |= (sbit & kMaskAlive) != 0;
+    s_pref[s] = cs;
+    c += cs;
+  }
+  s_scan[t] = c;
+  *alive = __syncthreads_or(live) != 0;
+  for (int off = 1; off < kBlock; off <<= 1) {
+    const int v = t >= off ? s_scan[t - off] : 0;
+    __syncthreads();
+    s_scan[t] += v;
+    __syncthreads();
+  }
+  int base = s_scan[t] - c;
+  for (int s = s0; s < s1; ++s) {
+    const int cs = s_pref[s];
+    s_pref[s] = base;
+    base += cs;
+  }
+  const int total = s_scan[kBlock - 1];
+  __syncthreads();
+  return total;
+}
+
+// Entry j < total of the phase's tile list -> (system, global tile).  The
+// owner is the last system whose prefix is <= j (systems without tiles in
+// the phase share the prefix of their successor, which is larger than j).
+__device__ __forceinline__ void tile_of(const BatchParams& P, const int* s_pref, int j, int* sys, int* gt) {
+  int lo = 0, hi = P.nsys - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_pref[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  *sys = lo;
+  *gt = P.tstart[lo] + (j - s_pref[lo]);
+}
+
+// Off-diagonal part of one row of slice sl: sum over the slice width of
+// val * v[col] (loads issued kUnroll at a time).
+__device__ __forceinline__ double row_offdiag(const BatchParams& P, const double* v, int sl, int lane) {
+  const int o0 = __ldg(P.soff + sl);
+  const int w = __ldg(P.soff + sl + 1) - o0;
+  const int32_t* cp = P.col + (int64_t)o0 * 32 + lane;
+  const double* vp = P.val + (int64_t)o0 * 32 + lane;
+  double acc = 0.0;
+  for (int m0 = 0; m0 < w; m0 += kUnroll) {
+    int c[kUnroll];
+    double a[kUnroll], x[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (m0 + u < w) {
+        c[u] = ld_stream(cp + (m0 + u) * 32);
+        a[u] = ld_stream(vp + (m0 + u) * 32);
+      }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (m0 + u < w) x[u] = v[c[u]];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (m0 + u < w) acc = fma(a[u], x[u], acc);
+  }
+  return acc;
+}
+
+// Sum of a system's slice partials in slice order (warp 0), given to every thread.
+template <int NV>
+__device__ __forceinline__ void system_sum(const BatchParams& P, int sys, double (&out)[NV]) {
+  __shared__ double s_out[NV];
+  if (threadIdx.x < 32) {
+    const int s0 = P.tstart[sys] * kWarps, ns = P.ntile[sys] * kWarps;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = 0.0;
+      for (int t = threadIdx.x; t < ns; t += 32) a += __ldcg(P.tpart + (size_t)(s0 + t) * kNP + j);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (threadIdx.x == 0) s_out[j] = a;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = s_out[j];
+  __syncthreads();
+}
+
+// New stage of sys, tagged with the current phase (one writer per system and phase).
+__device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int stage, unsigned seq) {
+  const unsigned long long before = __ldcg(P.sstate + sys) & 0xffull;
+  P.sstate[sys] = ((unsigned long long)seq << 16) | (before << 8) | (unsigned long long)stage;
+}
+
+// One phase over the tile list [0, T) of the current phase.  CTA c takes the
+// contiguous chunk [c T / G, (c+1) T / G), which spans few systems.  For each
+// tile, row(sys, i, v) handles row i (one thread per row) and returns NV
+// values to be summed over the system; each warp reduces its slice and
+// stores one partial per value.  When the CTA leaves a system's segment of
+// its chunk it adds the segment's tile count to the system's counter; the
+// CTA that completes the count sums the system's slice partials in slice
+// order (independent of G) and calls done(sys, sums) in thread 0.
+template <int NV, class Row, class Done>
+__device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
+                                          Row row, Done done) {
+  __shared__ int s_last;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int j1 = (int)((int64_t)T * (g.cta + 1) / g.G);
+  int j = (int)((int64_t)T * g.cta / g.G);
+  while (j < j1) {
+    int sys, gt;
+    tile_of(P, s_pref, j, &sys, &gt);
+    const int je = min(j1, s_pref[sys] + P.ntile[sys]);  // end of this system's segment
+    for (int jj = j; jj < je; ++jj, ++gt) {
+      double v[NV > 0 ? NV : 1];
+      row(sys, gt * kTile + t, v);
+      if constexpr (NV > 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) P.tpart[((size_t)gt * kWarps + warp) * kNP + k] = v[k];
+        }
+      }
+    }
+    if constexpr (NV > 0) {
+      if (lane == 0) __threadfence();  // partials visible before the count
+      __syncthreads();
+      if (t == 0) {
+        const unsigned add = (unsigned)(je - j);
+        const unsigned prev = atomicAdd(P.cnt + sys, add);
+        const int last = prev + add == (unsigned)P.ntile[sys];
+        if (last) P.cnt[sys] = 0u;  // reset for the next phase (after its barrier)
+        __threadfence();
+        s_last = last;
+      }
+      __syncthreads();
+      if (s_last) {
+        double sm[NV];
+        system_sum<NV>(P, sys, sm);
+        if (t == 0) done(sys, sm);
+      }
+    }
+    j = je;
+  }
+}
+
+// MINB: resident CTAs per SM the registers are budgeted for (an autotuner choice).
+template <bool JAC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) {
+  __shared__ int s_pref[kMaxBatch];
+  __shared__ int s_scan[kBlock];
+  Grid g(P.st, P.timeout_ns, P.skip_seq);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned seq = 0;  // phase number; the initial stage words carry 0
+  for (;;) {
+    // ---- R: residual of the stage 0 / 3 systems, their test, (re)start
+    ++seq;
+    bool alive = false;
+    int T = build_tiles(P, kMaskR, seq, s_pref, s_scan, &alive);
+    if (!alive) break;
+    if (T > 0) {
+      run_phase<3>(
+          P, s_pref, T, g,
+          [&](int, int i, double* v) {
+            const double xi = P.xh[i];
+            const double ax = (JAC ? xi : __ldg(P.dg + i) * xi) + row_offdiag(P, P.xh, i >> 5, lane);
+            const double bi = P.bh[i];
+            const double ri = bi - ax;
+            P.r[i] = ri;
+            P.p[i] = ri;
+            const double d = JAC ? __ldg(P.dg + i) : 1.0;
+            v[0] = ri * ri;  // r^.r^ = r.z
+            v[1] = d * ri * ri;  // r.r
+            v[2] = d * bi * bi;  // b.b
+          },
+          [&](int sys, const double* sm) {
+            const bool first = P.bb[sys] < 0.0;
+            if (first) P.bb[sys] = sm[2];
+            const double bb = P.bb[sys];
+            const double rel = bb > 0.0 ? sqrt(sm[1]) / sqrt(bb) : 0.0;
+            P.relres[sys] = rel;
+            P.rho[sys] = sm[0];
+            P.rr[sys] = sm[1];
+            int st = P.status[sys], next = 2;
+            if (bb == 0.0) {
+              st = kOk;
+              P.zero[sys] = 1;
+            } else if (st == kBreakdown || st == kNumeric) {
+              // keep: the residual was only wanted for the report
+            } else if (!isfinite(rel)) {
+              st = kNumeric;
+            } else if (rel <= P.tol) {
+              st = kOk;
+            } else if (P.k[sys] >= P.maxit) {
+              st = kNotConverged;
+            } else if (first) {
+              st = kStRunning;
+              next = 1;
+            } else if (P.restarts[sys] >= P.max_restarts) {
+              st = kNotConverged;
+            } else {
+              P.restarts[sys] += 1;
+              st = kStRunning;
+              next = 1;
+            }
+            P.status[sys] = st;
+            set_stage(P, sys, next, seq);
+          });
+      if (!g.sync()) return;
+    }
+    // ---- A: q = A p, alpha
+    ++seq;
+    T = build_tiles(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    if (T == 0) continue;
+    run_phase<1>(
+        P, s_pref, T, g,
+        [&](int, int i, double* v) {
+          const double pi = P.p[i];
+          const double qi = (JAC ? pi : __ldg(P.dg + i) * pi) + row_offdiag(P, P.p, i >> 5, lane);
+          P.q[i] = qi;
+          v[0] = pi * qi;
+        },
+        [&](int sys, const double* sm) {
+          const double rho = P.rho[sys];
+          if (!isfinite(sm[0]) || !isfinite(rho)) {
+            P.status[sys] = kNumeric;
+            set_stage(P, sys, 0, seq);  // residual of the current x, then stop
+          } else if (sm[0] <= 0.0) {
+            P.status[sys] = kBreakdown;
+            set_stage(P, sys, 0, seq);
+          } else {
+            P.alpha[sys] = rho / sm[0];
+          }
+        });
+    if (!g.sync()) return;
+    // ---- B: r -= alpha q, rho' = r^.r^, rr = r.r, beta, stopping test
+    ++seq;
+    T = build_tiles(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    run_phase<2>(
+        P, s_pref, T, g,
+        [&](int sys, int i, double* v) {
+          const double ri = fma(-P.alpha[sys], P.q[i], P.r[i]);
+          P.r[i] = ri;
+          const double d = JAC ? __ldg(P.dg + i) : 1.0;
+          v[0] = ri * ri;
+          v[1] = d * ri * ri;
+        },
+        [&](int sys, const double* sm) {
+          P.beta[sys] = sm[0] / P.rho[sys];
+          P.rho[sys] = sm[0];
+          P.rr[sys] = sm[1];
+          const int k = P.k[sys] + 1;
+          P.k[sys] = k;
+          if (sqrt(sm[1]) <= P.tol * sqrt(P.bb[sys]) || k >= P.maxit) set_stage(P, sys, 3, seq);
+        });
+    if (!g.sync()) return;
+    // ---- C: x += alpha p; p = r + beta p unless the loop ended
+    ++seq;
+    T = build_tiles(P, kMaskC, seq, s_pref, s_scan, &alive);
+    run_phase<0>(
+        P, s_pref, T, g,
+        [&](int sys, int i, double*) {
+          const double pi = P.p[i];
+          P.xh[i] = fma(P.alpha[sys], pi, P.xh[i]);
+          if (eff_stage(__ldcg(P.sstate + sys), seq) == 1) P.p[i] = fma(P.beta[sys], pi, P.r[i]);
+        },
+        [&](int, const double*) {});
+    if (!g.sync()) return;
+  }
+  (void)warp;
+}
+
+// Per-system copies into the concatenated vectors: b^ = D^-1/2 b, x^ = D^1/2 x
+// with Jacobi (b, x unchanged without); zeros on padding rows.
+__global__ void batch_gather_kernel(const double* const* b, const double* const* x, const int64_t* n,
+                                    const int64_t* r0, const int32_t* ntile, const double* disq,
+                                    const double* dsq, int jac, double* bh, double* xh) {
+  const int s = blockIdx.y;
+  const int64_t ns = n[s], base = r0[s], npad = (int64_t)ntile[s] * kTile;
+  const double* bs = b[s];
+  const double* xs = x[s];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = base + i;
+    if (i < ns) {
+      bh[gi] = jac ? bs[i] * disq[gi] : bs[i];
+      xh[gi] = jac ? xs[i] * dsq[gi] : xs[i];
+    } else {
+      bh[gi] = 0.0;
+      xh[gi] = 0.0;
+    }
+  }
+}
+
+// x = D^-1/2 x^ (x^ without Jacobi) back into the caller's vectors; x = 0 for b = 0.
+__global__ void batch_scatter_kernel(double* const* x, const int64_t* n, const int64_t* r0,
+                                     const double* disq, int jac, const double* xh, const int* zero) {
+  const int s = blockIdx.y;
+  const int64_t ns = n[s], base = r0[s];
+  double* xs = x[s];
+  const bool z = zero[s] != 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = base + i;
+    xs[i] = z ? 0.0 : (jac ? xh[gi] * disq[gi] : xh[gi]);
+  }
+}
+
+// Loop state of every system at the start of a solve.
+__global__ void batch_init_kernel(int nsys, double* bb, int* k, int* restarts, int* status, int* zero,
+                                  unsigned long long* sstate, unsigned* cnt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    bb[s] = -1.0;  // "not yet known": the first residual phase records b.b
+    k[s] = 0;
+    restarts[s] = 0;
+    status[s] = kStRunning;
+    zero[s] = 0;
+    sstate[s] = 0ull;  // stage 0, phase 0
+    cnt[s] = 0u;
+  }
+}
+
+// One system's rows into the concatenated slices (thread per padded row):
+// off-diagonal entries of row i in storage order, then padding (column = the
+// row itself, value 0) up to the slice width.  With SCALE the values are
+// A_ij / sqrt(A_ii A_jj), the two scales multiplied first so the scaled
+// matrix stays bitwise symmetric when A is.  col may be null (written with
+// the other value variant).
+template <bool SCALE>
+__global__ void batch_fill_kernel(int64_t n, int64_t npad, int64_t r0, int64_t sl0,
+                                  const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                  const double* __restrict__ vals, const double* __restrict__ ldisq,
+                                  const int32_t* __restrict__ soff, int32_t* col, double* val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = sl0 + (i >> 5), l = i & 31;
+    const int64_t base = (int64_t)soff[sl] * 32 + l;
+    const int w = soff[sl + 1] - soff[sl];
+    int m = 0;
+    if (i < n) {
+      const double si = SCALE ? ldisq[i] : 1.0;
+      for (int k = rowptr[i]; k < rowptr[i + 1] && m < w; ++k) {
+        const int c = colind[k];
+        if ((int64_t)c == i) continue;
+        if (col) col[base + (int64_t)m * 32] = (int32_t)(r0 + c);
+        val[base + (int64_t)m * 32] = SCALE ? vals[k] * (si * ldisq[c]) : vals[k];
+        ++m;
+      }
+    }
+    for (; m < w; ++m) {
+      if (col) col[base + (int64_t)m * 32] = (int32_t)(r0 + i);
+      val[base + (int64_t)m * 32] = 0.0;
+    }
+  }
+}
+
+// Diagonal vectors of one system at its rows of the concatenation: A_ii,
+// sqrt(A_ii), 1/sqrt(A_ii) (1 on padding rows and where A_ii <= 0, which
+// only the unpreconditioned solve accepts).
+__global__ void batch_diag_kernel(int64_t n, int64_t npad, int64_t r0, const double* __restrict__ diag,
+                                  double* gd, double* gdsq, double* gdisq) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = i < n ? diag[i] : 1.0;
+    const bool pos = d > 0.0;
+    const double s = pos ? sqrt(d) : 1.0;
+    gd[r0 + i] = d;
+    gdsq[r0 + i] = s;
+    gdisq[r0 + i] = pos ? 1.0 / s : 1.0;
+  }
+}
+
+// Kernel variants the autotuner chooses from: registers budgeted for 2, 3 or 4
+// resident CTAs per SM (more CTAs hide more memory latency; fewer registers
+// may spill).
+constexpr int kVariants = 3;
+constexpr int kVariantMinBlocks[kVariants] = {2, 3, 4};
+
+const void* batch_kernel(bool jac, int variant) {
+  switch (variant) {
+    case 0: return jac ? (const void*)batch_pcg_kernel<true, 2> : (const void*)batch_pcg_kernel<false, 2>;
+    case 1: return jac ? (const void*)batch_pcg_kernel<true, 3> : (const void*)batch_pcg_kernel<false, 3>;
+    default: return jac ? (const void*)batch_pcg_kernel<true, 4> : (const void*)batch_pcg_kernel<false, 4>;
+  }
+}
+
+unsigned blocks_for(int64_t items) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 4096));
+}
+
+}  // namespace
+
+// Device memory of a batch (owned by its cg_handle).
+struct BatchData {
+  int nsys = 0;
+  std::vector<cg_handle*> sys;     // per-system handles (validation, diagonal)
+  std::vector<int64_t> n, r0;      // rows and first concatenated row of each system
+  std::vector<int32_t> tstart, ntile;
+  int64_t rows = 0;                // padded rows in all
+  int ntiles = 0, nslices = 0;
+  int64_t entries = 0;             // slice entries (multiple of 32)
+  int32_t *d_tstart = nullptr, *d_ntile = nullptr, *soff = nullptr, *col = nullptr;
+  int64_t *d_n = nullptr, *d_r0 = nullptr;
+  double* val[2] = {nullptr, nullptr};  // [precond]: unscaled / Jacobi-scaled
+  double *dg = nullptr, *dsq = nullptr, *disq = nullptr;
+  double *r = nullptr, *p = nullptr, *q = nullptr, *xh = nullptr, *bh = nullptr;
+  double *rho = nullptr, *rr = nullptr, *bb = nullptr, *alpha = nullptr, *beta = nullptr,
+         *relres = nullptr;
+  int *k = nullptr, *restarts = nullptr, *status = nullptr, *zero = nullptr;
+  unsigned long long* sstate = nullptr;
+  unsigned* cnt = nullptr;
+  double* tpart = nullptr;
+  const double** d_b = nullptr;    // the caller's vector pointers, on the device
+  double** d_x = nullptr;
+  void** host_ptrs = nullptr;      // pinned staging of those pointers (2 nsys)
+  int grid_max = 0;                // co-resident CTAs of the most occupant variant
+  int vmax[kVariants] = {};        // co-resident CTAs of each kernel variant
+  int grid_tuned[2] = {0, 0};      // chosen CTAs per precond (0: not yet)
+  int var_tuned[2] = {0, 0};       // chosen kernel variant per precond
+  int tune_chosen[2] = {-1, -1};   // index of the chosen candidate
+  float tune_ms[2][kMaxCand] = {}; // autotuner timings of the candidates
+  int tune_grid[2][kMaxCand] = {};
+  int tune_minb[2][kMaxCand] = {};
+  int tune_count[2] = {0, 0};
+  // graph of one solve: status clear, gather, init, the persistent kernel, scatter
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gkey_jac = -1, gkey_grid = -1, gkey_var = -1, gkey_maxit = -1, gkey_restarts = -1;
+  double gkey_tol = -1.0, gkey_timeout = -1.0;
+  unsigned gkey_skip = 0;
+  std::string graph_refused;       // why graph capture failed (then: direct launches)
+  cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
+  bool ran_graph = false;          // form of the last solve
+  std::vector<int> host_status, host_iters, host_restarts;
+  std::vector<double> host_relres;
+};
+
+void cgi::batch_free(BatchData* b) {
+  if (!b) return;
+  for (cg_handle* h : b->sys) cg_destroy(h);
+  void* dev[] = {b->d_tstart, b->d_ntile, b->soff,     b->col,    b->d_n,  b->d_r0,   b->val[0],
+                 b->val[1],   b->dg,      b->dsq,      b->disq,   b->r,    b->p,      b->q,
+                 b->xh,       b->bh,      b->rho,      b->rr,     b->bb,   b->alpha,  b->beta,
+                 b->relres,   b->k,       b->restarts, b->status, b->zero, b->sstate, b->cnt,
+                 b->tpart,    (void*)b->d_b, (void*)b->d_x};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  delete b;
+}
+
+namespace {
+
+cg_status bfail(cg_handle* h, cg_status s, const std::string& msg) {
+  h->err = msg;
+  return s;
+}
+
+#define CGB_CUDA(h, call)                                                                    \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return bfail((h), e_ == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,          \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+  } while (0)
+
+// The concatenated values for one preconditioner (columns written with the first).
+cg_status ensure_batch_vals(cg_handle* h, bool jac) {
+  BatchData* B = h->batch;
+  if (B->val[jac]) return CG_OK;
+  const bool write_col = !B->val[0] && !B->val[1];
+  CGB_CUDA(h, cudaMalloc(&B->val[jac], sizeof(double) * (size_t)std::max<int64_t>(B->entries, 32)));
+  for (int s = 0; s < B->nsys; ++s) {
+    const cg_handle* hs = B->sys[(size_t)s];
+    const int64_t npad = (int64_t)B->ntile[(size_t)s] * kTile;
+    const int64_t r0 = B->r0[(size_t)s];
+    const int64_t sl0 = (int64_t)B->tstart[(size_t)s] * kWarps;
+    int32_t* col = write_col ? B->col : nullptr;
+    if (jac)
+      batch_fill_kernel<true><<<blocks_for(npad), 256, 0, h->stream>>>(
+          hs->n, npad, r0, sl0, hs->rowptr, hs->colind, hs->vals, B->disq + r0, B->soff, col, B->val[jac]);
+    else
+      batch_fill_kernel<false><<<blocks_for(npad), 256, 0, h->stream>>>(
+          hs->n, npad, r0, sl0, hs->rowptr, hs->colind, hs->vals, B->disq + r0, B->soff, col, B->val[jac]);
+  }
+  CGB_CUDA(h, cudaGetLastError());
+  CGB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return CG_OK;
+}
+
+BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
+  BatchData* B = h->batch;
+  BatchParams P{};
+  P.nsys = B->nsys;
+  P.tstart = B->d_tstart;
+  P.ntile = B->d_ntile;
+  P.soff = B->soff;
+  P.col = B->col;
+  P.val = B->val[jac];
+  P.dg = B->dg;
+  P.r = B->r;
+  P.p = B->p;
+  P.q = B->q;
+  P.xh = B->xh;
+  P.bh = B->bh;
+  P.rho = B->rho;
+  P.rr = B->rr;
+  P.bb = B->bb;
+  P.alpha = B->alpha;
+  P.beta = B->beta;
+  P.relres = B->relres;
+  P.k = B->k;
+  P.restarts = B->restarts;
+  P.status = B->status;
+  P.zero = B->zero;
+  P.sstate = B->sstate;
+  P.cnt = B->cnt;
+  P.tpart = B->tpart;
+  P.tol = tol;
+  P.maxit = maxit;
+  P.max_restarts = h->max_restarts;
+  P.st = h->st;
+  P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
+  P.skip_seq = h->skip_seq;
+  return P;
+}
+
+// The work of one solve on h->stream: clear the status words, gather b and
+// x, reset the systems, the persistent kernel on G CTAs and (unless this is
+// an autotuner trial, which must leave x alone) the scatter of x.
+cudaError_t enqueue_solve(cg_handle* h, cudaStream_t s, bool jac, int var, int G, double tol, int maxit,
+                          bool scatter) {
+  BatchData* B = h->batch;
+  BatchParams P = make_params(h, jac, tol, maxit);
+  const dim3 gg(64, (unsigned)B->nsys);
+  cudaError_t e = cudaMemsetAsync(h->st, 0, sizeof(DevState), s);
+  if (e != cudaSuccess) return e;
+  batch_gather_kernel<<<gg, 256, 0, s>>>(B->d_b, B->d_x, B->d_n, B->d_r0, B->d_ntile, B->disq, B->dsq,
+                                          jac ? 1 : 0, B->bh, B->xh);
+  batch_init_kernel<<<blocks_for(B->nsys), 256, 0, s>>>(B->nsys, B->bb, B->k, B->restarts, B->status,
+                                                         B->zero, B->sstate, B->cnt);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  void* args[] = {&P};
+  e = cudaLaunchCooperativeKernel(batch_kernel(jac, var), dim3((unsigned)G), dim3(kBlock), args, 0, s);
+  if (e != cudaSuccess || !scatter) return e;
+  batch_scatter_kernel<<<gg, 256, 0, s>>>(B->d_x, B->d_n, B->d_r0, B->disq, jac ? 1 : 0, B->xh, B->zero);
+  return cudaGetLastError();
+}
+
+// Run one solve (through the cached graph when use_graph) between the
+// handle's events; the device time goes to *ms.
+cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxit, bool use_graph,
+                    bool scatter, float* ms) {
+  BatchData* B = h->batch;
+  if (use_graph && B->graph_refused.empty()) {
+    const bool same = B->gexec && B->gkey_jac == (int)jac && B->gkey_grid == G && B->gkey_var == var &&
+                      B->gkey_tol == tol &&
+                      B->gkey_maxit == maxit && B->gkey_restarts == h->max_restarts &&
+                      B->gkey_timeout == h->timeout_ms && B->gkey_skip == h->skip_seq;
+    if (!same) {
+      if (B->gexec) cudaGraphExecDestroy(B->gexec);
+      if (B->graph) cudaGraphDestroy(B->graph);
+      B->gexec = nullptr;
+      B->graph = nullptr;
+      B->gkey_jac = -1;
+      // captured on a private stream (the caller's may be the legacy stream, which
+      // cannot capture); the graph is then launched on the caller's stream
+      if (!B->cap_stream) CGB_CUDA(h, cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+      CGB_CUDA(h, cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+      const cudaError_t e = enqueue_solve(h, B->cap_stream, jac, var, G, tol, maxit, true);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(B->cap_stream, &graph);
+      cudaError_t e3 = cudaSuccess;
+      if (e == cudaSuccess && e2 == cudaSuccess) e3 = cudaGraphInstantiate(&B->gexec, graph, 0);
+      if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        // a runtime that cannot capture or instantiate the cooperative launch:
+        // run the same kernels as direct launches from now on
+        if (graph) cudaGraphDestroy(graph);
+        B->gexec = nullptr;
+        cudaGetLastError();
+        B->graph_refused = cudaGetErrorString(e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3));
+        return run_solve(h, jac, var, G, tol, maxit, false, scatter, ms);
+      }
+      B->graph = graph;
+      B->gkey_jac = jac;
+      B->gkey_grid = G;
+      B->gkey_var = var;
+      B->gkey_tol = tol;
+      B->gkey_maxit = maxit;
+      B->gkey_restarts = h->max_restarts;
+      B->gkey_timeout = h->timeout_ms;
+      B->gkey_skip = h->skip_seq;
+    }
+    CGB_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+    CGB_CUDA(h, cudaGraphLaunch(B->gexec, h->stream));
+    CGB_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+    B->ran_graph = true;
+  } else {
+    B->ran_graph = false;
+    CGB_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+    const cudaError_t e = enqueue_solve(h, h->stream, jac, var, G, tol, maxit, scatter);
+    if (e != cudaSuccess)
+      return bfail(h, e == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,
+                   std::string("cg_solve_batch: launch: ") + cudaGetErrorString(e));
+    CGB_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  }
+  CGB_CUDA(h, cudaMemcpyAsync(h->host_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CGB_CUDA(h, cudaStreamSynchronize(h->stream));
+  CGB_CUDA(h, cudaEventElapsedTime(ms, h->ev0, h->ev1));
+  if (h->host_st->abort)
+    return bfail(h, CG_ERR_TIMEOUT, "cg_solve_batch: grid barrier " + std::to_string(h->host_st->err_barrier) +
+                                        " timed out in CTA " + std::to_string(h->host_st->err_cta));
+  return CG_OK;
+}
+
+// Autotuner: the kernel variant (registers budgeted for 2, 3 or 4 CTAs per SM)
+// and grid size for this handle and preconditioner, picked by timing short
+// trial solves (at most kTrialIters iterations each, x left untouched) of the
+// caller's own systems; the choice is kept in the handle.  Candidates: every
+// variant at its full residency, and the 2-CTA variant at one CTA per SM.
+constexpr int kTrialIters = 40;
+
+cg_status autotune(cg_handle* h, bool jac, double tol, int maxit) {
+  BatchData* B = h->batch;
+  std::vector<std::pair<int, int>> cand;  // (variant, grid)
+  for (int v = 0; v < kVariants; ++v)
+    if (B->vmax[v] > 0) cand.emplace_back(v, B->vmax[v]);
+  if (B->vmax[0] > h->sm_count) cand.emplace_back(0, h->sm_count);
+  float best = 3.0e38f;
+  int best_i = 0, nt = 0;
+  for (size_t c = 0; c < cand.size() && nt < kMaxCand; ++c) {
+    float ms = 0.0f;
+    const cg_status ts = run_solve(h, jac, cand[c].first, cand[c].second, tol,
+                                   std::min<int32_t>(maxit, kTrialIters), false, false, &ms);
+    if (ts != CG_OK) return ts;
+    B->tune_ms[jac][nt] = ms;
+    B->tune_grid[jac][nt] = cand[c].second;
+    B->tune_minb[jac][nt] = kVariantMinBlocks[cand[c].first];
+    if (ms < best) {
+      best = ms;
+      best_i = nt;
+    }
+    ++nt;
+  }
+  B->tune_count[jac] = nt;
+  B->tune_chosen[jac] = best_i;
+  B->var_tuned[jac] = cand[(size_t)best_i].first;
+  B->grid_tuned[jac] = cand[(size_t)best_i].second;
+  return CG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* rowptr,
+                          const int32_t* const* colind, const double* const* vals, cg_handle** out) {
+  if (!out) {
+    cgi::set_create_error("cg_batch_create: out is NULL");
+    return CG_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (nsys <= 0 || nsys > kMaxBatch) {
+    cgi::set_create_error("cg_batch_create: nsys must be in [1, " + std::to_string(kMaxBatch) + "]");
+    return CG_ERR_INVALID;
+  }
+  if (!n || !rowptr || !colind || !vals) {
+    cgi::set_create_error("cg_batch_create: NULL array");
+    return CG_ERR_INVALID;
+  }
+  for (int s = 0; s < nsys; ++s)
+    if (n[s] <= 0 || n[s] >= INT32_MAX) {
+      cgi::set_create_error("cg_batch_create: system " + std::to_string(s) + " has n outside [1, 2^31-1)");
+      return CG_ERR_INVALID;
+    }
+  cg_handle* h = new cg_handle();
+  BatchData* B = new BatchData();
+  h->batch = B;
+  auto bail = [&](cg_status s) {
+    cgi::set_create_error(h->err);
+    cg_destroy(h);
+    return s;
+  };
+#define CGB_CREATE(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bail(bfail(h, e_ == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,     \
+                        std::string(#call) + ": " + cudaGetErrorString(e_)));              \
+  } while (0)
+  int dev = 0;
+  CGB_CREATE(cudaGetDevice(&dev));
+  CGB_CREATE(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  CGB_CREATE(cudaMalloc(&h->st, sizeof(DevState)));
+  CGB_CREATE(cudaMallocHost(&h->host_st, sizeof(DevState)));
+  CGB_CREATE(cudaEventCreate(&h->ev0));
+  CGB_CREATE(cudaEventCreate(&h->ev1));
+  B->nsys = nsys;
+  B->n.assign(n, n + nsys);
+  B->r0.resize((size_t)nsys);
+  B->tstart.resize((size_t)nsys);
+  B->ntile.resize((size_t)nsys);
+  int64_t rows = 0, tiles = 0, nnz = 0;
+  for (int s = 0; s < nsys; ++s) {
+    cg_handle* hs = nullptr;
+    const cg_status st = cg_create(n[s], rowptr[s], colind[s], vals[s], &hs);
+    if (st != CG_OK)
+      return bail(bfail(h, st, "cg_batch_create: system " + std::to_string(s) + ": " + cg_last_error(nullptr)));
+    B->sys.push_back(hs);
+    B->r0[(size_t)s] = rows;
+    B->tstart[(size_t)s] = (int32_t)tiles;
+    const int64_t nt = (n[s] + kTile - 1) / kTile;
+    B->ntile[(size_t)s] = (int32_t)nt;
+    rows += nt * kTile;
+    tiles += nt;
+    nnz += hs->nnz;
+    if (rows >= INT32_MAX) return bail(bfail(h, CG_ERR_INVALID, "cg_batch_create: 2^31 rows or more in all"));
+  }
+  B->rows = rows;
+  B->ntiles = (int)tiles;
+  B->nslices = (int)(tiles * kWarps);
+  h->n = rows;
+  h->nnz = nnz;
+  // slice widths: the longest off-diagonal row of each 32-row slice
+  std::vector<int32_t> soff((size_t)B->nslices + 1, 0);
+  int64_t off = 0;
+  for (int s = 0; s < nsys; ++s) {
+    const cg_handle* hs = B->sys[(size_t)s];
+    std::vector<int32_t> nd((size_t)hs->n);
+    CGB_CREATE(cudaMemcpy(nd.data(), hs->ndiag, sizeof(int32_t) * (size_t)hs->n, cudaMemcpyDeviceToHost));
+    const std::vector<int32_t>& rp = hs->host_rowptr;
+    const int nsl = B->ntile[(size_t)s] * kWarps;
+    for (int j = 0; j < nsl; ++j) {
+      int w = 0;
+      const int64_t i1 = std::min<int64_t>(hs->n, (int64_t)j * 32 + 32);
+      for (int64_t i = (int64_t)j * 32; i < i1; ++i)
+        w = std::max(w, rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i]);
+      off += w;
+      soff[(size_t)B->tstart[(size_t)s] * kWarps + j + 1] = (int32_t)off;
+    }
+    if (off * 32 >= INT32_MAX) return bail(bfail(h, CG_ERR_INVALID, "cg_batch_create: matrices too large"));
+  }
+  B->entries = off * 32;
+  const size_t nv = (size_t)rows, ns = (size_t)nsys;
+  CGB_CREATE(cudaMalloc(&B->soff, sizeof(int32_t) * soff.size()));
+  CGB_CREATE(cudaMemcpy(B->soff, soff.data(), sizeof(int32_t) * soff.size(), cudaMemcpyHostToDevice));
+  CGB_CREATE(cudaMalloc(&B->col, sizeof(int32_t) * (size_t)std::max<int64_t>(B->entries, 32)));
+  CGB_CREATE(cudaMalloc(&B->d_tstart, sizeof(int32_t) * ns));
+  CGB_CREATE(cudaMalloc(&B->d_ntile, sizeof(int32_t) * ns));
+  CGB_CREATE(cudaMalloc(&B->d_n, sizeof(int64_t) * ns));
+  CGB_CREATE(cudaMalloc(&B->d_r0, sizeof(int64_t) * ns));
+  CGB_CREATE(cudaMemcpy(B->d_tstart, B->tstart.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+  CGB_CREATE(cudaMemcpy(B->d_ntile, B->ntile.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+  CGB_CREATE(cudaMemcpy(B->d_n, B->n.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice));
+  CGB_CREATE(cudaMemcpy(B->d_r0, B->r0.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice));
+  for (double** v : {&B->dg, &B->dsq, &B->disq, &B->r, &B->p, &B->q, &B->xh, &B->bh})
+    CGB_CREATE(cudaMalloc(v, sizeof(double) * nv));
+  for (double** v : {&B->rho, &B->rr, &B->bb, &B->alpha, &B->beta, &B->relres})
+    CGB_CREATE(cudaMalloc(v, sizeof(double) * ns));
+  for (int** v : {&B->k, &B->restarts, &B->status, &B->zero}) CGB_CREATE(cudaMalloc(v, sizeof(int) * ns));
+  CGB_CREATE(cudaMalloc(&B->sstate, sizeof(unsigned long long) * ns));
+  CGB_CREATE(cudaMalloc(&B->cnt, sizeof(unsigned) * ns));
+  CGB_CREATE(cudaMalloc(&B->tpart, sizeof(double) * (size_t)tiles * kWarps * kNP));
+  CGB_CREATE(cudaMalloc((void**)&B->d_b, sizeof(double*) * ns));
+  CGB_CREATE(cudaMalloc((void**)&B->d_x, sizeof(double*) * ns));
+  CGB_CREATE(cudaMallocHost((void**)&B->host_ptrs, sizeof(void*) * 2 * ns));
+  for (int s = 0; s < nsys; ++s) {
+    const cg_handle* hs = B->sys[(size_t)s];
+    const int64_t npad = (int64_t)B->ntile[(size_t)s] * kTile;
+    batch_diag_kernel<<<blocks_for(npad), 256>>>(hs->n, npad, B->r0[(size_t)s], hs->diag, B->dg, B->dsq,
+                                                 B->disq);
+  }
+  CGB_CREATE(cudaGetLastError());
+  CGB_CREATE(cudaDeviceSynchronize());
+  for (int v = 0; v < kVariants; ++v) {
+    int per_sm1 = 0, per_sm2 = 0;
+    CGB_CREATE(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, batch_kernel(true, v), kBlock, 0));
+    CGB_CREATE(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, batch_kernel(false, v), kBlock, 0));
+    B->vmax[v] = std::min(per_sm1, per_sm2) * h->sm_count;
+    B->grid_max = std::max(B->grid_max, B->vmax[v]);
+  }
+#undef CGB_CREATE
+  if (B->grid_max <= 0) return bail(bfail(h, CG_ERR_CUDA, "cg_batch_create: occupancy query failed"));
+  h->grid_max = B->grid_max;
+  B->host_status.assign(ns, 0);
+  B->host_iters.assign(ns, 0);
+  B->host_restarts.assign(ns, 0);
+  B->host_relres.assign(ns, 0.0);
+  *out = h;
+  return CG_OK;
+}
+
+cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x, double tol, int32_t maxit,
+                         int32_t precond, int32_t precision, int32_t* iters, double* relres) {
+  if (!h) return CG_ERR_INVALID;
+  BatchData* B = h->batch;
+  if (!B) return bfail(h, CG_ERR_INVALID, "cg_solve_batch: not a batch handle (made by cg_create)");
+  h->last = cg_solve_info{};
+  if (!b || !x || !(tol >= 0.0) || maxit < 0)
+    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: NULL vector array, tol < 0 or maxit < 0");
+  if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)
+    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: unknown preconditioner");
+  if (precision != CG_PREC_FP64)
+    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: batches solve in CG_PREC_FP64 only");
+  if (h->loop_mode == 3)
+    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: CG_OPT_LOOP_MODE 3 (unrolled) has no batch form");
+  const bool jac = precond == CG_PRECOND_JACOBI;
+  for (int s = 0; s < B->nsys; ++s) {
+    if (!b[s] || !x[s]) return bfail(h, CG_ERR_INVALID, "cg_solve_batch: NULL vector of system " + std::to_string(s));
+    if (jac && !B->sys[(size_t)s]->jacobi_ok)
+      return bfail(h, CG_ERR_INVALID,
+                   "cg_solve_batch: Jacobi needs a positive diagonal (system " + std::to_string(s) + ")");
+  }
+  cg_status vs = ensure_batch_vals(h, jac);
+  if (vs != CG_OK) return vs;
+  const size_t ns = (size_t)B->nsys;
+  // the previous solve's copies out of host_ptrs have completed (it synchronised)
+  std::memcpy(B->host_ptrs, b, sizeof(void*) * ns);
+  std::memcpy(B->host_ptrs + ns, x, sizeof(void*) * ns);
+  CGB_CUDA(h, cudaMemcpyAsync(B->d_b, B->host_ptrs, sizeof(void*) * ns, cudaMemcpyHostToDevice, h->stream));
+  CGB_CUDA(h, cudaMemcpyAsync(B->d_x, B->host_ptrs + ns, sizeof(void*) * ns, cudaMemcpyHostToDevice, h->stream));
+  int G = 0, var = 0;
+  if (h->grid_opt > 0) {
+    // a forced grid runs on the variant with the most registers that can hold it
+    G = std::min(h->grid_opt, B->grid_max);
+    while (var + 1 < kVariants && B->vmax[var] < G) ++var;
+  } else {
+    if (B->grid_tuned[jac] == 0) {
+      const cg_status ts = autotune(h, jac, tol, maxit);
+      if (ts != CG_OK) return ts;
+    }
+    G = B->grid_tuned[jac];
+    var = B->var_tuned[jac];
+  }
+  const bool use_graph = h->loop_mode != 1;
+  float ms = 0.0f;
+  const cg_status rs = run_solve(h, jac, var, G, tol, maxit, use_graph, true, &ms);
+  if (rs != CG_OK) return rs;
+  CGB_CUDA(h, cudaMemcpyAsync(B->host_iters.data(), B->k, sizeof(int) * ns, cudaMemcpyDeviceToHost, h->stream));
+  CGB_CUDA(h, cudaMemcpyAsync(B->host_restarts.data(), B->restarts, sizeof(int) * ns, cudaMemcpyDeviceToHost, h->stream));
+  CGB_CUDA(h, cudaMemcpyAsync(B->host_relres.data(), B->relres, sizeof(double) * ns, cudaMemcpyDeviceToHost, h->stream));
+  CGB_CUDA(h, cudaMemcpyAsync(B->host_status.data(), B->status, sizeof(int) * ns, cudaMemcpyDeviceToHost, h->stream));
+  CGB_CUDA(h, cudaStreamSynchronize(h->stream));
+  int worst_err = 0, nconv = 0, maxk = 0, rmax = 0;
+  int64_t bytes = 0;
+  double relmax = 0.0;
+  for (size_t s = 0; s < ns; ++s) {
+    const int st = B->host_status[s], k = B->host_iters[s];
+    if (iters) iters[s] = k;
+    if (relres) relres[s] = B->host_relres[s];
+    if (st < 0 && (worst_err == 0 || st < worst_err)) worst_err = st;
+    if (st == CG_NOT_CONVERGED) ++nconv;
+    maxk = std::max(maxk, k);
+    rmax = std::max(rmax, B->host_restarts[s]);
+    relmax = std::max(relmax, B->host_relres[s]);
+    const cg_handle* hs = B->sys[s];
+    // the single-system traffic model per iteration: CSR matrix and the loop's vectors
+    bytes += (12 * hs->nnz + 4 * (hs->n + 1) + (jac ? 104 : 88) * hs->n) * (int64_t)k;
+  }
+  cg_solve_info& I = h->last;
+  I.status = worst_err ? (cg_status)worst_err : (nconv ? CG_NOT_CONVERGED : CG_OK);
+  I.iters = maxk;
+  I.restarts = rmax;
+  I.grid_ctas = G;
+  I.relres_true = relmax;
+  I.relres_rec = relmax;
+  I.kernel_ms = ms;
+  I.bytes_moved = bytes;
+  I.kernel_bytes_per_iter = 0;
+  I.loop_form = B->ran_graph ? 2 : 1;
+  I.kernel_launches = 4;  // gather, init, the persistent kernel, scatter
+  if (worst_err)
+    return bfail(h, (cg_status)I.status, std::string("cg_solve_batch: at least one system ended with ") +
+                                             cg_status_string(worst_err));
+  return (cg_status)I.status;
+}
+
+cg_status cg_batch_get_system(const cg_handle* h, int32_t s, int32_t* status, int32_t* iters, int32_t* restarts,
+                              double* relres) {
+  if (!h || !h->batch || s < 0 || s >= h->batch->nsys) return CG_ERR_INVALID;
+  const BatchData* B = h->batch;
+  if (status) *status = B->host_status[(size_t)s];
+  if (iters) *iters = B->host_iters[(size_t)s];
+  if (restarts) *restarts = B->host_restarts[(size_t)s];
+  if (relres) *relres = B->host_relres[(size_t)s];
+  return CG_OK;
+}
+
+cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* count, int32_t* grids,
+                              int32_t* ctas_per_sm, float* ms, int32_t* chosen) {
+  if (!h || !h->batch || (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)) return CG_ERR_INVALID;
+  const BatchData* B = h->batch;
+  const int j = precond == CG_PRECOND_JACOBI;
+  if (count) *count = B->tune_count[j];
+  for (int c = 0; c < B->tune_count[j]; ++c) {
+    if (grids) grids[c] = B->tune_grid[j][c];
+    if (ctas_per_sm) ctas_per_sm[c] = B->tune_minb[j][c];
+    if (ms) ms[c] = B->tune_ms[j][c];
+  }
+  if (chosen) *chosen = B->tune_chosen[j];
+  return CG_OK;
+}
+
+}  // extern "C"
