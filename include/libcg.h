@@ -179,7 +179,7 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
  * solution.  One persistent cooperative kernel, captured with its gather and
  * scatter kernels in a CUDA graph (CG_OPT_LOOP_MODE 1: direct launch),
  * iterates all systems; a converged system drops out of the tile schedule.
- * The kernel variant (registers budgeted for 2, 3 or 4 resident CTAs per
+ * The kernel variant (registers budgeted for 3, 4 or 5 resident CTAs per
  * SM) and grid size come from an autotuner that times short trial solves of
  * these systems at the first solve of each preconditioner (x is not touched
  * by the trials; the choice is kept in the handle); CG_OPT_GRID_CTAS > 0

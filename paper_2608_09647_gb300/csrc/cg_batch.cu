@@ -41,22 +41,28 @@ using namespace cg;
 
 namespace {
 
-constexpr int kTile = kBlock;        // rows per tile (kWarps slices)
+constexpr int kTile = kBlock;        // rows per tile (kWarps slices, one per warp)
+constexpr int kGroup = 8;            // tiles per reduction group (2048 rows)
 constexpr int kMaxBatch = CG_BATCH_MAX_SYSTEMS;
-constexpr int kNP = 4;               // partial sums per slice
+constexpr int kNP = 4;               // partial sums per (group, warp)
 constexpr int kStRunning = 100;      // status of a system still being solved
 constexpr int kMaxCand = 8;          // autotuner candidates
+constexpr double kRrMarginB = 64.0;  // r.D r is computed while dmin r^.r^ <= 64 stop^2
 
-// stage masks of the phases
-constexpr unsigned kMaskR = (1u << 0) | (1u << 3);
-constexpr unsigned kMaskAB = 1u << 1;
-constexpr unsigned kMaskC = (1u << 1) | (1u << 3);
-constexpr unsigned kMaskAlive = (1u << 0) | (1u << 1) | (1u << 3);
+// stages and the phases that take them
+constexpr int kStResidual = 0, kStIter = 1, kStDone = 2, kStLastX = 3, kStRrPending = 4;
+constexpr unsigned kMaskR = (1u << kStResidual) | (1u << kStLastX);
+constexpr unsigned kMaskAB = 1u << kStIter;
+constexpr unsigned kMaskC = (1u << kStIter) | (1u << kStLastX) | (1u << kStRrPending);
+constexpr unsigned kMaskAlive = ~(1u << kStDone);
 
 struct BatchParams {
   int nsys;
   const int32_t* __restrict__ tstart;  // first tile of each system
   const int32_t* __restrict__ ntile;   // tiles of each system
+  const int32_t* __restrict__ gstart;  // first reduction group of each system
+  const int32_t* __restrict__ ngroup;  // reduction groups of each system
+  const double* __restrict__ dmin;     // smallest A_ii of each system
   const int32_t* __restrict__ soff;    // slice offsets (units of 32 entries)
   const int32_t* __restrict__ col;     // global (concatenated) column of each entry
   const double* __restrict__ val;
@@ -64,10 +70,10 @@ struct BatchParams {
   double *r, *p, *q, *xh;
   const double* __restrict__ bh;
   double *rho, *rr, *bb, *alpha, *beta, *relres;
-  int *k, *restarts, *status, *zero;
+  int *k, *restarts, *status, *zero, *wrr;
   unsigned long long* sstate;          // phase << 16 | stage before << 8 | stage after
-  unsigned* cnt;                       // tiles of the system finished in this phase
-  double* tpart;                       // kNP partials per slice
+  unsigned* cnt;                       // groups of the system finished in this phase
+  double* tpart;                       // kNP partials per (group, warp)
   double tol;
   int maxit, max_restarts;
   DevState* st;
@@ -79,92 +85,108 @@ __device__ __forceinline__ int eff_stage(unsigned long long w, unsigned seq) {
   return ((unsigned)(w >> 16) == seq) ? (int)((w >> 8) & 0xff) : (int)(w & 0xff);
 }
 
-// Exclusive prefix sum (in s_pref) of the tiles of the systems whose stage,
-// as seen in phase seq, is in `mask`; returns their total.  *alive gets
-// whether any system is still unfinished.
-__device__ int build_tiles(const BatchParams& P, unsigned mask, unsigned seq, int* s_pref, int* s_scan,
-                           bool* alive) {
-  const int t = threadIdx.x;
+// Exclusive prefix sum (in s_pref) of the reduction groups of the systems
+// whose stage, as seen in phase seq, is in `mask`; returns their total.
+// *alive gets whether any system is still unfinished.  Thread t owns a
+// contiguous run of systems; the runs' totals are scanned with warp shuffles.
+__device__ int build_list(const BatchParams& P, unsigned mask, unsigned seq, int* s_pref, int* s_warp,
+                          bool* alive) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int per = (P.nsys + kBlock - 1) / kBlock;
   const int s0 = min(P.nsys, t * per), s1 = min(P.nsys, s0 + per);
   int c = 0, live = 0;
   for (int s = s0; s < s1; ++s) {
     const unsigned sbit = 1u << eff_stage(__ldcg(P.sstate + s), seq);
-    const int cs = (sbit & mask) ? P.ntile[s] : 0;
+    const int cs = (sbit & mask) ? P.ngroup[s] : 0;
     live |= (sbit & kMaskAlive) != 0;
     s_pref[s] = cs;
     c += cs;
   }
-  s_scan[t] = c;
-  *alive = __syncthreads_or(live) != 0;
-  for (int off = 1; off < kBlock; off <<= 1) {
-    const int v = t >= off ? s_scan[t - off] : 0;
-    __syncthreads();
-    s_scan[t] += v;
-    __syncthreads();
+  int inc = c;  // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
   }
-  int base = s_scan[t] - c;
+  if (lane == 31) s_warp[warp] = inc;
+  *alive = __syncthreads_or(live) != 0;
+  int wbase = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const int v = s_warp[w];
+    wbase += w < warp ? v : 0;
+    total += v;
+  }
+  int base = wbase + inc - c;
   for (int s = s0; s < s1; ++s) {
     const int cs = s_pref[s];
     s_pref[s] = base;
     base += cs;
   }
-  const int total = s_scan[kBlock - 1];
   __syncthreads();
   return total;
 }
 
-// Entry j < total of the phase's tile list -> (system, global tile).  The
-// owner is the last system whose prefix is <= j (systems without tiles in
-// the phase share the prefix of their successor, which is larger than j).
-__device__ __forceinline__ void tile_of(const BatchParams& P, const int* s_pref, int j, int* sys, int* gt) {
+// The system owning entry j of the phase's list: the last system whose
+// prefix is <= j (systems without groups in the phase share the prefix of
+// their successor, which is larger than j).
+__device__ __forceinline__ int system_of(const BatchParams& P, const int* s_pref, int j) {
   int lo = 0, hi = P.nsys - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (s_pref[mid] <= j) lo = mid;
     else hi = mid - 1;
   }
-  *sys = lo;
-  *gt = P.tstart[lo] + (j - s_pref[lo]);
+  return lo;
 }
 
-// Off-diagonal part of one row of slice sl: sum over the slice width of
-// val * v[col] (loads issued kUnroll at a time).
-__device__ __forceinline__ double row_offdiag(const BatchParams& P, const double* v, int sl, int lane) {
+// acc + off-diagonal part of one row of slice sl: the sum over the slice
+// width of val * v[col], all loads of a slice issued together (widths 4 and
+// 8, those of the 5- and 9-point stencils, unrolled exactly).
+template <int W>
+__device__ __forceinline__ double slice_row(const int32_t* __restrict__ cp, const double* __restrict__ vp,
+                                            const double* __restrict__ v, double acc) {
+  int c[W];
+  double a[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) {
+    c[m] = ld_stream(cp + m * 32);
+    a[m] = ld_stream(vp + m * 32);
+  }
+#pragma unroll
+  for (int m = 0; m < W; ++m) acc = fma(a[m], v[c[m]], acc);
+  return acc;
+}
+
+__device__ __forceinline__ double row_spmv(const BatchParams& P, const double* __restrict__ v, int i,
+                                           double acc) {
+  const int sl = i >> 5, lane = i & 31;
   const int o0 = __ldg(P.soff + sl);
   const int w = __ldg(P.soff + sl + 1) - o0;
   const int32_t* cp = P.col + (int64_t)o0 * 32 + lane;
   const double* vp = P.val + (int64_t)o0 * 32 + lane;
-  double acc = 0.0;
-  for (int m0 = 0; m0 < w; m0 += kUnroll) {
-    int c[kUnroll];
-    double a[kUnroll], x[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (m0 + u < w) {
-        c[u] = ld_stream(cp + (m0 + u) * 32);
-        a[u] = ld_stream(vp + (m0 + u) * 32);
-      }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (m0 + u < w) x[u] = v[c[u]];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u)
-      if (m0 + u < w) acc = fma(a[u], x[u], acc);
+  if (w == 8) return slice_row<8>(cp, vp, v, acc);
+  if (w == 4) return slice_row<4>(cp, vp, v, acc);
+  for (int m0 = 0; m0 < w; m0 += 4) {
+    if (m0 + 4 <= w) {
+      acc = slice_row<4>(cp + m0 * 32, vp + m0 * 32, v, acc);
+    } else {
+      for (int m = m0; m < w; ++m) acc = fma(ld_stream(vp + m * 32), v[ld_stream(cp + m * 32)], acc);
+    }
   }
   return acc;
 }
 
-// Sum of a system's slice partials in slice order (warp 0), given to every thread.
+// Sum of a system's (group, warp) partials in order (warp 0), given to every thread.
 template <int NV>
 __device__ __forceinline__ void system_sum(const BatchParams& P, int sys, double (&out)[NV]) {
   __shared__ double s_out[NV];
   if (threadIdx.x < 32) {
-    const int s0 = P.tstart[sys] * kWarps, ns = P.ntile[sys] * kWarps;
+    const int p0 = P.gstart[sys] * kWarps, np = P.ngroup[sys] * kWarps;
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       double a = 0.0;
-      for (int t = threadIdx.x; t < ns; t += 32) a += __ldcg(P.tpart + (size_t)(s0 + t) * kNP + j);
+      for (int t = threadIdx.x; t < np; t += 32) a += __ldcg(P.tpart + (size_t)(p0 + t) * kNP + j);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       if (threadIdx.x == 0) s_out[j] = a;
@@ -182,54 +204,62 @@ __device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int sta
   P.sstate[sys] = ((unsigned long long)seq << 16) | (before << 8) | (unsigned long long)stage;
 }
 
-// One phase over the tile list [0, T) of the current phase.  CTA c takes the
-// contiguous chunk [c T / G, (c+1) T / G), which spans few systems.  For each
-// tile, row(sys, i, v) handles row i (one thread per row) and returns NV
-// values to be summed over the system; each warp reduces its slice and
-// stores one partial per value.  When the CTA leaves a system's segment of
-// its chunk it adds the segment's tile count to the system's counter; the
-// CTA that completes the count sums the system's slice partials in slice
-// order (independent of G) and calls done(sys, sums) in thread 0.
-template <int NV, class Row, class Done>
+// One phase over its list of reduction groups [0, T).  CTA c takes the
+// contiguous chunk [c T / G, (c+1) T / G), which spans few systems.  At the
+// start of each system's segment begin(sys) loads the system's scalars and
+// says whether its sums are wanted.  For every row i of a group, row(i, acc)
+// does the row's work and adds its NV contributions to the thread's
+// accumulators; the group's sums are then reduced per warp (xor tree) and
+// stored.  Leaving a segment, the CTA adds its group count to the system's
+// counter; the CTA that completes the count sums the system's partials in
+// (group, warp) order, independent of G, and calls done(sys, sums) in thread 0.
+template <int NV, class Begin, class Row, class Done>
 __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
-                                          Row row, Done done) {
+                                          Begin begin, Row row, Done done) {
   __shared__ int s_last;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int j1 = (int)((int64_t)T * (g.cta + 1) / g.G);
   int j = (int)((int64_t)T * g.cta / g.G);
   while (j < j1) {
-    int sys, gt;
-    tile_of(P, s_pref, j, &sys, &gt);
-    const int je = min(j1, s_pref[sys] + P.ntile[sys]);  // end of this system's segment
-    for (int jj = j; jj < je; ++jj, ++gt) {
-      double v[NV > 0 ? NV : 1];
-      row(sys, gt * kTile + t, v);
-      if constexpr (NV > 0) {
+    const int sys = system_of(P, s_pref, j);
+    const int je = min(j1, s_pref[sys] + P.ngroup[sys]);  // end of this system's segment
+    const bool sums = begin(sys);
+    const int tend = P.tstart[sys] + P.ntile[sys];
+    for (int jj = j; jj < je; ++jj) {
+      const int grp = jj - s_pref[sys];
+      const int t0 = P.tstart[sys] + grp * kGroup, t1 = min(t0 + kGroup, tend);
+      double acc[NV > 0 ? NV : 1];
+#pragma unroll
+      for (int k = 0; k < (NV > 0 ? NV : 1); ++k) acc[k] = 0.0;
+#pragma unroll 4
+      for (int gt = t0; gt < t1; ++gt) row(gt * kTile + t, acc);
+      if (NV > 0 && sums) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+          for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
         }
         if (lane == 0) {
+          double* dst = P.tpart + ((size_t)(P.gstart[sys] + grp) * kWarps + warp) * kNP;
 #pragma unroll
-          for (int k = 0; k < NV; ++k) P.tpart[((size_t)gt * kWarps + warp) * kNP + k] = v[k];
+          for (int k = 0; k < NV; ++k) dst[k] = acc[k];
         }
       }
     }
-    if constexpr (NV > 0) {
+    if (NV > 0 && sums) {
       if (lane == 0) __threadfence();  // partials visible before the count
       __syncthreads();
       if (t == 0) {
         const unsigned add = (unsigned)(je - j);
         const unsigned prev = atomicAdd(P.cnt + sys, add);
-        const int last = prev + add == (unsigned)P.ntile[sys];
+        const int last = prev + add == (unsigned)P.ngroup[sys];
         if (last) P.cnt[sys] = 0u;  // reset for the next phase (after its barrier)
         __threadfence();
         s_last = last;
       }
       __syncthreads();
       if (s_last) {
-        double sm[NV];
+        double sm[NV > 0 ? NV : 1];
         system_sum<NV>(P, sys, sm);
         if (t == 0) done(sys, sm);
       }
@@ -242,30 +272,37 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
 template <bool JAC, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) {
   __shared__ int s_pref[kMaxBatch];
-  __shared__ int s_scan[kBlock];
+  __shared__ int s_scan[kWarps];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* __restrict__ r = P.r;
+  double* __restrict__ p = P.p;
+  double* __restrict__ q = P.q;
+  double* __restrict__ xh = P.xh;
+  const double* __restrict__ bh = P.bh;
+  const double* __restrict__ dg = P.dg;
+  double c_alpha = 0.0, c_beta = 0.0;  // scalars of the current segment's system
+  bool c_flag = false, c_sum = false;
   unsigned seq = 0;  // phase number; the initial stage words carry 0
   for (;;) {
     // ---- R: residual of the stage 0 / 3 systems, their test, (re)start
     ++seq;
     bool alive = false;
-    int T = build_tiles(P, kMaskR, seq, s_pref, s_scan, &alive);
+    int T = build_list(P, kMaskR, seq, s_pref, s_scan, &alive);
     if (!alive) break;
     if (T > 0) {
       run_phase<3>(
-          P, s_pref, T, g,
-          [&](int, int i, double* v) {
-            const double xi = P.xh[i];
-            const double ax = (JAC ? xi : __ldg(P.dg + i) * xi) + row_offdiag(P, P.xh, i >> 5, lane);
-            const double bi = P.bh[i];
-            const double ri = bi - ax;
-            P.r[i] = ri;
-            P.p[i] = ri;
-            const double d = JAC ? __ldg(P.dg + i) : 1.0;
-            v[0] = ri * ri;  // r^.r^ = r.z
-            v[1] = d * ri * ri;  // r.r
-            v[2] = d * bi * bi;  // b.b
+          P, s_pref, T, g, [&](int) { return true; },
+          [&](int i, double* acc) {
+            const double xi = xh[i];
+            const double ri_ax = row_spmv(P, xh, i, JAC ? xi : __ldg(dg + i) * xi);
+            const double bi = bh[i];
+            const double ri = bi - ri_ax;
+            r[i] = ri;
+            p[i] = ri;
+            const double d = JAC ? __ldg(dg + i) : 1.0;
+            acc[0] = fma(ri, ri, acc[0]);      // r^.r^ = r.z
+            acc[1] = fma(d * ri, ri, acc[1]);  // r.r
+            acc[2] = fma(d * bi, bi, acc[2]);  // b.b
           },
           [&](int sys, const double* sm) {
             const bool first = P.bb[sys] < 0.0;
@@ -275,7 +312,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
             P.relres[sys] = rel;
             P.rho[sys] = sm[0];
             P.rr[sys] = sm[1];
-            int st = P.status[sys], next = 2;
+            P.wrr[sys] = JAC && P.dmin[sys] * sm[0] <= kRrMarginB * P.tol * P.tol * bb;
+            int st = P.status[sys], next = kStDone;
             if (bb == 0.0) {
               st = kOk;
               P.zero[sys] = 1;
@@ -289,13 +327,13 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
               st = kNotConverged;
             } else if (first) {
               st = kStRunning;
-              next = 1;
+              next = kStIter;
             } else if (P.restarts[sys] >= P.max_restarts) {
               st = kNotConverged;
             } else {
               P.restarts[sys] += 1;
               st = kStRunning;
-              next = 1;
+              next = kStIter;
             }
             P.status[sys] = st;
             set_stage(P, sys, next, seq);
@@ -304,64 +342,98 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     }
     // ---- A: q = A p, alpha
     ++seq;
-    T = build_tiles(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
     if (T == 0) continue;
     run_phase<1>(
-        P, s_pref, T, g,
-        [&](int, int i, double* v) {
-          const double pi = P.p[i];
-          const double qi = (JAC ? pi : __ldg(P.dg + i) * pi) + row_offdiag(P, P.p, i >> 5, lane);
-          P.q[i] = qi;
-          v[0] = pi * qi;
+        P, s_pref, T, g, [&](int) { return true; },
+        [&](int i, double* acc) {
+          const double pi = p[i];
+          const double qi = row_spmv(P, p, i, JAC ? pi : __ldg(dg + i) * pi);
+          q[i] = qi;
+          acc[0] = fma(pi, qi, acc[0]);
         },
         [&](int sys, const double* sm) {
           const double rho = P.rho[sys];
           if (!isfinite(sm[0]) || !isfinite(rho)) {
             P.status[sys] = kNumeric;
-            set_stage(P, sys, 0, seq);  // residual of the current x, then stop
+            set_stage(P, sys, kStResidual, seq);  // residual of the current x, then stop
           } else if (sm[0] <= 0.0) {
             P.status[sys] = kBreakdown;
-            set_stage(P, sys, 0, seq);
+            set_stage(P, sys, kStResidual, seq);
           } else {
             P.alpha[sys] = rho / sm[0];
           }
         });
     if (!g.sync()) return;
-    // ---- B: r -= alpha q, rho' = r^.r^, rr = r.r, beta, stopping test
+    // ---- B: r -= alpha q, rho' = r^.r^, r.r when near the stopping band, beta, test
     ++seq;
-    T = build_tiles(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
     run_phase<2>(
         P, s_pref, T, g,
-        [&](int sys, int i, double* v) {
-          const double ri = fma(-P.alpha[sys], P.q[i], P.r[i]);
-          P.r[i] = ri;
-          const double d = JAC ? __ldg(P.dg + i) : 1.0;
-          v[0] = ri * ri;
-          v[1] = d * ri * ri;
+        [&](int sys) {
+          c_alpha = P.alpha[sys];
+          c_flag = JAC && P.wrr[sys];
+          return true;
+        },
+        [&](int i, double* acc) {
+          const double ri = fma(-c_alpha, q[i], r[i]);
+          r[i] = ri;
+          acc[0] = fma(ri, ri, acc[0]);
+          if (c_flag) acc[1] = fma(__ldg(dg + i) * ri, ri, acc[1]);
         },
         [&](int sys, const double* sm) {
-          P.beta[sys] = sm[0] / P.rho[sys];
-          P.rho[sys] = sm[0];
-          P.rr[sys] = sm[1];
+          const double rho = sm[0];
+          P.beta[sys] = rho / P.rho[sys];
+          P.rho[sys] = rho;
           const int k = P.k[sys] + 1;
           P.k[sys] = k;
-          if (sqrt(sm[1]) <= P.tol * sqrt(P.bb[sys]) || k >= P.maxit) set_stage(P, sys, 3, seq);
+          const double stop2 = P.tol * P.tol * P.bb[sys];
+          bool conv;
+          if (!JAC || P.wrr[sys]) {
+            const double rr = JAC ? sm[1] : rho;
+            P.rr[sys] = rr;
+            conv = sqrt(rr) <= P.tol * sqrt(P.bb[sys]);
+          } else {
+            // r.D r >= dmin r^.r^: above the band the test fails for sure
+            conv = false;
+            if (P.dmin[sys] * rho <= stop2) {
+              P.wrr[sys] = 1;
+              set_stage(P, sys, kStRrPending, seq);  // exact r.D r in phase C
+              return;
+            }
+          }
+          if (JAC) P.wrr[sys] = P.dmin[sys] * rho <= kRrMarginB * stop2;
+          if (conv || k >= P.maxit) set_stage(P, sys, kStLastX, seq);
         });
     if (!g.sync()) return;
-    // ---- C: x += alpha p; p = r + beta p unless the loop ended
+    // ---- C: x += alpha p; p = r + beta p unless the loop ended; pending r.D r
     ++seq;
-    T = build_tiles(P, kMaskC, seq, s_pref, s_scan, &alive);
-    run_phase<0>(
+    T = build_list(P, kMaskC, seq, s_pref, s_scan, &alive);
+    run_phase<1>(
         P, s_pref, T, g,
-        [&](int sys, int i, double*) {
-          const double pi = P.p[i];
-          P.xh[i] = fma(P.alpha[sys], pi, P.xh[i]);
-          if (eff_stage(__ldcg(P.sstate + sys), seq) == 1) P.p[i] = fma(P.beta[sys], pi, P.r[i]);
+        [&](int sys) {
+          const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
+          c_alpha = P.alpha[sys];
+          c_beta = P.beta[sys];
+          c_flag = stg != kStLastX;  // p is still needed
+          c_sum = stg == kStRrPending;
+          return c_sum;
         },
-        [&](int, const double*) {});
+        [&](int i, double* acc) {
+          const double pi = p[i];
+          xh[i] = fma(c_alpha, pi, xh[i]);
+          const double ri = r[i];
+          if (c_flag) p[i] = fma(c_beta, pi, ri);
+          if (JAC && c_sum) acc[0] = fma(__ldg(dg + i) * ri, ri, acc[0]);
+        },
+        [&](int sys, const double* sm) {
+          P.rr[sys] = sm[0];
+          const bool conv = sqrt(sm[0]) <= P.tol * sqrt(P.bb[sys]);
+          // converged or out of iterations: x is final, so the true residual next
+          set_stage(P, sys, conv || P.k[sys] >= P.maxit ? kStResidual : kStIter, seq);
+        });
     if (!g.sync()) return;
   }
-  (void)warp;
 }
 
 // Per-system copies into the concatenated vectors: b^ = D^-1/2 b, x^ = D^1/2 x
@@ -402,13 +474,14 @@ __global__ void batch_scatter_kernel(double* const* x, const int64_t* n, const i
 
 // Loop state of every system at the start of a solve.
 __global__ void batch_init_kernel(int nsys, double* bb, int* k, int* restarts, int* status, int* zero,
-                                  unsigned long long* sstate, unsigned* cnt) {
+                                  int* wrr, unsigned long long* sstate, unsigned* cnt) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
     bb[s] = -1.0;  // "not yet known": the first residual phase records b.b
     k[s] = 0;
     restarts[s] = 0;
     status[s] = kStRunning;
     zero[s] = 0;
+    wrr[s] = 0;
     sstate[s] = 0ull;  // stage 0, phase 0
     cnt[s] = 0u;
   }
@@ -464,17 +537,17 @@ __global__ void batch_diag_kernel(int64_t n, int64_t npad, int64_t r0, const dou
   }
 }
 
-// Kernel variants the autotuner chooses from: registers budgeted for 2, 3 or 4
+// Kernel variants the autotuner chooses from: registers budgeted for 3, 4 or 5
 // resident CTAs per SM (more CTAs hide more memory latency; fewer registers
 // may spill).
 constexpr int kVariants = 3;
-constexpr int kVariantMinBlocks[kVariants] = {2, 3, 4};
+constexpr int kVariantMinBlocks[kVariants] = {3, 4, 5};
 
 const void* batch_kernel(bool jac, int variant) {
   switch (variant) {
-    case 0: return jac ? (const void*)batch_pcg_kernel<true, 2> : (const void*)batch_pcg_kernel<false, 2>;
-    case 1: return jac ? (const void*)batch_pcg_kernel<true, 3> : (const void*)batch_pcg_kernel<false, 3>;
-    default: return jac ? (const void*)batch_pcg_kernel<true, 4> : (const void*)batch_pcg_kernel<false, 4>;
+    case 0: return jac ? (const void*)batch_pcg_kernel<true, 3> : (const void*)batch_pcg_kernel<false, 3>;
+    case 1: return jac ? (const void*)batch_pcg_kernel<true, 4> : (const void*)batch_pcg_kernel<false, 4>;
+    default: return jac ? (const void*)batch_pcg_kernel<true, 5> : (const void*)batch_pcg_kernel<false, 5>;
   }
 }
 
@@ -494,13 +567,16 @@ struct BatchData {
   int ntiles = 0, nslices = 0;
   int64_t entries = 0;             // slice entries (multiple of 32)
   int32_t *d_tstart = nullptr, *d_ntile = nullptr, *soff = nullptr, *col = nullptr;
+  int32_t *d_gstart = nullptr, *d_ngroup = nullptr;
+  int ngroups = 0;                 // reduction groups in all
+  double* d_dmin = nullptr;        // smallest A_ii per system
   int64_t *d_n = nullptr, *d_r0 = nullptr;
   double* val[2] = {nullptr, nullptr};  // [precond]: unscaled / Jacobi-scaled
   double *dg = nullptr, *dsq = nullptr, *disq = nullptr;
   double *r = nullptr, *p = nullptr, *q = nullptr, *xh = nullptr, *bh = nullptr;
   double *rho = nullptr, *rr = nullptr, *bb = nullptr, *alpha = nullptr, *beta = nullptr,
          *relres = nullptr;
-  int *k = nullptr, *restarts = nullptr, *status = nullptr, *zero = nullptr;
+  int *k = nullptr, *restarts = nullptr, *status = nullptr, *zero = nullptr, *wrr = nullptr;
   unsigned long long* sstate = nullptr;
   unsigned* cnt = nullptr;
   double* tpart = nullptr;
@@ -536,7 +612,7 @@ void cgi::batch_free(BatchData* b) {
                  b->val[1],   b->dg,      b->dsq,      b->disq,   b->r,    b->p,      b->q,
                  b->xh,       b->bh,      b->rho,      b->rr,     b->bb,   b->alpha,  b->beta,
                  b->relres,   b->k,       b->restarts, b->status, b->zero, b->sstate, b->cnt,
-                 b->tpart,    (void*)b->d_b, (void*)b->d_x};
+                 b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
@@ -591,6 +667,10 @@ BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
   P.nsys = B->nsys;
   P.tstart = B->d_tstart;
   P.ntile = B->d_ntile;
+  P.gstart = B->d_gstart;
+  P.ngroup = B->d_ngroup;
+  P.dmin = B->d_dmin;
+  P.wrr = B->wrr;
   P.soff = B->soff;
   P.col = B->col;
   P.val = B->val[jac];
@@ -635,7 +715,7 @@ cudaError_t enqueue_solve(cg_handle* h, cudaStream_t s, bool jac, int var, int G
   batch_gather_kernel<<<gg, 256, 0, s>>>(B->d_b, B->d_x, B->d_n, B->d_r0, B->d_ntile, B->disq, B->dsq,
                                           jac ? 1 : 0, B->bh, B->xh);
   batch_init_kernel<<<blocks_for(B->nsys), 256, 0, s>>>(B->nsys, B->bb, B->k, B->restarts, B->status,
-                                                         B->zero, B->sstate, B->cnt);
+                                                         B->zero, B->wrr, B->sstate, B->cnt);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   void* args[] = {&P};
@@ -711,11 +791,11 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
   return CG_OK;
 }
 
-// Autotuner: the kernel variant (registers budgeted for 2, 3 or 4 CTAs per SM)
+// Autotuner: the kernel variant (registers budgeted for 3, 4 or 5 CTAs per SM)
 // and grid size for this handle and preconditioner, picked by timing short
 // trial solves (at most kTrialIters iterations each, x left untouched) of the
 // caller's own systems; the choice is kept in the handle.  Candidates: every
-// variant at its full residency, and the 2-CTA variant at one CTA per SM.
+// variant at its full residency, and the 3-CTA variant at one CTA per SM.
 constexpr int kTrialIters = 40;
 
 cg_status autotune(cg_handle* h, bool jac, double tol, int maxit) {
@@ -855,10 +935,28 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
     CGB_CREATE(cudaMalloc(v, sizeof(double) * nv));
   for (double** v : {&B->rho, &B->rr, &B->bb, &B->alpha, &B->beta, &B->relres})
     CGB_CREATE(cudaMalloc(v, sizeof(double) * ns));
-  for (int** v : {&B->k, &B->restarts, &B->status, &B->zero}) CGB_CREATE(cudaMalloc(v, sizeof(int) * ns));
+  for (int** v : {&B->k, &B->restarts, &B->status, &B->zero, &B->wrr}) CGB_CREATE(cudaMalloc(v, sizeof(int) * ns));
+  {
+    std::vector<int32_t> gst(ns), ngr(ns);
+    std::vector<double> dmin(ns);
+    int groups = 0;
+    for (size_t s = 0; s < ns; ++s) {
+      gst[s] = groups;
+      ngr[s] = (B->ntile[s] + kGroup - 1) / kGroup;
+      groups += ngr[s];
+      dmin[s] = B->sys[s]->jacobi_ok ? B->sys[s]->dmin : 1.0;
+    }
+    B->ngroups = groups;
+    CGB_CREATE(cudaMalloc(&B->d_gstart, sizeof(int32_t) * ns));
+    CGB_CREATE(cudaMalloc(&B->d_ngroup, sizeof(int32_t) * ns));
+    CGB_CREATE(cudaMalloc(&B->d_dmin, sizeof(double) * ns));
+    CGB_CREATE(cudaMemcpy(B->d_gstart, gst.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+    CGB_CREATE(cudaMemcpy(B->d_ngroup, ngr.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+    CGB_CREATE(cudaMemcpy(B->d_dmin, dmin.data(), sizeof(double) * ns, cudaMemcpyHostToDevice));
+  }
   CGB_CREATE(cudaMalloc(&B->sstate, sizeof(unsigned long long) * ns));
   CGB_CREATE(cudaMalloc(&B->cnt, sizeof(unsigned) * ns));
-  CGB_CREATE(cudaMalloc(&B->tpart, sizeof(double) * (size_t)tiles * kWarps * kNP));
+  CGB_CREATE(cudaMalloc(&B->tpart, sizeof(double) * (size_t)B->ngroups * kWarps * kNP));
   CGB_CREATE(cudaMalloc((void**)&B->d_b, sizeof(double*) * ns));
   CGB_CREATE(cudaMalloc((void**)&B->d_x, sizeof(double*) * ns));
   CGB_CREATE(cudaMallocHost((void**)&B->host_ptrs, sizeof(void*) * 2 * ns));
