@@ -390,6 +390,33 @@ def run_batch(args, world, rank, dev, torch, cg):
         e2e = {"value": world * args.steps / e2e_s, "unit": "batches/s",
                "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot}
 
+    # the same systems solved one after another by cg_solve (plain FP64 Jacobi-PCG,
+    # one launch per system), for comparison on the same GPU
+    seq = None
+    if not args.no_sequential:
+        handles = [cg.cg_create(A.n, *c) for A, c in zip(systems, dev_csr)]
+        bsq = [b.clone() for b in bs]  # own (16-byte aligned) vectors per system
+        xsq = [torch.zeros_like(b) for b in bsq]
+        for hs, bi, xi in zip(handles, bsq, xsq):  # warm: build each handle's loop matrix
+            cg.cg_solve(hs, bi, xi, tol, maxit, precond)
+        for xi in xsq:
+            xi.zero_()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for hs, bi, xi in zip(handles, bsq, xsq):
+            st, _, _ = cg.cg_solve(hs, bi, xi, tol, maxit, precond)
+            if st != cg.CG_OK:
+                raise RuntimeError(f"sequential solve failed: {cg.status_string(st)}")
+        e1.record()
+        barrier()
+        seq_ms = e0.elapsed_time(e1)
+        for hs in handles:
+            cg.cg_destroy(hs)
+        seq = {"ms": seq_ms, "what": "cg_solve on each system in turn (FP64 Jacobi-PCG, auto loop form)",
+               "batched_speedup": seq_ms / ms_per_step}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gold = batch_golden_iters(len(systems))
@@ -421,6 +448,7 @@ def run_batch(args, world, rank, dev, torch, cg):
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "sequential_fp64": seq,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -438,6 +466,8 @@ def main():
                     help="seconds of oracle CPU time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="batch workloads: skip the one-system-at-a-time comparison")
     ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled"])
     args = ap.parse_args()
     if args.warmup < 3:

@@ -265,3 +265,31 @@ def test_full_512_system_batch_matches_the_oracle_counts():
         rel_or = oracle.true_relres(A, bs[i], xs[i])
         assert rel_or <= gold["tol"] * (1 + 1e-6), (i, rel_or)
         assert abs(rels[i] - rel_or) <= 1e-6 * rel_or + 1e-15
+
+
+def test_sudden_convergence_takes_the_exact_stopping_test():
+    """Systems whose residual collapses in one iteration (few distinct eigenvalues of the
+    scaled matrix): the recursive test must still be taken on the exact r.r, so the
+    counts equal the oracle's."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(5)
+    d = rng.uniform(1.0, 10.0, 900)
+    diag = sp.diags(d).tocsr()
+    blk = sp.block_diag([sp.csr_matrix(np.array([[2.0, 1.0], [1.0, 2.0]]))] * 450).tocsr()
+    scale = sp.diags(rng.uniform(0.5, 2.0, 900))
+    blk = (scale @ blk @ scale).tocsr()
+    mats = []
+    for M, name in ((diag, "diag"), (blk, "blocks2x2")):
+        M.sort_indices()
+        mats.append(gen.CSR(900, M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                            M.data.astype(np.float64), name))
+    systems = mats + [gen.lap2d(16)]
+    bs = rhs(systems, 61)
+    B = Batch(systems)
+    res = B.solve(bs, 1e-10, 100, cg.CG_PRECOND_JACOBI)
+    assert res[0] == cg.CG_OK
+    for s, A in enumerate(systems):
+        ref = oracle.pcg(A, bs[s], tol=1e-10, maxit=100, precond=1)
+        assert res[1][s] == ref.iters, (A.name, res[1][s], ref.iters)
+    assert res[1][0] == 1 and res[1][1] == 2
+    check_against_oracle(systems, bs, res, 1e-10, 100, cg.CG_PRECOND_JACOBI)
