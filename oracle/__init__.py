@@ -8,7 +8,8 @@ package imports nothing from the product package.
 Citations (the paper: "A Preliminary Study on Simultaneous Coscheduling for
 Discrete GPU vs. Fused GPU"): CSR SpMV, Sec. 3.1; CG iteration, Alg. 1;
 fp64 throughout, Sec. 3.1; recomputed final residual, Sec. 3.1.  The readings
-R1-R6 taken where the paper is silent are listed in ``oracle.c``.
+R1-R7 taken where the paper is silent are listed in ``oracle.c``; the FSAI
+preconditioner and its MLP (not in the paper) are in ``oracle.fsai`` (F1-F8).
 """
 from __future__ import annotations
 

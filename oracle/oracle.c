@@ -304,3 +304,222 @@ int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const dou
   for (int i = 0; i < 7; ++i) free(f[i]);
   return status;
 }
+
+/*
+ * ---------------------------------------------------------------------------
+ * Factorized sparse approximate inverse preconditioner M^-1 = G^T G
+ * (Kolotilina & Yeremin 1993; not in the paper, project-defined).  G is lower
+ * triangular in CSR form (grp, gci, gval; columns ascending, the diagonal
+ * entry last in each row).  Applying it: t = G r (row sums in storage
+ * order), z = G^T t (z_j accumulates G_ij t_i for i ascending).
+ * R7 (reading): the PCG with this preconditioner is Alg. 1 with z = G^T G r
+ * and rho = r.z, under the same R1-R4 rules as or_pcg.
+ */
+static void fsai_apply(int64_t n, const int32_t* grp, const int32_t* gci, const double* gval,
+                       const double* r, double* t, double* z) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) s += gval[k] * r[gci[k]];
+    t[i] = s;
+  }
+  for (int64_t j = 0; j < n; ++j) z[j] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) z[gci[k]] += gval[k] * t[i];
+}
+
+/* PCG with M^-1 = G^T G (R7); *rz_min gets the smallest r.z of the run. */
+int or_pcg_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
+                double* x, double tol, int32_t maxit, int32_t max_restarts, double* res_hist,
+                double* rz_min, or_result* out) {
+  memset(out, 0, sizeof(*out));
+  if (n < 0 || maxit < 0 || !(tol >= 0.0)) {
+    out->status = OR_ERR_INVALID;
+    return out->status;
+  }
+  const double bb = or_dot(n, b, b);
+  if (rz_min) *rz_min = INFINITY;
+  if (bb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    out->status = OR_OK;
+    return OR_OK;
+  }
+  const double bnorm = sqrt(bb);
+  const size_t nv = (size_t)(n > 0 ? n : 1);
+  double* r = (double*)malloc(sizeof(double) * nv);
+  double* z = (double*)malloc(sizeof(double) * nv);
+  double* p = (double*)malloc(sizeof(double) * nv);
+  double* q = (double*)malloc(sizeof(double) * nv);
+  double* t = (double*)malloc(sizeof(double) * nv);
+  if (!r || !z || !p || !q || !t) {
+    free(r); free(z); free(p); free(q); free(t);
+    out->status = OR_ERR_OOM;
+    return out->status;
+  }
+  int32_t k = 0, restarts = 0, status = OR_NOT_CONVERGED;
+  double rr = 0.0;
+  for (;;) {
+    or_spmv(n, rowptr, colind, vals, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    fsai_apply(n, grp, gci, gval, r, t, z);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+    double rho = or_dot(n, r, z);
+    rr = or_dot(n, r, r);
+    int stop = 0;
+    for (;;) {
+      if (rz_min && rho < *rz_min) *rz_min = rho;
+      if (res_hist) res_hist[k] = sqrt(rr) / bnorm;
+      if (sqrt(rr) <= tol * bnorm) break;
+      if (k >= maxit) break;
+      or_spmv(n, rowptr, colind, vals, p, q);
+      const double pq = or_dot(n, p, q);
+      if (!isfinite(pq) || !isfinite(rho)) { status = OR_ERR_NUMERIC; stop = 1; break; }
+      if (pq <= 0.0) { status = OR_ERR_BREAKDOWN; stop = 1; break; }
+      const double alpha = rho / pq;
+      for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+      for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+      fsai_apply(n, grp, gci, gval, r, t, z);
+      const double rho_new = or_dot(n, r, z);
+      rr = or_dot(n, r, r);
+      const double beta = rho_new / rho;
+      rho = rho_new;
+      for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+      ++k;
+    }
+    if (stop) break;
+    out->relres_true = or_true_relres(n, rowptr, colind, vals, b, x);
+    if (!isfinite(out->relres_true)) { status = OR_ERR_NUMERIC; break; }
+    if (out->relres_true <= tol) { status = OR_OK; break; }
+    if (k >= maxit || restarts >= max_restarts) { status = OR_NOT_CONVERGED; break; }
+    ++restarts;
+  }
+  out->relres_rec = sqrt(rr) / bnorm;
+  if (status == OR_ERR_NUMERIC || status == OR_ERR_BREAKDOWN)
+    out->relres_true = or_true_relres(n, rowptr, colind, vals, b, x);
+  out->iters = k;
+  out->restarts = restarts;
+  out->status = status;
+  free(r); free(z); free(p); free(q); free(t);
+  return status;
+}
+
+/* fp32 G^T G application: t = G r, z = G^T t with fp32 values and sums. */
+static void fsai_apply32(int64_t n, const int32_t* grp, const int32_t* gci, const float* g32,
+                         const float* r, float* t, float* z) {
+  for (int64_t i = 0; i < n; ++i) {
+    float s = 0.0f;
+    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) s += g32[k] * r[gci[k]];
+    t[i] = s;
+  }
+  for (int64_t j = 0; j < n; ++j) z[j] = 0.0f;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) z[gci[k]] += g32[k] * t[i];
+}
+
+/* Inner fp32 PCG of the refinement with M^-1 = G32^T G32 (R6 with R7). */
+static int32_t pcg32_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind,
+                          const float* vals32, const int32_t* grp, const int32_t* gci,
+                          const float* g32, const float* rhs, float* d, double tol_in,
+                          int32_t maxit, float* r, float* z, float* p, float* q, float* t,
+                          int32_t* status_out) {
+  double bb = 0.0;
+  for (int64_t i = 0; i < n; ++i) bb += (double)rhs[i] * (double)rhs[i];
+  for (int64_t i = 0; i < n; ++i) { d[i] = 0.0f; r[i] = rhs[i]; }
+  fsai_apply32(n, grp, gci, g32, r, t, z);
+  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  double rho = 0.0, rr = bb;
+  for (int64_t i = 0; i < n; ++i) rho += (double)r[i] * (double)z[i];
+  int32_t k = 0;
+  *status_out = OR_NOT_CONVERGED;
+  for (;;) {
+    if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; break; }
+    if (k >= maxit) break;
+    for (int64_t i = 0; i < n; ++i) {
+      float s = 0.0f;
+      for (int64_t kk = rowptr[i]; kk < rowptr[i + 1]; ++kk) s += vals32[kk] * p[colind[kk]];
+      q[i] = s;
+    }
+    double pq = 0.0;
+    for (int64_t i = 0; i < n; ++i) pq += (double)p[i] * (double)q[i];
+    if (!isfinite(pq) || !isfinite(rho)) { *status_out = OR_ERR_NUMERIC; break; }
+    if (pq <= 0.0) { *status_out = OR_ERR_BREAKDOWN; break; }
+    const float alpha = (float)(rho / pq);
+    for (int64_t i = 0; i < n; ++i) d[i] += alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    fsai_apply32(n, grp, gci, g32, r, t, z);
+    double rho_new = 0.0;
+    rr = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      rho_new += (double)r[i] * (double)z[i];
+      rr += (double)r[i] * (double)r[i];
+    }
+    const float beta = (float)(rho_new / rho);
+    rho = rho_new;
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    ++k;
+  }
+  return k;
+}
+
+/* fp32-inner / fp64-outer refinement (R6) whose inner PCG uses M^-1 = G^T G (R7). */
+int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                   const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
+                   double* x, double tol, double tol_in, int32_t maxit, int32_t max_outer,
+                   double* outer_hist, or_result* out) {
+  memset(out, 0, sizeof(*out));
+  if (n < 0 || maxit < 0 || max_outer < 0 || !(tol >= 0.0) || !(tol_in > 0.0)) {
+    out->status = OR_ERR_INVALID;
+    return out->status;
+  }
+  const double bb = or_dot(n, b, b);
+  if (bb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    out->status = OR_OK;
+    return OR_OK;
+  }
+  const int64_t nnz = rowptr[n], gnnz = grp[n];
+  const size_t nv = (size_t)(n > 0 ? n : 1);
+  double* r = (double*)malloc(sizeof(double) * nv);
+  float* vals32 = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+  float* g32 = (float*)malloc(sizeof(float) * (size_t)(gnnz > 0 ? gnnz : 1));
+  float* f[7];
+  int ok = r && vals32 && g32;
+  for (int i = 0; i < 7; ++i) { f[i] = (float*)malloc(sizeof(float) * nv); ok = ok && f[i]; }
+  if (!ok) {
+    free(r); free(vals32); free(g32);
+    for (int i = 0; i < 7; ++i) free(f[i]);
+    out->status = OR_ERR_OOM;
+    return out->status;
+  }
+  float *r32 = f[0], *d = f[1], *rw = f[2], *z = f[3], *p = f[4], *q = f[5], *t = f[6];
+  for (int64_t k = 0; k < nnz; ++k) vals32[k] = (float)vals[k];
+  for (int64_t k = 0; k < gnnz; ++k) g32[k] = (float)gval[k];
+  const double bnorm = sqrt(bb);
+  int32_t inner_total = 0, outer = 0, status = OR_NOT_CONVERGED;
+  double relres = 0.0;
+  for (;;) {
+    or_spmv(n, rowptr, colind, vals, x, r);
+    double rr = 0.0;
+    for (int64_t i = 0; i < n; ++i) { r[i] = b[i] - r[i]; rr += r[i] * r[i]; }
+    relres = sqrt(rr) / bnorm;
+    if (outer_hist) outer_hist[outer] = relres;
+    if (!isfinite(relres)) { status = OR_ERR_NUMERIC; break; }
+    if (relres <= tol) { status = OR_OK; break; }
+    if (outer >= max_outer || inner_total >= maxit) { status = OR_NOT_CONVERGED; break; }
+    for (int64_t i = 0; i < n; ++i) r32[i] = (float)r[i];
+    int32_t st;
+    inner_total += pcg32_fsai(n, rowptr, colind, vals32, grp, gci, g32, r32, d, tol_in,
+                              maxit - inner_total, rw, z, p, q, t, &st);
+    if (st == OR_ERR_NUMERIC || st == OR_ERR_BREAKDOWN) { status = st; break; }
+    for (int64_t i = 0; i < n; ++i) x[i] += (double)d[i];
+    ++outer;
+  }
+  out->iters = inner_total;
+  out->restarts = outer;
+  out->relres_rec = relres;
+  out->relres_true = or_true_relres(n, rowptr, colind, vals, b, x);
+  out->status = status;
+  free(r); free(vals32); free(g32);
+  for (int i = 0; i < 7; ++i) free(f[i]);
+  return status;
+}

@@ -1,0 +1,175 @@
+"""Pins of the FSAI oracle (oracle/fsai.py) against facts fixed by the mathematics:
+the exact inverse factor on a full pattern, the Kaporin minimiser property, finite
+differences, the Jacobi special case, SPD-ness, and hand-checked rounding and
+feature values.  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import cgproblems as gen
+import oracle
+from oracle import fsai
+
+
+def dense_csr(M, name):
+    import scipy.sparse as sp
+    S = sp.csr_matrix(M)
+    S.sort_indices()
+    return gen.CSR(M.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32),
+                   S.data.astype(np.float64), name)
+
+
+def random_spd(n, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=(n, n))
+    return B @ B.T + n * np.eye(n)
+
+
+def test_bf16_rounding_table():
+    # 8 significant bits, ties to even
+    cases = {1.0: 1.0, 1.0 + 2 ** -8: 1.0, 1.0 + 3 * 2 ** -8: 1.0 + 2 ** -6,
+             1.0 + 2 ** -9: 1.0, 1.0 + 2 ** -8 + 2 ** -12: 1.0 + 2 ** -7,
+             -3.0: -3.0, 0.0: 0.0, 255.5: 256.0, 254.5: 254.0, 1e-20: 1e-20 * 0 + fsai.bf16(1e-20)}
+    for x, want in cases.items():
+        assert fsai.bf16(x) == want, (x, fsai.bf16(x), want)
+    x = np.random.default_rng(0).normal(size=1000)
+    r = fsai.bf16(x)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2 ** -8)
+    assert np.array_equal(fsai.bf16(r), r)
+
+
+def test_full_pattern_gives_the_exact_inverse_factor():
+    """On a dense SPD matrix tril(A) is the full lower pattern, so classic FSAI is the
+    inverse Cholesky factor: G A G^T = I, and PCG converges in one iteration."""
+    M = random_spd(12, 1)
+    A = dense_csr(M, "dense12")
+    g = fsai.classic(A)
+    G = fsai.g_matrix(A, g).toarray()
+    assert np.allclose(G @ M @ G.T, np.eye(12), atol=1e-12)
+    L = np.linalg.cholesky(M)
+    assert np.allclose(G, np.linalg.inv(L), atol=1e-12)
+    b = M @ np.ones(12)
+    s = fsai.pcg(A, g, b, tol=1e-12, maxit=50)
+    assert s.status == oracle.OK and s.iters == 1
+
+
+@pytest.mark.parametrize("make", [lambda: gen.q1aniso(10, 1.5, 0.7, 0.02, 4),
+                                  lambda: gen.lap2d(9, 9, 0.1),
+                                  lambda: gen.diff3d27(5, 1.0, 2)])
+def test_classic_fsai_minimises_the_kaporin_number(make):
+    A = make()
+    g = fsai.classic(A)
+    G = fsai.g_matrix(A, g)
+    S = A.to_scipy()
+    assert np.allclose((G @ S @ G.T).diagonal(), 1.0, atol=1e-12)   # normalisation of F2
+    L0, dG = fsai.kaporin(A, g)
+    assert np.linalg.norm(dG) < 1e-10                                # stationary point
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        pert = g + 1e-2 * rng.normal(size=g.size) * np.abs(g)
+        assert fsai.kaporin(A, pert)[0] > L0
+    # scale invariance of the Kaporin number
+    assert abs(fsai.kaporin(A, 3.0 * g)[0] - L0) < 1e-12
+
+
+def fd_check(f, x, grad, idx, h):
+    for k in idx:
+        e = np.zeros_like(x)
+        e[k] = h
+        num = (f(x + e) - f(x - e)) / (2 * h)
+        assert abs(num - grad[k]) <= 1e-6 * max(1.0, abs(num)) * max(1.0, np.max(np.abs(grad))), \
+            (k, num, grad[k])
+
+
+def test_kaporin_and_residual_gradients_match_finite_differences():
+    A = gen.q1aniso(8, 1.5, 1.1, 0.1, 5)
+    rng = np.random.default_rng(3)
+    g = fsai.classic(A) * (1 + 0.1 * rng.normal(size=len(fsai.tril(A)[1])))
+    L, dG = fsai.kaporin(A, g)
+    fd_check(lambda v: fsai.kaporin(A, v)[0], g, dG, rng.choice(g.size, 25, replace=False), 1e-6)
+    R = rng.normal(size=(3, A.n))
+    LR, dR = fsai.residual_term(A, g, R)
+    fd_check(lambda v: fsai.residual_term(A, v, R)[0], g, dR, rng.choice(g.size, 25, replace=False), 1e-6)
+
+
+def test_parameter_gradient_matches_finite_differences():
+    """Through features, MLP and the G mapping (fp64 mode, no bf16 rounding)."""
+    A = gen.q1aniso(7, 1.5, 0.3, 0.05, 6)
+    rng = np.random.default_rng(4)
+    p = fsai.init_params(1).astype(np.float64)
+    p[-65:] = rng.normal(0, 0.05, 65)   # a non-zero output layer
+    R = rng.normal(size=(2, A.n))
+    f = lambda v: fsai.loss_and_grad(A, v, R, 0.1, round_bf16=False)[0]
+    L, grad = fsai.loss_and_grad(A, p, R, 0.1, round_bf16=False)
+    idx = np.concatenate([rng.choice(2048, 12, replace=False),           # W1
+                          2048 + 64 + rng.choice(4096, 12, replace=False),  # W2
+                          np.arange(6337 - 65, 6337)[rng.choice(65, 10, replace=False)],
+                          [2048 + 3, 2048 + 64 + 4096 + 5]])             # b1, b2
+    fd_check(f, p, grad, idx, 1e-6)
+
+
+def test_zero_output_layer_is_jacobi():
+    """o = 0 gives G = D^-1/2: the same G, Kaporin value and PCG iterations as Jacobi."""
+    A = gen.q1aniso(14, 1.5, 2.0, 0.01, 8)
+    p = fsai.init_params(3)
+    g = fsai.learned(A, p)
+    trp, tci, _ = fsai.tril(A)
+    rows = np.repeat(np.arange(A.n), np.diff(trp))
+    jac = np.where(rows == tci, 1.0 / np.sqrt(fsai.diag(A))[rows], 0.0)
+    assert np.allclose(g, jac, rtol=0, atol=1e-15 * np.max(jac))
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    s1 = fsai.pcg(A, g, b, tol=1e-9, maxit=2000)
+    s2 = oracle.pcg(A, b, tol=1e-9, maxit=2000, precond=1)
+    assert s1.status == s2.status == oracle.OK and s1.iters == s2.iters
+    # same iterates up to the rounding of r / sqrt(d) / sqrt(d) versus r / d
+    assert np.linalg.norm(s1.x - s2.x) <= 1e-7 * np.linalg.norm(s2.x)
+
+
+def test_learned_factor_is_spd_and_pcg_stays_positive():
+    A = gen.q1aniso(10, 1.5, 0.9, 0.2, 9)
+    rng = np.random.default_rng(11)
+    p = fsai.init_params(5).astype(np.float64)
+    p[-65:] = rng.normal(0, 0.05, 65)   # small enough to keep G well conditioned
+    g = fsai.learned(A, p)
+    G = fsai.g_matrix(A, g).toarray()
+    assert np.all(np.diag(G) > 0)
+    np.linalg.cholesky(G @ A.to_dense() @ G.T)    # SPD
+    b = oracle.spmv(A, gen.xstar(A.n, 4))
+    s = fsai.pcg(A, g, b, tol=1e-9, maxit=2000)
+    assert s.status == oracle.OK and s.rz_min > 0
+
+
+def test_features_of_a_constant_laplacian_row():
+    """Interior row of the 5-point unit Laplacian on a 6 x 6 grid (row i = 8, x = 2, y = 1)."""
+    A = gen.lap2d(6)
+    F = fsai.features(A)
+    trp, tci, _ = fsai.tril(A)
+    i = 8
+    rows = F[trp[i]:trp[i + 1]]
+    assert list(tci[trp[i]:trp[i + 1]]) == [2, 7, 8]
+    # offsets of A: -6, -1, 0, 1, 6 -> tril slots (-6, -1, 0)
+    assert np.array_equal(rows[:, 0:8].argmax(1), [0, 1, 2])
+    assert np.allclose(rows[:, 8], [-0.25, -0.25, 1.0])
+    assert np.allclose(rows[:, 9], 0.0)
+    assert np.allclose(rows[0, 10:15], [-0.25, -0.25, 1.0, -0.25, -0.25])
+    assert np.allclose(rows[:, 15:19], 0.0) and np.allclose(rows[:, 28], 1.0)
+    # row j = 2 (y = 0) lies on the boundary below: no offset -6 entry
+    assert np.allclose(rows[0, 19:24], [0.0, -0.25, 1.0, -0.25, -0.25])
+
+
+def test_adam_first_step_moves_each_parameter_by_lr():
+    p = np.zeros(5)
+    g = np.array([1.0, -2.0, 1e-3, 0.0, 5.0])
+    p1, m, v = fsai.adam(p, g, np.zeros(5), np.zeros(5), 1, lr=0.1)
+    assert np.allclose(p1[[0, 1, 2, 4]], -0.1 * np.sign(g[[0, 1, 2, 4]]), rtol=1e-4)
+    assert p1[3] == 0.0
+
+
+def test_fsai_refinement_reaches_tolerance():
+    A = gen.q1aniso(16, 1.5, 0.2, 0.01, 12)
+    g = fsai.classic(A)
+    b = oracle.spmv(A, gen.xstar(A.n, 6))
+    s = fsai.pcg_ir(A, g, b, tol=1e-10, tol_in=1e-4)
+    assert s.status == oracle.OK and s.relres_true <= 1e-10
+    assert oracle.true_relres(A, b, s.x) <= 1e-10
