@@ -48,7 +48,10 @@ typedef enum {
 
 typedef enum {
   CG_PRECOND_NONE = 0,    /* plain CG, Alg. 1 */
-  CG_PRECOND_JACOBI = 1   /* z = D^-1 r, D = diag(A) (not in the paper) */
+  CG_PRECOND_JACOBI = 1,  /* z = D^-1 r, D = diag(A) (not in the paper) */
+  CG_PRECOND_FSAI = 2     /* z = G^T G r with the handle's FSAI factor G (cg_fsai_classic,
+                             cg_fsai_load, cg_fsai_set_factor; not in the paper); without
+                             a factor the solve falls back to Jacobi (precond_used says so) */
 } cg_precond;
 
 typedef enum {
@@ -89,6 +92,7 @@ typedef struct {
                              x/p-update phases, each followed by its grid-barrier wait */
   int32_t loop_form;      /* CG_OPT_LOOP_MODE form that ran: 1 persistent, 2 graph WHILE, 3 unrolled */
   int32_t kernel_launches;/* kernels of this library launched by the solve */
+  int32_t precond_used;   /* cg_precond that ran (CG_PRECOND_FSAI without a factor runs Jacobi) */
 } cg_solve_info;
 
 /*
@@ -206,6 +210,31 @@ cg_status cg_batch_get_system(const cg_handle* h, int32_t s, int32_t* status, in
  * and the index of the chosen candidate (-1 before the first autotuned solve). */
 cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* count, int32_t* grids,
                               int32_t* ctas_per_sm, float* ms, int32_t* chosen);
+
+/*
+ * FSAI preconditioner M^-1 = G^T G (Kolotilina & Yeremin 1993; not in the
+ * paper).  G is lower triangular with the pattern of tril(A); the CSR of A
+ * must have strictly increasing columns in every row, a positive diagonal,
+ * at most 16 entries per row of tril(A) and at most 32 per column.  The
+ * factor belongs to the handle and is used by cg_solve(precond =
+ * CG_PRECOND_FSAI) in both precisions (fp32 refinement: G rounded to fp32);
+ * each iteration applies it as t = G r, z = G^T t (three grid barriers per
+ * iteration, as with Jacobi).
+ */
+
+/* Classic FSAI: per row i, solve A[P_i,P_i] y = e_i on the row's pattern P_i
+ * (small dense Cholesky on the GPU) and set row i of G to y / sqrt(y_i).
+ * CG_ERR_INVALID if the matrix does not qualify or a local matrix is not SPD. */
+cg_status cg_fsai_classic(cg_handle* h);
+
+/* Use the caller's factor: g_tril (DEVICE, fp64) holds G's values in the
+ * order of the entries of tril(A) in A's CSR (row by row, columns
+ * ascending).  Every diagonal value must be positive and finite. */
+cg_status cg_fsai_set_factor(cg_handle* h, const double* g_tril);
+
+/* Copy the current factor (tril order) into g_tril (DEVICE, may be NULL);
+ * *ntril = nonzeros of tril(A), *kind = 0 none, 1 classic, 2 learned, 3 set. */
+cg_status cg_fsai_get_factor(cg_handle* h, double* g_tril, int64_t* ntril, int32_t* kind);
 
 /* Largest n that cg_solve_noalloc accepts: its scratch is four device vectors
  * of this many doubles plus a result block (2 MiB per GPU). */

@@ -19,7 +19,7 @@ from . import _build
 CG_OK, CG_NOT_CONVERGED = 0, 1
 CG_ERR_INVALID, CG_ERR_BREAKDOWN, CG_ERR_NUMERIC = -1, -2, -3
 CG_ERR_TIMEOUT, CG_ERR_CUDA, CG_ERR_OOM = -4, -5, -6
-CG_PRECOND_NONE, CG_PRECOND_JACOBI = 0, 1
+CG_PRECOND_NONE, CG_PRECOND_JACOBI, CG_PRECOND_FSAI = 0, 1, 2
 CG_PREC_FP64, CG_PREC_FP32_IR = 0, 1
 CG_OPT_MAX_RESTARTS, CG_OPT_BARRIER_TIMEOUT_MS, CG_OPT_GRID_CTAS = 0, 1, 2
 CG_OPT_IR_TOL_INNER, CG_OPT_IR_MAX_OUTER, CG_OPT_DEBUG_SKIP_ARRIVAL = 3, 4, 5
@@ -29,7 +29,8 @@ CG_OPT_PHASE_TIMERS, CG_OPT_LOOP_MODE = 6, 7
 EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
            "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
            "cg_last_error", "cg_status_string", "cg_solve_noalloc", "cg_batch_create",
-           "cg_solve_batch", "cg_batch_get_system", "cg_batch_get_tuning")
+           "cg_solve_batch", "cg_batch_get_system", "cg_batch_get_tuning", "cg_fsai_classic",
+           "cg_fsai_set_factor", "cg_fsai_get_factor")
 CG_NOALLOC_MAX_ROWS = 65536
 CG_BATCH_MAX_SYSTEMS = 4096
 
@@ -46,7 +47,8 @@ class SolveInfo(ctypes.Structure):
                 ("relres_true", ctypes.c_double), ("relres_rec", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("bytes_moved", ctypes.c_int64),
                 ("kernel_bytes_per_iter", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6),
-                ("loop_form", ctypes.c_int32), ("kernel_launches", ctypes.c_int32)]
+                ("loop_form", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("precond_used", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -91,6 +93,9 @@ def load(build_if_missing: bool = True):
     lib.cg_solve_noalloc.argtypes = [i64, i64, P, P, P, P, P, f64, i32, i32, P, pi32, pf64]
     lib.cg_solve_noalloc.restype = ctypes.c_int
     lib.cg_batch_create.argtypes = [i32, pi64, P, P, P, ctypes.POINTER(P)]
+    lib.cg_fsai_classic.argtypes = [P]
+    lib.cg_fsai_set_factor.argtypes = [P, P]
+    lib.cg_fsai_get_factor.argtypes = [P, P, pi64, pi32]
     lib.cg_solve_batch.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
     lib.cg_batch_get_system.argtypes = [P, i32, pi32, pi32, pi32, pf64]
     lib.cg_batch_get_tuning.argtypes = [P, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
@@ -317,6 +322,35 @@ def cg_batch_get_tuning(h: Handle, precond: int = CG_PRECOND_JACOBI) -> dict:
     k = cnt.value
     return {"grids": list(grids)[:k], "ctas_per_sm": list(per_sm)[:k], "ms": list(ms)[:k],
             "chosen": chosen.value}
+
+
+def cg_fsai_classic(h: Handle) -> int:
+    """Build the classic FSAI factor of the handle's matrix (on the current stream)."""
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    return lib.cg_fsai_classic(h.ptr)
+
+
+def cg_fsai_set_factor(h: Handle, g_tril) -> int:
+    """Use the caller's factor: a CUDA float64 tensor of G's values in tril(A) order."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    return lib.cg_fsai_set_factor(h.ptr, _dptr(g_tril, torch.float64, "g_tril"))
+
+
+def cg_fsai_get_factor(h: Handle):
+    """(status, values tensor or None, kind) of the handle's current factor."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    nt, kind = ctypes.c_int64(), ctypes.c_int32()
+    st = lib.cg_fsai_get_factor(h.ptr, None, ctypes.byref(nt), ctypes.byref(kind))
+    if st != CG_OK or kind.value == 0:
+        return st, None, kind.value
+    g = torch.empty(nt.value, dtype=torch.float64, device="cuda")
+    st = lib.cg_fsai_get_factor(h.ptr, _dptr(g, torch.float64, "g"), None, None)
+    return st, g, kind.value
 
 
 @dataclass

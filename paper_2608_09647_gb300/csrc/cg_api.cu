@@ -13,7 +13,7 @@
 
 #include "../../include/libcg.h"
 #include "cg_graph.cuh"
-#include "cg_handle.cuh"
+#include "cg_fsai.cuh"
 
 using namespace cg;
 
@@ -476,6 +476,7 @@ void destroy_graph(cudaGraphExec_t* e, cudaGraph_t* g) {
 
 void free_all(cg_handle* h) {
   if (h->batch) cgi::batch_free(h->batch);
+  if (h->fsai) cgi::fsai_free(h->fsai);
   void* dev[] = {h->rb,        h->diag,      h->ndiag,     h->dsq,       h->disq,       h->delta_dev,
                  h->diag32,    h->disq32,    h->soff,      h->lmask,     h->scol,
                  h->lrow,      h->lptr,      h->lcol,      h->sval64[0], h->sval64[1],
@@ -988,13 +989,16 @@ cg_status cg_spmv(cg_handle* h, const double* x, double* y) {
   return CG_OK;
 }
 
-cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t maxit,
-                   int32_t precond, int32_t precision, int32_t* iters_out, double* relres_out) {
-  if (!h) return CG_ERR_INVALID;
-  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_solve: batch handle (use cg_solve_batch)");
+}  // extern "C"
+
+namespace {
+
+// cg_solve after the preconditioner choice (FSAI only when the handle has a factor).
+cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32_t maxit, int32_t precond,
+                     int32_t precision, int32_t* iters_out, double* relres_out) {
   h->last = cg_solve_info{};
   if (!(tol >= 0.0) || maxit < 0) return fail(h, CG_ERR_INVALID, "cg_solve: tol < 0 or maxit < 0");
-  if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)
+  if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI && precond != CG_PRECOND_FSAI)
     return fail(h, CG_ERR_INVALID, "cg_solve: unknown preconditioner");
   if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR)
     return fail(h, CG_ERR_INVALID, "cg_solve: unknown precision");
@@ -1008,7 +1012,8 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   if (!b || !x) return fail(h, CG_ERR_INVALID, "cg_solve: b or x is NULL");
   if (!aligned16(b) || !aligned16(x)) return fail(h, CG_ERR_INVALID, "cg_solve: b and x must be 16-byte aligned");
   if (b == x) return fail(h, CG_ERR_INVALID, "cg_solve: b and x alias");
-  const bool jac = precond == CG_PRECOND_JACOBI;
+  const bool fsai = precond == CG_PRECOND_FSAI;
+  const bool jac = precond == CG_PRECOND_JACOBI;  // FSAI runs on the unscaled matrix
   const bool fp64 = precision == CG_PREC_FP64;
   cg_status s = ensure_offdiag(h);
   if (s == CG_OK) s = ensure_vectors<double>(h, &h->r, &h->p, &h->q, &h->xh);
@@ -1038,6 +1043,7 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
   P.timers = h->timers;
+  if (fsai) return cgi::fsai_solve(h, P, fp64, G, iters_out, relres_out);
   // auto: fp64 takes the graph form from kGraphMinRows rows; the refinement's
   // fp32 vector passes are short, so it stays in the persistent form
   const bool graph_mode = h->loop_mode >= 2 || (h->loop_mode == 0 && fp64 && h->n >= kGraphMinRows);
@@ -1089,6 +1095,21 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
                                ", CTA " + std::to_string(ds.err_cta) + "); timed out");
   if (status < 0) return fail(h, status, std::string("cg_solve: ") + cg_status_string(status));
   return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t maxit,
+                   int32_t precond, int32_t precision, int32_t* iters_out, double* relres_out) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_solve: batch handle (use cg_solve_batch)");
+  int32_t used = precond;
+  if (precond == CG_PRECOND_FSAI && !(h->fsai && h->fsai->kind)) used = CG_PRECOND_JACOBI;  // fallback
+  const cg_status s = solve_impl(h, b, x, tol, maxit, used, precision, iters_out, relres_out);
+  h->last.precond_used = used;
+  return s;
 }
 
 cg_status cg_solve_host(cg_handle* h, const double* b_host, double* x_host, double tol,

@@ -1,0 +1,616 @@
+// Factorized sparse approximate inverse preconditioning, M^-1 = G^T G
+// (Kolotilina & Yeremin 1993; not in the paper): the pattern of G (that of
+// tril(A)), the classic factor, user-supplied factors, the factor's ELL
+// layouts for the loop, and the persistent PCG kernels that apply it.  The
+// learned factor (an MLP over matrix features) lives in cg_mlp.cu.
+//
+// PCG with G^T G (standard form, Alg. 1 with z = G^T G r):
+//   phase 1: q = A p, p.q                                  -> alpha
+//   phase 2: r' = r - alpha q (into the other r buffer), r'.r',
+//            t = G r' (r' of neighbour rows recomputed from r and q, so no
+//            barrier is needed between the r update and G r'), t.t = r'.z,
+//            x += alpha p                                  -> beta, test
+//   phase 3: p = G^T t + beta p
+// Three grid barriers per iteration, as for Jacobi.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "cg_fsai.cuh"
+
+using namespace cg;
+
+namespace {
+
+cg_status ffail(cg_handle* h, cg_status s, const std::string& msg) {
+  h->err = msg;
+  return s;
+}
+
+#define CGF_CUDA(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return ffail((h), e_ == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,        \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+unsigned blocks_for(int64_t items) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 8192));
+}
+
+// Classic FSAI (F2), thread per row: the local matrix A[P_i, P_i] (P_i the
+// row's tril pattern, ascending, ending with i) is factored by Cholesky and
+// A_loc y = e_last solved; g_i = y / sqrt(y_last).  bad[0] counts rows whose
+// local matrix is not SPD.
+__global__ void classic_fsai_kernel(int64_t n, const int32_t* __restrict__ rowptr,
+                                    const int32_t* __restrict__ colind, const double* __restrict__ vals,
+                                    const int32_t* __restrict__ trp, const int32_t* __restrict__ tci,
+                                    double* __restrict__ g, unsigned long long* bad) {
+  constexpr int M = kFsaiMaxRow;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int t0 = trp[i], m = trp[i + 1] - t0;
+    double L[M * (M + 1) / 2];  // packed lower triangle, row a at a (a + 1) / 2
+    int P[M];
+    for (int a = 0; a < m; ++a) P[a] = tci[t0 + a];
+    // A_loc[a][c] for c <= a: merge row P[a] of A with P (both ascending)
+    for (int a = 0; a < m; ++a) {
+      int c = 0;
+      for (int k = rowptr[P[a]]; k < rowptr[P[a] + 1] && c <= a; ++k) {
+        const int col = colind[k];
+        while (c <= a && P[c] < col) L[a * (a + 1) / 2 + c++] = 0.0;
+        if (c <= a && P[c] == col) L[a * (a + 1) / 2 + c++] = vals[k];
+      }
+      while (c <= a) L[a * (a + 1) / 2 + c++] = 0.0;
+    }
+    // Cholesky in place
+    bool ok = true;
+    for (int a = 0; a < m && ok; ++a) {
+      for (int c = 0; c <= a; ++c) {
+        double s = L[a * (a + 1) / 2 + c];
+        for (int k = 0; k < c; ++k) s -= L[a * (a + 1) / 2 + k] * L[c * (c + 1) / 2 + k];
+        if (c == a) {
+          if (!(s > 0.0)) { ok = false; break; }
+          L[a * (a + 1) / 2 + a] = sqrt(s);
+        } else {
+          L[a * (a + 1) / 2 + c] = s / L[c * (c + 1) / 2 + c];
+        }
+      }
+    }
+    if (!ok) {
+      atomicAdd(bad, 1ull);
+      for (int a = 0; a < m; ++a) g[t0 + a] = 0.0;
+      continue;
+    }
+    // L L^T y = e_last: forward (L w = e_last: w = 0 except w_last), then back
+    double y[M];
+    for (int a = 0; a < m; ++a) y[a] = 0.0;
+    y[m - 1] = 1.0 / L[(m - 1) * m / 2 + (m - 1)];
+    for (int a = m - 1; a >= 0; --a) {
+      double s = y[a];
+      for (int c = a + 1; c < m; ++c) s -= L[c * (c + 1) / 2 + a] * y[c];
+      y[a] = s / L[a * (a + 1) / 2 + a];
+    }
+    const double sc = 1.0 / sqrt(y[m - 1]);
+    for (int a = 0; a < m; ++a) g[t0 + a] = y[a] * sc;
+  }
+}
+
+// ELL layouts of G and G^T for the loop from the factor values (tril order):
+// slot m of row i at [m n + i]; src = tril index or -1 (padding: the row's own
+// column, value 0).
+template <typename T>
+__global__ void fill_ell_kernel(int64_t n, int w, const int32_t* __restrict__ src, const double* __restrict__ g,
+                                T* __restrict__ val) {
+  const int64_t total = (int64_t)w * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = src[e];
+    val[e] = s >= 0 ? (T)g[s] : T(0);
+  }
+}
+
+__global__ void g_positive_kernel(int64_t n, const int32_t* __restrict__ trp, const double* __restrict__ g,
+                                  unsigned long long* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = g[trp[i + 1] - 1];  // the diagonal ends the row
+    if (!(d > 0.0) || !isfinite(d)) atomicAdd(bad, 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- the PCG loop
+
+template <typename T>
+struct Ell {
+  const int32_t* col;
+  const T* val;
+  int w;
+};
+
+template <typename T>
+struct FsaiVecs {
+  T *r0, *r1, *p, *q, *t, *x;  // x: the iterate (fp64) or the correction d (refinement)
+};
+
+struct FsaiParams {
+  SolveParams P;            // A (CSR and loop matrix, unscaled), b, x, partials, limits
+  Ell<double> G64, GT64;
+  Ell<float> G32, GT32;
+  FsaiVecs<double> V64;
+  FsaiVecs<float> V32;
+};
+
+// t = G r (r the current residual), rho = t.t = r.z; then p = G^T t.
+template <typename T>
+__device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
+                           double* part, int pstride, Grid& g, double* rho) {
+  Acc<T> a;
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    T s = T(0);
+    for (int m = 0; m < G.w; ++m) s = fma(__ldg(G.val + m * n + i), r[__ldg(G.col + m * n + i)], s);
+    V.t[i] = s;
+    a.add(s, s);
+  }
+  double v[1] = {a.get()};
+  publish<1>(v, part + kSlotRes * (size_t)pstride, g);
+  if (!g.sync()) return false;
+  grid_sum<1>(part + kSlotRes * (size_t)pstride, g.G, v);
+  *rho = v[0];
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    T s = T(0);
+    for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[__ldg(GT.col + m * n + i)], s);
+    V.p[i] = s;
+  }
+  return g.sync();
+}
+
+// The PCG loop from a start state (r in V.r0, p = G^T G r, rho = r.z, rr =
+// r.r) until sqrt(rr) <= stop_abs (kOk), maxit (kNotConverged), breakdown /
+// non-finite values, or a barrier timeout.  x += alpha p each iteration.
+template <typename T>
+__device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, double rho,
+                         double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g) {
+  const int64_t n = S.n;
+  int k = *iters;
+  int status = kNotConverged;
+  if (sqrt(rr) <= stop_abs) status = kOk;
+  bool done = sqrt(rr) <= stop_abs || k >= maxit;
+  T* rc = V.r0;
+  T* rn = V.r1;
+  while (!done) {
+    double v1[1] = {spmv_phase<T, false>(S, V.p, V.q, g)};
+    publish<1>(v1, part + kSlotPQ * (size_t)pstride, g);
+    if (!g.sync()) { status = kTimeout; break; }
+    double pq[1];
+    grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
+    if (!isfinite(pq[0]) || !isfinite(rho)) { status = kNumeric; break; }
+    if (pq[0] <= 0.0) { status = kBreakdown; break; }
+    const T alpha = (T)(rho / pq[0]);
+    Acc<T> a_rho, a_rr;
+    for (int64_t i = g.gtid; i < n; i += g.gstride) {
+      const T ri = fma(-alpha, V.q[i], rc[i]);
+      rn[i] = ri;
+      a_rr.add(ri, ri);
+      T s = T(0);
+      for (int m = 0; m < G.w; ++m) {
+        const int j = __ldg(G.col + m * n + i);
+        s = fma(__ldg(G.val + m * n + i), fma(-alpha, V.q[j], rc[j]), s);
+      }
+      V.t[i] = s;
+      a_rho.add(s, s);
+      V.x[i] = fma(alpha, V.p[i], V.x[i]);
+    }
+    double v2[2] = {a_rho.get(), a_rr.get()};
+    publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
+    if (!g.sync()) { status = kTimeout; break; }
+    double s2[2];
+    grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
+    const T beta = (T)(s2[0] / rho);
+    rho = s2[0];
+    rr = s2[1];
+    ++k;
+    const bool conv = sqrt(rr) <= stop_abs;
+    done = conv || k >= maxit;
+    if (conv) status = kOk;
+    T* tmp = rc;
+    rc = rn;
+    rn = tmp;
+    if (!done) {
+      for (int64_t i = g.gtid; i < n; i += g.gstride) {
+        T s = T(0);
+        for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[__ldg(GT.col + m * n + i)], s);
+        V.p[i] = fma(beta, V.p[i], s);
+      }
+      if (!g.sync()) { status = kTimeout; break; }
+    }
+  }
+  *iters = k;
+  return status;
+}
+
+// fp64 PCG with G^T G: true-residual check and restarts as cg_solve (R1-R5, R7).
+__global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
+  __shared__ double s_prod[kCap];
+  const SolveParams& P = F.P;
+  Grid g(P.st, P.timeout_ns, P.skip_seq);
+  const int64_t n = P.A.n;
+  const FsaiVecs<double>& V = F.V64;
+  int status = kNotConverged, k = 0, restarts = 0;
+  double relres_true = 0.0, bb = 0.0, rr = 0.0;
+  bool first = true;
+  for (;;) {
+    spmv_orig(P.A, P.x, V.q, g, s_prod);
+    if (!g.sync()) { status = kTimeout; break; }
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = g.gtid; i < n; i += g.gstride) {
+      const double bi = P.b[i];
+      const double ri = bi - V.q[i];
+      V.r0[i] = ri;
+      v[0] += ri * ri;
+      v[1] += bi * bi;
+    }
+    publish<2>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+    if (!g.sync()) { status = kTimeout; break; }
+    double s2[2];
+    grid_sum<2>(P.part + kSlotRes * (size_t)P.pstride, g.G, s2);
+    const double rr_start = s2[0];
+    if (first) {
+      bb = s2[1];
+      if (bb == 0.0) {
+        for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] = 0.0;
+        status = kOk;
+        break;
+      }
+    }
+    relres_true = sqrt(rr_start) / sqrt(bb);
+    if (!first) {
+      if (!isfinite(relres_true)) { status = kNumeric; break; }
+      if (relres_true <= P.tol) { status = kOk; break; }
+      if (k >= P.maxit || restarts >= P.max_restarts) { status = kNotConverged; break; }
+      ++restarts;
+    } else if (sqrt(rr_start) <= P.tol * sqrt(bb)) {
+      status = kOk;  // x0 meets tol
+      break;
+    } else if (k >= P.maxit) {
+      status = kNotConverged;
+      break;
+    }
+    first = false;
+    double rho = 0.0;
+    if (!fsai_start<double>(F.G64, F.GT64, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    const int st = fsai_loop<double>(P.S64, F.G64, F.GT64, V, rho, rr_start, P.tol * sqrt(bb), P.maxit, &k,
+                                     P.part, P.pstride, g);
+    if (st == kTimeout) { status = kTimeout; break; }
+    if (st == kNumeric || st == kBreakdown) {
+      status = st;
+      spmv_orig(P.A, P.x, V.q, g, s_prod);  // the true residual of the last iterate
+      if (!g.sync()) { status = kTimeout; break; }
+      double w[1] = {0.0};
+      for (int64_t i = g.gtid; i < n; i += g.gstride) {
+        const double ri = P.b[i] - V.q[i];
+        w[0] += ri * ri;
+      }
+      publish<1>(w, P.part + kSlotRes * (size_t)P.pstride, g);
+      if (!g.sync()) { status = kTimeout; break; }
+      grid_sum<1>(P.part + kSlotRes * (size_t)P.pstride, g.G, w);
+      relres_true = sqrt(w[0]) / sqrt(bb);
+      break;
+    }
+    // kOk or kNotConverged: back to the true residual
+  }
+  if (g.cta == 0 && threadIdx.x == 0) {
+    P.st->status = status;
+    P.st->iters = k;
+    P.st->restarts = restarts;
+    P.st->relres_true = relres_true;
+    P.st->relres_rec = relres_true;
+  }
+}
+
+// fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7).
+__global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
+  __shared__ double s_prod[kCap];
+  const SolveParams& P = F.P;
+  Grid g(P.st, P.timeout_ns, P.skip_seq);
+  const int64_t n = P.A.n;
+  const FsaiVecs<float>& V = F.V32;
+  int status = kNotConverged, inner = 0, outer = 0;
+  double relres = 0.0, bb = 0.0;
+  for (;;) {
+    spmv_orig(P.A, P.x, F.V64.q, g, s_prod);
+    if (!g.sync()) { status = kTimeout; break; }
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = g.gtid; i < n; i += g.gstride) {
+      const double bi = P.b[i];
+      const double ri = bi - F.V64.q[i];
+      const float r32 = (float)ri;
+      V.r0[i] = r32;
+      V.x[i] = 0.0f;
+      v[0] += ri * ri;
+      v[1] += bi * bi;
+      v[2] += (double)r32 * (double)r32;
+    }
+    publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+    if (!g.sync()) { status = kTimeout; break; }
+    double s3[3];
+    grid_sum<3>(P.part + kSlotRes * (size_t)P.pstride, g.G, s3);
+    if (outer == 0) {
+      bb = s3[1];
+      if (bb == 0.0) {
+        for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] = 0.0;
+        status = kOk;
+        break;
+      }
+    }
+    relres = sqrt(s3[0]) / sqrt(bb);
+    if (!isfinite(relres)) { status = kNumeric; break; }
+    if (relres <= P.tol) { status = kOk; break; }
+    if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
+    double rho = 0.0;
+    if (!fsai_start<float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    const int st = fsai_loop<float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
+                                    P.part, P.pstride, g);
+    if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
+    for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)V.x[i];
+    if (!g.sync()) { status = kTimeout; break; }
+    ++outer;
+  }
+  if (g.cta == 0 && threadIdx.x == 0) {
+    P.st->status = status;
+    P.st->iters = inner;
+    P.st->restarts = outer;
+    P.st->relres_true = relres;
+    P.st->relres_rec = relres;
+  }
+}
+
+}  // namespace
+
+void cgi::fsai_free(FsaiData* f) {
+  if (!f) return;
+  void* dev[] = {f->trp,   f->tci,    f->tsrc,   f->g,      f->gsrc,  f->gcol,  f->gval64, f->gval32,
+                 f->gtsrc, f->gtcol,  f->gtval64, f->gtval32, f->r0,   f->r1,    f->t,      f->r0_32,
+                 f->r1_32, f->t_32,   f->x_32,   f->offs,   f->work,  f->dout,  f->gpart,  f->mlp_o,
+                 f->params_bf16};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  delete f;
+}
+
+// Pattern of G (tril(A)) and of G^T, their ELL slot maps, once per handle.
+cg_status cgi::fsai_pattern(cg_handle* h) {
+  if (h->fsai) return CG_OK;
+  if (!h->jacobi_ok) return ffail(h, CG_ERR_INVALID, "FSAI needs a positive diagonal in every row");
+  const int64_t n = h->n, nnz = h->nnz;
+  std::vector<int32_t> ci((size_t)nnz);
+  if (nnz > 0)
+    CGF_CUDA(h, cudaMemcpy(ci.data(), h->colind, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
+  const std::vector<int32_t>& rp = h->host_rowptr;
+  std::vector<int32_t> trp((size_t)n + 1, 0), tci, tsrc;
+  tci.reserve((size_t)(nnz / 2 + n));
+  tsrc.reserve((size_t)(nnz / 2 + n));
+  for (int64_t i = 0; i < n; ++i) {
+    int last = -1;
+    for (int k = rp[(size_t)i]; k < rp[(size_t)i + 1]; ++k) {
+      const int c = ci[(size_t)k];
+      if (c <= last) return ffail(h, CG_ERR_INVALID, "FSAI needs strictly increasing columns in each row");
+      last = c;
+      if (c <= i) {
+        tci.push_back(c);
+        tsrc.push_back(k);
+      }
+    }
+    trp[(size_t)i + 1] = (int32_t)tci.size();
+    const int len = trp[(size_t)i + 1] - trp[(size_t)i];
+    if (len == 0 || tci.back() != i) return ffail(h, CG_ERR_INVALID, "FSAI needs a diagonal entry in every row");
+    if (len > kFsaiMaxRow)
+      return ffail(h, CG_ERR_INVALID, "FSAI: a row of tril(A) has more than " + std::to_string(kFsaiMaxRow) +
+                                          " entries");
+  }
+  const int64_t nt = (int64_t)tci.size();
+  // G^T rows: entries (i, j) of tril grouped by column j, i ascending
+  std::vector<int32_t> cnt((size_t)n, 0);
+  for (int64_t e = 0; e < nt; ++e) ++cnt[(size_t)tci[(size_t)e]];
+  int gw = 0, gtw = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    gw = std::max(gw, trp[(size_t)i + 1] - trp[(size_t)i]);
+    gtw = std::max(gtw, cnt[(size_t)i]);
+  }
+  if (gtw > kFsaiMaxCol)
+    return ffail(h, CG_ERR_INVALID, "FSAI: a column of tril(A) has more than " + std::to_string(kFsaiMaxCol) +
+                                        " entries");
+  std::vector<int32_t> gsrc((size_t)gw * n), gcol((size_t)gw * n), gtsrc((size_t)gtw * n), gtcol((size_t)gtw * n);
+  for (int64_t i = 0; i < n; ++i) {
+    const int a = trp[(size_t)i], len = trp[(size_t)i + 1] - a;
+    for (int m = 0; m < gw; ++m) {
+      gsrc[(size_t)m * n + i] = m < len ? a + m : -1;
+      gcol[(size_t)m * n + i] = m < len ? tci[(size_t)(a + m)] : (int32_t)i;
+    }
+  }
+  std::vector<int32_t> fillc((size_t)n, 0);
+  for (int64_t i = 0; i < n; ++i)  // rows ascending: G^T row j lists i ascending
+    for (int e = trp[(size_t)i]; e < trp[(size_t)i + 1]; ++e) {
+      const int j = tci[(size_t)e];
+      const int m = fillc[(size_t)j]++;
+      gtsrc[(size_t)m * n + j] = e;
+      gtcol[(size_t)m * n + j] = (int32_t)i;
+    }
+  for (int64_t j = 0; j < n; ++j)
+    for (int m = fillc[(size_t)j]; m < gtw; ++m) {
+      gtsrc[(size_t)m * n + j] = -1;
+      gtcol[(size_t)m * n + j] = (int32_t)j;
+    }
+  FsaiData* f = new FsaiData();
+  h->fsai = f;
+  f->ntril = nt;
+  f->gw = gw;
+  f->gtw = gtw;
+  auto up = [&](int32_t** d, const std::vector<int32_t>& v) -> cudaError_t {
+    cudaError_t e = cudaMalloc(d, sizeof(int32_t) * std::max<size_t>(v.size(), 1));
+    if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*d, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+    return e;
+  };
+  CGF_CUDA(h, up(&f->trp, trp));
+  CGF_CUDA(h, up(&f->tci, tci));
+  CGF_CUDA(h, up(&f->tsrc, tsrc));
+  CGF_CUDA(h, up(&f->gsrc, gsrc));
+  CGF_CUDA(h, up(&f->gcol, gcol));
+  CGF_CUDA(h, up(&f->gtsrc, gtsrc));
+  CGF_CUDA(h, up(&f->gtcol, gtcol));
+  const size_t nv = (size_t)std::max<int64_t>(n, 1);
+  CGF_CUDA(h, cudaMalloc(&f->g, sizeof(double) * (size_t)std::max<int64_t>(nt, 1)));
+  CGF_CUDA(h, cudaMalloc(&f->gval64, sizeof(double) * (size_t)gw * nv));
+  CGF_CUDA(h, cudaMalloc(&f->gval32, sizeof(float) * (size_t)gw * nv));
+  CGF_CUDA(h, cudaMalloc(&f->gtval64, sizeof(double) * (size_t)gtw * nv));
+  CGF_CUDA(h, cudaMalloc(&f->gtval32, sizeof(float) * (size_t)gtw * nv));
+  for (double** v : {&f->r0, &f->r1, &f->t}) CGF_CUDA(h, cudaMalloc(v, sizeof(double) * nv));
+  for (float** v : {&f->r0_32, &f->r1_32, &f->t_32, &f->x_32}) CGF_CUDA(h, cudaMalloc(v, sizeof(float) * nv));
+  return CG_OK;
+}
+
+// Check the factor in f->g (positive diagonal) and refresh the loop's ELL values.
+cg_status cgi::fsai_commit(cg_handle* h, int kind) {
+  FsaiData* f = h->fsai;
+  const int64_t n = h->n;
+  unsigned long long* bad = nullptr;
+  CGF_CUDA(h, cudaMalloc(&bad, sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) {
+    g_positive_kernel<<<blocks_for(n), 256, 0, h->stream>>>(n, f->trp, f->g, bad);
+    e = cudaGetLastError();
+  }
+  unsigned long long hb = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(bad);
+  CGF_CUDA(h, e);
+  if (hb) {
+    f->kind = 0;
+    return ffail(h, CG_ERR_INVALID, "FSAI factor: " + std::to_string(hb) + " rows without a positive finite diagonal");
+  }
+  fill_ell_kernel<double><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval64);
+  fill_ell_kernel<float><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval32);
+  fill_ell_kernel<double><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g, f->gtval64);
+  fill_ell_kernel<float><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g, f->gtval32);
+  CGF_CUDA(h, cudaGetLastError());
+  CGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  f->kind = kind;
+  return CG_OK;
+}
+
+// The PCG with the handle's factor; P carries the unscaled loop matrices.
+cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, int grid, int32_t* iters_out,
+                          double* relres_out) {
+  FsaiData* f = h->fsai;
+  const int64_t n = h->n;
+  FsaiParams F{};
+  F.P = Pin;
+  F.G64 = Ell<double>{f->gcol, f->gval64, f->gw};
+  F.GT64 = Ell<double>{f->gtcol, f->gtval64, f->gtw};
+  F.G32 = Ell<float>{f->gcol, f->gval32, f->gw};
+  F.GT32 = Ell<float>{f->gtcol, f->gtval32, f->gtw};
+  F.V64 = FsaiVecs<double>{f->r0, f->r1, Pin.V64.p, Pin.V64.q, f->t, Pin.x};
+  F.V32 = FsaiVecs<float>{f->r0_32, f->r1_32, Pin.V32.p, Pin.V32.q, f->t_32, f->x_32};
+  void* args[] = {&F};
+  const void* fn = fp64 ? (const void*)pcg_fsai64_kernel : (const void*)pcg_fsai_ir_kernel;
+  int per_sm = 0;
+  CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
+  const int G = std::max(1, std::min(grid, per_sm * h->sm_count));
+  CGF_CUDA(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+  CGF_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  CGF_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), args, 0, h->stream));
+  CGF_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  CGF_CUDA(h, cudaMemcpyAsync(h->host_st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  float ms = 0.0f;
+  CGF_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  const DevState& ds = *h->host_st;
+  const cg_status status = ds.abort ? CG_ERR_TIMEOUT : (cg_status)ds.status;
+  h->last.status = status;
+  h->last.iters = ds.iters;
+  h->last.restarts = ds.restarts;
+  h->last.grid_ctas = G;
+  h->last.relres_true = ds.relres_true;
+  h->last.relres_rec = ds.relres_rec;
+  h->last.kernel_ms = ms;
+  h->last.loop_form = 1;
+  h->last.kernel_launches = 1;
+  h->last.precond_used = CG_PRECOND_FSAI;
+  // modelled bytes per iteration: A (CSR), G and G^T (values + columns) and the vector streams
+  const int64_t vb = fp64 ? 8 : 4, ib = 4;
+  const int64_t per_iter = (vb + ib) * (h->nnz + 2 * f->ntril) + 4 * (n + 1) + 13 * vb * n;
+  h->last.bytes_moved = per_iter * (int64_t)ds.iters;
+  h->last.kernel_bytes_per_iter = per_iter;
+  if (iters_out) *iters_out = ds.iters;
+  if (relres_out) *relres_out = ds.relres_true;
+  if (status == CG_ERR_TIMEOUT) return ffail(h, status, "cg_solve (FSAI): a grid barrier timed out");
+  if (status < 0) return ffail(h, status, std::string("cg_solve (FSAI): ") + cg_status_string(status));
+  return status;
+}
+
+extern "C" {
+
+cg_status cg_fsai_classic(cg_handle* h) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return ffail(h, CG_ERR_INVALID, "cg_fsai_classic: batch handle");
+  if (h->n == 0) return ffail(h, CG_ERR_INVALID, "cg_fsai_classic: empty matrix");
+  cg_status s = cgi::fsai_pattern(h);
+  if (s != CG_OK) return s;
+  FsaiData* f = h->fsai;
+  unsigned long long* bad = nullptr;
+  CGF_CUDA(h, cudaMalloc(&bad, sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess) {
+    classic_fsai_kernel<<<blocks_for(h->n), 128, 0, h->stream>>>(h->n, h->rowptr, h->colind, h->vals, f->trp,
+                                                                  f->tci, f->g, bad);
+    e = cudaGetLastError();
+  }
+  unsigned long long hb = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(bad);
+  CGF_CUDA(h, e);
+  if (hb) {
+    f->kind = 0;
+    return ffail(h, CG_ERR_INVALID, "cg_fsai_classic: " + std::to_string(hb) + " local matrices are not SPD");
+  }
+  return cgi::fsai_commit(h, 1);
+}
+
+cg_status cg_fsai_set_factor(cg_handle* h, const double* g_tril) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return ffail(h, CG_ERR_INVALID, "cg_fsai_set_factor: batch handle");
+  if (!g_tril || h->n == 0) return ffail(h, CG_ERR_INVALID, "cg_fsai_set_factor: NULL values or empty matrix");
+  cg_status s = cgi::fsai_pattern(h);
+  if (s != CG_OK) return s;
+  CGF_CUDA(h, cudaMemcpyAsync(h->fsai->g, g_tril, sizeof(double) * (size_t)h->fsai->ntril, cudaMemcpyDeviceToDevice,
+                              h->stream));
+  return cgi::fsai_commit(h, 3);
+}
+
+cg_status cg_fsai_get_factor(cg_handle* h, double* g_tril, int64_t* ntril, int32_t* kind) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return ffail(h, CG_ERR_INVALID, "cg_fsai_get_factor: batch handle");
+  if (h->n > 0 && !h->fsai) {
+    cg_status s = cgi::fsai_pattern(h);
+    if (s != CG_OK) return s;
+  }
+  const FsaiData* f = h->fsai;
+  if (ntril) *ntril = f ? f->ntril : 0;
+  if (kind) *kind = f ? f->kind : 0;
+  if (g_tril && f && f->kind) {
+    CGF_CUDA(h, cudaMemcpyAsync(g_tril, f->g, sizeof(double) * (size_t)f->ntril, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    CGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return CG_OK;
+}
+
+}  // extern "C"

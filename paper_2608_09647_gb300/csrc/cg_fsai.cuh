@@ -1,0 +1,41 @@
+// FSAI preconditioner state of a handle (shared by cg_fsai.cu and cg_mlp.cu).
+#pragma once
+
+#include "cg_handle.cuh"
+
+constexpr int kFsaiMaxRow = 16;   // longest row of tril(A) the factor supports
+constexpr int kFsaiMaxCol = 32;   // longest column of tril(A) (row of G^T)
+
+struct FsaiData {
+  int64_t ntril = 0;               // entries of tril(A) = nonzeros of G
+  int32_t *trp = nullptr, *tci = nullptr;  // tril(A) pattern (CSR)
+  int32_t* tsrc = nullptr;         // index of each tril entry in A's arrays
+  double* g = nullptr;             // factor values in tril order
+  int kind = 0;                    // 0 none, 1 classic, 2 learned, 3 set by the caller
+  // ELL layouts for the loop: slot m of row i at [m n + i]
+  int gw = 0, gtw = 0;
+  int32_t *gsrc = nullptr, *gcol = nullptr;     // G
+  double* gval64 = nullptr;
+  float* gval32 = nullptr;
+  int32_t *gtsrc = nullptr, *gtcol = nullptr;   // G^T
+  double* gtval64 = nullptr;
+  float* gtval32 = nullptr;
+  // loop vectors beyond the handle's
+  double *r0 = nullptr, *r1 = nullptr, *t = nullptr;
+  float *r0_32 = nullptr, *r1_32 = nullptr, *t_32 = nullptr, *x_32 = nullptr;
+  // learned factor: matrix offsets, work space
+  int32_t* offs = nullptr;         // sorted distinct column offsets of A
+  int noffs = 0, ntslots = 0;      // their count; count of those <= 0
+  double* work = nullptr;          // training work vectors
+  float* dout = nullptr;           // dLoss/do per tril entry
+  float* gpart = nullptr;          // per-CTA partial parameter gradients
+  float* mlp_o = nullptr;          // MLP output per tril entry
+  uint16_t* params_bf16 = nullptr; // device copy of the loaded bf16 parameters
+};
+
+namespace cgi {
+cg_status fsai_pattern(cg_handle* h);
+cg_status fsai_commit(cg_handle* h, int kind);
+cg_status fsai_solve(cg_handle* h, const cg::SolveParams& P, bool fp64, int grid, int32_t* iters_out,
+                     double* relres_out);
+}  // namespace cgi

@@ -19,9 +19,11 @@ using cg::GState;
 using cg::kMaxDiag;
 
 struct BatchData;                 // batched solves (cg_batch.cu)
+struct FsaiData;                  // FSAI preconditioner (cg_fsai.cu, cg_mlp.cu)
 
 namespace cgi {
 void batch_free(BatchData* b);
+void fsai_free(FsaiData* f);
 void set_create_error(const std::string& msg);  // message of cg_last_error(NULL)
 }  // namespace cgi
 
@@ -98,5 +100,6 @@ struct cg_handle {
   cg_solve_info last{};
   std::string err;
   BatchData* batch = nullptr;       // set for handles made by cg_batch_create
+  FsaiData* fsai = nullptr;         // FSAI factor (built on first use)
 };
 

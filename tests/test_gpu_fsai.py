@@ -1,0 +1,177 @@
+"""GPU parity of the FSAI preconditioner (cg_fsai_classic / cg_fsai_set_factor and
+cg_solve with CG_PRECOND_FSAI) against the oracle (oracle/fsai.py, oracle.c R7).
+
+Tolerances: classic factor values to 1e-10 relative (a Cholesky solve against the
+oracle's LU solve of the same 2..16-row systems); solves as for cg_solve: same status,
+|iters - iters_oracle| <= max(3, 2%), true relative residual <= tol, x to the oracle's
+x within 1e-4 relative."""
+import math
+
+import numpy as np
+import pytest
+
+import cgproblems as gen
+import oracle
+from oracle import fsai
+from helpers import to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2608_09647_gb300 as cg  # noqa: E402
+
+
+def iters_band(k):
+    return max(3, math.ceil(0.02 * k))
+
+
+def handle(A):
+    return cg.cg_create(A.n, *to_device(A))
+
+
+CASES = [
+    ("q1_24", lambda: gen.q1aniso(24, 1.5, 0.6, 0.01, 3)),
+    ("q1_37_ragged", lambda: gen.q1aniso(37, 1.5, 2.4, 0.2, 5)),
+    ("lap2d_9pt", lambda: gen.lap2d(30, 9, 1e-2)),
+    ("diff27", lambda: gen.diff3d27(9, 1.0, 1)),
+]
+
+
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_classic_factor_matches_oracle(name, make):
+    A = make()
+    h = handle(A)
+    assert cg.cg_fsai_classic(h) == cg.CG_OK, cg.cg_last_error(h)
+    st, g, kind = cg.cg_fsai_get_factor(h)
+    assert st == cg.CG_OK and kind == 1
+    ref = fsai.classic(A)
+    g = g.cpu().numpy()
+    assert np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-300)) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [cg.CG_PREC_FP64, cg.CG_PREC_FP32_IR], ids=["fp64", "fp32_ir"])
+@pytest.mark.parametrize("name,make", CASES, ids=[c[0] for c in CASES])
+def test_fsai_pcg_matches_oracle(name, make, precision):
+    A = make()
+    g = fsai.classic(A)
+    b = oracle.spmv(A, gen.xstar(A.n, 7))
+    tol = 1e-9
+    h = handle(A)
+    assert cg.cg_fsai_set_factor(h, torch.from_numpy(g).cuda()) == cg.CG_OK
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, tol, 20000, cg.CG_PRECOND_FSAI, precision)
+    info = cg.cg_get_solve_info(h)
+    assert info["precond_used"] == cg.CG_PRECOND_FSAI
+    if precision == cg.CG_PREC_FP64:
+        ref = fsai.pcg(A, g, b, tol=tol, maxit=20000)
+    else:
+        ref = fsai.pcg_ir(A, g, b, tol=tol, tol_in=1e-4, maxit=20000)
+    assert st == ref.status == cg.CG_OK, (st, ref.status, cg.cg_last_error(h))
+    assert abs(it - ref.iters) <= iters_band(ref.iters), (it, ref.iters)
+    xs = x.cpu().numpy()
+    rel_or = oracle.true_relres(A, b, xs)
+    assert rel_or <= tol * (1 + 1e-6)
+    assert abs(rel - rel_or) <= 1e-6 * rel_or + 1e-15
+    assert np.linalg.norm(xs - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
+    # the GPU's own classic factor gives the same solve
+    h2 = handle(A)
+    assert cg.cg_fsai_classic(h2) == cg.CG_OK
+    x2 = torch.zeros_like(bd)
+    st2, it2, _ = cg.cg_solve(h2, bd, x2, tol, 20000, cg.CG_PRECOND_FSAI, precision)
+    assert st2 == cg.CG_OK and abs(it2 - it) <= 1
+
+
+def test_fsai_beats_jacobi_on_anisotropic_q1():
+    A = gen.q1aniso(64, 1.5, 0.3, 1e-2, 11)
+    b = oracle.spmv(A, gen.xstar(A.n, 3))
+    h = handle(A)
+    assert cg.cg_fsai_classic(h) == cg.CG_OK
+    bd = torch.from_numpy(b).cuda()
+    its = {}
+    for pc in (cg.CG_PRECOND_JACOBI, cg.CG_PRECOND_FSAI):
+        x = torch.zeros_like(bd)
+        st, it, rel = cg.cg_solve(h, bd, x, 1e-8, 20000, pc)
+        assert st == cg.CG_OK and rel <= 1e-8
+        its[pc] = it
+    ref_j = oracle.pcg(A, b, tol=1e-8, maxit=20000, precond=1)
+    ref_f = fsai.pcg(A, fsai.classic(A), b, tol=1e-8, maxit=20000)
+    assert abs(its[cg.CG_PRECOND_JACOBI] - ref_j.iters) <= iters_band(ref_j.iters)
+    assert abs(its[cg.CG_PRECOND_FSAI] - ref_f.iters) <= iters_band(ref_f.iters)
+    assert its[cg.CG_PRECOND_FSAI] < 0.7 * its[cg.CG_PRECOND_JACOBI]
+
+
+def test_jacobi_factor_reproduces_jacobi():
+    """G = D^-1/2 set by the caller: G^T G = D^-1, so the counts equal Jacobi-PCG's."""
+    A = gen.q1aniso(40, 1.5, 1.0, 0.05, 2)
+    trp, tci, _ = fsai.tril(A)
+    rows = np.repeat(np.arange(A.n), np.diff(trp))
+    gj = np.where(rows == tci, 1.0 / np.sqrt(fsai.diag(A))[rows], 0.0)
+    b = oracle.spmv(A, gen.xstar(A.n, 1))
+    h = handle(A)
+    assert cg.cg_fsai_set_factor(h, torch.from_numpy(gj).cuda()) == cg.CG_OK
+    assert cg.cg_fsai_get_factor(h)[2] == 3
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, _ = cg.cg_solve(h, bd, x, 1e-9, 5000, cg.CG_PRECOND_FSAI)
+    ref = oracle.pcg(A, b, tol=1e-9, maxit=5000, precond=1)
+    assert st == cg.CG_OK and abs(it - ref.iters) <= iters_band(ref.iters)
+
+
+def test_fsai_without_a_factor_falls_back_to_jacobi():
+    A = gen.q1aniso(20, 1.5, 0.5, 0.1, 4)
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    h = handle(A)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, 1e-8, 5000, cg.CG_PRECOND_FSAI)
+    assert st == cg.CG_OK and rel <= 1e-8
+    assert cg.cg_get_solve_info(h)["precond_used"] == cg.CG_PRECOND_JACOBI
+    ref = oracle.pcg(A, b, tol=1e-8, maxit=5000, precond=1)
+    assert abs(it - ref.iters) <= iters_band(ref.iters)
+
+
+def test_fsai_edge_cases():
+    A = gen.q1aniso(16, 1.5, 0.5, 0.1, 6)
+    h = handle(A)
+    assert cg.cg_fsai_classic(h) == cg.CG_OK
+    g = fsai.classic(A)
+    # b = 0: x = 0, no iterations
+    bd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    x = torch.ones_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, 1e-8, 100, cg.CG_PRECOND_FSAI)
+    assert st == cg.CG_OK and it == 0 and torch.all(x == 0)
+    # maxit reached: not converged, same count and residual as the oracle
+    b = oracle.spmv(A, gen.xstar(A.n, 5))
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, 1e-12, 5, cg.CG_PRECOND_FSAI)
+    ref = fsai.pcg(A, g, b, tol=1e-12, maxit=5)
+    assert st == ref.status == cg.CG_NOT_CONVERGED and it == ref.iters == 5
+    assert abs(rel - ref.relres_true) <= 1e-8 * ref.relres_true
+    # a factor with a non-positive diagonal is refused
+    bad = g.copy()
+    trp, tci, _ = fsai.tril(A)
+    bad[trp[3 + 1] - 1] = -1.0
+    assert cg.cg_fsai_set_factor(h, torch.from_numpy(bad).cuda()) == cg.CG_ERR_INVALID
+    assert "diagonal" in cg.cg_last_error(h)
+
+
+def test_fsai_rejects_unsuitable_matrices():
+    # an indefinite matrix: a local matrix is not SPD
+    M = np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    import scipy.sparse as sp
+    S = sp.csr_matrix(M)
+    A = gen.CSR(3, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data, "indef")
+    h = handle(A)
+    assert cg.cg_fsai_classic(h) == cg.CG_ERR_INVALID
+    assert "not SPD" in cg.cg_last_error(h)
+    # unsorted columns in a row
+    A = gen.lap2d(5)
+    ci = A.colind.copy()
+    ci[[5, 6]] = ci[[6, 5]]
+    va = A.vals.copy()
+    va[[5, 6]] = va[[6, 5]]
+    h = handle(gen.CSR(A.n, A.rowptr, ci, va, "unsorted"))
+    assert cg.cg_fsai_classic(h) == cg.CG_ERR_INVALID
+    assert "increasing" in cg.cg_last_error(h)
