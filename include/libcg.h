@@ -236,6 +236,48 @@ cg_status cg_fsai_set_factor(cg_handle* h, const double* g_tril);
  * *ntril = nonzeros of tril(A), *kind = 0 none, 1 classic, 2 learned, 3 set. */
 cg_status cg_fsai_get_factor(cg_handle* h, double* g_tril, int64_t* ntril, int32_t* kind);
 
+/*
+ * Learned FSAI factor (not in the paper): an MLP with CG_MLP_INPUTS inputs,
+ * two hidden ReLU layers of CG_MLP_HIDDEN units and one output maps local
+ * features of every entry (i, j) of tril(A) to G_ij.  Features (A_ii = d_i,
+ * s(i,k) = A_ik / sqrt(d_i d_k)): [0:8] one-hot slot of j - i among the
+ * non-positive column offsets of A; [8] s(i,j); [9] log(d_j / d_i); [10:19]
+ * s(i, i + o_m) and [19:28] s(j, j + o_m) over the sorted distinct column
+ * offsets o_m of A (the matrix may have at most 9); [28] 1; [29:32] 0.
+ * Output o: G_ij = o / sqrt(d_j) for j < i and G_ii = softplus(o + c0) /
+ * sqrt(d_i) with softplus(c0) = 1, so a zero output layer is Jacobi.
+ * Parameters, in this order (row-major, a row per output unit):
+ *   W1[64][32], b1[64], W2[64][64], b2[64], W3[64], b3  (CG_MLP_PARAMS values).
+ * Layers 1 and 2 run on the tensor cores with bf16 inputs and fp32 sums.
+ */
+#define CG_MLP_INPUTS 32
+#define CG_MLP_HIDDEN 64
+#define CG_MLP_PARAMS 6337
+
+/* Compute the handle's factor with the MLP (inference).  weights_bf16: HOST
+ * array of CG_MLP_PARAMS bfloat16 values (bytes = 2 * CG_MLP_PARAMS). */
+cg_status cg_fsai_load(cg_handle* h, const void* weights_bf16, int64_t bytes);
+
+/*
+ * Training loss of the MLP on the handle's matrix and its gradient.
+ * params: DEVICE fp32[CG_MLP_PARAMS] (rounded to bf16 for the forward pass);
+ * grad: DEVICE fp32[CG_MLP_PARAMS], overwritten with dLoss/dparams; resid:
+ * DEVICE fp64[nresid][n] residual vectors r_k (may be NULL when nresid = 0).
+ *   Loss = log((1/n) sum_i g_i^T A g_i) - (2/n) sum_i log G_ii      (Kaporin)
+ *        + lambda (1/K) sum_k ||A G^T G r_k - r_k||^2 / ||r_k||^2.
+ * *loss_out (host) receives the loss.  Reductions run in a fixed order: the
+ * same inputs give the same bits.  Does not change the handle's factor.
+ */
+cg_status cg_fsai_loss_grad(cg_handle* h, const float* params, float* grad, const double* resid,
+                            int32_t nresid, double lambda, double* loss_out);
+
+/* One Adam step (Kingma & Ba) on DEVICE fp32 arrays of count values:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps); step >= 1.
+ * Enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream). */
+cg_status cg_adam_step(float* params, const float* grad, float* m, float* v, int64_t count, float lr,
+                       float beta1, float beta2, float eps, int32_t step, void* cuda_stream);
+
 /* Largest n that cg_solve_noalloc accepts: its scratch is four device vectors
  * of this many doubles plus a result block (2 MiB per GPU). */
 #define CG_NOALLOC_MAX_ROWS 65536

@@ -30,7 +30,9 @@ EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
            "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
            "cg_last_error", "cg_status_string", "cg_solve_noalloc", "cg_batch_create",
            "cg_solve_batch", "cg_batch_get_system", "cg_batch_get_tuning", "cg_fsai_classic",
-           "cg_fsai_set_factor", "cg_fsai_get_factor")
+           "cg_fsai_set_factor", "cg_fsai_get_factor", "cg_fsai_load", "cg_fsai_loss_grad",
+           "cg_adam_step")
+CG_MLP_INPUTS, CG_MLP_HIDDEN, CG_MLP_PARAMS = 32, 64, 6337
 CG_NOALLOC_MAX_ROWS = 65536
 CG_BATCH_MAX_SYSTEMS = 4096
 
@@ -96,6 +98,10 @@ def load(build_if_missing: bool = True):
     lib.cg_fsai_classic.argtypes = [P]
     lib.cg_fsai_set_factor.argtypes = [P, P]
     lib.cg_fsai_get_factor.argtypes = [P, P, pi64, pi32]
+    lib.cg_fsai_load.argtypes = [P, P, i64]
+    lib.cg_fsai_loss_grad.argtypes = [P, P, P, P, i32, f64, pf64]
+    f32 = ctypes.c_float
+    lib.cg_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
     lib.cg_solve_batch.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
     lib.cg_batch_get_system.argtypes = [P, i32, pi32, pi32, pi32, pf64]
     lib.cg_batch_get_tuning.argtypes = [P, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
@@ -351,6 +357,52 @@ def cg_fsai_get_factor(h: Handle):
     g = torch.empty(nt.value, dtype=torch.float64, device="cuda")
     st = lib.cg_fsai_get_factor(h.ptr, _dptr(g, torch.float64, "g"), None, None)
     return st, g, kind.value
+
+
+def bf16_bits(params) -> "np.ndarray":
+    """fp32 values -> bfloat16 bit patterns (round to nearest even), the format of
+    cg_fsai_load's weights."""
+    import numpy as np
+    u = np.ascontiguousarray(params, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def cg_fsai_load(h: Handle, params) -> int:
+    """Compute the handle's FSAI factor with the MLP; params: CG_MLP_PARAMS fp32 values
+    (host array or tensor), rounded to bf16 for the call."""
+    import numpy as np
+    if hasattr(params, "detach"):
+        params = params.detach().cpu().numpy()
+    bits = bf16_bits(np.asarray(params, dtype=np.float32))
+    if bits.size != CG_MLP_PARAMS:
+        raise ValueError(f"expected {CG_MLP_PARAMS} parameters")
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    return lib.cg_fsai_load(h.ptr, ctypes.c_void_p(bits.ctypes.data), bits.nbytes)
+
+
+def cg_fsai_loss_grad(h: Handle, params, grad, resid=None, lam: float = 0.1):
+    """Loss of the MLP on the handle's matrix and its gradient (written into grad).
+    params, grad: CUDA float32 tensors of CG_MLP_PARAMS; resid: CUDA float64 [k, n] or
+    None.  Returns (status, loss)."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    loss = ctypes.c_double(0.0)
+    k = 0 if resid is None else int(resid.shape[0])
+    st = lib.cg_fsai_loss_grad(h.ptr, _dptr(params, torch.float32, "params"), _dptr(grad, torch.float32, "grad"),
+                               None if resid is None else _dptr(resid, torch.float64, "resid"), k, float(lam),
+                               ctypes.byref(loss))
+    return st, loss.value
+
+
+def cg_adam_step(params, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8) -> int:
+    """One Adam step on CUDA float32 tensors (current stream)."""
+    import torch
+    return load().cg_adam_step(_dptr(params, torch.float32, "params"), _dptr(grad, torch.float32, "grad"),
+                               _dptr(m, torch.float32, "m"), _dptr(v, torch.float32, "v"), params.numel(),
+                               float(lr), float(beta1), float(beta2), float(eps), int(step), _stream_ptr())
 
 
 @dataclass

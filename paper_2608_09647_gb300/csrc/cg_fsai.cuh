@@ -24,13 +24,16 @@ struct FsaiData {
   double *r0 = nullptr, *r1 = nullptr, *t = nullptr;
   float *r0_32 = nullptr, *r1_32 = nullptr, *t_32 = nullptr, *x_32 = nullptr;
   // learned factor: matrix offsets, work space
-  int32_t* offs = nullptr;         // sorted distinct column offsets of A
+  int32_t* offs = nullptr;         // sorted distinct column offsets of A (device)
+  int host_offs[9] = {};           // the same on the host
   int noffs = 0, ntslots = 0;      // their count; count of those <= 0
+  int32_t* trow = nullptr;         // row of each tril entry
   double* work = nullptr;          // training work vectors
+  double* rpart = nullptr;         // block partial sums of the loss kernels
   float* dout = nullptr;           // dLoss/do per tril entry
   float* gpart = nullptr;          // per-CTA partial parameter gradients
   float* mlp_o = nullptr;          // MLP output per tril entry
-  uint16_t* params_bf16 = nullptr; // device copy of the loaded bf16 parameters
+  float* params32 = nullptr;       // parameters given to cg_fsai_load (device, fp32)
 };
 
 namespace cgi {
