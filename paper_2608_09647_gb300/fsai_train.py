@@ -20,7 +20,7 @@ import time
 
 import numpy as np
 
-from . import (CG_MLP_HIDDEN, CG_MLP_INPUTS, CG_MLP_PARAMS, CG_OK, CG_NOT_CONVERGED, CG_PREC_FP32_IR,
+from . import (CG_MLP_HIDDEN, CG_MLP_INPUTS, CG_MLP_PARAMS, CG_OK, CG_NOT_CONVERGED, CG_PREC_FP32_IR, CG_PREC_FP64,
                CG_PRECOND_FSAI, CG_PRECOND_JACOBI, CGError, cg_adam_step, cg_create, cg_destroy,
                cg_fsai_classic, cg_fsai_load, cg_fsai_loss_grad, cg_get_solve_info, cg_last_error, cg_solve,
                cg_spmv)
@@ -117,16 +117,23 @@ def solve_stats(P, precond, tol=1e-8, maxit=100000, precision=CG_PREC_FP32_IR, r
 
 
 def compare(problems, params, tol=1e-8, precision=CG_PREC_FP32_IR, reps=2):
-    """Per matrix: Jacobi, classic FSAI and learned FSAI iterations and times."""
+    """Per matrix: Jacobi, classic FSAI and learned FSAI iterations, solve times
+    (device time of the solve launch) and factor setup times (host wall time of
+    cg_fsai_classic / cg_fsai_load, which synchronise)."""
     rows = []
+    params = params.detach().cpu().numpy() if hasattr(params, "detach") else params
     for P in problems:
         r = {"n": P.A.n, "name": P.A.name}
         r["jacobi_iters"], r["jacobi_s"], _, _ = solve_stats(P, CG_PRECOND_JACOBI, tol, precision=precision, reps=reps)
+        t0 = time.perf_counter()
         if cg_fsai_classic(P.h) != CG_OK:
             raise CGError(-1, cg_last_error(P.h))
+        r["classic_setup_s"] = time.perf_counter() - t0
         r["classic_iters"], r["classic_s"], _, _ = solve_stats(P, CG_PRECOND_FSAI, tol, precision=precision, reps=reps)
+        t0 = time.perf_counter()
         if cg_fsai_load(P.h, params) != CG_OK:
             raise CGError(-1, cg_last_error(P.h))
+        r["learned_setup_s"] = time.perf_counter() - t0
         r["learned_iters"], r["learned_s"], _, used = solve_stats(P, CG_PRECOND_FSAI, tol, precision=precision,
                                                                   reps=reps)
         assert used == CG_PRECOND_FSAI
@@ -163,6 +170,7 @@ def main():
     ap.add_argument("--test-sides", type=int, nargs=2, default=(256, 1024))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--precision", choices=["fp32_ir", "fp64"], default="fp32_ir")
     args = ap.parse_args()
     t0 = time.time()
     tr = [q1_problem(i, args.seed, *args.train_sides) for i in range(args.train)]
@@ -171,14 +179,19 @@ def main():
     t2 = time.time()
     for P in tr:
         P.close()
-    te = [q1_problem(args.train + i, args.seed, *args.test_sides, snapshots=()) for i in range(args.test)]
-    rows = compare(te, params)
+    rows = []
+    prec = CG_PREC_FP32_IR if args.precision == "fp32_ir" else CG_PREC_FP64
+    for i in range(args.test):  # one held-out matrix at a time (they reach 10^6 rows)
+        P = q1_problem(args.train + i, args.seed, *args.test_sides, snapshots=())
+        rows += compare([P], params, precision=prec)
+        P.close()
     t3 = time.time()
     summary = summarize(rows)
     res = {"train": args.train, "test": args.test, "epochs": args.epochs, "lr": args.lr, "lam": args.lam,
+           "precision": args.precision,
            "train_sides": list(args.train_sides), "test_sides": list(args.test_sides), "loss_history": hist,
            "seconds": {"setup": t1 - t0, "train": t2 - t1, "evaluate": t3 - t2}, "summary": summary,
-           "per_matrix": rows, "params_bf16_sha": None}
+           "per_matrix": rows}
     print(json.dumps(summary, indent=1))
     if args.out:
         with open(args.out, "w") as f:
