@@ -125,6 +125,9 @@ def compare(problems, params, tol=1e-8, precision=CG_PREC_FP32_IR, reps=2):
     for P in problems:
         r = {"n": P.A.n, "name": P.A.name}
         r["jacobi_iters"], r["jacobi_s"], _, _ = solve_stats(P, CG_PRECOND_JACOBI, tol, precision=precision, reps=reps)
+        # the plain fp64 Jacobi-PCG baseline (auto loop form)
+        r["jacobi64_iters"], r["jacobi64_s"], _, _ = solve_stats(P, CG_PRECOND_JACOBI, tol, precision=CG_PREC_FP64,
+                                                                 reps=reps)
         t0 = time.perf_counter()
         if cg_fsai_classic(P.h) != CG_OK:
             raise CGError(-1, cg_last_error(P.h))
@@ -149,6 +152,11 @@ def summarize(rows):
     for a, b in (("learned", "jacobi"), ("learned", "classic"), ("classic", "jacobi")):
         out[f"{a}_vs_{b}_iters"] = q([r[f"{a}_iters"] / r[f"{b}_iters"] for r in rows])
         out[f"{a}_vs_{b}_time"] = q([r[f"{a}_s"] / r[f"{b}_s"] for r in rows])
+    # against plain fp64 Jacobi-PCG, in time to tolerance (the iteration counts differ in kind
+    # when the compared solve refines)
+    out["learned_vs_jacobi64_time"] = q([r["learned_s"] / r["jacobi64_s"] for r in rows])
+    out["learned_setup_plus_solve_vs_jacobi64_time"] = q([(r["learned_s"] + r["learned_setup_s"]) / r["jacobi64_s"]
+                                                          for r in rows])
     return out
 
 
