@@ -466,6 +466,8 @@ def main():
                     help="seconds of oracle CPU time for the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-spmv-compare", action="store_true",
+                    help="skip the cg_spmv vs cuSPARSE comparison")
     ap.add_argument("--no-sequential", action="store_true",
                     help="batch workloads: skip the one-system-at-a-time comparison")
     ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled"])
@@ -587,6 +589,35 @@ def main():
         e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
                "h2d_bytes_per_step": 16 * A.n, "d2h_bytes_per_step": 8 * A.n}
 
+    # the caller-CSR SpMV (cg_spmv) against cuSPARSE through torch's CSR tensor, the
+    # comparison the paper makes for its own kernel (Sec. 4.1)
+    spmv = None
+    if not args.no_spmv_compare:
+        At = torch.sparse_csr_tensor(rp, ci, va, size=(A.n, A.n))
+        y1 = torch.empty_like(xs)
+        y2 = torch.empty_like(xs)
+
+        def timed(fn, reps=10):
+            for _ in range(3):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        t_lib = timed(lambda: cg.cg_spmv(h, xs, y1))
+        t_cus = timed(lambda: y2.copy_(At @ xs))
+        agree = bool(torch.allclose(y1, y2, rtol=1e-12, atol=1e-12))
+        sb = 12 * A.nnz + 4 * (A.n + 1) + 16 * A.n
+        spmv = {"libcg_ms": t_lib, "cusparse_ms": t_cus, "libcg_gbs": sb / t_lib / 1e6,
+                "cusparse_gbs": sb / t_cus / 1e6, "libcg_vs_cusparse": t_cus / t_lib,
+                "bytes_model": sb, "results_agree": agree,
+                "note": "cusparse time includes torch's output copy (8n bytes more)"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -625,6 +656,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "cpu_baseline": cpu,
+            "spmv": spmv,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
