@@ -69,23 +69,30 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_sha():
+# Sources that define each workload's timed kernels: a committed traffic figure
+# counts only while these files are unchanged.
+KERNEL_SOURCES = {
+    "single": ("cg_device.cuh", "cg_kernels.cuh", "cg_graph.cuh", "cg_api.cu"),
+    "batch": ("cg_device.cuh", "cg_kernels.cuh", "cg_batch.cu"),
+}
+
+
+def kernel_source_sha(kind="single"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2608_09647_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kind]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload):
-    """DRAM bytes per launch of the solver kernel from the committed ncu summary, if it
-    was taken from the current kernel sources (else None)."""
+def ncu_traffic(workload, kind="single"):
+    """DRAM bytes of the timed kernels from the committed ncu summary, if it was taken
+    from the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(workload)
-    if not d or d.get("kernel_sha") != kernel_source_sha():
+    if not d or d.get("kernel_sha") != kernel_source_sha(kind):
         return None
     return d
 
@@ -365,6 +372,10 @@ def run_batch(args, world, rank, dev, torch, cg):
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
     launches = sum(inf["kernel_launches"] for _, _, inf in infos)
     form = {1: "persistent", 2: "graph"}.get(infos[0][2]["loop_form"], "?")
+    # DRAM bytes of one launch from the committed ncu capture (a smaller batch, scaled by
+    # the row-iterations processed), while the kernel sources are unchanged
+    tr = ncu_traffic(args.workload, "batch")
+    traffic = int(tr["dram_bytes_per_row_iter"] * sum(n_i * k_i for n_i, k_i in zip(ns, its))) if tr else None
 
     e2e = None
     if not args.no_e2e:
@@ -440,7 +451,7 @@ def run_batch(args, world, rank, dev, torch, cg):
                        "grid_ctas": infos[0][2]["grid_ctas"], "autotuner": tuning,
                        "loop_mode": args.loop_mode},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "timed_unit": "one batched solve: the persistent batch kernel (whole launch)",
                          "loop_form": form,
                          "bytes_model": "sum over systems of iters x (12 nnz + 4 (n+1) + 104 n)"},

@@ -116,6 +116,21 @@ __global__ void fill_ell_kernel(int64_t n, int w, const int32_t* __restrict__ sr
   }
 }
 
+// Diagonal layouts of G and G^T: entry e = (i, j) of tril(A) in slot s_e of
+// row i of G and in slot nd - 1 - s_e of row j of G^T (the offsets of G^T are
+// those of G negated, in reverse order).  Every position is written at most
+// once; the rest stays 0 from the memset.
+template <typename T>
+__global__ void fill_dia_kernel(int64_t nt, int64_t n, int nd, const int32_t* __restrict__ trow,
+                                const int32_t* __restrict__ tci, const int8_t* __restrict__ slot,
+                                const double* __restrict__ g, T* __restrict__ gv, T* __restrict__ gtv) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = slot[e];
+    gv[(int64_t)s * n + trow[e]] = (T)g[e];
+    gtv[(int64_t)(nd - 1 - s) * n + tci[e]] = (T)g[e];
+  }
+}
+
 __global__ void g_positive_kernel(int64_t n, const int32_t* __restrict__ trp, const double* __restrict__ g,
                                   unsigned long long* bad) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -127,12 +142,22 @@ __global__ void g_positive_kernel(int64_t n, const int32_t* __restrict__ trp, co
 
 // ---------------------------------------------------------------- the PCG loop
 
+// G or G^T for the loop: slot m of row i at [m n + i]; the column is col[m n + i]
+// (ELL) or, in the diagonal layout (DIA), i + delta[m] clamped into [0, n) (the
+// value is 0 wherever the diagonal leaves the pattern).
 template <typename T>
 struct Ell {
   const int32_t* col;
   const T* val;
   int w;
+  int delta[kFsaiMaxDiag];
 };
+
+template <bool DIA, typename T>
+__device__ __forceinline__ int ell_col(const Ell<T>& E, int m, int64_t i, int64_t n) {
+  if (DIA) return min(max((int)i + E.delta[m], 0), (int)n - 1);
+  return __ldg(E.col + m * n + i);
+}
 
 template <typename T>
 struct FsaiVecs {
@@ -148,13 +173,13 @@ struct FsaiParams {
 };
 
 // t = G r (r the current residual), rho = t.t = r.z; then p = G^T t.
-template <typename T>
+template <bool DIA, typename T>
 __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
                            double* part, int pstride, Grid& g, double* rho) {
   Acc<T> a;
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
     T s = T(0);
-    for (int m = 0; m < G.w; ++m) s = fma(__ldg(G.val + m * n + i), r[__ldg(G.col + m * n + i)], s);
+    for (int m = 0; m < G.w; ++m) s = fma(__ldg(G.val + m * n + i), r[ell_col<DIA>(G, m, i, n)], s);
     V.t[i] = s;
     a.add(s, s);
   }
@@ -165,7 +190,7 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
   *rho = v[0];
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
     T s = T(0);
-    for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[__ldg(GT.col + m * n + i)], s);
+    for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[ell_col<DIA>(GT, m, i, n)], s);
     V.p[i] = s;
   }
   return g.sync();
@@ -174,7 +199,7 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
 // The PCG loop from a start state (r in V.r0, p = G^T G r, rho = r.z, rr =
 // r.r) until sqrt(rr) <= stop_abs (kOk), maxit (kNotConverged), breakdown /
 // non-finite values, or a barrier timeout.  x += alpha p each iteration.
-template <typename T>
+template <bool DIA, typename T>
 __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, double rho,
                          double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g) {
   const int64_t n = S.n;
@@ -200,7 +225,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
       a_rr.add(ri, ri);
       T s = T(0);
       for (int m = 0; m < G.w; ++m) {
-        const int j = __ldg(G.col + m * n + i);
+        const int j = ell_col<DIA>(G, m, i, n);
         s = fma(__ldg(G.val + m * n + i), fma(-alpha, V.q[j], rc[j]), s);
       }
       V.t[i] = s;
@@ -225,7 +250,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     if (!done) {
       for (int64_t i = g.gtid; i < n; i += g.gstride) {
         T s = T(0);
-        for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[__ldg(GT.col + m * n + i)], s);
+        for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[ell_col<DIA>(GT, m, i, n)], s);
         V.p[i] = fma(beta, V.p[i], s);
       }
       if (!g.sync()) { status = kTimeout; break; }
@@ -236,6 +261,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
 }
 
 // fp64 PCG with G^T G: true-residual check and restarts as cg_solve (R1-R5, R7).
+template <bool DIA>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
   __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
@@ -284,8 +310,8 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
     }
     first = false;
     double rho = 0.0;
-    if (!fsai_start<double>(F.G64, F.GT64, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
-    const int st = fsai_loop<double>(P.S64, F.G64, F.GT64, V, rho, rr_start, P.tol * sqrt(bb), P.maxit, &k,
+    if (!fsai_start<DIA, double>(F.G64, F.GT64, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    const int st = fsai_loop<DIA, double>(P.S64, F.G64, F.GT64, V, rho, rr_start, P.tol * sqrt(bb), P.maxit, &k,
                                      P.part, P.pstride, g);
     if (st == kTimeout) { status = kTimeout; break; }
     if (st == kNumeric || st == kBreakdown) {
@@ -315,6 +341,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
 }
 
 // fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7).
+template <bool DIA>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
@@ -354,8 +381,8 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
     if (relres <= P.tol) { status = kOk; break; }
     if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
     double rho = 0.0;
-    if (!fsai_start<float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
-    const int st = fsai_loop<float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
+    if (!fsai_start<DIA, float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    const int st = fsai_loop<DIA, float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
                                     P.part, P.pstride, g);
     if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
     for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)V.x[i];
@@ -378,7 +405,7 @@ void cgi::fsai_free(FsaiData* f) {
   void* dev[] = {f->trp,   f->tci,    f->tsrc,   f->g,      f->gsrc,  f->gcol,  f->gval64, f->gval32,
                  f->gtsrc, f->gtcol,  f->gtval64, f->gtval32, f->r0,   f->r1,    f->t,      f->r0_32,
                  f->r1_32, f->t_32,   f->x_32,   f->offs,   f->work,  f->dout,  f->gpart,  f->mlp_o,
-                 f->params32, f->trow, f->rpart};
+                 f->params32, f->trow, f->rpart, f->tslot};
   for (void* p : dev)
     if (p) cudaFree(p);
   delete f;
@@ -447,11 +474,34 @@ cg_status cgi::fsai_pattern(cg_handle* h) {
       gtsrc[(size_t)m * n + j] = -1;
       gtcol[(size_t)m * n + j] = (int32_t)j;
     }
+  // diagonal layout when tril(A) lies on at most kFsaiMaxDiag offsets
+  std::vector<int32_t> toffs;
+  std::vector<int32_t> trow((size_t)nt);
+  for (int64_t i = 0; i < n; ++i)
+    for (int e = trp[(size_t)i]; e < trp[(size_t)i + 1]; ++e) {
+      trow[(size_t)e] = (int32_t)i;
+      const int o = tci[(size_t)e] - (int)i;
+      if ((int)toffs.size() <= kFsaiMaxDiag && std::find(toffs.begin(), toffs.end(), o) == toffs.end())
+        toffs.push_back(o);
+    }
+  const bool dia = (int)toffs.size() <= kFsaiMaxDiag;
+  std::vector<int8_t> tslot;
+  if (dia) {
+    std::sort(toffs.begin(), toffs.end());
+    tslot.resize((size_t)nt);
+    for (int64_t e = 0; e < nt; ++e) {
+      const int o = tci[(size_t)e] - trow[(size_t)e];
+      tslot[(size_t)e] = (int8_t)(std::lower_bound(toffs.begin(), toffs.end(), o) - toffs.begin());
+    }
+  }
   FsaiData* f = new FsaiData();
   h->fsai = f;
   f->ntril = nt;
   f->gw = gw;
   f->gtw = gtw;
+  f->dia = dia ? 1 : 0;
+  f->nd = dia ? (int)toffs.size() : 0;
+  for (int m = 0; m < f->nd; ++m) f->doff[m] = toffs[(size_t)m];
   auto up = [&](int32_t** d, const std::vector<int32_t>& v) -> cudaError_t {
     cudaError_t e = cudaMalloc(d, sizeof(int32_t) * std::max<size_t>(v.size(), 1));
     if (e == cudaSuccess && !v.empty()) e = cudaMemcpy(*d, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
@@ -464,7 +514,14 @@ cg_status cgi::fsai_pattern(cg_handle* h) {
   CGF_CUDA(h, up(&f->gcol, gcol));
   CGF_CUDA(h, up(&f->gtsrc, gtsrc));
   CGF_CUDA(h, up(&f->gtcol, gtcol));
+  CGF_CUDA(h, up(&f->trow, trow));
+  if (dia) {
+    CGF_CUDA(h, cudaMalloc(&f->tslot, std::max<size_t>(tslot.size(), 1)));
+    if (nt > 0) CGF_CUDA(h, cudaMemcpy(f->tslot, tslot.data(), tslot.size(), cudaMemcpyHostToDevice));
+  }
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
+  gw = std::max(gw, f->nd);  // value arrays serve either layout
+  gtw = std::max(gtw, f->nd);
   CGF_CUDA(h, cudaMalloc(&f->g, sizeof(double) * (size_t)std::max<int64_t>(nt, 1)));
   CGF_CUDA(h, cudaMalloc(&f->gval64, sizeof(double) * (size_t)gw * nv));
   CGF_CUDA(h, cudaMalloc(&f->gval32, sizeof(float) * (size_t)gw * nv));
@@ -495,10 +552,24 @@ cg_status cgi::fsai_commit(cg_handle* h, int kind) {
     f->kind = 0;
     return ffail(h, CG_ERR_INVALID, "FSAI factor: " + std::to_string(hb) + " rows without a positive finite diagonal");
   }
-  fill_ell_kernel<double><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval64);
-  fill_ell_kernel<float><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval32);
-  fill_ell_kernel<double><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g, f->gtval64);
-  fill_ell_kernel<float><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g, f->gtval32);
+  if (f->dia) {
+    const size_t w = (size_t)f->nd * (size_t)n;
+    CGF_CUDA(h, cudaMemsetAsync(f->gval64, 0, sizeof(double) * w, h->stream));
+    CGF_CUDA(h, cudaMemsetAsync(f->gtval64, 0, sizeof(double) * w, h->stream));
+    CGF_CUDA(h, cudaMemsetAsync(f->gval32, 0, sizeof(float) * w, h->stream));
+    CGF_CUDA(h, cudaMemsetAsync(f->gtval32, 0, sizeof(float) * w, h->stream));
+    fill_dia_kernel<double><<<blocks_for(f->ntril), 256, 0, h->stream>>>(f->ntril, n, f->nd, f->trow, f->tci,
+                                                                         f->tslot, f->g, f->gval64, f->gtval64);
+    fill_dia_kernel<float><<<blocks_for(f->ntril), 256, 0, h->stream>>>(f->ntril, n, f->nd, f->trow, f->tci,
+                                                                        f->tslot, f->g, f->gval32, f->gtval32);
+  } else {
+    fill_ell_kernel<double><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval64);
+    fill_ell_kernel<float><<<blocks_for((int64_t)f->gw * n), 256, 0, h->stream>>>(n, f->gw, f->gsrc, f->g, f->gval32);
+    fill_ell_kernel<double><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g,
+                                                                                    f->gtval64);
+    fill_ell_kernel<float><<<blocks_for((int64_t)f->gtw * n), 256, 0, h->stream>>>(n, f->gtw, f->gtsrc, f->g,
+                                                                                   f->gtval32);
+  }
   CGF_CUDA(h, cudaGetLastError());
   CGF_CUDA(h, cudaStreamSynchronize(h->stream));
   f->kind = kind;
@@ -512,14 +583,20 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, int g
   const int64_t n = h->n;
   FsaiParams F{};
   F.P = Pin;
-  F.G64 = Ell<double>{f->gcol, f->gval64, f->gw};
-  F.GT64 = Ell<double>{f->gtcol, f->gtval64, f->gtw};
-  F.G32 = Ell<float>{f->gcol, f->gval32, f->gw};
-  F.GT32 = Ell<float>{f->gtcol, f->gtval32, f->gtw};
+  const int w = f->dia ? f->nd : f->gw, wt = f->dia ? f->nd : f->gtw;
+  F.G64 = Ell<double>{f->gcol, f->gval64, w, {}};
+  F.GT64 = Ell<double>{f->gtcol, f->gtval64, wt, {}};
+  F.G32 = Ell<float>{f->gcol, f->gval32, w, {}};
+  F.GT32 = Ell<float>{f->gtcol, f->gtval32, wt, {}};
+  for (int m = 0; m < (f->dia ? f->nd : 0); ++m) {
+    F.G64.delta[m] = F.G32.delta[m] = f->doff[m];
+    F.GT64.delta[m] = F.GT32.delta[m] = -f->doff[f->nd - 1 - m];
+  }
   F.V64 = FsaiVecs<double>{f->r0, f->r1, Pin.V64.p, Pin.V64.q, f->t, Pin.x};
   F.V32 = FsaiVecs<float>{f->r0_32, f->r1_32, Pin.V32.p, Pin.V32.q, f->t_32, f->x_32};
   void* args[] = {&F};
-  const void* fn = fp64 ? (const void*)pcg_fsai64_kernel : (const void*)pcg_fsai_ir_kernel;
+  const void* fn = fp64 ? (f->dia ? (const void*)pcg_fsai64_kernel<true> : (const void*)pcg_fsai64_kernel<false>)
+                        : (f->dia ? (const void*)pcg_fsai_ir_kernel<true> : (const void*)pcg_fsai_ir_kernel<false>);
   int per_sm = 0;
   CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
   const int G = std::max(1, std::min(grid, per_sm * h->sm_count));
@@ -546,6 +623,7 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, int g
   // modelled bytes per iteration: A (CSR), G and G^T (values + columns) and the vector streams
   const int64_t vb = fp64 ? 8 : 4, ib = 4;
   const int64_t per_iter = (vb + ib) * (h->nnz + 2 * f->ntril) + 4 * (n + 1) + 13 * vb * n;
+  h->last.loop_form = 1;
   h->last.bytes_moved = per_iter * (int64_t)ds.iters;
   h->last.kernel_bytes_per_iter = per_iter;
   if (iters_out) *iters_out = ds.iters;

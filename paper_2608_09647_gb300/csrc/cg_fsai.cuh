@@ -5,6 +5,7 @@
 
 constexpr int kFsaiMaxRow = 16;   // longest row of tril(A) the factor supports
 constexpr int kFsaiMaxCol = 32;   // longest column of tril(A) (row of G^T)
+constexpr int kFsaiMaxDiag = 8;   // most offsets of tril(A) for the diagonal layout
 
 struct FsaiData {
   int64_t ntril = 0;               // entries of tril(A) = nonzeros of G
@@ -14,6 +15,9 @@ struct FsaiData {
   int kind = 0;                    // 0 none, 1 classic, 2 learned, 3 set by the caller
   // ELL layouts for the loop: slot m of row i at [m n + i]
   int gw = 0, gtw = 0;
+  int dia = 0, nd = 0;             // diagonal layout: its offset count and offsets
+  int32_t doff[kFsaiMaxDiag] = {};
+  int8_t* tslot = nullptr;         // diagonal slot of each tril entry
   int32_t *gsrc = nullptr, *gcol = nullptr;     // G
   double* gval64 = nullptr;
   float* gval32 = nullptr;

@@ -636,15 +636,6 @@ cg_status mlp_prepare(cg_handle* h) {
   int nts = 0;
   for (int o : offs) nts += o <= 0;
   if (nts > 8) return mfail(h, CG_ERR_INVALID, "learned FSAI: more than 8 offsets in tril(A)");
-  std::vector<int32_t> trow((size_t)f->ntril);
-  {
-    std::vector<int32_t> trp((size_t)n + 1);
-    CGM_CUDA(h, cudaMemcpy(trp.data(), f->trp, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost));
-    for (int64_t i = 0; i < n; ++i)
-      for (int e = trp[(size_t)i]; e < trp[(size_t)i + 1]; ++e) trow[(size_t)e] = (int32_t)i;
-  }
-  CGM_CUDA(h, cudaMalloc(&f->trow, sizeof(int32_t) * std::max<size_t>(trow.size(), 1)));
-  CGM_CUDA(h, cudaMemcpy(f->trow, trow.data(), sizeof(int32_t) * trow.size(), cudaMemcpyHostToDevice));
   CGM_CUDA(h, cudaMalloc(&f->offs, sizeof(int32_t) * kMaxOffs));
   f->noffs = (int)offs.size();
   f->ntslots = nts;
