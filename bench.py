@@ -32,6 +32,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+Q1_1024 = {"s": 1024, "sigma_a": 1.5, "theta": 0.7, "eps": 0.01, "seed": 3}
+FSAI_WEIGHTS = os.path.join(ROOT, "paper_2608_09647_gb300", "fsai_q1aniso_bf16.npy")
+
 WORKLOADS = {
     # name: (builder, kwargs, precond, precision, tol, maxit, description)
     "poisson3d_256": ("lap3d7", {"N": 256}, "jacobi", "fp64", 1e-8, 10000,
@@ -39,13 +42,27 @@ WORKLOADS = {
     "poisson2d_64": ("lap2d", {"N": 64}, "none", "fp64", 1e-8, 1000,
                      "2-D 5-point Poisson 64x64, FP64 CG to 1e-8"),
     "poisson3d_128": ("lap3d7", {"N": 128}, "jacobi", "fp64", 1e-8, 10000,
-                      "3-D 7-point Poisson 128^3, FP64 Jacobi-PCG to 1e-8 (profiling size)"),
+                      "3-D 7-point Poisson 128^3, FP64 Jacobi-PCG to 1e-8"),
+    "poisson3d_192": ("lap3d7", {"N": 192}, "jacobi", "fp64", 1e-8, 10000,
+                      "3-D 7-point Poisson 192^3, FP64 Jacobi-PCG to 1e-8 (profiling size: "
+                      "larger than L2, a few GB on the device)"),
     "diffusion27_160": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp32_ir",
                         1e-10, 100000,
                         "3-D 27-point lognormal diffusion 160^3, FP32 inner / FP64 refinement to 1e-10"),
     "diffusion27_160_fp64": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp64",
                              1e-10, 100000,
                              "3-D 27-point lognormal diffusion 160^3, FP64 Jacobi-PCG to 1e-10"),
+    "q1aniso_1024_learned": ("q1aniso", Q1_1024, "fsai_learned", "fp32_ir", 1e-8, 200000,
+                             "2-D rotated-anisotropy Q1 diffusion 1024^2 (a_c lognormal sigma 1.5, theta 0.7, "
+                             "eps 0.01), learned FSAI, FP32 inner / FP64 refinement to 1e-8"),
+    "q1aniso_1024_classic": ("q1aniso", Q1_1024, "fsai_classic", "fp32_ir", 1e-8, 200000,
+                             "the same matrix, classic FSAI, FP32 inner / FP64 refinement to 1e-8"),
+    "q1aniso_1024_jacobi_fp64": ("q1aniso", Q1_1024, "jacobi", "fp64", 1e-8, 200000,
+                                 "the same matrix, plain FP64 Jacobi-PCG to 1e-8"),
+    "q1aniso_1024_learned_fp64": ("q1aniso", Q1_1024, "fsai_learned", "fp64", 1e-8, 200000,
+                                  "the same matrix, learned FSAI, FP64 PCG to 1e-8"),
+    "batch64": ("batch", {"count": 64, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
+                "the first 64 systems of the 512-system batch (profiling size)"),
     "batch512": ("batch", {"count": 512, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                  "512 systems in one launch: 2-D 5-/9-point anisotropic Laplacians, side uniform "
                  "in [32, 512], eps log-uniform in [1e-3, 1]; FP64 Jacobi-PCG to 1e-8 each"),
@@ -177,10 +194,23 @@ def time_oracle_sample(A, b, precond, precision, tol, budget_s):
     matrix, as many as fit the budget.  Returns (seconds per iteration, iterations run)."""
     import oracle
     pc = 1 if precond == "jacobi" else 0
+    g = None
+    if precond.startswith("fsai"):  # the oracle's own factor (setup not timed)
+        from oracle import fsai
+        import numpy as np
+        if precond == "fsai_classic":
+            g = fsai.classic(A)
+        else:
+            bits = np.load(FSAI_WEIGHTS)
+            g = fsai.learned(A, (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64))
     m = 2
     while True:
         t0 = time.perf_counter()
-        if precision == "fp64":
+        if g is not None and precision == "fp64":
+            fsai.pcg(A, g, b, tol=0.0, maxit=m, max_restarts=0)
+        elif g is not None:
+            fsai.pcg_ir(A, g, b, tol=0.0, tol_in=1e-30, maxit=m, max_outer=1)
+        elif precision == "fp64":
             oracle.pcg(A, b, tol=0.0, maxit=m, precond=pc, max_restarts=0)
         else:
             oracle.pcg_ir(A, b, tol=0.0, tol_in=1e-30, maxit=m, max_outer=1, precond=pc)
@@ -259,7 +289,7 @@ def run_reference(args):
 def batch_systems(workload):
     import cgproblems as gen
     kw = WORKLOADS[workload][1]
-    params = gen.batch_members(kw["count"], kw["seed"])
+    params = gen.batch_members(512, kw["seed"])[:kw["count"]]
     return params, [gen.lap2d(side, pts, eps) for side, pts, eps in params]
 
 
@@ -324,6 +354,8 @@ def run_batch(args, world, rank, dev, torch, cg):
     h = cg.cg_batch_create([c[0] for c in dev_csr], [c[1] for c in dev_csr], [c[2] for c in dev_csr])
     if args.loop_mode in ("persistent", "graph"):
         assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, 1 if args.loop_mode == "persistent" else 2) == cg.CG_OK
+    if args.grid:
+        assert cg.cg_set_option(h, cg.CG_OPT_GRID_CTAS, args.grid) == cg.CG_OK
     torch.cuda.synchronize()
 
     def step():
@@ -482,6 +514,7 @@ def main():
     ap.add_argument("--no-sequential", action="store_true",
                     help="batch workloads: skip the one-system-at-a-time comparison")
     ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled"])
+    ap.add_argument("--grid", type=int, default=0, help="force the persistent grid (CTAs; 0 = automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -508,7 +541,7 @@ def main():
     if builder == "batch":
         run_batch(args, world, rank, dev, torch, cg)
         return
-    precond = cg.CG_PRECOND_JACOBI if precond_s == "jacobi" else cg.CG_PRECOND_NONE
+    precond = {"jacobi": cg.CG_PRECOND_JACOBI, "none": cg.CG_PRECOND_NONE}.get(precond_s, cg.CG_PRECOND_FSAI)
     precision = cg.CG_PREC_FP64 if precision_s == "fp64" else cg.CG_PREC_FP32_IR
 
     # every rank solves its own copy of the system (replicas: weak scaling)
@@ -522,6 +555,17 @@ def main():
     assert cg.cg_spmv(h, xs, b) == cg.CG_OK        # b = A x* on the device
     x = torch.zeros_like(b)
     torch.cuda.synchronize()
+    setup_ms = None
+    if precond_s.startswith("fsai"):  # the factor, once per matrix (timed on its own)
+        t0 = time.perf_counter()
+        if precond_s == "fsai_classic":
+            st = cg.cg_fsai_classic(h)
+        else:
+            bits = np.load(FSAI_WEIGHTS)
+            st = cg.cg_fsai_load(h, (bits.astype(np.uint32) << 16).view(np.float32))
+        if st != cg.CG_OK:
+            raise RuntimeError(f"FSAI setup failed: {cg.cg_last_error(h)}")
+        setup_ms = (time.perf_counter() - t0) * 1e3
 
     def step():
         x.zero_()
@@ -570,7 +614,7 @@ def main():
     peak, peak_kind = load_peaks()
     achieved = kern_bytes / (kern_ms / 1e3) / 1e9
     achieved_own = own_bytes / (kern_ms / 1e3) / 1e9
-    bpi = bytes_per_iter(A.n, A.nnz, precond_s, precision_s)
+    bpi = kern_bytes / max(1, sum(iters))  # the library's model for this preconditioner
     form = {1: "persistent", 2: "graph", 3: "unrolled"}.get(infos[0][2]["loop_form"], "?")
     launches = sum(inf["kernel_launches"] for _, _, inf in infos)
     tr = ncu_traffic(args.workload)
@@ -650,7 +694,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision_s == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n": A.n, "nnz": A.nnz,
-                       "tol": tol, "iters": iters[0], "relres_true_max": relres,
+                       "tol": tol, "iters": iters[0], "relres_true_max": relres, "precond": precond_s,
+                       "precond_setup_ms": setup_ms,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (no flush)",
                        "grid_ctas": infos[0][2]["grid_ctas"], "loop_mode": args.loop_mode},
             "iter_us": 1e3 * kern_ms / sum(iters),
