@@ -49,12 +49,17 @@ WORKLOADS = {
     "diffusion27_160": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp32_ir",
                         1e-10, 100000,
                         "3-D 27-point lognormal diffusion 160^3, FP32 inner / FP64 refinement to 1e-10"),
+    "diffusion27_160_ru": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp32_ru", 1e-10, 100000,
+                           "3-D 27-point lognormal diffusion 160^3, FP32 Jacobi-PCG with FP64 reliable "
+                           "updates to 1e-10"),
     "diffusion27_160_fp64": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "jacobi", "fp64",
                              1e-10, 100000,
                              "3-D 27-point lognormal diffusion 160^3, FP64 Jacobi-PCG to 1e-10"),
     "q1aniso_1024_learned": ("q1aniso", Q1_1024, "fsai_learned", "fp32_ir", 1e-8, 200000,
                              "2-D rotated-anisotropy Q1 diffusion 1024^2 (a_c lognormal sigma 1.5, theta 0.7, "
                              "eps 0.01), learned FSAI, FP32 inner / FP64 refinement to 1e-8"),
+    "q1aniso_1024_learned_ru": ("q1aniso", Q1_1024, "fsai_learned", "fp32_ru", 1e-8, 200000,
+                                "the same matrix, learned FSAI, FP32 PCG with FP64 reliable updates to 1e-8"),
     "q1aniso_1024_classic": ("q1aniso", Q1_1024, "fsai_classic", "fp32_ir", 1e-8, 200000,
                              "the same matrix, classic FSAI, FP32 inner / FP64 refinement to 1e-8"),
     "q1aniso_1024_jacobi_fp64": ("q1aniso", Q1_1024, "jacobi", "fp64", 1e-8, 200000,
@@ -542,7 +547,7 @@ def main():
         run_batch(args, world, rank, dev, torch, cg)
         return
     precond = {"jacobi": cg.CG_PRECOND_JACOBI, "none": cg.CG_PRECOND_NONE}.get(precond_s, cg.CG_PRECOND_FSAI)
-    precision = cg.CG_PREC_FP64 if precision_s == "fp64" else cg.CG_PREC_FP32_IR
+    precision = {"fp64": cg.CG_PREC_FP64, "fp32_ir": cg.CG_PREC_FP32_IR, "fp32_ru": cg.CG_PREC_FP32_RU}[precision_s]
 
     # every rank solves its own copy of the system (replicas: weak scaling)
     A = build_matrix(args.workload)

@@ -56,15 +56,20 @@ typedef enum {
 
 typedef enum {
   CG_PREC_FP64 = 0,       /* every value, vector and reduction in fp64 (Sec. 3.1) */
-  CG_PREC_FP32_IR = 1     /* fp32 inner PCG, fp64 outer iterative refinement (not in the paper) */
+  CG_PREC_FP32_IR = 1,    /* fp32 inner PCG, fp64 outer iterative refinement (not in the paper) */
+  CG_PREC_FP32_RU = 2     /* fp32 PCG with fp64 reliable updates: as CG_PREC_FP32_IR, but the
+                             search direction survives each fp64 update (p = z' + (r'.z'/rho) p)
+                             instead of restarting, so the iteration count stays close to fp64
+                             PCG's (not in the paper); persistent loop form only */
 } cg_precision;
 
 typedef enum {
   CG_OPT_MAX_RESTARTS = 0,        /* residual-replacement restarts after a false convergence (default 3) */
   CG_OPT_BARRIER_TIMEOUT_MS = 1,  /* grid-barrier wait limit in ms (default 2000) */
   CG_OPT_GRID_CTAS = 2,           /* persistent-kernel CTAs; 0 = choose automatically (default) */
-  CG_OPT_IR_TOL_INNER = 3,        /* inner relative tolerance of fp32 refinement (default 1e-4) */
-  CG_OPT_IR_MAX_OUTER = 4,        /* refinement steps cap (default 30) */
+  CG_OPT_IR_TOL_INNER = 3,        /* inner relative tolerance of fp32 refinement (default 1e-4), or the
+                                     residual reduction that triggers a reliable update (default 0.1) */
+  CG_OPT_IR_MAX_OUTER = 4,        /* refinement steps / reliable updates cap (default 30) */
   CG_OPT_DEBUG_SKIP_ARRIVAL = 5,  /* fault injection: CTA 0 skips arrival at grid barrier #value
                                      (1-based; 0 = off), so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */

@@ -8,7 +8,7 @@ package imports nothing from the product package.
 Citations (the paper: "A Preliminary Study on Simultaneous Coscheduling for
 Discrete GPU vs. Fused GPU"): CSR SpMV, Sec. 3.1; CG iteration, Alg. 1;
 fp64 throughout, Sec. 3.1; recomputed final residual, Sec. 3.1.  The readings
-R1-R7 taken where the paper is silent are listed in ``oracle.c``; the FSAI
+R1-R8 taken where the paper is silent are listed in ``oracle.c``; the FSAI
 preconditioner and its MLP (not in the paper) are in ``oracle.fsai`` (F1-F8).
 """
 from __future__ import annotations
@@ -61,6 +61,8 @@ def _bind(lib):
     lib.or_pcg_ir.argtypes = [i64, P, P, P, P, P, f64, f64, i32, i32, i32, P,
                               ctypes.POINTER(_Result)]
     lib.or_pcg_ir.restype = ctypes.c_int
+    lib.or_pcg_ru.argtypes = lib.or_pcg_ir.argtypes
+    lib.or_pcg_ru.restype = ctypes.c_int
     return lib
 
 
@@ -150,5 +152,21 @@ def pcg_ir(A, b, x0=None, tol=1e-10, tol_in=1e-4, maxit=100000, max_outer=30,
     res = _Result()
     _load().or_pcg_ir(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, tol_in, maxit,
                       max_outer, precond, _p(oh), ctypes.byref(res))
+    return Solve(x, res.status, res.iters, res.restarts, res.relres_rec, res.relres_true,
+                 outer_hist=oh[: res.restarts + 1])
+
+
+def pcg_ru(A, b, x0=None, tol=1e-10, tol_in=1e-4, maxit=100000, max_updates=30,
+           precond=1) -> Solve:
+    """fp32 inner PCG with fp64 reliable updates (reading R8): the refinement of R6 with
+    the search direction carried over each update.  iters = total inner iterations,
+    restarts = fp64 updates."""
+    n, rp, ci, va = _csr(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    oh = np.full(max_updates + 1, np.nan)
+    res = _Result()
+    _load().or_pcg_ru(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, tol_in, maxit,
+                      max_updates, precond, _p(oh), ctypes.byref(res))
     return Solve(x, res.status, res.iters, res.restarts, res.relres_rec, res.relres_true,
                  outer_hist=oh[: res.restarts + 1])

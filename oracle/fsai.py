@@ -317,6 +317,8 @@ def _bind_fsai(lib):
     lib.or_pcg_ir_fsai.argtypes = [i64, P, P, P, P, P, P, P, P, f64, f64, i32, i32, P,
                                    ctypes.POINTER(_Result)]
     lib.or_pcg_ir_fsai.restype = ctypes.c_int
+    lib.or_pcg_ru_fsai.argtypes = lib.or_pcg_ir_fsai.argtypes
+    lib.or_pcg_ru_fsai.restype = ctypes.c_int
     lib._fsai_bound = True
     return lib
 
@@ -341,8 +343,10 @@ def pcg(A, gvals, b, x0=None, tol=1e-8, maxit=1000, max_restarts=3, res_hist=Fal
     return s
 
 
-def pcg_ir(A, gvals, b, x0=None, tol=1e-8, tol_in=1e-4, maxit=100000, max_outer=30) -> Solve:
-    """fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7)."""
+def pcg_ir(A, gvals, b, x0=None, tol=1e-8, tol_in=1e-4, maxit=100000, max_outer=30,
+           carry=False) -> Solve:
+    """fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7);
+    carry=True carries the search direction over the fp64 updates (R8)."""
     lib = _bind_fsai(_load())
     n, rp, ci, va = _csr(A)
     trp, tci, _ = tril(A)
@@ -351,7 +355,8 @@ def pcg_ir(A, gvals, b, x0=None, tol=1e-8, tol_in=1e-4, maxit=100000, max_outer=
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     oh = np.full(max_outer + 1, np.nan)
     res = _Result()
-    lib.or_pcg_ir_fsai(n, _p(rp), _p(ci), _p(va), _p(trp), _p(tci), _p(gv), _p(b), _p(x), tol,
-                       tol_in, maxit, max_outer, _p(oh), ctypes.byref(res))
+    fn = lib.or_pcg_ru_fsai if carry else lib.or_pcg_ir_fsai
+    fn(n, _p(rp), _p(ci), _p(va), _p(trp), _p(tci), _p(gv), _p(b), _p(x), tol, tol_in, maxit,
+       max_outer, _p(oh), ctypes.byref(res))
     return Solve(x, res.status, res.iters, res.restarts, res.relres_rec, res.relres_true,
                  outer_hist=oh[: res.restarts + 1])

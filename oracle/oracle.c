@@ -29,6 +29,13 @@
  *      fp64 true residual and x += d, inner fp32 Jacobi-PCG with fp32
  *      vectors, fp64-accumulated dot products, alpha/beta formed in fp64 and
  *      rounded to fp32 for the fp32 vector updates.
+ *   R8 reliable updates (not in the paper; Sleijpen & van der Vorst 1996,
+ *      the mixed-precision form of Clark et al. 2010): R6 with the search
+ *      direction carried over each fp64 update.  The inner solve of each
+ *      outer step ends on its last direction p_k (no update after the last
+ *      step) and remembers rho_k = r.z before that step; the next inner solve
+ *      starts from the replaced residual r' with p = z' + (r'.z' / rho_k) p_k
+ *      instead of p = z', so the Krylov information is not thrown away.
  * Sums run in index order.  Compiled with -ffp-contract=off so no fused
  * multiply-add changes the rounding.
  */
@@ -189,18 +196,24 @@ int or_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, const double
 static int32_t pcg32(int64_t n, const int32_t* rowptr, const int32_t* colind,
                      const float* vals32, const float* dinv32, const float* rhs, float* d,
                      double tol_in, int32_t maxit, int32_t precond, float* r, float* z,
-                     float* p, float* q, int32_t* status_out) {
+                     float* p, float* q, int32_t* status_out, int carry, double* rho_io) {
   double bb = 0.0;
   for (int64_t i = 0; i < n; ++i) bb += (double)rhs[i] * (double)rhs[i];
   for (int64_t i = 0; i < n; ++i) { d[i] = 0.0f; r[i] = rhs[i]; }
   for (int64_t i = 0; i < n; ++i) z[i] = precond ? r[i] * dinv32[i] : r[i];
-  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
   double rho = 0.0, rr = bb;
   for (int64_t i = 0; i < n; ++i) rho += (double)r[i] * (double)z[i];
+  if (carry && *rho_io > 0.0) { /* R8: keep the last direction */
+    const float beta0 = (float)(rho / *rho_io);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta0 * p[i];
+  } else {
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  }
+  *rho_io = rho;
   int32_t k = 0;
   *status_out = OR_NOT_CONVERGED;
+  if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; return k; }
   for (;;) {
-    if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; break; }
     if (k >= maxit) break;
     for (int64_t i = 0; i < n; ++i) {
       float s = 0.0f;
@@ -221,10 +234,13 @@ static int32_t pcg32(int64_t n, const int32_t* rowptr, const int32_t* colind,
       rho_new += (double)r[i] * (double)z[i];
       rr += (double)r[i] * (double)r[i];
     }
+    ++k;
+    *rho_io = rho; /* rho_k of the step just taken */
+    if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; break; }
+    if (k >= maxit) break; /* p stays the last direction */
     const float beta = (float)(rho_new / rho);
     rho = rho_new;
     for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
-    ++k;
   }
   return k;
 }
@@ -238,9 +254,10 @@ static int32_t pcg32(int64_t n, const int32_t* rowptr, const int32_t* colind,
  * out->iters = total inner iterations, out->restarts = refinement steps,
  * outer_hist (optional, [max_outer+1]) = ||r||/||b|| at each outer test.
  */
-int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
-              const double* b, double* x, double tol, double tol_in, int32_t maxit,
-              int32_t max_outer, int32_t precond, double* outer_hist, or_result* out) {
+static int pcg_refine(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                      const double* b, double* x, double tol, double tol_in, int32_t maxit,
+                      int32_t max_outer, int32_t precond, double* outer_hist, or_result* out,
+                      int carry) {
   memset(out, 0, sizeof(*out));
   if (n < 0 || maxit < 0 || max_outer < 0 || !(tol >= 0.0) || !(tol_in > 0.0) ||
       (precond != 0 && precond != 1)) {
@@ -276,7 +293,7 @@ int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const dou
     for (int64_t i = 0; i < n; ++i) dinv32[i] = precond ? (float)dinv[i] : 1.0f;
     const double bnorm = sqrt(bb);
     int32_t inner_total = 0, outer = 0;
-    double relres = 0.0;
+    double relres = 0.0, rho_carry = 0.0;
     for (;;) {
       or_spmv(n, rowptr, colind, vals, x, r);
       double rr = 0.0;
@@ -289,7 +306,7 @@ int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const dou
       for (int64_t i = 0; i < n; ++i) r32[i] = (float)r[i];
       int32_t st;
       inner_total += pcg32(n, rowptr, colind, vals32, dinv32, r32, d, tol_in, maxit - inner_total,
-                           precond, rr32, z, p, q, &st);
+                           precond, rr32, z, p, q, &st, carry, &rho_carry);
       if (st == OR_ERR_NUMERIC || st == OR_ERR_BREAKDOWN) { status = st; break; }
       for (int64_t i = 0; i < n; ++i) x[i] += (double)d[i];
       ++outer;
@@ -303,6 +320,21 @@ int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const dou
   free(r); free(dinv); free(vals32);
   for (int i = 0; i < 7; ++i) free(f[i]);
   return status;
+}
+
+int or_pcg_ir(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+              const double* b, double* x, double tol, double tol_in, int32_t maxit,
+              int32_t max_outer, int32_t precond, double* outer_hist, or_result* out) {
+  return pcg_refine(n, rowptr, colind, vals, b, x, tol, tol_in, maxit, max_outer, precond,
+                    outer_hist, out, 0);
+}
+
+/* R8: the refinement with the search direction carried over each fp64 update. */
+int or_pcg_ru(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+              const double* b, double* x, double tol, double tol_in, int32_t maxit,
+              int32_t max_updates, int32_t precond, double* outer_hist, or_result* out) {
+  return pcg_refine(n, rowptr, colind, vals, b, x, tol, tol_in, maxit, max_updates, precond,
+                    outer_hist, out, 1);
 }
 
 /*
@@ -421,18 +453,24 @@ static int32_t pcg32_fsai(int64_t n, const int32_t* rowptr, const int32_t* colin
                           const float* vals32, const int32_t* grp, const int32_t* gci,
                           const float* g32, const float* rhs, float* d, double tol_in,
                           int32_t maxit, float* r, float* z, float* p, float* q, float* t,
-                          int32_t* status_out) {
+                          int32_t* status_out, int carry, double* rho_io) {
   double bb = 0.0;
   for (int64_t i = 0; i < n; ++i) bb += (double)rhs[i] * (double)rhs[i];
   for (int64_t i = 0; i < n; ++i) { d[i] = 0.0f; r[i] = rhs[i]; }
   fsai_apply32(n, grp, gci, g32, r, t, z);
-  for (int64_t i = 0; i < n; ++i) p[i] = z[i];
   double rho = 0.0, rr = bb;
   for (int64_t i = 0; i < n; ++i) rho += (double)r[i] * (double)z[i];
+  if (carry && *rho_io > 0.0) { /* R8 */
+    const float beta0 = (float)(rho / *rho_io);
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta0 * p[i];
+  } else {
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i];
+  }
+  *rho_io = rho;
   int32_t k = 0;
   *status_out = OR_NOT_CONVERGED;
+  if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; return k; }
   for (;;) {
-    if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; break; }
     if (k >= maxit) break;
     for (int64_t i = 0; i < n; ++i) {
       float s = 0.0f;
@@ -453,19 +491,22 @@ static int32_t pcg32_fsai(int64_t n, const int32_t* rowptr, const int32_t* colin
       rho_new += (double)r[i] * (double)z[i];
       rr += (double)r[i] * (double)r[i];
     }
+    ++k;
+    *rho_io = rho;
+    if (sqrt(rr) <= tol_in * sqrt(bb)) { *status_out = OR_OK; break; }
+    if (k >= maxit) break;
     const float beta = (float)(rho_new / rho);
     rho = rho_new;
     for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
-    ++k;
   }
   return k;
 }
 
 /* fp32-inner / fp64-outer refinement (R6) whose inner PCG uses M^-1 = G^T G (R7). */
-int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
-                   const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
-                   double* x, double tol, double tol_in, int32_t maxit, int32_t max_outer,
-                   double* outer_hist, or_result* out) {
+static int fsai_refine(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                       const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
+                       double* x, double tol, double tol_in, int32_t maxit, int32_t max_outer,
+                       double* outer_hist, or_result* out, int carry) {
   memset(out, 0, sizeof(*out));
   if (n < 0 || maxit < 0 || max_outer < 0 || !(tol >= 0.0) || !(tol_in > 0.0)) {
     out->status = OR_ERR_INVALID;
@@ -496,7 +537,7 @@ int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
   for (int64_t k = 0; k < gnnz; ++k) g32[k] = (float)gval[k];
   const double bnorm = sqrt(bb);
   int32_t inner_total = 0, outer = 0, status = OR_NOT_CONVERGED;
-  double relres = 0.0;
+  double relres = 0.0, rho_carry = 0.0;
   for (;;) {
     or_spmv(n, rowptr, colind, vals, x, r);
     double rr = 0.0;
@@ -509,7 +550,7 @@ int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
     for (int64_t i = 0; i < n; ++i) r32[i] = (float)r[i];
     int32_t st;
     inner_total += pcg32_fsai(n, rowptr, colind, vals32, grp, gci, g32, r32, d, tol_in,
-                              maxit - inner_total, rw, z, p, q, t, &st);
+                              maxit - inner_total, rw, z, p, q, t, &st, carry, &rho_carry);
     if (st == OR_ERR_NUMERIC || st == OR_ERR_BREAKDOWN) { status = st; break; }
     for (int64_t i = 0; i < n; ++i) x[i] += (double)d[i];
     ++outer;
@@ -522,4 +563,21 @@ int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, cons
   free(r); free(vals32); free(g32);
   for (int i = 0; i < 7; ++i) free(f[i]);
   return status;
+}
+
+int or_pcg_ir_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                   const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
+                   double* x, double tol, double tol_in, int32_t maxit, int32_t max_outer,
+                   double* outer_hist, or_result* out) {
+  return fsai_refine(n, rowptr, colind, vals, grp, gci, gval, b, x, tol, tol_in, maxit, max_outer,
+                     outer_hist, out, 0);
+}
+
+/* R8 with M^-1 = G32^T G32 (R7). */
+int or_pcg_ru_fsai(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
+                   const int32_t* grp, const int32_t* gci, const double* gval, const double* b,
+                   double* x, double tol, double tol_in, int32_t maxit, int32_t max_updates,
+                   double* outer_hist, or_result* out) {
+  return fsai_refine(n, rowptr, colind, vals, grp, gci, gval, b, x, tol, tol_in, maxit,
+                     max_updates, outer_hist, out, 1);
 }

@@ -20,7 +20,7 @@ CG_OK, CG_NOT_CONVERGED = 0, 1
 CG_ERR_INVALID, CG_ERR_BREAKDOWN, CG_ERR_NUMERIC = -1, -2, -3
 CG_ERR_TIMEOUT, CG_ERR_CUDA, CG_ERR_OOM = -4, -5, -6
 CG_PRECOND_NONE, CG_PRECOND_JACOBI, CG_PRECOND_FSAI = 0, 1, 2
-CG_PREC_FP64, CG_PREC_FP32_IR = 0, 1
+CG_PREC_FP64, CG_PREC_FP32_IR, CG_PREC_FP32_RU = 0, 1, 2
 CG_OPT_MAX_RESTARTS, CG_OPT_BARRIER_TIMEOUT_MS, CG_OPT_GRID_CTAS = 0, 1, 2
 CG_OPT_IR_TOL_INNER, CG_OPT_IR_MAX_OUTER, CG_OPT_DEBUG_SKIP_ARRIVAL = 3, 4, 5
 CG_OPT_PHASE_TIMERS, CG_OPT_LOOP_MODE = 6, 7

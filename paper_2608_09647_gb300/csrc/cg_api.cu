@@ -910,8 +910,10 @@ cg_status cg_create(int64_t n, const int32_t* rowptr, const int32_t* colind, con
   // persistent-kernel residency (the smallest over the kernels we may launch)
   const int g1 = max_coresident(pcg64_kernel<true>, h->sm_count);
   const int g2 = max_coresident(pcg64_kernel<false>, h->sm_count);
-  const int g3 = max_coresident(pcg_ir_kernel<true>, h->sm_count);
-  const int g4 = max_coresident(pcg_ir_kernel<false>, h->sm_count);
+  const int g3 = std::min(max_coresident(pcg_ir_kernel<true, false>, h->sm_count),
+                          max_coresident(pcg_ir_kernel<true, true>, h->sm_count));
+  const int g4 = std::min(max_coresident(pcg_ir_kernel<false, false>, h->sm_count),
+                          max_coresident(pcg_ir_kernel<false, true>, h->sm_count));
   h->grid_max = std::min(std::min(g1, g2), std::min(g3, g4));
   const int g5 = std::min(std::min(max_coresident(g_upd_r<double, true>, h->sm_count),
                                    max_coresident(g_upd_r<double, false>, h->sm_count)),
@@ -954,6 +956,7 @@ cg_status cg_set_option(cg_handle* h, int32_t option, double value) {
     case CG_OPT_IR_TOL_INNER:
       if (!(value > 0 && value < 1)) break;
       h->tol_in = value;
+      h->tol_in_set = true;
       return CG_OK;
     case CG_OPT_IR_MAX_OUTER:
       if (!(value >= 0 && value <= 1000)) break;
@@ -1000,7 +1003,7 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   if (!(tol >= 0.0) || maxit < 0) return fail(h, CG_ERR_INVALID, "cg_solve: tol < 0 or maxit < 0");
   if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI && precond != CG_PRECOND_FSAI)
     return fail(h, CG_ERR_INVALID, "cg_solve: unknown preconditioner");
-  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR)
+  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR && precision != CG_PREC_FP32_RU)
     return fail(h, CG_ERR_INVALID, "cg_solve: unknown precision");
   if (precond == CG_PRECOND_JACOBI && !h->jacobi_ok)
     return fail(h, CG_ERR_INVALID, "cg_solve: Jacobi needs a positive diagonal in every row");
@@ -1015,6 +1018,7 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   const bool fsai = precond == CG_PRECOND_FSAI;
   const bool jac = precond == CG_PRECOND_JACOBI;  // FSAI runs on the unscaled matrix
   const bool fp64 = precision == CG_PREC_FP64;
+  const bool carry = precision == CG_PREC_FP32_RU;  // reliable updates: persistent form only
   cg_status s = ensure_offdiag(h);
   if (s == CG_OK) s = ensure_vectors<double>(h, &h->r, &h->p, &h->q, &h->xh);
   if (s == CG_OK && fp64) s = ensure_vals<double>(h, &h->sval64[jac], &h->lval64[jac], jac);
@@ -1037,16 +1041,16 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   P.pstride = h->grid_part;
   P.st = h->st;
   P.tol = tol;
-  P.tol_in = h->tol_in;
+  P.tol_in = h->tol_in_set ? h->tol_in : (carry ? kRuTolInner : kIrTolInner);
   P.maxit = maxit;
   P.max_restarts = fp64 ? h->max_restarts : h->max_outer;
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
   P.timers = h->timers;
-  if (fsai) return cgi::fsai_solve(h, P, fp64, G, iters_out, relres_out);
+  if (fsai) return cgi::fsai_solve(h, P, fp64, carry, G, iters_out, relres_out);
   // auto: fp64 takes the graph form from kGraphMinRows rows; the refinement's
   // fp32 vector passes are short, so it stays in the persistent form
-  const bool graph_mode = h->loop_mode >= 2 || (h->loop_mode == 0 && fp64 && h->n >= kGraphMinRows);
+  const bool graph_mode = !carry && (h->loop_mode >= 2 || (h->loop_mode == 0 && fp64 && h->n >= kGraphMinRows));
   if (graph_mode && fp64)
     return solve_graph64(h, P, jac, h->loop_mode == 3 ? kUnrollIters : 0, iters_out, relres_out);
   if (graph_mode) return solve_graph_ir(h, P, jac, iters_out, relres_out);
@@ -1055,7 +1059,8 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   if (fp64)
     fn = jac ? (const void*)pcg64_kernel<true> : (const void*)pcg64_kernel<false>;
   else
-    fn = jac ? (const void*)pcg_ir_kernel<true> : (const void*)pcg_ir_kernel<false>;
+    fn = carry ? (jac ? (const void*)pcg_ir_kernel<true, true> : (const void*)pcg_ir_kernel<false, true>)
+               : (jac ? (const void*)pcg_ir_kernel<true, false> : (const void*)pcg_ir_kernel<false, false>);
   CG_CUDA(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
   CG_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   CG_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kBlock), args, 0, h->stream));

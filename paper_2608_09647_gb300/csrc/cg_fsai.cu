@@ -172,10 +172,11 @@ struct FsaiParams {
   FsaiVecs<float> V32;
 };
 
-// t = G r (r the current residual), rho = t.t = r.z; then p = G^T t.
+// t = G r (r the current residual), rho = t.t = r.z; then p = G^T t, or with
+// rho_prev > 0 (reliable updates, R8) p = G^T t + (rho / rho_prev) p.
 template <bool DIA, typename T>
 __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
-                           double* part, int pstride, Grid& g, double* rho) {
+                           double* part, int pstride, Grid& g, double* rho, double rho_prev = 0.0) {
   Acc<T> a;
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
     T s = T(0);
@@ -188,10 +189,12 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
   if (!g.sync()) return false;
   grid_sum<1>(part + kSlotRes * (size_t)pstride, g.G, v);
   *rho = v[0];
+  const bool carry = rho_prev > 0.0;
+  const T beta = carry ? (T)(v[0] / rho_prev) : T(0);
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
     T s = T(0);
     for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[ell_col<DIA>(GT, m, i, n)], s);
-    V.p[i] = s;
+    V.p[i] = carry ? fma(beta, V.p[i], s) : s;
   }
   return g.sync();
 }
@@ -201,8 +204,10 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
 // non-finite values, or a barrier timeout.  x += alpha p each iteration.
 template <bool DIA, typename T>
 __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, double rho,
-                         double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g) {
+                         double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g,
+                         double* rho_last = nullptr) {
   const int64_t n = S.n;
+  if (rho_last) *rho_last = rho;
   int k = *iters;
   int status = kNotConverged;
   if (sqrt(rr) <= stop_abs) status = kOk;
@@ -238,6 +243,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     double s2[2];
     grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     const T beta = (T)(s2[0] / rho);
+    if (rho_last) *rho_last = rho;
     rho = s2[0];
     rr = s2[1];
     ++k;
@@ -340,8 +346,9 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
   }
 }
 
-// fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7).
-template <bool DIA>
+// fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7);
+// CARRY: reliable updates (R8), the search direction survives each fp64 update.
+template <bool DIA, bool CARRY>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
@@ -349,7 +356,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   const int64_t n = P.A.n;
   const FsaiVecs<float>& V = F.V32;
   int status = kNotConverged, inner = 0, outer = 0;
-  double relres = 0.0, bb = 0.0;
+  double relres = 0.0, bb = 0.0, rho_k = 0.0;
   for (;;) {
     spmv_orig(P.A, P.x, F.V64.q, g, s_prod);
     if (!g.sync()) { status = kTimeout; break; }
@@ -381,9 +388,10 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
     if (relres <= P.tol) { status = kOk; break; }
     if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
     double rho = 0.0;
-    if (!fsai_start<DIA, float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    if (!fsai_start<DIA, float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho,
+                                CARRY && outer > 0 ? rho_k : 0.0)) { status = kTimeout; break; }
     const int st = fsai_loop<DIA, float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
-                                    P.part, P.pstride, g);
+                                    P.part, P.pstride, g, &rho_k);
     if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
     for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)V.x[i];
     if (!g.sync()) { status = kTimeout; break; }
@@ -577,8 +585,8 @@ cg_status cgi::fsai_commit(cg_handle* h, int kind) {
 }
 
 // The PCG with the handle's factor; P carries the unscaled loop matrices.
-cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, int grid, int32_t* iters_out,
-                          double* relres_out) {
+cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, bool carry, int grid,
+                          int32_t* iters_out, double* relres_out) {
   FsaiData* f = h->fsai;
   const int64_t n = h->n;
   FsaiParams F{};
@@ -595,8 +603,10 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, int g
   F.V64 = FsaiVecs<double>{f->r0, f->r1, Pin.V64.p, Pin.V64.q, f->t, Pin.x};
   F.V32 = FsaiVecs<float>{f->r0_32, f->r1_32, Pin.V32.p, Pin.V32.q, f->t_32, f->x_32};
   void* args[] = {&F};
-  const void* fn = fp64 ? (f->dia ? (const void*)pcg_fsai64_kernel<true> : (const void*)pcg_fsai64_kernel<false>)
-                        : (f->dia ? (const void*)pcg_fsai_ir_kernel<true> : (const void*)pcg_fsai_ir_kernel<false>);
+  const void* fn;
+  if (fp64) fn = f->dia ? (const void*)pcg_fsai64_kernel<true> : (const void*)pcg_fsai64_kernel<false>;
+  else if (carry) fn = f->dia ? (const void*)pcg_fsai_ir_kernel<true, true> : (const void*)pcg_fsai_ir_kernel<false, true>;
+  else fn = f->dia ? (const void*)pcg_fsai_ir_kernel<true, false> : (const void*)pcg_fsai_ir_kernel<false, false>;
   int per_sm = 0;
   CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
   const int G = std::max(1, std::min(grid, per_sm * h->sm_count));

@@ -43,6 +43,6 @@ struct FsaiData {
 namespace cgi {
 cg_status fsai_pattern(cg_handle* h);
 cg_status fsai_commit(cg_handle* h, int kind);
-cg_status fsai_solve(cg_handle* h, const cg::SolveParams& P, bool fp64, int grid, int32_t* iters_out,
-                     double* relres_out);
+cg_status fsai_solve(cg_handle* h, const cg::SolveParams& P, bool fp64, bool carry, int grid,
+                     int32_t* iters_out, double* relres_out);
 }  // namespace cgi

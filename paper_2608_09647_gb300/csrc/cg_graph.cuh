@@ -128,14 +128,22 @@ __global__ void __launch_bounds__(kBlock) g_upd_r(GArgs a) {
   const LoopVecs<T>& V = vecs_of<T>(P);
   double pq[1];
   grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
-  const double rho = a.gs->rho;
-  if (!isfinite(pq[0]) || !isfinite(rho) || pq[0] <= 0.0) {
-    if (g.cta == 0 && threadIdx.x == 0)
-      a.gs->status = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : kBreakdown;
-    return;
+  // the scalars once per CTA (fp64 divisions and tests in every thread would
+  // load GB300's narrow fp64 pipe), shared through shared memory
+  __shared__ double s_alpha;
+  __shared__ int s_stop, s_want;
+  if (threadIdx.x == 0) {
+    const double rho = a.gs->rho;
+    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+    if (st && g.cta == 0) a.gs->status = st;
+    s_stop = st;
+    s_alpha = rho / pq[0];
+    s_want = JAC && rr_wanted(S, rho, a.gs->stop_abs * a.gs->stop_abs);
   }
-  const T alpha = (T)(rho / pq[0]);
-  const bool want_rr = JAC && rr_wanted(S, rho, a.gs->stop_abs * a.gs->stop_abs);
+  __syncthreads();
+  if (s_stop) return;
+  const T alpha = (T)s_alpha;
+  const bool want_rr = s_want != 0;
   double v[2] = {0.0, 0.0};
   update_r_phase<T, JAC>(S, V, alpha, want_rr, v[0], v[1], g);
   publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
@@ -177,19 +185,35 @@ __global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
     double pq[1], s2[2];
     grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
     grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, a.G_upd, s2);
-    const double rho = gs->rho;
-    const T alpha = (T)(rho / pq[0]);
-    const T beta = (T)(s2[0] / rho);
-    rho1 = s2[0];
-    rr1 = s2[1];
-    const double stop2 = gs->stop_abs * gs->stop_abs;
-    if (JAC && !rr_wanted(S, rho, stop2) && rr_bound_test(S, rho1, stop2, &rr1) < 0) {
+    // scalars once per CTA, shared (see g_upd_r)
+    __shared__ double s_sc[4];  // alpha, beta, rr1
+    __shared__ int s_fl[2];     // exact r.r from g_rr needed; done | conv << 1
+    if (threadIdx.x == 0) {
+      const double rho = gs->rho;
+      const double stop2 = gs->stop_abs * gs->stop_abs;
+      double rr = s2[1];
+      s_sc[0] = rho / pq[0];
+      s_sc[1] = s2[0] / rho;
+      s_fl[0] = JAC && !rr_wanted(S, rho, stop2) && rr_bound_test(S, s2[0], stop2, &rr) < 0;
+      s_sc[2] = rr;
+    }
+    __syncthreads();
+    if (s_fl[0]) {  // uniform across the CTA
       double v3[1];  // written by g_rr
       grid_sum<1>(P.part + kSlotRr * (size_t)P.pstride, a.G_upd, v3);
-      rr1 = v3[0];
+      if (threadIdx.x == 0) s_sc[2] = v3[0];
     }
-    conv = sqrt(rr1) <= gs->stop_abs;
-    done = conv || k1 >= P.maxit;
+    if (threadIdx.x == 0) {
+      const bool c = sqrt(s_sc[2]) <= gs->stop_abs;
+      s_fl[1] = (c || k1 >= P.maxit ? 1 : 0) | (c ? 2 : 0);
+    }
+    __syncthreads();
+    const T alpha = (T)s_sc[0];
+    const T beta = (T)s_sc[1];
+    rho1 = s2[0];
+    rr1 = s_sc[2];
+    conv = (s_fl[1] & 2) != 0;
+    done = (s_fl[1] & 1) != 0;
     double* out = P.x;
     if (done) update_xp_phase<T, JAC, true, OUT_ADD>(S, V, alpha, beta, out, g);
     else update_xp_phase<T, JAC, false, OUT_ADD>(S, V, alpha, beta, out, g);

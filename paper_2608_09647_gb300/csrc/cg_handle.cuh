@@ -79,6 +79,7 @@ struct cg_handle {
   int max_restarts = 3;
   double timeout_ms = 2000.0;
   double tol_in = 1e-4;
+  bool tol_in_set = false;          // CG_OPT_IR_TOL_INNER given (else the precision's default)
   int max_outer = 30;
   unsigned skip_seq = 0;
   int timers = 0;

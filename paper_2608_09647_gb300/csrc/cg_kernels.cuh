@@ -40,6 +40,8 @@ constexpr int kCap = 2048;                 // nonzeros of one caller-CSR row blo
 constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
 constexpr int kLongRow = 128;              // off-diagonal entries above which a row leaves SELL
 constexpr int kUnroll = 8;                 // slice columns whose loads are issued together
+constexpr double kIrTolInner = 1e-4;       // default inner tolerance: refinement (restarting)
+constexpr double kRuTolInner = 1e-1;       // default update threshold: reliable updates
 constexpr int kMaxDiag = 32;               // most distinct offsets of the diagonal (DIA) layout
 
 // --------------------------------------------------------------------------
@@ -615,7 +617,9 @@ __device__ __forceinline__ void update_xp_phase(const Sell<T>& S, const LoopVecs
 template <typename T, bool JAC, bool OUT_ADD>
 __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, double rr,
                        double stop_abs, int maxit, int* iters, double* rr_out, double* out,
-                       double* part, int pstride, Grid& g, PhaseClock& clk) {
+                       double* part, int pstride, Grid& g, PhaseClock& clk,
+                       double* rho_last = nullptr) {
+  if (rho_last) *rho_last = rho;  // r.z before the last step taken (reliable updates)
   int k = *iters;
   int status = kNotConverged;
   bool done = sqrt(rr) <= stop_abs || k >= maxit;  // a4: tested before every SpMV
@@ -629,11 +633,20 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     clk.lap(g.st, 1);
     double pq[1];
     grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
-    if (!isfinite(pq[0]) || !isfinite(rho)) { status = kNumeric; break; }
-    if (pq[0] <= 0.0) { status = kBreakdown; break; }
-    const T alpha = (T)(rho / pq[0]);
+    // scalars once per CTA in thread 0, shared (fp64 divisions and tests in every
+    // thread would load GB300's narrow fp64 pipe)
+    __shared__ double s_sc[3];
+    __shared__ int s_fl[2];
+    if (threadIdx.x == 0) {
+      s_fl[0] = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+      s_sc[0] = rho / pq[0];
+      s_fl[1] = JAC && rr_wanted(S, rho, stop_abs * stop_abs);
+    }
+    __syncthreads();
+    if (s_fl[0]) { status = s_fl[0]; break; }
+    const T alpha = (T)s_sc[0];
     // a2: r^ -= alpha q; r.z, r.r (r.r only when the test needs it)
-    const bool want_rr = JAC && rr_wanted(S, rho, stop_abs * stop_abs);
+    const bool want_rr = s_fl[1] != 0;
     double v2[2] = {0.0, 0.0};
     update_r_phase<T, JAC>(S, V, alpha, want_rr, v2[0], v2[1], g);
     publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
@@ -642,10 +655,18 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     clk.lap(g.st, 3);
     double s2[2];
     grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
-    const T beta = (T)(s2[0] / rho);
+    if (threadIdx.x == 0) {
+      double rr_ = s2[1];
+      s_sc[1] = s2[0] / rho;
+      s_fl[0] = JAC && !want_rr && rr_bound_test(S, s2[0], stop_abs * stop_abs, &rr_) < 0;
+      s_sc[2] = rr_;
+    }
+    __syncthreads();
+    const T beta = (T)s_sc[1];
+    if (rho_last) *rho_last = rho;
     rho = s2[0];
-    rr = s2[1];
-    if (JAC && !want_rr && rr_bound_test(S, rho, stop_abs * stop_abs, &rr) < 0) {
+    rr = s_sc[2];
+    if (s_fl[0]) {
       double v3[1] = {rr_phase<T>(S, V, g)};  // rho fell into the band early: exact r.r
       publish<1>(v3, part + kSlotRr * (size_t)pstride, g);
       if (!g.sync()) { status = kTimeout; break; }
@@ -653,7 +674,9 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
       rr = v3[0];
     }
     ++k;
-    const bool conv = sqrt(rr) <= stop_abs;
+    if (threadIdx.x == 0) s_fl[1] = sqrt(rr) <= stop_abs;
+    __syncthreads();
+    const bool conv = s_fl[1] != 0;
     done = conv || k >= maxit;
     if (conv) status = kOk;
     // a3: x^ += alpha p; p = r^ + beta p (last iteration: write the caller's x)
@@ -771,8 +794,11 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
 
 // fp32-inner / fp64-outer iterative refinement (reading R6): the outer fp64
 // residual, solution update and convergence test, the inner fp32 (scaled
-// Jacobi) CG with fp64-accumulated dot products, all in one launch.
-template <bool JAC>
+// Jacobi) CG with fp64-accumulated dot products, all in one launch.  CARRY
+// (reliable updates, R8): after each fp64 update the inner CG continues from
+// the replaced residual with its last search direction, p = r^' + (r^'.r^' /
+// rho_k) p_k, instead of restarting from p = r^'.
+template <bool JAC, bool CARRY>
 __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
   __shared__ double s_prod[kCap];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
@@ -780,7 +806,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
   const int64_t n = P.A.n;
   const LoopVecs<float>& V = P.V32;
   int status = kNotConverged, inner = 0, outer = 0;
-  double relres = 0.0, bb = 0.0, rr32 = 0.0;
+  double relres = 0.0, bb = 0.0, rr32 = 0.0, rho_k = 0.0;
   for (;;) {
     // outer fp64 residual r = b - A x fused with the inner start:
     // r^32 = fl32(D^-1/2 r), d^ = 0
@@ -792,7 +818,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
       const double ri = bi - P.V64.q[i];
       const float rh = (float)(JAC ? ri * __ldg(P.disq + i) : ri);
       V.r[i] = rh;
-      V.p[i] = rh;
+      if (!CARRY || outer == 0) V.p[i] = rh;
       V.xh[i] = 0.0f;
       const double rh2 = (double)rh * (double)rh;
       v[0] += ri * ri;
@@ -816,8 +842,14 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
     if (!isfinite(relres)) { status = kNumeric; break; }
     if (relres <= P.tol) { status = kOk; break; }
     if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
+    if (CARRY && outer > 0 && rho_k > 0.0) {  // p = r^' + beta p_k
+      const float beta = (float)(s4[2] / rho_k);
+      for (int64_t i = g.gtid; i < n; i += g.gstride) V.p[i] = fma(beta, V.p[i], V.r[i]);
+      if (!g.sync()) { status = kTimeout; break; }
+    }
     const int st = cg_loop<float, JAC, true>(P.S32, V, s4[2], s4[3], P.tol_in * sqrt(s4[3]),
-                                             P.maxit, &inner, &rr32, P.x, P.part, P.pstride, g, clk);
+                                             P.maxit, &inner, &rr32, P.x, P.part, P.pstride, g, clk,
+                                             &rho_k);
     if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
     ++outer;
   }

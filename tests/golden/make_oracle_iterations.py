@@ -23,7 +23,10 @@ import oracle  # noqa: E402
 
 OUT = os.path.join(HERE, "oracle_iterations.json")
 
-# name: (builder, kwargs, solver, precond, tol, maxit, tol_in)
+Q1_1024 = {"s": 1024, "sigma_a": 1.5, "theta": 0.7, "eps": 0.01, "seed": 3}
+WEIGHTS = os.path.join(ROOT, "paper_2608_09647_gb300", "fsai_q1aniso_bf16.npy")
+
+# name: (builder, kwargs, solver, precond, tol, maxit, tol_in); precond 2 = learned FSAI
 CASES = {
     "poisson2d_64": ("lap2d", {"N": 64}, "pcg", 0, 1e-8, 1000, None),
     "poisson3d_256": ("lap3d7", {"N": 256}, "pcg", 1, 1e-8, 10000, None),
@@ -31,6 +34,12 @@ CASES = {
                              100000, None),
     "diffusion27_160": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "ir", 1, 1e-10, 100000,
                         1e-4),
+    "diffusion27_160_ru": ("diff3d27", {"N": 160, "sigma": 1.0, "seed": 0}, "ru", 1, 1e-10, 100000,
+                           0.1),
+    "q1aniso_1024_jacobi_fp64": ("q1aniso", Q1_1024, "pcg", 1, 1e-8, 200000, None),
+    "q1aniso_1024_learned": ("q1aniso", Q1_1024, "ir", 2, 1e-8, 200000, 1e-4),
+    "q1aniso_1024_learned_ru": ("q1aniso", Q1_1024, "ru", 2, 1e-8, 200000, 0.1),
+    "q1aniso_1024_learned_fp64": ("q1aniso", Q1_1024, "pcg", 2, 1e-8, 200000, None),
 }
 
 
@@ -41,8 +50,18 @@ def run(name):
     xs = gen.xstar(A.n, 0)
     b = oracle.spmv(A, xs)
     t1 = time.time()
-    if solver == "pcg":
+    if precond == 2:  # the learned FSAI factor of the committed weights, by the oracle's MLP
+        from oracle import fsai
+        bits = np.load(WEIGHTS)
+        g = fsai.learned(A, (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64))
+        if solver == "pcg":
+            s = fsai.pcg(A, g, b, tol=tol, maxit=maxit)
+        else:
+            s = fsai.pcg_ir(A, g, b, tol=tol, tol_in=tol_in, maxit=maxit, carry=solver == "ru")
+    elif solver == "pcg":
         s = oracle.pcg(A, b, tol=tol, maxit=maxit, precond=precond)
+    elif solver == "ru":
+        s = oracle.pcg_ru(A, b, tol=tol, tol_in=tol_in, maxit=maxit, precond=precond)
     else:
         s = oracle.pcg_ir(A, b, tol=tol, tol_in=tol_in, maxit=maxit, precond=precond)
     t2 = time.time()

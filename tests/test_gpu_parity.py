@@ -455,3 +455,35 @@ def test_fp32_refinement_edge_cases(mode):
     st, it, rel, x, info = run(b, 3)                        # inner budget of 3 iterations
     assert st == cg.CG_NOT_CONVERGED and it == 3
     assert abs(rel - oracle.true_relres(A, b, x)) <= 1e-6 * rel
+
+
+RU_CASES = [("q1_48", lambda: gen.q1aniso(48, 1.5, 0.7, 0.01, 3)),
+            ("lap9_50", lambda: gen.lap2d(50, 9, 1e-3)),
+            ("diff27_14", lambda: gen.diff3d27(14, 1.0, 2))]
+
+
+@pytest.mark.parametrize("precond", [cg.CG_PRECOND_JACOBI, cg.CG_PRECOND_NONE], ids=["jacobi", "none"])
+@pytest.mark.parametrize("name,make", RU_CASES, ids=[c[0] for c in RU_CASES])
+def test_reliable_updates_match_oracle(name, make, precond):
+    """fp32 PCG with fp64 reliable updates (R8, default update threshold 0.1) against the
+    oracle; it must also need fewer inner iterations than the restarting refinement."""
+    A = make()
+    b = oracle.spmv(A, gen.xstar(A.n, 4))
+    tol = 1e-9
+    ref = oracle.pcg_ru(A, b, tol=tol, tol_in=0.1, maxit=100000, precond=precond)
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, tol, 100000, precond, cg.CG_PREC_FP32_RU)
+    info = cg.cg_get_solve_info(h)
+    assert st == ref.status == cg.CG_OK, (st, cg.cg_last_error(h))
+    # update decisions are taken on fp32 recursive residuals whose rounding differs
+    # (Kahan-compensated fp32 sums here, fp64 sums of fp32 products in the oracle)
+    assert abs(it - ref.iters) <= max(5, math.ceil(0.1 * ref.iters)), (it, ref.iters)
+    assert abs(info["restarts"] - ref.restarts) <= 2, (info["restarts"], ref.restarts)
+    xs = x.cpu().numpy()
+    assert oracle.true_relres(A, b, xs) <= tol * (1 + 1e-6)
+    x2 = torch.zeros_like(bd)
+    st2, it_ir, _ = cg.cg_solve(h, bd, x2, tol, 100000, precond, cg.CG_PREC_FP32_IR)
+    assert st2 == cg.CG_OK and it < it_ir
