@@ -513,6 +513,13 @@ const void* spmv_kernel_for(int uw, bool dia, bool jac) {
   return dia ? spmv_kernel_w<T, false, true>(uw) : spmv_kernel_w<T, false, false>(uw);
 }
 
+}  // namespace
+
+// The graph-form fp32 SpMV kernel of the unscaled loop matrix (FSAI refinement).
+const void* cgi::spmv_kernel_f32(const cg_handle* h) { return spmv_kernel_for<float>(h->uniform_w, h->dia != 0, false); }
+
+namespace {
+
 // Append a kernel node after `dep` (may be null) to graph g.
 template <typename... Args>
 cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn,

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "cg_fsai.cuh"
+#include "cg_graph.cuh"
 
 using namespace cg;
 
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
   const int64_t n = P.A.n;
   const FsaiVecs<double>& V = F.V64;
   int status = kNotConverged, k = 0, restarts = 0;
-  double relres_true = 0.0, bb = 0.0, rr = 0.0;
+  double relres_true = 0.0, bb = 0.0;
   bool first = true;
   for (;;) {
     spmv_orig(P.A, P.x, V.q, g, s_prod);
@@ -406,6 +407,358 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   }
 }
 
+
+// ---------------------------------------------------------------- graph form
+// The fp32 refinement loop with G^T G as CUDA graph nodes (large systems):
+//   outer WHILE { q64 = A x | r32 = fl32(b - q64), d = 0 | t = G r32 |
+//                 start (1 CTA: fp64 test, limits, carry factor) | p = G^T t (+ beta0 p) |
+//                 inner WHILE { q = A p, p.q | alpha, r', t = G r', d += alpha p |
+//                               beta, test, p = G^T t + beta p or x64 += d } }
+// Every phase is its own kernel (the kernel boundaries are the barriers); each
+// CTA re-forms the scalars from the fixed-order partials of the previous kernel.
+constexpr int kSlotT = kSlotRes + 3;  // t.t of the start pass
+constexpr int64_t kFsaiGraphMinRows = 1 << 19;  // auto loop form: graph from here (fp32 inner)
+
+struct FArgs {
+  GArgs a;
+  Ell<float> G, GT;
+  float* r[2];  // current residual in r[k & 1]
+  float* t;
+  float* d;     // the inner solve's correction
+  int carry;    // reliable updates (R8)
+};
+
+__global__ void __launch_bounds__(kBlock) gf_res(FArgs F) {
+  const SolveParams& P = F.a.P;
+  Grid g = graph_grid();
+  float* r = F.r[F.a.gs->k & 1];
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) {
+    const double bi = P.b[i];
+    const double ri = bi - P.V64.q[i];
+    const float r32 = (float)ri;
+    r[i] = r32;
+    F.d[i] = 0.0f;
+    v[0] += ri * ri;
+    v[1] += bi * bi;
+    v[2] += (double)r32 * (double)r32;
+  }
+  publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+}
+
+template <bool DIA>
+__global__ void __launch_bounds__(kBlock) gf_t(FArgs F) {
+  const SolveParams& P = F.a.P;
+  Grid g = graph_grid();
+  const int64_t n = P.A.n;
+  const float* r = F.r[F.a.gs->k & 1];
+  Acc<float> a;
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    float s = 0.0f;
+    for (int m = 0; m < F.G.w; ++m) s = fmaf(__ldg(F.G.val + m * n + i), r[ell_col<DIA>(F.G, m, i, n)], s);
+    F.t[i] = s;
+    a.add(s, s);
+  }
+  double v[1] = {a.get()};
+  publish<1>(v, P.part + kSlotT * (size_t)P.pstride, g);
+}
+
+// One CTA: the fp64 residual test and limits; the next inner solve's state.
+template <bool COND>
+__global__ void gf_start(FArgs F) {
+  const SolveParams& P = F.a.P;
+  double s[3], tt[1];
+  grid_sum<3>(P.part + kSlotRes * (size_t)P.pstride, F.a.G_upd, s);
+  grid_sum<1>(P.part + kSlotT * (size_t)P.pstride, F.a.G_upd, tt);
+  if (threadIdx.x != 0) return;
+  GState* gs = F.a.gs;
+  if (!gs->started) {
+    gs->started = 1;
+    gs->bb = s[1];
+    gs->k = 0;
+    gs->outer = 0;
+    gs->status = kRunning;
+    gs->rho_k = 0.0;
+  }
+  const double rel = gs->bb > 0.0 ? sqrt(s[0]) / sqrt(gs->bb) : 0.0;
+  gs->relres_true = rel;
+  bool stop = true;
+  int status = gs->status;
+  if (status == kBreakdown || status == kNumeric) {
+    // the previous inner solve failed; x keeps the last good iterate
+  } else if (gs->bb == 0.0) {
+    status = kOk;
+  } else if (!isfinite(rel)) {
+    status = kNumeric;
+  } else if (rel <= P.tol) {
+    status = kOk;
+  } else if (gs->outer >= P.max_restarts || gs->k >= P.maxit) {
+    status = kNotConverged;
+  } else {
+    stop = false;
+  }
+  bool inner = false;
+  if (!stop) {
+    gs->beta0 = (F.carry && gs->outer > 0 && gs->rho_k > 0.0) ? tt[0] / gs->rho_k : 0.0;
+    gs->rho = tt[0];
+    gs->rho_k = tt[0];
+    gs->rr = s[2];
+    gs->stop_abs = P.tol_in * sqrt(s[2]);
+    gs->k_start = gs->k;
+    gs->outer += 1;
+    gs->ctr = 0;
+    status = kRunning;
+    inner = !(sqrt(s[2]) <= gs->stop_abs);
+  }
+  gs->status = status;
+  if constexpr (COND) {
+    cudaGraphSetConditional(F.a.h2, stop ? 0u : 1u);
+    cudaGraphSetConditional(F.a.h, inner ? 1u : 0u);
+  }
+}
+
+// p = G^T t, or p = G^T t + beta0 p when the direction is carried over.
+template <bool DIA>
+__global__ void __launch_bounds__(kBlock) gf_p0(FArgs F) {
+  const SolveParams& P = F.a.P;
+  if (F.a.gs->status != kRunning) return;
+  Grid g = graph_grid();
+  const int64_t n = P.A.n;
+  const float beta0 = (float)F.a.gs->beta0;
+  float* p = P.V32.p;
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    float s = 0.0f;
+    for (int m = 0; m < F.GT.w; ++m) s = fmaf(__ldg(F.GT.val + m * n + i), F.t[ell_col<DIA>(F.GT, m, i, n)], s);
+    p[i] = beta0 != 0.0f ? fmaf(beta0, p[i], s) : s;
+  }
+}
+
+template <bool DIA>
+__global__ void __launch_bounds__(kBlock) gf_upd_r(FArgs F) {
+  const SolveParams& P = F.a.P;
+  GState* gs = F.a.gs;
+  if (gs->status != kRunning) return;
+  Grid g = graph_grid();
+  const int64_t n = P.A.n;
+  double pq[1];
+  grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, F.a.G_spmv, pq);
+  __shared__ double s_alpha;
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) {  // scalars once per CTA
+    const double rho = gs->rho;
+    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+    if (st && g.cta == 0) gs->status = st;
+    s_stop = st;
+    s_alpha = rho / pq[0];
+  }
+  __syncthreads();
+  if (s_stop) return;
+  const float alpha = (float)s_alpha;
+  const int k = gs->k;
+  const float* rc = F.r[k & 1];
+  float* rn = F.r[(k + 1) & 1];
+  const float* q = P.V32.q;
+  const float* p = P.V32.p;
+  Acc<float> a_rho, a_rr;
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    const float ri = fmaf(-alpha, q[i], rc[i]);
+    rn[i] = ri;
+    a_rr.add(ri, ri);
+    float s = 0.0f;
+    for (int m = 0; m < F.G.w; ++m) {
+      const int j = ell_col<DIA>(F.G, m, i, n);
+      s = fmaf(__ldg(F.G.val + m * n + i), fmaf(-alpha, q[j], rc[j]), s);
+    }
+    F.t[i] = s;
+    a_rho.add(s, s);
+    F.d[i] = fmaf(alpha, p[i], F.d[i]);
+  }
+  double v[2] = {a_rho.get(), a_rr.get()};
+  publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
+}
+
+template <bool DIA, bool COND>
+__global__ void __launch_bounds__(kBlock) gf_upd_p(FArgs F) {
+  const SolveParams& P = F.a.P;
+  GState* gs = F.a.gs;
+  Grid g = graph_grid();
+  const int64_t n = P.A.n;
+  const bool failed = gs->status != kRunning;
+  double s2[2] = {0.0, 0.0};
+  __shared__ double s_beta;
+  __shared__ int s_fl;  // done | conv << 1
+  const int k1 = gs->k + 1;
+  if (!failed) {
+    grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, F.a.G_upd, s2);
+    if (threadIdx.x == 0) {
+      s_beta = s2[0] / gs->rho;
+      const bool conv = sqrt(s2[1]) <= gs->stop_abs;
+      s_fl = (conv || k1 >= P.maxit ? 1 : 0) | (conv ? 2 : 0);
+    }
+    __syncthreads();
+    if (!(s_fl & 1)) {
+      const float beta = (float)s_beta;
+      float* p = P.V32.p;
+      for (int64_t i = g.gtid; i < n; i += g.gstride) {
+        float s = 0.0f;
+        for (int m = 0; m < F.GT.w; ++m) s = fmaf(__ldg(F.GT.val + m * n + i), F.t[ell_col<DIA>(F.GT, m, i, n)], s);
+        p[i] = fmaf(beta, p[i], s);
+      }
+    } else {
+      for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)F.d[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&gs->ctr, 1u) == g.G - 1) {  // every CTA has read the state and finished
+      gs->ctr = 0;
+      const bool done = failed || (s_fl & 1);
+      if (!failed) {
+        gs->rho_k = gs->rho;
+        gs->rho = s2[0];
+        gs->rr = s2[1];
+        gs->k = k1;
+        gs->status = (s_fl & 1) ? ((s_fl & 2) ? kOk : kNotConverged) : kRunning;
+      }
+      __threadfence();
+      if constexpr (COND) cudaGraphSetConditional(F.a.h, done ? 0u : 1u);
+    }
+  }
+}
+
+cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn, unsigned grid,
+                     unsigned block, void** args) {
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(fn);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(block);
+  kp.kernelParams = args;
+  return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
+}
+
+cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin);
+
+cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int32_t* iters_out, double* relres_out) {
+  FsaiData* f = h->fsai;
+  const SolveParams& P = F.a.P;
+  if (!f->gexec || f->gkey_b != P.b || f->gkey_x != P.x || f->gkey_tol != P.tol || f->gkey_maxit != P.maxit ||
+      f->gkey_tol_in != P.tol_in || f->gkey_outer != P.max_restarts || f->gkey_carry != (int)carry ||
+      f->gkey_kind != f->dia) {
+    const cg_status s = build_fsai_graph(h, F);
+    if (s != CG_OK) return s;
+    f->gkey_b = P.b;
+    f->gkey_x = P.x;
+    f->gkey_tol = P.tol;
+    f->gkey_maxit = P.maxit;
+    f->gkey_tol_in = P.tol_in;
+    f->gkey_outer = P.max_restarts;
+    f->gkey_carry = carry;
+    f->gkey_kind = f->dia;
+  }
+  CGF_CUDA(h, cudaMemsetAsync(h->gs, 0, sizeof(GState), h->stream));
+  CGF_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  CGF_CUDA(h, cudaGraphLaunch(f->gexec, h->stream));
+  CGF_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  CGF_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
+  CGF_CUDA(h, cudaStreamSynchronize(h->stream));
+  float ms = 0.0f;
+  CGF_CUDA(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  const GState& gs = *h->host_gs;
+  const int status = gs.status;
+  const int64_t n = h->n;
+  h->last.status = status;
+  h->last.iters = gs.k;
+  h->last.restarts = gs.outer;
+  h->last.grid_ctas = h->grid_graph;
+  h->last.relres_true = gs.relres_true;
+  h->last.relres_rec = gs.relres_true;
+  h->last.kernel_ms = ms;
+  h->last.loop_form = 2;
+  h->last.kernel_launches = (int32_t)std::min<int64_t>(5 * (int64_t)(gs.outer + 1) + 3 * (int64_t)gs.k + 1, INT32_MAX);
+  h->last.precond_used = CG_PRECOND_FSAI;
+  const int64_t per_iter = 8 * (h->nnz + 2 * f->ntril) + 4 * (n + 1) + 13 * 4 * n;
+  h->last.bytes_moved = per_iter * (int64_t)gs.k;
+  h->last.kernel_bytes_per_iter = per_iter;
+  if (iters_out) *iters_out = gs.k;
+  if (relres_out) *relres_out = gs.relres_true;
+  if (status < 0) return ffail(h, (cg_status)status, std::string("cg_solve (FSAI): ") + cg_status_string(status));
+  return (cg_status)status;
+}
+
+
+void destroy_fsai_graph(FsaiData* f) {
+  if (f->gexec) cudaGraphExecDestroy(f->gexec);
+  if (f->graph) cudaGraphDestroy(f->graph);
+  f->gexec = nullptr;
+  f->graph = nullptr;
+}
+
+cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin) {
+  FsaiData* f = h->fsai;
+  destroy_fsai_graph(f);
+  cudaGraph_t g;
+  CGF_CUDA(h, cudaGraphCreate(&g, 0));
+  f->graph = g;
+  cudaGraphConditionalHandle outer_h, inner_h;
+  CGF_CUDA(h, cudaGraphConditionalHandleCreate(&outer_h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams op{};
+  op.type = cudaGraphNodeTypeConditional;
+  op.conditional.handle = outer_h;
+  op.conditional.type = cudaGraphCondTypeWhile;
+  op.conditional.size = 1;
+  cudaGraphNode_t on;
+  CGF_CUDA(h, cudaGraphAddNode(&on, g, nullptr, nullptr, 0, &op));
+  cudaGraph_t ob = op.conditional.phGraph_out[0];
+  CGF_CUDA(h, cudaGraphConditionalHandleCreate(&inner_h, ob, 0, cudaGraphCondAssignDefault));
+  FArgs F = Fin;
+  F.a.h = inner_h;
+  F.a.h2 = outer_h;
+  const void* f_spmv = cgi::spmv_kernel_f32(h);
+  int per_sm = 0;
+  CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f_spmv, kBlock, 0));
+  const unsigned G = (unsigned)h->grid_graph;
+  const unsigned Gq = (unsigned)std::max(1, std::min(per_sm * h->sm_count, h->grid_part));
+  F.a.G_spmv = Gq;
+  F.a.G_upd = G;
+  // kernel arguments are copied into the nodes at creation
+  Csr<double> A = F.a.P.A;
+  const double* gx = F.a.P.x;
+  double* gq = F.a.P.V64.q;
+  void* a_spmv[] = {&A, &gx, &gq};
+  void* a_f[] = {&F};
+  void* a_ga[] = {&F.a};
+  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  const bool dia = f->dia != 0;
+  cudaGraphNode_t n, prev;
+  CGF_CUDA(h, add_node(ob, &n, nullptr, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
+  prev = n;
+  CGF_CUDA(h, add_node(ob, &n, prev, (const void*)gf_res, G, kBlock, a_f));
+  prev = n;
+  CGF_CUDA(h, add_node(ob, &n, prev, dia ? (const void*)gf_t<true> : (const void*)gf_t<false>, G, kBlock, a_f));
+  prev = n;
+  CGF_CUDA(h, add_node(ob, &n, prev, (const void*)gf_start<true>, 1, 32, a_f));
+  prev = n;
+  CGF_CUDA(h, add_node(ob, &n, prev, dia ? (const void*)gf_p0<true> : (const void*)gf_p0<false>, G, kBlock, a_f));
+  prev = n;
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = inner_h;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  CGF_CUDA(h, cudaGraphAddNode(&n, ob, &prev, nullptr, 1, &ip));
+  cudaGraph_t ib = ip.conditional.phGraph_out[0];
+  cudaGraphNode_t b1, b2, b3;
+  CGF_CUDA(h, add_node(ib, &b1, nullptr, f_spmv, Gq, kBlock, a_ga));
+  CGF_CUDA(h, add_node(ib, &b2, b1, dia ? (const void*)gf_upd_r<true> : (const void*)gf_upd_r<false>, G, kBlock,
+                       a_f));
+  CGF_CUDA(h, add_node(ib, &b3, b2, dia ? (const void*)gf_upd_p<true, true> : (const void*)gf_upd_p<false, true>, G,
+                       kBlock, a_f));
+  CGF_CUDA(h, add_node(g, &n, on, (const void*)g_flush_ir, G, kBlock, a_ga));
+  CGF_CUDA(h, cudaGraphInstantiate(&f->gexec, g, 0));
+  return CG_OK;
+}
+
 }  // namespace
 
 void cgi::fsai_free(FsaiData* f) {
@@ -416,6 +769,7 @@ void cgi::fsai_free(FsaiData* f) {
                  f->params32, f->trow, f->rpart, f->tslot};
   for (void* p : dev)
     if (p) cudaFree(p);
+  destroy_fsai_graph(f);
   delete f;
 }
 
@@ -602,6 +956,19 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, bool 
   }
   F.V64 = FsaiVecs<double>{f->r0, f->r1, Pin.V64.p, Pin.V64.q, f->t, Pin.x};
   F.V32 = FsaiVecs<float>{f->r0_32, f->r1_32, Pin.V32.p, Pin.V32.q, f->t_32, f->x_32};
+  if (!fp64 && (h->loop_mode == 2 || (h->loop_mode == 0 && n >= kFsaiGraphMinRows))) {
+    FArgs FA{};
+    FA.a.P = Pin;
+    FA.a.gs = h->gs;
+    FA.G = F.G32;
+    FA.GT = F.GT32;
+    FA.r[0] = f->r0_32;
+    FA.r[1] = f->r1_32;
+    FA.t = f->t_32;
+    FA.d = f->x_32;
+    FA.carry = carry ? 1 : 0;
+    return solve_fsai_graph(h, FA, carry, iters_out, relres_out);
+  }
   void* args[] = {&F};
   const void* fn;
   if (fp64) fn = f->dia ? (const void*)pcg_fsai64_kernel<true> : (const void*)pcg_fsai64_kernel<false>;

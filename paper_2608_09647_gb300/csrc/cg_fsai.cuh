@@ -38,6 +38,13 @@ struct FsaiData {
   float* gpart = nullptr;          // per-CTA partial parameter gradients
   float* mlp_o = nullptr;          // MLP output per tril entry
   float* params32 = nullptr;       // parameters given to cg_fsai_load (device, fp32)
+  // graph form of the fp32 refinement loop
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey_b = nullptr;
+  const void* gkey_x = nullptr;
+  double gkey_tol = -1.0, gkey_tol_in = -1.0;
+  int gkey_maxit = -1, gkey_outer = -1, gkey_carry = -1, gkey_kind = -1;
 };
 
 namespace cgi {
@@ -45,4 +52,5 @@ cg_status fsai_pattern(cg_handle* h);
 cg_status fsai_commit(cg_handle* h, int kind);
 cg_status fsai_solve(cg_handle* h, const cg::SolveParams& P, bool fp64, bool carry, int grid,
                      int32_t* iters_out, double* relres_out);
+const void* spmv_kernel_f32(const cg_handle* h);  // graph-form SpMV of the unscaled fp32 loop matrix
 }  // namespace cgi

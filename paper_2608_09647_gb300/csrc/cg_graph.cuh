@@ -33,6 +33,8 @@ struct GState {
   int started;         // 0 before the first prologue of a solve
   unsigned ctr;        // arrivals of the current x/p pass (last-CTA election)
   int outer;           // refinement: inner solves started
+  double rho_k;        // reliable updates: r.z before the last step of the inner solve
+  double beta0;        // reliable updates: carry factor of the next inner solve's p
 };
 
 struct GArgs {
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kBlock) g_flush(GArgs a) {
 }
 
 // Partial ||b - q||^2 with q = A x (true residual, a5).
-__global__ void __launch_bounds__(kBlock) g_true(GArgs a) {
+static __global__ void __launch_bounds__(kBlock) g_true(GArgs a) {
   const SolveParams& P = a.P;
   Grid g = graph_grid();
   double v[1] = {0.0};
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kBlock) g_true(GArgs a) {
 }
 
 // One CTA: the true relative residual and the solve's final status.
-__global__ void g_final64(GArgs a) {
+static __global__ void g_final64(GArgs a) {
   const unsigned G = a.G_upd;
   double s[1];
   grid_sum<1>(a.P.part + kSlotRes * (size_t)a.P.pstride, G, s);
@@ -367,7 +369,7 @@ __global__ void g_start_ir(GArgs a) {
 }
 
 // After the outer loop: b = 0 gives x = 0.
-__global__ void __launch_bounds__(kBlock) g_flush_ir(GArgs a) {
+static __global__ void __launch_bounds__(kBlock) g_flush_ir(GArgs a) {
   if (a.gs->bb != 0.0) return;
   Grid g = graph_grid();
   for (int64_t i = g.gtid; i < a.P.A.n; i += g.gstride) a.P.x[i] = 0.0;

@@ -8,8 +8,10 @@ Jacobi-PCG produces on them (cg_solve stopped after a few iteration counts).
     python -m paper_2608_09647_gb300.fsai_train --train 2000 --test 200 --out fsai.json
 
 trains on seeded rotated-anisotropy Q1 matrices and compares learned FSAI with
-Jacobi and classic FSAI on held-out ones (iterations and time to 1e-8 with fp32
-refinement).  Not in the paper.
+Jacobi and classic FSAI on held-out ones (iterations and time to 1e-8; fp32 inner
+iterations with fp64 reliable updates by default).  ``--params FILE.npy`` skips
+training and evaluates stored weights (fp32 values, or bf16 bit patterns as
+uint16).  Not in the paper.
 """
 from __future__ import annotations
 
@@ -20,7 +22,8 @@ import time
 
 import numpy as np
 
-from . import (CG_MLP_HIDDEN, CG_MLP_INPUTS, CG_MLP_PARAMS, CG_OK, CG_NOT_CONVERGED, CG_PREC_FP32_IR, CG_PREC_FP64,
+from . import (CG_MLP_HIDDEN, CG_MLP_INPUTS, CG_MLP_PARAMS, CG_OK, CG_NOT_CONVERGED, CG_PREC_FP32_IR,
+               CG_PREC_FP32_RU, CG_PREC_FP64,
                CG_PRECOND_FSAI, CG_PRECOND_JACOBI, CGError, cg_adam_step, cg_create, cg_destroy,
                cg_fsai_classic, cg_fsai_load, cg_fsai_loss_grad, cg_get_solve_info, cg_last_error, cg_solve,
                cg_spmv)
@@ -160,6 +163,17 @@ def summarize(rows):
     return out
 
 
+def load_params(path: str) -> np.ndarray:
+    """fp32 parameters from an .npy file of fp32 values or of bf16 bit patterns (uint16)."""
+    w = np.load(path)
+    if w.dtype == np.uint16:
+        w = (w.astype(np.uint32) << 16).view(np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32).ravel()
+    if w.size != CG_MLP_PARAMS:
+        raise ValueError(f"{path}: {w.size} parameters, expected {CG_MLP_PARAMS}")
+    return w
+
+
 def q1_problem(index: int, seed: int, side_lo: int, side_hi: int, snapshots=(2, 8, 32)):
     import cgproblems as gen
     side, theta, eps, mseed = gen.q1_params(index, seed, side_lo, side_hi)
@@ -178,25 +192,31 @@ def main():
     ap.add_argument("--test-sides", type=int, nargs=2, default=(256, 1024))
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=None)
-    ap.add_argument("--precision", choices=["fp32_ir", "fp64"], default="fp32_ir")
+    ap.add_argument("--precision", choices=["fp32_ru", "fp32_ir", "fp64"], default="fp32_ru")
+    ap.add_argument("--params", default=None, help="evaluate these weights instead of training")
     args = ap.parse_args()
     t0 = time.time()
-    tr = [q1_problem(i, args.seed, *args.train_sides) for i in range(args.train)]
-    t1 = time.time()
-    params, hist = train(tr, args.epochs, args.lr, args.lam, args.seed, log=print)
-    t2 = time.time()
-    for P in tr:
-        P.close()
+    if args.params:
+        params, hist = load_params(args.params), []
+        t1 = t2 = time.time()
+    else:
+        tr = [q1_problem(i, args.seed, *args.train_sides) for i in range(args.train)]
+        t1 = time.time()
+        params, hist = train(tr, args.epochs, args.lr, args.lam, args.seed, log=print)
+        t2 = time.time()
+        for P in tr:
+            P.close()
     rows = []
-    prec = CG_PREC_FP32_IR if args.precision == "fp32_ir" else CG_PREC_FP64
+    prec = {"fp32_ru": CG_PREC_FP32_RU, "fp32_ir": CG_PREC_FP32_IR, "fp64": CG_PREC_FP64}[args.precision]
     for i in range(args.test):  # one held-out matrix at a time (they reach 10^6 rows)
         P = q1_problem(args.train + i, args.seed, *args.test_sides, snapshots=())
         rows += compare([P], params, precision=prec)
         P.close()
     t3 = time.time()
     summary = summarize(rows)
-    res = {"train": args.train, "test": args.test, "epochs": args.epochs, "lr": args.lr, "lam": args.lam,
-           "precision": args.precision,
+    # held-out matrices are q1_params indices train .. train + test - 1 either way
+    res = {"train": args.train, "trained_here": not args.params, "test": args.test, "epochs": args.epochs,
+           "lr": args.lr, "lam": args.lam, "precision": args.precision, "params": args.params,
            "train_sides": list(args.train_sides), "test_sides": list(args.test_sides), "loss_history": hist,
            "seconds": {"setup": t1 - t0, "train": t2 - t1, "evaluate": t3 - t2}, "summary": summary,
            "per_matrix": rows}
@@ -204,7 +224,8 @@ def main():
     if args.out:
         with open(args.out, "w") as f:
             json.dump(res, f, indent=1)
-        np.save(args.out.rsplit(".", 1)[0] + "_params.npy", params.cpu().numpy())
+        if not args.params:
+            np.save(args.out.rsplit(".", 1)[0] + "_params.npy", params.cpu().numpy())
 
 
 if __name__ == "__main__":

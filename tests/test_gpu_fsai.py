@@ -186,3 +186,40 @@ def test_fsai_rejects_unsuitable_matrices():
     h = handle(gen.CSR(A.n, A.rowptr, ci, va, "unsorted"))
     assert cg.cg_fsai_classic(h) == cg.CG_ERR_INVALID
     assert "increasing" in cg.cg_last_error(h)
+
+
+@pytest.mark.parametrize("precision", [cg.CG_PREC_FP32_IR, cg.CG_PREC_FP32_RU], ids=["fp32_ir", "fp32_ru"])
+@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "graph"])
+@pytest.mark.parametrize("name,make", CASES[:3] + [("q1_260", lambda: gen.q1aniso(260, 1.5, 1.9, 0.004, 8))],
+                         ids=[c[0] for c in CASES[:3]] + ["q1_260"])
+def test_fsai_refinement_loop_forms_match_oracle(name, make, mode, precision):
+    """Both loop forms of the fp32 FSAI refinement (the persistent kernel and the graph of
+    phase kernels under WHILE nodes) against the oracle; the automatic choice is the graph
+    form from 2^19 rows."""
+    A = make()
+    g = fsai.classic(A)
+    b = oracle.spmv(A, gen.xstar(A.n, 9))
+    tol = 1e-9
+    h = handle(A)
+    assert cg.cg_fsai_set_factor(h, torch.from_numpy(g).cuda()) == cg.CG_OK
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, tol, 100000, cg.CG_PRECOND_FSAI, precision)
+    info = cg.cg_get_solve_info(h)
+    assert info["loop_form"] == mode
+    carry = precision == cg.CG_PREC_FP32_RU
+    ref = fsai.pcg_ir(A, g, b, tol=tol, tol_in=0.1 if carry else 1e-4, maxit=100000, carry=carry)
+    assert st == ref.status == cg.CG_OK, (st, cg.cg_last_error(h))
+    band = ru_band(ref.iters) if carry else iters_band(ref.iters)
+    assert abs(it - ref.iters) <= band, (it, ref.iters)
+    assert abs(info["restarts"] - ref.restarts) <= (2 if carry else 0)
+    xs = x.cpu().numpy()
+    assert oracle.true_relres(A, b, xs) <= tol * (1 + 1e-6)
+    assert abs(rel - oracle.true_relres(A, b, xs)) <= 1e-6 * rel + 1e-15
+    # auto picks the graph form from 2^19 rows
+    h2 = handle(A)
+    assert cg.cg_fsai_set_factor(h2, torch.from_numpy(g).cuda()) == cg.CG_OK
+    x2 = torch.zeros_like(bd)
+    assert cg.cg_solve(h2, bd, x2, tol, 100000, cg.CG_PRECOND_FSAI, precision)[0] == cg.CG_OK
+    assert cg.cg_get_solve_info(h2)["loop_form"] == (2 if A.n >= 1 << 19 else 1)
