@@ -73,10 +73,14 @@ typedef enum {
   CG_OPT_DEBUG_SKIP_ARRIVAL = 5,  /* fault injection: CTA 0 skips arrival at grid barrier #value
                                      (1-based; 0 = off), so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
-  CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64: graph from 2^20 rows, else persistent), 1 one persistent cooperative launch,
-                                     2 CUDA graph with a device-side WHILE node (nested WHILE
-                                     nodes for fp32 refinement), 3 fp64 only: graphs of 8
-                                     unrolled iterations relaunched by the host until done */
+  CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: graph from 2^20 rows;
+                                     fp32 FSAI refinement: graph from 2^19 rows; else persistent),
+                                     1 one persistent cooperative launch, 2 CUDA graph with a
+                                     device-side WHILE node (nested WHILE nodes for fp32
+                                     refinement), 3 graphs of 8 unrolled iterations relaunched by
+                                     the host until done (fp64 Jacobi / plain CG and the fp32 FSAI
+                                     refinement; elsewhere as 2).  The Jacobi reliable-update solve
+                                     and the fp64 FSAI solve always take form 1. */
 } cg_option;
 
 /* Statistics of the most recent cg_solve on a handle. */

@@ -515,9 +515,6 @@ const void* spmv_kernel_for(int uw, bool dia, bool jac) {
 
 }  // namespace
 
-// The graph-form fp32 SpMV kernel of the unscaled loop matrix (FSAI refinement).
-const void* cgi::spmv_kernel_f32(const cg_handle* h) { return spmv_kernel_for<float>(h->uniform_w, h->dia != 0, false); }
-
 namespace {
 
 // Append a kernel node after `dep` (may be null) to graph g.

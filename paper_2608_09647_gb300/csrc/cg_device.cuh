@@ -98,6 +98,34 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks, uin
   return s_ok != 0;
 }
 
+// Sum of v over the CTA in a fixed order, valid in thread 0 only.  A warp-wide
+// fp64 add occupies GB300's fp64 pipe (2 lanes per clock per SM) for 16
+// clocks, so the tree is kept to one warp: every thread stores its values,
+// lane l of warp 0 sums threads l, l+32, ... in that order and the 32 lane
+// sums meet in an xor-tree: 416 fp64 lane operations per value, against
+// 3,328 for an xor-tree in every warp followed by every thread summing the
+// warp sums (block_sum).
+template <int NV>
+__device__ __forceinline__ void cta_sum0(double (&v)[NV]) {
+  __shared__ double s_v[NV][kBlock];
+  __syncthreads();  // s_v may still be read by warp 0 of a previous call
+#pragma unroll
+  for (int j = 0; j < NV; ++j) s_v[j][threadIdx.x] = v[j];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double t = s_v[j][lane];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) t += s_v[j][w * 32 + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      v[j] = t;
+    }
+  }
+}
+
 // Sum of v over the CTA in a fixed order (warp xor-tree, then warp 0 over the
 // per-warp sums); the result is returned to every thread.
 template <int NV>

@@ -154,10 +154,36 @@ struct Ell {
   int delta[kFsaiMaxDiag];
 };
 
-template <bool DIA, typename T>
-__device__ __forceinline__ int ell_col(const Ell<T>& E, int m, int64_t i, int64_t n) {
-  if (DIA) return min(max((int)i + E.delta[m], 0), (int)n - 1);
-  return __ldg(E.col + m * n + i);
+
+// Slot form of G and G^T in the loop kernels (template parameter W): kEll =
+// column arrays, kDiaAny = diagonal layout with a run-time slot count, W > 0 =
+// diagonal layout with exactly W slots (the common stencil widths: 3 for a
+// 2-D 5-point, 4 for a 3-D 7-point, 5 for a 2-D 9-point or Q1 pattern).
+constexpr int kEll = 0, kDiaAny = -1;
+
+// sum_m E(i, m) * f(column of slot m) in slot order.  With W slots known at
+// compile time every load of the row is issued before the first product (a
+// loop over a run-time count waits a full memory latency per slot).
+template <int W, typename T, typename Fn>
+__device__ __forceinline__ T ell_row(const Ell<T>& E, int64_t i, int64_t n, Fn&& f) {
+  T s = T(0);
+  if constexpr (W > 0) {
+    T e[W], v[W];
+#pragma unroll
+    for (int m = 0; m < W; ++m) {
+      e[m] = __ldg(E.val + (int64_t)m * n + i);
+      v[m] = f(min(max((int)i + E.delta[m], 0), (int)n - 1));
+    }
+#pragma unroll
+    for (int m = 0; m < W; ++m) s = fma(e[m], v[m], s);
+  } else if constexpr (W == kDiaAny) {
+#pragma unroll
+    for (int m = 0; m < kFsaiMaxDiag; ++m)
+      if (m < E.w) s = fma(__ldg(E.val + (int64_t)m * n + i), f(min(max((int)i + E.delta[m], 0), (int)n - 1)), s);
+  } else {
+    for (int m = 0; m < E.w; ++m) s = fma(__ldg(E.val + m * n + i), f(__ldg(E.col + m * n + i)), s);
+  }
+  return s;
 }
 
 template <typename T>
@@ -175,13 +201,12 @@ struct FsaiParams {
 
 // t = G r (r the current residual), rho = t.t = r.z; then p = G^T t, or with
 // rho_prev > 0 (reliable updates, R8) p = G^T t + (rho / rho_prev) p.
-template <bool DIA, typename T>
+template <int W, typename T>
 __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
                            double* part, int pstride, Grid& g, double* rho, double rho_prev = 0.0) {
   Acc<T> a;
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    T s = T(0);
-    for (int m = 0; m < G.w; ++m) s = fma(__ldg(G.val + m * n + i), r[ell_col<DIA>(G, m, i, n)], s);
+    const T s = ell_row<W>(G, i, n, [&](int j) { return r[j]; });
     V.t[i] = s;
     a.add(s, s);
   }
@@ -193,8 +218,7 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
   const bool carry = rho_prev > 0.0;
   const T beta = carry ? (T)(v[0] / rho_prev) : T(0);
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    T s = T(0);
-    for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[ell_col<DIA>(GT, m, i, n)], s);
+    const T s = ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; });
     V.p[i] = carry ? fma(beta, V.p[i], s) : s;
   }
   return g.sync();
@@ -203,7 +227,7 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
 // The PCG loop from a start state (r in V.r0, p = G^T G r, rho = r.z, rr =
 // r.r) until sqrt(rr) <= stop_abs (kOk), maxit (kNotConverged), breakdown /
 // non-finite values, or a barrier timeout.  x += alpha p each iteration.
-template <bool DIA, typename T>
+template <int W, typename T>
 __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, double rho,
                          double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g,
                          double* rho_last = nullptr) {
@@ -221,19 +245,23 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     if (!g.sync()) { status = kTimeout; break; }
     double pq[1];
     grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
-    if (!isfinite(pq[0]) || !isfinite(rho)) { status = kNumeric; break; }
-    if (pq[0] <= 0.0) { status = kBreakdown; break; }
-    const T alpha = (T)(rho / pq[0]);
+    // the scalars once per CTA (an fp64 divide or square root in every
+    // thread would load GB300's narrow fp64 pipe), shared through shared memory
+    __shared__ double s_sc[2];
+    __shared__ int s_fl;
+    if (threadIdx.x == 0) {
+      s_fl = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+      s_sc[0] = rho / pq[0];
+    }
+    __syncthreads();
+    if (s_fl) { status = s_fl; break; }
+    const T alpha = (T)s_sc[0];
     Acc<T> a_rho, a_rr;
     for (int64_t i = g.gtid; i < n; i += g.gstride) {
       const T ri = fma(-alpha, V.q[i], rc[i]);
       rn[i] = ri;
       a_rr.add(ri, ri);
-      T s = T(0);
-      for (int m = 0; m < G.w; ++m) {
-        const int j = ell_col<DIA>(G, m, i, n);
-        s = fma(__ldg(G.val + m * n + i), fma(-alpha, V.q[j], rc[j]), s);
-      }
+      const T s = ell_row<W>(G, i, n, [&](int j) { return fma(-alpha, V.q[j], rc[j]); });
       V.t[i] = s;
       a_rho.add(s, s);
       V.x[i] = fma(alpha, V.p[i], V.x[i]);
@@ -243,12 +271,17 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     if (!g.sync()) { status = kTimeout; break; }
     double s2[2];
     grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
-    const T beta = (T)(s2[0] / rho);
+    if (threadIdx.x == 0) {
+      s_sc[1] = s2[0] / rho;
+      s_fl = sqrt(s2[1]) <= stop_abs;
+    }
+    __syncthreads();
+    const T beta = (T)s_sc[1];
+    const bool conv = s_fl != 0;
     if (rho_last) *rho_last = rho;
     rho = s2[0];
     rr = s2[1];
     ++k;
-    const bool conv = sqrt(rr) <= stop_abs;
     done = conv || k >= maxit;
     if (conv) status = kOk;
     T* tmp = rc;
@@ -256,8 +289,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     rn = tmp;
     if (!done) {
       for (int64_t i = g.gtid; i < n; i += g.gstride) {
-        T s = T(0);
-        for (int m = 0; m < GT.w; ++m) s = fma(__ldg(GT.val + m * n + i), V.t[ell_col<DIA>(GT, m, i, n)], s);
+        const T s = ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; });
         V.p[i] = fma(beta, V.p[i], s);
       }
       if (!g.sync()) { status = kTimeout; break; }
@@ -268,7 +300,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
 }
 
 // fp64 PCG with G^T G: true-residual check and restarts as cg_solve (R1-R5, R7).
-template <bool DIA>
+template <int W>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
   __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
@@ -317,8 +349,8 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
     }
     first = false;
     double rho = 0.0;
-    if (!fsai_start<DIA, double>(F.G64, F.GT64, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
-    const int st = fsai_loop<DIA, double>(P.S64, F.G64, F.GT64, V, rho, rr_start, P.tol * sqrt(bb), P.maxit, &k,
+    if (!fsai_start<W, double>(F.G64, F.GT64, V, V.r0, n, P.part, P.pstride, g, &rho)) { status = kTimeout; break; }
+    const int st = fsai_loop<W, double>(P.S64, F.G64, F.GT64, V, rho, rr_start, P.tol * sqrt(bb), P.maxit, &k,
                                      P.part, P.pstride, g);
     if (st == kTimeout) { status = kTimeout; break; }
     if (st == kNumeric || st == kBreakdown) {
@@ -349,7 +381,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
 
 // fp32-inner / fp64-outer refinement (R6) with the inner M^-1 = G32^T G32 (R7);
 // CARRY: reliable updates (R8), the search direction survives each fp64 update.
-template <bool DIA, bool CARRY>
+template <int W, bool CARRY>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
@@ -389,9 +421,9 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
     if (relres <= P.tol) { status = kOk; break; }
     if (outer >= P.max_restarts || inner >= P.maxit) { status = kNotConverged; break; }
     double rho = 0.0;
-    if (!fsai_start<DIA, float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho,
+    if (!fsai_start<W, float>(F.G32, F.GT32, V, V.r0, n, P.part, P.pstride, g, &rho,
                                 CARRY && outer > 0 ? rho_k : 0.0)) { status = kTimeout; break; }
-    const int st = fsai_loop<DIA, float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
+    const int st = fsai_loop<W, float>(P.S32, F.G32, F.GT32, V, rho, s3[2], P.tol_in * sqrt(s3[2]), P.maxit, &inner,
                                     P.part, P.pstride, g, &rho_k);
     if (st == kTimeout || st == kNumeric || st == kBreakdown) { status = st; break; }
     for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)V.x[i];
@@ -410,14 +442,20 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
 
 // ---------------------------------------------------------------- graph form
 // The fp32 refinement loop with G^T G as CUDA graph nodes (large systems):
-//   outer WHILE { q64 = A x | r32 = fl32(b - q64), d = 0 | t = G r32 |
-//                 start (1 CTA: fp64 test, limits, carry factor) | p = G^T t (+ beta0 p) |
-//                 inner WHILE { q = A p, p.q | alpha, r', t = G r', d += alpha p |
-//                               beta, test, p = G^T t + beta p or x64 += d } }
-// Every phase is its own kernel (the kernel boundaries are the barriers); each
-// CTA re-forms the scalars from the fixed-order partials of the previous kernel.
+//   outer WHILE { x64 += d (after an inner solve) | q64 = A x | r32 = fl32(b - q64), d = 0 |
+//                 t = G r32 | start (1 CTA: fp64 test, limits, carry factor) | p = G^T t (+ beta0 p) |
+//                 inner WHILE { q = A p, p.q -> alpha | r', t = G r', d += alpha p -> beta, test |
+//                               p = G^T t + beta p } }
+// Every phase is its own kernel (the kernel boundaries are the barriers).  The
+// last CTA of a reducing kernel sums its fixed-order partials once and stores
+// the scalars for the next kernel, so no CTA waits on a reduction at its start.
 constexpr int kSlotT = kSlotRes + 3;  // t.t of the start pass
 constexpr int64_t kFsaiGraphMinRows = 1 << 19;  // auto loop form: graph from here (fp32 inner)
+constexpr int kFsaiUnroll = 8;                   // inner iterations per graph of the unrolled form
+constexpr int kFsaiOuterKernels = 6;             // kernels of one outer step
+// Residency of the graph form's phase kernels: 4 CTAs (32 warps) per SM keeps
+// the unrolled diagonal-layout loops within 64 registers without spilling.
+constexpr int kFsaiPhaseCtas = 4;
 
 struct FArgs {
   GArgs a;
@@ -431,6 +469,7 @@ struct FArgs {
 __global__ void __launch_bounds__(kBlock) gf_res(FArgs F) {
   const SolveParams& P = F.a.P;
   Grid g = graph_grid();
+  if (g.cta == 0 && threadIdx.x == 0) F.a.gs->xflush = 0;  // gf_xadd has finished
   float* r = F.r[F.a.gs->k & 1];
   double v[3] = {0.0, 0.0, 0.0};
   for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) {
@@ -446,16 +485,15 @@ __global__ void __launch_bounds__(kBlock) gf_res(FArgs F) {
   publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
 }
 
-template <bool DIA>
-__global__ void __launch_bounds__(kBlock) gf_t(FArgs F) {
+template <int W>
+__global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_t(FArgs F) {
   const SolveParams& P = F.a.P;
   Grid g = graph_grid();
   const int64_t n = P.A.n;
   const float* r = F.r[F.a.gs->k & 1];
   Acc<float> a;
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    float s = 0.0f;
-    for (int m = 0; m < F.G.w; ++m) s = fmaf(__ldg(F.G.val + m * n + i), r[ell_col<DIA>(F.G, m, i, n)], s);
+    const float s = ell_row<W>(F.G, i, n, [&](int j) { return r[j]; });
     F.t[i] = s;
     a.add(s, s);
   }
@@ -509,8 +547,10 @@ __global__ void gf_start(FArgs F) {
     gs->ctr = 0;
     status = kRunning;
     inner = !(sqrt(s[2]) <= gs->stop_abs);
+    if (!inner) status = kOk;  // this inner solve has nothing to do; the outer loop goes on
   }
   gs->status = status;
+  gs->finished = stop ? 1 : 0;
   if constexpr (COND) {
     cudaGraphSetConditional(F.a.h2, stop ? 0u : 1u);
     cudaGraphSetConditional(F.a.h, inner ? 1u : 0u);
@@ -518,8 +558,8 @@ __global__ void gf_start(FArgs F) {
 }
 
 // p = G^T t, or p = G^T t + beta0 p when the direction is carried over.
-template <bool DIA>
-__global__ void __launch_bounds__(kBlock) gf_p0(FArgs F) {
+template <int W>
+__global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_p0(FArgs F) {
   const SolveParams& P = F.a.P;
   if (F.a.gs->status != kRunning) return;
   Grid g = graph_grid();
@@ -527,33 +567,52 @@ __global__ void __launch_bounds__(kBlock) gf_p0(FArgs F) {
   const float beta0 = (float)F.a.gs->beta0;
   float* p = P.V32.p;
   for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    float s = 0.0f;
-    for (int m = 0; m < F.GT.w; ++m) s = fmaf(__ldg(F.GT.val + m * n + i), F.t[ell_col<DIA>(F.GT, m, i, n)], s);
+    const float s = ell_row<W>(F.GT, i, n, [&](int j) { return F.t[j]; });
     p[i] = beta0 != 0.0f ? fmaf(beta0, p[i], s) : s;
   }
 }
 
-template <bool DIA>
-__global__ void __launch_bounds__(kBlock) gf_upd_r(FArgs F) {
+// x64 += d when the previous inner solve ended (converged or at maxit; not
+// after a breakdown, so x keeps the last good iterate).  First node of an
+// outer step; gf_res clears the flag.
+__global__ void __launch_bounds__(kBlock) gf_xadd(FArgs F) {
+  if (!F.a.gs->xflush) return;
+  const SolveParams& P = F.a.P;
+  Grid g = graph_grid();
+  for (int64_t i = g.gtid; i < P.A.n; i += g.gstride) P.x[i] += (double)F.d[i];
+}
+
+// a1: q = A p (fp32 loop matrix, W_A / DIA_A as g_spmv), p.q.  The last CTA
+// forms alpha = rho / p.q and the breakdown / non-finite test once.
+template <int WA, bool DIAA>
+__global__ void __launch_bounds__(kBlock) gf_spmv(FArgs F) {
+  const SolveParams& P = F.a.P;
+  GState* gs = F.a.gs;
+  if (gs->status != kRunning) return;
+  Grid g = graph_grid();
+  double v[1], pq[1];
+  if constexpr (WA > 0) v[0] = spmv_phase_w<float, false, WA, DIAA>(P.S32, P.V32.p, P.V32.q, g);
+  else v[0] = spmv_phase<float, false>(P.S32, P.V32.p, P.V32.q, g);
+  if (!publish_last<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g, &gs->ctr_q, pq)) return;
+  if (threadIdx.x == 0) {
+    const double rho = gs->rho;
+    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+    gs->alpha = rho / pq[0];
+    if (st) gs->status = st;
+  }
+}
+
+// a2: r' = r - alpha q (into the other r buffer), t = G r' (r' of neighbour
+// rows recomputed from r and q), d += alpha p; partials (t.t = r'.z, r'.r').
+// The last CTA forms beta, the inner test and the next loop state.
+template <int W>
+__global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_upd_r(FArgs F) {
   const SolveParams& P = F.a.P;
   GState* gs = F.a.gs;
   if (gs->status != kRunning) return;
   Grid g = graph_grid();
   const int64_t n = P.A.n;
-  double pq[1];
-  grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, F.a.G_spmv, pq);
-  __shared__ double s_alpha;
-  __shared__ int s_stop;
-  if (threadIdx.x == 0) {  // scalars once per CTA
-    const double rho = gs->rho;
-    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
-    if (st && g.cta == 0) gs->status = st;
-    s_stop = st;
-    s_alpha = rho / pq[0];
-  }
-  __syncthreads();
-  if (s_stop) return;
-  const float alpha = (float)s_alpha;
+  const float alpha = (float)gs->alpha;
   const int k = gs->k;
   const float* rc = F.r[k & 1];
   float* rn = F.r[(k + 1) & 1];
@@ -564,66 +623,46 @@ __global__ void __launch_bounds__(kBlock) gf_upd_r(FArgs F) {
     const float ri = fmaf(-alpha, q[i], rc[i]);
     rn[i] = ri;
     a_rr.add(ri, ri);
-    float s = 0.0f;
-    for (int m = 0; m < F.G.w; ++m) {
-      const int j = ell_col<DIA>(F.G, m, i, n);
-      s = fmaf(__ldg(F.G.val + m * n + i), fmaf(-alpha, q[j], rc[j]), s);
-    }
+    const float s = ell_row<W>(F.G, i, n, [&](int j) { return fmaf(-alpha, q[j], rc[j]); });
     F.t[i] = s;
     a_rho.add(s, s);
     F.d[i] = fmaf(alpha, p[i], F.d[i]);
   }
-  double v[2] = {a_rho.get(), a_rr.get()};
-  publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
-}
-
-template <bool DIA, bool COND>
-__global__ void __launch_bounds__(kBlock) gf_upd_p(FArgs F) {
-  const SolveParams& P = F.a.P;
-  GState* gs = F.a.gs;
-  Grid g = graph_grid();
-  const int64_t n = P.A.n;
-  const bool failed = gs->status != kRunning;
-  double s2[2] = {0.0, 0.0};
-  __shared__ double s_beta;
-  __shared__ int s_fl;  // done | conv << 1
-  const int k1 = gs->k + 1;
-  if (!failed) {
-    grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, F.a.G_upd, s2);
-    if (threadIdx.x == 0) {
-      s_beta = s2[0] / gs->rho;
-      const bool conv = sqrt(s2[1]) <= gs->stop_abs;
-      s_fl = (conv || k1 >= P.maxit ? 1 : 0) | (conv ? 2 : 0);
-    }
-    __syncthreads();
-    if (!(s_fl & 1)) {
-      const float beta = (float)s_beta;
-      float* p = P.V32.p;
-      for (int64_t i = g.gtid; i < n; i += g.gstride) {
-        float s = 0.0f;
-        for (int m = 0; m < F.GT.w; ++m) s = fmaf(__ldg(F.GT.val + m * n + i), F.t[ell_col<DIA>(F.GT, m, i, n)], s);
-        p[i] = fmaf(beta, p[i], s);
-      }
-    } else {
-      for (int64_t i = g.gtid; i < n; i += g.gstride) P.x[i] += (double)F.d[i];
+  double v[2] = {a_rho.get(), a_rr.get()}, s2[2];
+  if (!publish_last<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g, &gs->ctr, s2)) return;
+  if (threadIdx.x == 0) {
+    const int k1 = k + 1;
+    const bool conv = sqrt(s2[1]) <= gs->stop_abs;
+    gs->beta = s2[0] / gs->rho;
+    gs->rho_k = gs->rho;  // reliable updates: r.z before this step
+    gs->rho = s2[0];
+    gs->rr = s2[1];
+    gs->k = k1;
+    if (conv || k1 >= P.maxit) {
+      gs->status = conv ? kOk : kNotConverged;
+      gs->xflush = 1;
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&gs->ctr, 1u) == g.G - 1) {  // every CTA has read the state and finished
-      gs->ctr = 0;
-      const bool done = failed || (s_fl & 1);
-      if (!failed) {
-        gs->rho_k = gs->rho;
-        gs->rho = s2[0];
-        gs->rr = s2[1];
-        gs->k = k1;
-        gs->status = (s_fl & 1) ? ((s_fl & 2) ? kOk : kNotConverged) : kRunning;
-      }
-      __threadfence();
-      if constexpr (COND) cudaGraphSetConditional(F.a.h, done ? 0u : 1u);
-    }
+}
+
+// a3: p = G^T t + beta p while the inner solve runs; sets the inner WHILE
+// condition (COND) from the state the previous kernels left.
+template <int W, bool COND>
+__global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_upd_p(FArgs F) {
+  const SolveParams& P = F.a.P;
+  const GState* gs = F.a.gs;
+  const bool running = gs->status == kRunning;
+  if constexpr (COND) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(F.a.h, running ? 1u : 0u);
+  }
+  if (!running) return;
+  Grid g = graph_grid();
+  const int64_t n = P.A.n;
+  const float beta = (float)gs->beta;
+  float* p = P.V32.p;
+  for (int64_t i = g.gtid; i < n; i += g.gstride) {
+    const float s = ell_row<W>(F.GT, i, n, [&](int j) { return F.t[j]; });
+    p[i] = fmaf(beta, p[i], s);
   }
 }
 
@@ -637,16 +676,22 @@ cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, 
   return cudaGraphAddKernelNode(node, g, dep ? &dep : nullptr, dep ? 1 : 0, &kp);
 }
 
-cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin);
+cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin, int unroll);
 
-cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int32_t* iters_out, double* relres_out) {
+// unroll == 0: one launch of the graph with nested WHILE nodes.  unroll > 0:
+// the host launches the outer-step graph, then iteration graphs until the
+// inner solve leaves kRunning, until the outer loop has finished (every loop
+// is bounded by maxit and the outer-step limit, both tested on the device).
+cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int unroll, int32_t* iters_out,
+                           double* relres_out) {
   FsaiData* f = h->fsai;
   const SolveParams& P = F.a.P;
   if (!f->gexec || f->gkey_b != P.b || f->gkey_x != P.x || f->gkey_tol != P.tol || f->gkey_maxit != P.maxit ||
       f->gkey_tol_in != P.tol_in || f->gkey_outer != P.max_restarts || f->gkey_carry != (int)carry ||
-      f->gkey_kind != f->dia) {
-    const cg_status s = build_fsai_graph(h, F);
+      f->gkey_kind != f->dia || f->gkey_unroll != unroll) {
+    const cg_status s = build_fsai_graph(h, F, unroll);
     if (s != CG_OK) return s;
+    f->gkey_unroll = unroll;
     f->gkey_b = P.b;
     f->gkey_x = P.x;
     f->gkey_tol = P.tol;
@@ -658,7 +703,28 @@ cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int32_t* it
   }
   CGF_CUDA(h, cudaMemsetAsync(h->gs, 0, sizeof(GState), h->stream));
   CGF_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-  CGF_CUDA(h, cudaGraphLaunch(f->gexec, h->stream));
+  int64_t launches = 0;
+  if (unroll == 0) {
+    CGF_CUDA(h, cudaGraphLaunch(f->gexec, h->stream));
+  } else {
+    auto read_state = [&]() -> cudaError_t {
+      cudaError_t e = cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream);
+      return e == cudaSuccess ? cudaStreamSynchronize(h->stream) : e;
+    };
+    for (;;) {
+      CGF_CUDA(h, cudaGraphLaunch(f->gexec, h->stream));
+      launches += kFsaiOuterKernels;
+      CGF_CUDA(h, read_state());
+      if (h->host_gs->finished) break;
+      while (h->host_gs->status == kRunning) {
+        CGF_CUDA(h, cudaGraphLaunch(f->gexec_it, h->stream));
+        launches += 3 * (int64_t)unroll;
+        CGF_CUDA(h, read_state());
+      }
+    }
+    CGF_CUDA(h, cudaGraphLaunch(f->gexec_ep, h->stream));
+    launches += 1;
+  }
   CGF_CUDA(h, cudaEventRecord(h->ev1, h->stream));
   CGF_CUDA(h, cudaMemcpyAsync(h->host_gs, h->gs, sizeof(GState), cudaMemcpyDeviceToHost, h->stream));
   CGF_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -670,12 +736,13 @@ cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int32_t* it
   h->last.status = status;
   h->last.iters = gs.k;
   h->last.restarts = gs.outer;
-  h->last.grid_ctas = h->grid_graph;
+  h->last.grid_ctas = f->ggrid;
   h->last.relres_true = gs.relres_true;
   h->last.relres_rec = gs.relres_true;
   h->last.kernel_ms = ms;
-  h->last.loop_form = 2;
-  h->last.kernel_launches = (int32_t)std::min<int64_t>(5 * (int64_t)(gs.outer + 1) + 3 * (int64_t)gs.k + 1, INT32_MAX);
+  h->last.loop_form = unroll > 0 ? 3 : 2;
+  if (unroll == 0) launches = kFsaiOuterKernels * (int64_t)(gs.outer + 1) + 3 * (int64_t)gs.k + 1;
+  h->last.kernel_launches = (int32_t)std::min<int64_t>(launches, INT32_MAX);
   h->last.precond_used = CG_PRECOND_FSAI;
   const int64_t per_iter = 8 * (h->nnz + 2 * f->ntril) + 4 * (n + 1) + 13 * 4 * n;
   h->last.bytes_moved = per_iter * (int64_t)gs.k;
@@ -688,18 +755,163 @@ cg_status solve_fsai_graph(cg_handle* h, const FArgs& F, bool carry, int32_t* it
 
 
 void destroy_fsai_graph(FsaiData* f) {
-  if (f->gexec) cudaGraphExecDestroy(f->gexec);
-  if (f->graph) cudaGraphDestroy(f->graph);
-  f->gexec = nullptr;
-  f->graph = nullptr;
+  for (cudaGraphExec_t* e : {&f->gexec, &f->gexec_it, &f->gexec_ep}) {
+    if (*e) cudaGraphExecDestroy(*e);
+    *e = nullptr;
+  }
+  for (cudaGraph_t* g : {&f->graph, &f->graph_it, &f->graph_ep}) {
+    if (*g) cudaGraphDestroy(*g);
+    *g = nullptr;
+  }
+  f->gkey_unroll = -1;
 }
 
-cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin) {
+// Grids and kernels shared by both graph forms.
+struct FsaiGraphPlan {
+  FArgs F;
+  Csr<double> A;
+  const double* x;
+  double* q64;
+  const void* f_spmv;
+  unsigned G, Gq, Gs;
+  int w;  // slot form of G and G^T
+};
+
+// Slot form of the handle's factor (see kEll / kDiaAny).
+int fsai_slots(const FsaiData* f) {
+  if (!f->dia) return kEll;
+  return (f->nd >= 3 && f->nd <= 5) ? f->nd : kDiaAny;
+}
+
+// The instantiation of a kernel template for slot form w.
+template <class Pick>
+const void* by_slots(int w) {
+  switch (w) {
+    case 3: return Pick::template fn<3>();
+    case 4: return Pick::template fn<4>();
+    case 5: return Pick::template fn<5>();
+    case kEll: return Pick::template fn<kEll>();
+    default: return Pick::template fn<kDiaAny>();
+  }
+}
+struct PickT { template <int W> static const void* fn() { return (const void*)gf_t<W>; } };
+struct PickP0 { template <int W> static const void* fn() { return (const void*)gf_p0<W>; } };
+struct PickUpdR { template <int W> static const void* fn() { return (const void*)gf_upd_r<W>; } };
+// gf_spmv for the loop matrix's uniform slice width uw (as the fp32 g_spmv).
+const void* gf_spmv_for(int uw, bool dia) {
+  switch (uw) {
+    case 4: return dia ? (const void*)gf_spmv<4, true> : (const void*)gf_spmv<4, false>;
+    case 6: return dia ? (const void*)gf_spmv<6, true> : (const void*)gf_spmv<6, false>;
+    case 8: return dia ? (const void*)gf_spmv<8, true> : (const void*)gf_spmv<8, false>;
+    case 26: return dia ? (const void*)gf_spmv<26, true> : (const void*)gf_spmv<0, false>;
+    default: return (const void*)gf_spmv<0, false>;
+  }
+}
+template <bool COND>
+struct PickUpdP { template <int W> static const void* fn() { return (const void*)gf_upd_p<W, COND>; } };
+struct Pick64 { template <int W> static const void* fn() { return (const void*)pcg_fsai64_kernel<W>; } };
+template <bool CARRY>
+struct PickIr { template <int W> static const void* fn() { return (const void*)pcg_fsai_ir_kernel<W, CARRY>; } };
+
+// CTAs of the vector-phase kernels: one wave at the kernels' own residency,
+// bounded by the partial slots.
+int fsai_graph_grid(const cg_handle* h) {
+  const int w = fsai_slots(h->fsai);
+  const void* fns[] = {(const void*)gf_res,          by_slots<PickT>(w),           by_slots<PickP0>(w),
+                       by_slots<PickUpdR>(w),        by_slots<PickUpdP<true>>(w),  by_slots<PickUpdP<false>>(w),
+                       (const void*)gf_xadd,         (const void*)g_flush_ir};
+  int per_sm = 1 << 30;
+  for (const void* fn : fns) {
+    int k = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fn, kBlock, 0) != cudaSuccess) return 0;
+    per_sm = std::min(per_sm, k);
+  }
+  return std::max(1, std::min(per_sm * h->sm_count, h->grid_part));
+}
+
+cudaError_t plan_fsai_graph(cg_handle* h, const FArgs& Fin, FsaiGraphPlan& pl) {
+  pl.F = Fin;
+  pl.f_spmv = gf_spmv_for(h->uniform_w, h->dia != 0);
+  int per_sm = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.f_spmv, kBlock, 0);
+  if (e != cudaSuccess) return e;
+  // the phase kernels' own residency (fp32, few registers), not the fp64 loop's
+  pl.G = (unsigned)fsai_graph_grid(h);
+  if (pl.G == 0) return cudaErrorInvalidValue;
+  h->fsai->ggrid = (int)pl.G;
+  pl.Gq = (unsigned)std::max(1, std::min(per_sm * h->sm_count, h->grid_part));
+  pl.F.a.G_spmv = pl.Gq;
+  pl.F.a.G_upd = pl.G;
+  pl.A = pl.F.a.P.A;
+  pl.x = pl.F.a.P.x;
+  pl.q64 = pl.F.a.P.V64.q;
+  pl.Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  pl.w = fsai_slots(h->fsai);
+  return cudaSuccess;
+}
+
+// One outer step: x64 += d, q64 = A x, r = fl32(b - q64), t = G r, the start test, p.
+// COND selects the start kernel that sets the WHILE conditions.
+template <bool COND>
+cudaError_t add_outer_step(cudaGraph_t gr, FsaiGraphPlan& pl, cudaGraphNode_t* last) {
+  void* a_spmv[] = {&pl.A, &pl.x, &pl.q64};
+  void* a_f[] = {&pl.F};
+  const void* fns[kFsaiOuterKernels] = {(const void*)gf_xadd,        (const void*)spmv_kernel<double>,
+                                        (const void*)gf_res,         by_slots<PickT>(pl.w),
+                                        (const void*)gf_start<COND>, by_slots<PickP0>(pl.w)};
+  const unsigned grids[kFsaiOuterKernels] = {pl.G, pl.Gs, pl.G, pl.G, 1, pl.G};
+  cudaGraphNode_t prev = nullptr, n;
+  for (int k = 0; k < kFsaiOuterKernels; ++k) {
+    const unsigned block = fns[k] == (const void*)gf_start<COND> ? 32u : (unsigned)kBlock;
+    const cudaError_t e = add_node(gr, &n, prev, fns[k], grids[k], block, k == 1 ? a_spmv : a_f);
+    if (e != cudaSuccess) return e;
+    prev = n;
+  }
+  *last = prev;
+  return cudaSuccess;
+}
+
+// One inner iteration after `prev`: q = A p, p.q | r', t = G r', d | p.
+template <bool COND>
+cudaError_t add_inner_iteration(cudaGraph_t gr, FsaiGraphPlan& pl, cudaGraphNode_t* prev) {
+  void* a_f[] = {&pl.F};
+  cudaGraphNode_t b1, b2, b3;
+  cudaError_t e = add_node(gr, &b1, *prev, pl.f_spmv, pl.Gq, kBlock, a_f);
+  if (e == cudaSuccess) e = add_node(gr, &b2, b1, by_slots<PickUpdR>(pl.w), pl.G, kBlock, a_f);
+  if (e == cudaSuccess) e = add_node(gr, &b3, b2, by_slots<PickUpdP<COND>>(pl.w), pl.G, kBlock, a_f);
+  *prev = b3;
+  return e;
+}
+
+// The unrolled form: f->graph = one outer step, f->graph_it = `unroll` inner
+// iterations (no conditional nodes, so every kernel node can be profiled),
+// f->graph_ep = the b = 0 epilogue.
+cg_status build_fsai_unrolled(cg_handle* h, const FArgs& Fin, int unroll) {
+  FsaiData* f = h->fsai;
+  FsaiGraphPlan pl;
+  CGF_CUDA(h, plan_fsai_graph(h, Fin, pl));
+  cudaGraphNode_t last = nullptr;
+  CGF_CUDA(h, add_outer_step<false>(f->graph, pl, &last));
+  CGF_CUDA(h, cudaGraphCreate(&f->graph_it, 0));
+  cudaGraphNode_t prev = nullptr;
+  for (int u = 0; u < unroll; ++u) CGF_CUDA(h, add_inner_iteration<false>(f->graph_it, pl, &prev));
+  CGF_CUDA(h, cudaGraphCreate(&f->graph_ep, 0));
+  void* a_ga[] = {&pl.F.a};
+  cudaGraphNode_t n;
+  CGF_CUDA(h, add_node(f->graph_ep, &n, nullptr, (const void*)g_flush_ir, pl.G, kBlock, a_ga));
+  CGF_CUDA(h, cudaGraphInstantiate(&f->gexec, f->graph, 0));
+  CGF_CUDA(h, cudaGraphInstantiate(&f->gexec_it, f->graph_it, 0));
+  CGF_CUDA(h, cudaGraphInstantiate(&f->gexec_ep, f->graph_ep, 0));
+  return CG_OK;
+}
+
+cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin, int unroll) {
   FsaiData* f = h->fsai;
   destroy_fsai_graph(f);
   cudaGraph_t g;
   CGF_CUDA(h, cudaGraphCreate(&g, 0));
   f->graph = g;
+  if (unroll > 0) return build_fsai_unrolled(h, Fin, unroll);
   cudaGraphConditionalHandle outer_h, inner_h;
   CGF_CUDA(h, cudaGraphConditionalHandleCreate(&outer_h, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams op{};
@@ -714,33 +926,11 @@ cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin) {
   FArgs F = Fin;
   F.a.h = inner_h;
   F.a.h2 = outer_h;
-  const void* f_spmv = cgi::spmv_kernel_f32(h);
-  int per_sm = 0;
-  CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f_spmv, kBlock, 0));
-  const unsigned G = (unsigned)h->grid_graph;
-  const unsigned Gq = (unsigned)std::max(1, std::min(per_sm * h->sm_count, h->grid_part));
-  F.a.G_spmv = Gq;
-  F.a.G_upd = G;
+  FsaiGraphPlan pl;
+  CGF_CUDA(h, plan_fsai_graph(h, F, pl));
   // kernel arguments are copied into the nodes at creation
-  Csr<double> A = F.a.P.A;
-  const double* gx = F.a.P.x;
-  double* gq = F.a.P.V64.q;
-  void* a_spmv[] = {&A, &gx, &gq};
-  void* a_f[] = {&F};
-  void* a_ga[] = {&F.a};
-  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
-  const bool dia = f->dia != 0;
-  cudaGraphNode_t n, prev;
-  CGF_CUDA(h, add_node(ob, &n, nullptr, (const void*)spmv_kernel<double>, Gs, kBlock, a_spmv));
-  prev = n;
-  CGF_CUDA(h, add_node(ob, &n, prev, (const void*)gf_res, G, kBlock, a_f));
-  prev = n;
-  CGF_CUDA(h, add_node(ob, &n, prev, dia ? (const void*)gf_t<true> : (const void*)gf_t<false>, G, kBlock, a_f));
-  prev = n;
-  CGF_CUDA(h, add_node(ob, &n, prev, (const void*)gf_start<true>, 1, 32, a_f));
-  prev = n;
-  CGF_CUDA(h, add_node(ob, &n, prev, dia ? (const void*)gf_p0<true> : (const void*)gf_p0<false>, G, kBlock, a_f));
-  prev = n;
+  cudaGraphNode_t prev = nullptr, n;
+  CGF_CUDA(h, add_outer_step<true>(ob, pl, &prev));
   cudaGraphNodeParams ip{};
   ip.type = cudaGraphNodeTypeConditional;
   ip.conditional.handle = inner_h;
@@ -748,13 +938,10 @@ cg_status build_fsai_graph(cg_handle* h, const FArgs& Fin) {
   ip.conditional.size = 1;
   CGF_CUDA(h, cudaGraphAddNode(&n, ob, &prev, nullptr, 1, &ip));
   cudaGraph_t ib = ip.conditional.phGraph_out[0];
-  cudaGraphNode_t b1, b2, b3;
-  CGF_CUDA(h, add_node(ib, &b1, nullptr, f_spmv, Gq, kBlock, a_ga));
-  CGF_CUDA(h, add_node(ib, &b2, b1, dia ? (const void*)gf_upd_r<true> : (const void*)gf_upd_r<false>, G, kBlock,
-                       a_f));
-  CGF_CUDA(h, add_node(ib, &b3, b2, dia ? (const void*)gf_upd_p<true, true> : (const void*)gf_upd_p<false, true>, G,
-                       kBlock, a_f));
-  CGF_CUDA(h, add_node(g, &n, on, (const void*)g_flush_ir, G, kBlock, a_ga));
+  cudaGraphNode_t bprev = nullptr;
+  CGF_CUDA(h, add_inner_iteration<true>(ib, pl, &bprev));
+  void* a_ga[] = {&pl.F.a};
+  CGF_CUDA(h, add_node(g, &n, on, (const void*)g_flush_ir, pl.G, kBlock, a_ga));
   CGF_CUDA(h, cudaGraphInstantiate(&f->gexec, g, 0));
   return CG_OK;
 }
@@ -956,7 +1143,7 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, bool 
   }
   F.V64 = FsaiVecs<double>{f->r0, f->r1, Pin.V64.p, Pin.V64.q, f->t, Pin.x};
   F.V32 = FsaiVecs<float>{f->r0_32, f->r1_32, Pin.V32.p, Pin.V32.q, f->t_32, f->x_32};
-  if (!fp64 && (h->loop_mode == 2 || (h->loop_mode == 0 && n >= kFsaiGraphMinRows))) {
+  if (!fp64 && (h->loop_mode >= 2 || (h->loop_mode == 0 && n >= kFsaiGraphMinRows))) {
     FArgs FA{};
     FA.a.P = Pin;
     FA.a.gs = h->gs;
@@ -967,13 +1154,14 @@ cg_status cgi::fsai_solve(cg_handle* h, const SolveParams& Pin, bool fp64, bool 
     FA.t = f->t_32;
     FA.d = f->x_32;
     FA.carry = carry ? 1 : 0;
-    return solve_fsai_graph(h, FA, carry, iters_out, relres_out);
+    return solve_fsai_graph(h, FA, carry, h->loop_mode == 3 ? kFsaiUnroll : 0, iters_out, relres_out);
   }
   void* args[] = {&F};
   const void* fn;
-  if (fp64) fn = f->dia ? (const void*)pcg_fsai64_kernel<true> : (const void*)pcg_fsai64_kernel<false>;
-  else if (carry) fn = f->dia ? (const void*)pcg_fsai_ir_kernel<true, true> : (const void*)pcg_fsai_ir_kernel<false, true>;
-  else fn = f->dia ? (const void*)pcg_fsai_ir_kernel<true, false> : (const void*)pcg_fsai_ir_kernel<false, false>;
+  const int sw = fsai_slots(f);
+  if (fp64) fn = by_slots<Pick64>(sw);
+  else if (carry) fn = by_slots<PickIr<true>>(sw);
+  else fn = by_slots<PickIr<false>>(sw);
   int per_sm = 0;
   CGF_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
   const int G = std::max(1, std::min(grid, per_sm * h->sm_count));

@@ -38,13 +38,16 @@ struct FsaiData {
   float* gpart = nullptr;          // per-CTA partial parameter gradients
   float* mlp_o = nullptr;          // MLP output per tril entry
   float* params32 = nullptr;       // parameters given to cg_fsai_load (device, fp32)
-  // graph form of the fp32 refinement loop
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // graph forms of the fp32 refinement loop: one graph with nested WHILE
+  // nodes, or (unrolled) an outer-step graph, an 8-iteration graph and an
+  // epilogue graph relaunched by the host
+  cudaGraph_t graph = nullptr, graph_it = nullptr, graph_ep = nullptr;
+  cudaGraphExec_t gexec = nullptr, gexec_it = nullptr, gexec_ep = nullptr;
   const void* gkey_b = nullptr;
   const void* gkey_x = nullptr;
   double gkey_tol = -1.0, gkey_tol_in = -1.0;
-  int gkey_maxit = -1, gkey_outer = -1, gkey_carry = -1, gkey_kind = -1;
+  int gkey_maxit = -1, gkey_outer = -1, gkey_carry = -1, gkey_kind = -1, gkey_unroll = -1;
+  int ggrid = 0;  // CTAs of the graph form's vector-phase kernels
 };
 
 namespace cgi {
@@ -52,5 +55,4 @@ cg_status fsai_pattern(cg_handle* h);
 cg_status fsai_commit(cg_handle* h, int kind);
 cg_status fsai_solve(cg_handle* h, const cg::SolveParams& P, bool fp64, bool carry, int grid,
                      int32_t* iters_out, double* relres_out);
-const void* spmv_kernel_f32(const cg_handle* h);  // graph-form SpMV of the unscaled fp32 loop matrix
 }  // namespace cgi

@@ -35,6 +35,12 @@ struct GState {
   int outer;           // refinement: inner solves started
   double rho_k;        // reliable updates: r.z before the last step of the inner solve
   double beta0;        // reliable updates: carry factor of the next inner solve's p
+  int finished;        // refinement: the outer loop has stopped (host test of the unrolled form)
+  // FSAI refinement graph: scalars formed once by the producing kernel's last CTA
+  double alpha;        // rho / p.q of the current iteration
+  double beta;         // rho' / rho
+  int xflush;          // the inner solve has ended: x64 += d before the next outer step
+  unsigned ctr_q;      // arrivals of the SpMV launch (last-CTA election)
 };
 
 struct GArgs {

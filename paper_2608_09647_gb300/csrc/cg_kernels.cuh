@@ -228,14 +228,44 @@ struct Grid {
   __device__ __forceinline__ bool sync() { return grid_barrier(st, G, timeout_ns, ++seq, skip_seq); }
 };
 
-// Write this CTA's block sums of v[0..NV) into part[j*G + cta].
+// Write this CTA's block sums of v[0..NV) into part[j*G + cta] (v is
+// consumed: afterwards it holds the sums in thread 0 only).
 template <int NV>
 __device__ __forceinline__ void publish(double (&v)[NV], double* part, const Grid& g) {
-  block_sum<NV>(v);
+  cta_sum0<NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) part[(size_t)j * g.G + g.cta] = v[j];
   }
+}
+
+// publish, then elect the last CTA of the launch to arrive (counter *ctr):
+// it sums the G partials once (thread t takes partials t, t + kBlock, ...;
+// then cta_sum0), leaves the totals in thread 0's tot, resets the counter and
+// returns true in every one of its threads.  Consumers then read finished
+// scalars instead of re-summing G partials in every CTA.  Writer: partial,
+// fence, counter; reader: counter, fence, L2 loads (no stale L1 lines).
+template <int NV>
+__device__ __forceinline__ bool publish_last(double (&v)[NV], double* part, const Grid& g, unsigned* ctr,
+                                             double (&tot)[NV]) {
+  __shared__ int s_last;
+  publish<NV>(v, part, g);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(ctr, 1u) == g.G - 1;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double t = 0.0;
+    for (unsigned c = threadIdx.x; c < g.G; c += kBlock) t += __ldcg(part + (size_t)j * g.G + c);
+    tot[j] = t;
+  }
+  cta_sum0<NV>(tot);
+  if (threadIdx.x == 0) *ctr = 0;
+  return true;
 }
 
 template <typename T> struct Vec;

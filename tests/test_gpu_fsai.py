@@ -189,13 +189,13 @@ def test_fsai_rejects_unsuitable_matrices():
 
 
 @pytest.mark.parametrize("precision", [cg.CG_PREC_FP32_IR, cg.CG_PREC_FP32_RU], ids=["fp32_ir", "fp32_ru"])
-@pytest.mark.parametrize("mode", [1, 2], ids=["persistent", "graph"])
+@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
 @pytest.mark.parametrize("name,make", CASES[:3] + [("q1_260", lambda: gen.q1aniso(260, 1.5, 1.9, 0.004, 8))],
                          ids=[c[0] for c in CASES[:3]] + ["q1_260"])
 def test_fsai_refinement_loop_forms_match_oracle(name, make, mode, precision):
-    """Both loop forms of the fp32 FSAI refinement (the persistent kernel and the graph of
-    phase kernels under WHILE nodes) against the oracle; the automatic choice is the graph
-    form from 2^19 rows."""
+    """The loop forms of the fp32 FSAI refinement (the persistent kernel, the graph of
+    phase kernels under WHILE nodes, and the same kernels in unrolled graphs relaunched by
+    the host) against the oracle; the automatic choice is the graph form from 2^19 rows."""
     A = make()
     g = fsai.classic(A)
     b = oracle.spmv(A, gen.xstar(A.n, 9))
@@ -223,3 +223,25 @@ def test_fsai_refinement_loop_forms_match_oracle(name, make, mode, precision):
     x2 = torch.zeros_like(bd)
     assert cg.cg_solve(h2, bd, x2, tol, 100000, cg.CG_PRECOND_FSAI, precision)[0] == cg.CG_OK
     assert cg.cg_get_solve_info(h2)["loop_form"] == (2 if A.n >= 1 << 19 else 1)
+
+
+@pytest.mark.parametrize("precision", [cg.CG_PREC_FP32_IR, cg.CG_PREC_FP32_RU], ids=["fp32_ir", "fp32_ru"])
+def test_fsai_unrolled_graph_equals_while_graph(precision):
+    """The unrolled graphs run the WHILE graph's kernels in the same order with the same
+    grids, so the two forms give the same x bit for bit and the same counts."""
+    A = gen.q1aniso(130, 1.5, 0.4, 0.01, 12)
+    g = fsai.classic(A)
+    b = oracle.spmv(A, gen.xstar(A.n, 3))
+    bd = torch.from_numpy(b).cuda()
+    out = {}
+    for mode in (2, 3):
+        h = handle(A)
+        assert cg.cg_fsai_set_factor(h, torch.from_numpy(g).cuda()) == cg.CG_OK
+        assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
+        x = torch.zeros_like(bd)
+        st, it, rel = cg.cg_solve(h, bd, x, 1e-9, 100000, cg.CG_PRECOND_FSAI, precision)
+        assert st == cg.CG_OK, cg.cg_last_error(h)
+        info = cg.cg_get_solve_info(h)
+        out[mode] = (x.cpu().numpy(), it, info["restarts"], rel)
+    assert np.array_equal(out[2][0], out[3][0])
+    assert out[2][1:] == out[3][1:]
