@@ -562,14 +562,22 @@ def main():
     torch.cuda.synchronize()
     setup_ms = None
     if precond_s.startswith("fsai"):  # the factor, once per matrix (timed on its own)
+        def setup(hh):
+            if precond_s == "fsai_classic":
+                st = cg.cg_fsai_classic(hh)
+            else:
+                bits = np.load(FSAI_WEIGHTS)
+                st = cg.cg_fsai_load(hh, (bits.astype(np.uint32) << 16).view(np.float32))
+            if st != cg.CG_OK:
+                raise RuntimeError(f"FSAI setup failed: {cg.cg_last_error(hh)}")
+        # once on a scratch handle first: the first use of the setup kernels
+        # (module loading) is not part of a factor's cost
+        hw = cg.cg_create(A.n, rp, ci, va)
+        setup(hw)
+        cg.cg_destroy(hw)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if precond_s == "fsai_classic":
-            st = cg.cg_fsai_classic(h)
-        else:
-            bits = np.load(FSAI_WEIGHTS)
-            st = cg.cg_fsai_load(h, (bits.astype(np.uint32) << 16).view(np.float32))
-        if st != cg.CG_OK:
-            raise RuntimeError(f"FSAI setup failed: {cg.cg_last_error(h)}")
+        setup(h)  # the whole setup on a fresh handle: pattern, factor, loop layouts
         setup_ms = (time.perf_counter() - t0) * 1e3
 
     def step():

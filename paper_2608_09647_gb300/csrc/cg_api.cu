@@ -213,6 +213,7 @@ cg_status cuda_fail(cg_handle* h, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
   } while (0)
 
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 unsigned grid_for(int64_t items) {
@@ -263,6 +264,39 @@ int auto_grid(const cg_handle* h) {
   return (int)std::min<int64_t>(want, h->grid_max);
 }
 
+}  // namespace
+
+// Every distinct off-diagonal offset j - i of the caller's CSR, once per
+// handle (device table of kOffSlots slots; noffs_all = -1 when they do not fit).
+cg_status cgi::ensure_offsets(cg_handle* h) {
+  if (h->noffs_all != cg_handle::kOffsUnknown) return CG_OK;
+  const int64_t n = h->n;
+  std::vector<int> ht(kOffSlots + 1, kOffEmpty);
+  ht[kOffSlots] = 0;
+  if (n > 0) {
+    int* tab = nullptr;
+    CG_CUDA(h, cudaMalloc(&tab, sizeof(int) * (kOffSlots + 1)));
+    cudaError_t e = cudaMemcpy(tab, ht.data(), sizeof(int) * (kOffSlots + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      offsets_kernel<<<grid_for(n), 256>>>(n, h->rowptr, h->colind, tab, tab + kOffSlots);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ht.data(), tab, sizeof(int) * (kOffSlots + 1), cudaMemcpyDeviceToHost);
+    cudaFree(tab);
+    if (e != cudaSuccess) return cuda_fail(h, e, "diagonal offsets");
+  }
+  std::vector<int32_t> offs;
+  for (int t = 0; t < kOffSlots; ++t)
+    if (ht[(size_t)t] != kOffEmpty) offs.push_back(ht[(size_t)t]);
+  std::sort(offs.begin(), offs.end());
+  static_assert(kOffSlots <= cg_handle::kOffsAll, "offset table larger than the handle's copy");
+  h->noffs_all = ht[kOffSlots] ? -1 : (int32_t)offs.size();
+  for (int m = 0; m < std::max(h->noffs_all, 0); ++m) h->offs_all[m] = offs[(size_t)m];
+  return CG_OK;
+}
+
+namespace {
+
 // SELL-32 structure of the off-diagonal part (shared by every value
 // variant) and the diagonal vectors.
 cg_status ensure_offdiag(cg_handle* h) {
@@ -277,24 +311,12 @@ cg_status ensure_offdiag(cg_handle* h) {
   int64_t nnz_od_all = 0;
   for (int64_t i = 0; i < n; ++i) nnz_od_all += rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
   if (n > 0 && nnz_od_all > 0) {
-    int* tab = nullptr;
-    CG_CUDA(h, cudaMalloc(&tab, sizeof(int) * (kOffSlots + 1)));
-    std::vector<int> ht(kOffSlots + 1, kOffEmpty);
-    ht[kOffSlots] = 0;
-    cudaError_t e = cudaMemcpy(tab, ht.data(), sizeof(int) * (kOffSlots + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-      offsets_kernel<<<grid_for(n), 256>>>(n, h->rowptr, h->colind, tab, tab + kOffSlots);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(ht.data(), tab, sizeof(int) * (kOffSlots + 1), cudaMemcpyDeviceToHost);
-    cudaFree(tab);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cg_create: diagonal offsets");
-    std::vector<int32_t> offs;
-    for (int t = 0; t < kOffSlots; ++t)
-      if (ht[(size_t)t] != kOffEmpty) offs.push_back(ht[(size_t)t]);
-    std::sort(offs.begin(), offs.end());
-    const int nd_ = (int)offs.size();
-    if (!ht[kOffSlots] && nd_ > 0 && nd_ <= kMaxDiag && nnz_od_all * 10 >= (int64_t)nd_ * n * 9) {
+    const cg_status so = cgi::ensure_offsets(h);
+    if (so != CG_OK) return so;
+    const int nd_ = std::max(h->noffs_all, 0);
+    const bool fits = h->noffs_all >= 0;
+    std::vector<int32_t> offs(h->offs_all, h->offs_all + nd_);
+    if (fits && nd_ > 0 && nd_ <= kMaxDiag && nnz_od_all * 10 >= (int64_t)nd_ * n * 9) {
       h->dia = 1;
       h->uniform_w = nd_;
       for (int m = 0; m < nd_; ++m) h->delta[m] = offs[(size_t)m];

@@ -186,6 +186,27 @@ __device__ __forceinline__ T ell_row(const Ell<T>& E, int64_t i, int64_t n, Fn&&
   return s;
 }
 
+// The rows gtid, gtid + gstride, ... of a grid-stride loop, two at a time:
+// load(i) reads a row's inputs and forms its results (no stores), store(i, v)
+// writes them, in row order.  Both rows' loads are in flight before the first
+// store, which the compiler may not move loads across.
+template <class Load, class Store>
+__device__ __forceinline__ void rows_x2(const Grid& g, int64_t n, Load&& load, Store&& store) {
+  int64_t i = g.gtid;
+  for (; i + g.gstride < n; i += 2 * g.gstride) {
+    const auto a = load(i);
+    const auto b = load(i + g.gstride);
+    store(i, a);
+    store(i + g.gstride, b);
+  }
+  if (i < n) store(i, load(i));
+}
+
+template <typename T>
+struct RowUpd {
+  T r, t, x;
+};
+
 template <typename T>
 struct FsaiVecs {
   T *r0, *r1, *p, *q, *t, *x;  // x: the iterate (fp64) or the correction d (refinement)
@@ -205,11 +226,12 @@ template <int W, typename T>
 __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
                            double* part, int pstride, Grid& g, double* rho, double rho_prev = 0.0) {
   Acc<T> a;
-  for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    const T s = ell_row<W>(G, i, n, [&](int j) { return r[j]; });
-    V.t[i] = s;
-    a.add(s, s);
-  }
+  rows_x2(
+      g, n, [&](int64_t i) { return ell_row<W>(G, i, n, [&](int j) { return r[j]; }); },
+      [&](int64_t i, T s) {
+        V.t[i] = s;
+        a.add(s, s);
+      });
   double v[1] = {a.get()};
   publish<1>(v, part + kSlotRes * (size_t)pstride, g);
   if (!g.sync()) return false;
@@ -217,10 +239,13 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
   *rho = v[0];
   const bool carry = rho_prev > 0.0;
   const T beta = carry ? (T)(v[0] / rho_prev) : T(0);
-  for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    const T s = ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; });
-    V.p[i] = carry ? fma(beta, V.p[i], s) : s;
-  }
+  rows_x2(
+      g, n,
+      [&](int64_t i) {
+        const T s = ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; });
+        return carry ? fma(beta, V.p[i], s) : s;
+      },
+      [&](int64_t i, T pi) { V.p[i] = pi; });
   return g.sync();
 }
 
@@ -257,15 +282,22 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     if (s_fl) { status = s_fl; break; }
     const T alpha = (T)s_sc[0];
     Acc<T> a_rho, a_rr;
-    for (int64_t i = g.gtid; i < n; i += g.gstride) {
-      const T ri = fma(-alpha, V.q[i], rc[i]);
-      rn[i] = ri;
-      a_rr.add(ri, ri);
-      const T s = ell_row<W>(G, i, n, [&](int j) { return fma(-alpha, V.q[j], rc[j]); });
-      V.t[i] = s;
-      a_rho.add(s, s);
-      V.x[i] = fma(alpha, V.p[i], V.x[i]);
-    }
+    rows_x2(
+        g, n,
+        [&](int64_t i) {
+          RowUpd<T> u;
+          u.r = fma(-alpha, V.q[i], rc[i]);
+          u.t = ell_row<W>(G, i, n, [&](int j) { return fma(-alpha, V.q[j], rc[j]); });
+          u.x = fma(alpha, V.p[i], V.x[i]);
+          return u;
+        },
+        [&](int64_t i, const RowUpd<T>& u) {
+          rn[i] = u.r;
+          a_rr.add(u.r, u.r);
+          V.t[i] = u.t;
+          a_rho.add(u.t, u.t);
+          V.x[i] = u.x;
+        });
     double v2[2] = {a_rho.get(), a_rr.get()};
     publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
@@ -288,10 +320,9 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     rc = rn;
     rn = tmp;
     if (!done) {
-      for (int64_t i = g.gtid; i < n; i += g.gstride) {
-        const T s = ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; });
-        V.p[i] = fma(beta, V.p[i], s);
-      }
+      rows_x2(
+          g, n, [&](int64_t i) { return fma(beta, V.p[i], ell_row<W>(GT, i, n, [&](int j) { return V.t[j]; })); },
+          [&](int64_t i, T pi) { V.p[i] = pi; });
       if (!g.sync()) { status = kTimeout; break; }
     }
   }
@@ -619,15 +650,22 @@ __global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_upd_r(FArgs F) {
   const float* q = P.V32.q;
   const float* p = P.V32.p;
   Acc<float> a_rho, a_rr;
-  for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    const float ri = fmaf(-alpha, q[i], rc[i]);
-    rn[i] = ri;
-    a_rr.add(ri, ri);
-    const float s = ell_row<W>(F.G, i, n, [&](int j) { return fmaf(-alpha, q[j], rc[j]); });
-    F.t[i] = s;
-    a_rho.add(s, s);
-    F.d[i] = fmaf(alpha, p[i], F.d[i]);
-  }
+  rows_x2(
+      g, n,
+      [&](int64_t i) {
+        RowUpd<float> u;
+        u.r = fmaf(-alpha, q[i], rc[i]);
+        u.t = ell_row<W>(F.G, i, n, [&](int j) { return fmaf(-alpha, q[j], rc[j]); });
+        u.x = fmaf(alpha, p[i], F.d[i]);
+        return u;
+      },
+      [&](int64_t i, const RowUpd<float>& u) {
+        rn[i] = u.r;
+        a_rr.add(u.r, u.r);
+        F.t[i] = u.t;
+        a_rho.add(u.t, u.t);
+        F.d[i] = u.x;
+      });
   double v[2] = {a_rho.get(), a_rr.get()}, s2[2];
   if (!publish_last<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g, &gs->ctr, s2)) return;
   if (threadIdx.x == 0) {
@@ -660,10 +698,9 @@ __global__ void __launch_bounds__(kBlock, kFsaiPhaseCtas) gf_upd_p(FArgs F) {
   const int64_t n = P.A.n;
   const float beta = (float)gs->beta;
   float* p = P.V32.p;
-  for (int64_t i = g.gtid; i < n; i += g.gstride) {
-    const float s = ell_row<W>(F.GT, i, n, [&](int j) { return F.t[j]; });
-    p[i] = fmaf(beta, p[i], s);
-  }
+  rows_x2(
+      g, n, [&](int64_t i) { return fmaf(beta, p[i], ell_row<W>(F.GT, i, n, [&](int j) { return F.t[j]; })); },
+      [&](int64_t i, float pi) { p[i] = pi; });
 }
 
 cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, cudaGraphNode_t dep, const void* fn, unsigned grid,
@@ -960,10 +997,264 @@ void cgi::fsai_free(FsaiData* f) {
   delete f;
 }
 
-// Pattern of G (tril(A)) and of G^T, their ELL slot maps, once per handle.
-cg_status cgi::fsai_pattern(cg_handle* h) {
-  if (h->fsai) return CG_OK;
-  if (!h->jacobi_ok) return ffail(h, CG_ERR_INVALID, "FSAI needs a positive diagonal in every row");
+namespace {
+
+// ---------------------------------------------------------------- pattern
+// Device build of the tril(A) pattern.  Pass 1 (thread per row) validates each
+// row as the host build does (strictly increasing columns, a diagonal, at most
+// kFsaiMaxRow tril entries; the first failing row in row order is reported:
+// key row * 4 + code, atomicMin), and counts the row's tril length, each
+// column's tril entries (the widest column is G^T's width) and the distinct
+// tril offsets (open-addressing table; more than kFsaiMaxDiag -> ELL).
+constexpr int kPatSlots = 32;
+constexpr unsigned long long kPatNoErr = ~0ull;
+struct PatInfo {
+  unsigned long long first_err;
+  int gw, gtw, overflow, asym;
+  int table[kPatSlots];
+};
+
+__global__ void tril_count_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                  int32_t* __restrict__ len, int32_t* __restrict__ cnt, PatInfo* info) {
+  int my_gw = 0, my_gtw = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k0 = rowptr[i], k1 = rowptr[i + 1];
+    int last = -1, l = 0, code = 0;
+    for (int k = k0; k < k1; ++k) {
+      const int c = colind[k];
+      if (c <= last) {
+        code = 1;
+        break;
+      }
+      last = c;
+      if (c <= i) ++l;
+    }
+    if (!code) {
+      if (l == 0 || colind[k0 + l - 1] != (int)i) code = 2;
+      else if (l > kFsaiMaxRow) code = 3;
+    }
+    if (code) {
+      atomicMin(&info->first_err, (unsigned long long)i * 4ull + (unsigned long long)code);
+      len[i] = 0;
+      continue;
+    }
+    len[i] = l;
+    my_gw = max(my_gw, l);
+    for (int m = 0; m < l; ++m) {
+      const int j = colind[k0 + m];
+      my_gtw = max(my_gtw, atomicAdd(&cnt[j], 1) + 1);
+      const int o = j - (int)i;
+      unsigned hs = ((unsigned)o * 2654435761u) >> 27;  // 5 bits
+      int t = 0;
+      for (; t < kPatSlots; ++t, hs = (hs + 1) & (kPatSlots - 1)) {
+        const int v = *((volatile int*)&info->table[hs]);
+        if (v == o) break;
+        if (v == INT32_MIN) {
+          const int old = atomicCAS(&info->table[hs], INT32_MIN, o);
+          if (old == INT32_MIN || old == o) break;
+        }
+      }
+      if (t == kPatSlots) info->overflow = 1;
+    }
+  }
+  my_gw = __reduce_max_sync(0xffffffffu, my_gw);
+  my_gtw = __reduce_max_sync(0xffffffffu, my_gtw);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&info->gw, my_gw);
+    atomicMax(&info->gtw, my_gtw);
+  }
+}
+
+// Pass 2 (thread per row): tril entries e = trp[i] + m are the row's first
+// len entries (columns ascending); their column, source index, row and
+// diagonal slot; G's ELL slot map (padding: src -1, own column).
+struct PatOffs {
+  int nd;
+  int off[kFsaiMaxDiag];
+};
+__global__ void tril_fill_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                 const int32_t* __restrict__ trp, int gw, PatOffs po, int32_t* __restrict__ tci,
+                                 int32_t* __restrict__ tsrc, int32_t* __restrict__ trow, int8_t* __restrict__ tslot,
+                                 int32_t* __restrict__ gsrc, int32_t* __restrict__ gcol) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int e0 = trp[i], l = trp[i + 1] - e0, k0 = rowptr[i];
+    for (int m = 0; m < gw; ++m) {
+      const int64_t at = (int64_t)m * n + i;
+      if (m < l) {
+        const int c = colind[k0 + m];
+        tci[e0 + m] = c;
+        tsrc[e0 + m] = k0 + m;
+        trow[e0 + m] = (int32_t)i;
+        if (tslot) {
+          int sl = 0;
+          while (sl < po.nd - 1 && po.off[sl] != c - (int)i) ++sl;
+          tslot[e0 + m] = (int8_t)sl;
+        }
+        gsrc[at] = e0 + m;
+        gcol[at] = c;
+      } else {
+        gsrc[at] = -1;
+        gcol[at] = (int32_t)i;
+      }
+    }
+  }
+}
+
+// Pass 3 (thread per column j): with a symmetric structure the tril entries
+// of column j are (c, j) for the columns c >= j of row j, ascending; entry
+// (c, j) is found in row c's tril part by binary search.  A missing mirror or
+// a count that differs from pass 1's sets asym (the host build takes over).
+__global__ void gt_fill_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                               const int32_t* __restrict__ trp, const int32_t* __restrict__ cnt, int gtw,
+                               int32_t* __restrict__ gtsrc, int32_t* __restrict__ gtcol, PatInfo* info) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    int m = 0;
+    bool bad = false;
+    for (int k = rowptr[j]; k < rowptr[j + 1] && !bad; ++k) {
+      const int c = colind[k];
+      if (c < (int)j) continue;
+      const int a = rowptr[c], lc = trp[c + 1] - trp[c];
+      int lo = 0, hi = lc - 1, p = -1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = colind[a + mid];
+        if (v == (int)j) {
+          p = mid;
+          break;
+        }
+        if (v < (int)j) lo = mid + 1;
+        else hi = mid - 1;
+      }
+      if (p < 0 || m >= gtw) {
+        bad = true;
+        break;
+      }
+      gtsrc[(int64_t)m * n + j] = trp[c] + p;
+      gtcol[(int64_t)m * n + j] = c;
+      ++m;
+    }
+    if (bad || m != cnt[j]) {
+      info->asym = 1;
+      continue;
+    }
+    for (; m < gtw; ++m) {
+      gtsrc[(int64_t)m * n + j] = -1;
+      gtcol[(int64_t)m * n + j] = (int32_t)j;
+    }
+  }
+}
+
+std::string pattern_error(int code) {
+  switch (code) {
+    case 1: return "FSAI needs strictly increasing columns in each row";
+    case 2: return "FSAI needs a diagonal entry in every row";
+    default: return "FSAI: a row of tril(A) has more than " + std::to_string(kFsaiMaxRow) + " entries";
+  }
+}
+
+// The device build (passes 1-3; the host scans the row lengths).  Leaves
+// *fallback = true, and f untouched, when the structure is not symmetric.
+cg_status pattern_device(cg_handle* h, FsaiData* f, bool* fallback) {
+  *fallback = false;
+  const int64_t n = h->n;
+  const unsigned nb = blocks_for(n);
+  std::vector<void*> tmp;
+  struct Guard {
+    std::vector<void*>& v;
+    ~Guard() {
+      for (void* p : v) cudaFree(p);
+    }
+  } guard{tmp};
+  int32_t *len = nullptr, *cnt = nullptr;
+  PatInfo* info = nullptr;
+  CGF_CUDA(h, cudaMalloc(&len, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+  tmp.push_back(len);
+  CGF_CUDA(h, cudaMalloc(&cnt, sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)));
+  tmp.push_back(cnt);
+  CGF_CUDA(h, cudaMalloc(&info, sizeof(PatInfo)));
+  tmp.push_back(info);
+  PatInfo hi{};
+  hi.first_err = kPatNoErr;
+  for (int t = 0; t < kPatSlots; ++t) hi.table[t] = INT32_MIN;
+  CGF_CUDA(h, cudaMemcpy(info, &hi, sizeof(PatInfo), cudaMemcpyHostToDevice));
+  if (n > 0) {
+    CGF_CUDA(h, cudaMemset(cnt, 0, sizeof(int32_t) * (size_t)n));
+    tril_count_kernel<<<nb, 256>>>(n, h->rowptr, h->colind, len, cnt, info);
+    CGF_CUDA(h, cudaGetLastError());
+  }
+  CGF_CUDA(h, cudaMemcpy(&hi, info, sizeof(PatInfo), cudaMemcpyDeviceToHost));
+  if (hi.first_err != kPatNoErr) return ffail(h, CG_ERR_INVALID, pattern_error((int)(hi.first_err & 3ull)));
+  if (hi.gtw > kFsaiMaxCol)
+    return ffail(h, CG_ERR_INVALID, "FSAI: a column of tril(A) has more than " + std::to_string(kFsaiMaxCol) +
+                                        " entries");
+  std::vector<int32_t> trp((size_t)n + 1, 0);
+  if (n > 0) CGF_CUDA(h, cudaMemcpy(trp.data() + 1, len, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < n; ++i) trp[(size_t)i + 1] += trp[(size_t)i];
+  const int64_t nt = trp[(size_t)n];
+  std::vector<int32_t> toffs;
+  for (int t = 0; t < kPatSlots; ++t)
+    if (hi.table[t] != INT32_MIN) toffs.push_back(hi.table[t]);
+  std::sort(toffs.begin(), toffs.end());
+  const bool dia = !hi.overflow && (int)toffs.size() <= kFsaiMaxDiag;
+  PatOffs po{};
+  po.nd = dia ? (int)toffs.size() : 0;
+  for (int m = 0; m < po.nd; ++m) po.off[m] = toffs[(size_t)m];
+  const int gw = hi.gw, gtw = hi.gtw;
+  FsaiData d{};  // the arrays, moved into f on success
+  auto alloc = [&](int32_t** p, int64_t count) -> cudaError_t {
+    const cudaError_t e = cudaMalloc(p, sizeof(int32_t) * (size_t)std::max<int64_t>(count, 1));
+    if (e == cudaSuccess) tmp.push_back(*p);
+    return e;
+  };
+  CGF_CUDA(h, alloc(&d.trp, n + 1));
+  CGF_CUDA(h, alloc(&d.tci, nt));
+  CGF_CUDA(h, alloc(&d.tsrc, nt));
+  CGF_CUDA(h, alloc(&d.trow, nt));
+  CGF_CUDA(h, alloc(&d.gsrc, (int64_t)gw * n));
+  CGF_CUDA(h, alloc(&d.gcol, (int64_t)gw * n));
+  CGF_CUDA(h, alloc(&d.gtsrc, (int64_t)gtw * n));
+  CGF_CUDA(h, alloc(&d.gtcol, (int64_t)gtw * n));
+  if (dia) {
+    CGF_CUDA(h, cudaMalloc(&d.tslot, (size_t)std::max<int64_t>(nt, 1)));
+    tmp.push_back(d.tslot);
+  }
+  CGF_CUDA(h, cudaMemcpy(d.trp, trp.data(), sizeof(int32_t) * trp.size(), cudaMemcpyHostToDevice));
+  if (n > 0) {
+    tril_fill_kernel<<<nb, 256>>>(n, h->rowptr, h->colind, d.trp, gw, po, d.tci, d.tsrc, d.trow, d.tslot, d.gsrc,
+                                  d.gcol);
+    CGF_CUDA(h, cudaGetLastError());
+    gt_fill_kernel<<<nb, 256>>>(n, h->rowptr, h->colind, d.trp, cnt, gtw, d.gtsrc, d.gtcol, info);
+    CGF_CUDA(h, cudaGetLastError());
+  }
+  int asym = 0;
+  CGF_CUDA(h, cudaMemcpy(&asym, &info->asym, sizeof(int), cudaMemcpyDeviceToHost));
+  if (asym) {
+    *fallback = true;  // the guard frees every array
+    return CG_OK;
+  }
+  tmp.resize(3);  // keep len, cnt, info for the guard; the pattern arrays move into f
+  f->trp = d.trp;
+  f->tci = d.tci;
+  f->tsrc = d.tsrc;
+  f->trow = d.trow;
+  f->gsrc = d.gsrc;
+  f->gcol = d.gcol;
+  f->gtsrc = d.gtsrc;
+  f->gtcol = d.gtcol;
+  f->tslot = d.tslot;
+  f->ntril = nt;
+  f->gw = gw;
+  f->gtw = gtw;
+  f->dia = dia ? 1 : 0;
+  f->nd = po.nd;
+  for (int m = 0; m < po.nd; ++m) f->doff[m] = po.off[m];
+  return CG_OK;
+}
+
+// Host build of the pattern (any CSR structure): the fallback when the
+// structure is not symmetric, so that column j of tril(A) is not the upper
+// half of row j.
+cg_status pattern_host(cg_handle* h, FsaiData* f) {
   const int64_t n = h->n, nnz = h->nnz;
   std::vector<int32_t> ci((size_t)nnz);
   if (nnz > 0)
@@ -1043,8 +1334,6 @@ cg_status cgi::fsai_pattern(cg_handle* h) {
       tslot[(size_t)e] = (int8_t)(std::lower_bound(toffs.begin(), toffs.end(), o) - toffs.begin());
     }
   }
-  FsaiData* f = new FsaiData();
-  h->fsai = f;
   f->ntril = nt;
   f->gw = gw;
   f->gtw = gtw;
@@ -1068,9 +1357,15 @@ cg_status cgi::fsai_pattern(cg_handle* h) {
     CGF_CUDA(h, cudaMalloc(&f->tslot, std::max<size_t>(tslot.size(), 1)));
     if (nt > 0) CGF_CUDA(h, cudaMemcpy(f->tslot, tslot.data(), tslot.size(), cudaMemcpyHostToDevice));
   }
+  return CG_OK;
+}
+
+// Value arrays of both layouts and the loop's work vectors.
+cg_status alloc_loop_arrays(cg_handle* h, FsaiData* f) {
+  const int64_t n = h->n, nt = f->ntril;
   const size_t nv = (size_t)std::max<int64_t>(n, 1);
-  gw = std::max(gw, f->nd);  // value arrays serve either layout
-  gtw = std::max(gtw, f->nd);
+  const int gw = std::max(f->gw, f->nd);  // value arrays serve either layout
+  const int gtw = std::max(f->gtw, f->nd);
   CGF_CUDA(h, cudaMalloc(&f->g, sizeof(double) * (size_t)std::max<int64_t>(nt, 1)));
   CGF_CUDA(h, cudaMalloc(&f->gval64, sizeof(double) * (size_t)gw * nv));
   CGF_CUDA(h, cudaMalloc(&f->gval32, sizeof(float) * (size_t)gw * nv));
@@ -1078,6 +1373,27 @@ cg_status cgi::fsai_pattern(cg_handle* h) {
   CGF_CUDA(h, cudaMalloc(&f->gtval32, sizeof(float) * (size_t)gtw * nv));
   for (double** v : {&f->r0, &f->r1, &f->t}) CGF_CUDA(h, cudaMalloc(v, sizeof(double) * nv));
   for (float** v : {&f->r0_32, &f->r1_32, &f->t_32, &f->x_32}) CGF_CUDA(h, cudaMalloc(v, sizeof(float) * nv));
+  return CG_OK;
+}
+
+}  // namespace
+
+// Pattern of G (tril(A)) and of G^T, their ELL slot maps and the loop's
+// value and vector arrays, once per handle.  Built on the device; the host
+// build covers structures that are not symmetric.
+cg_status cgi::fsai_pattern(cg_handle* h) {
+  if (h->fsai) return CG_OK;
+  if (!h->jacobi_ok) return ffail(h, CG_ERR_INVALID, "FSAI needs a positive diagonal in every row");
+  FsaiData* f = new FsaiData();
+  bool fallback = false;
+  cg_status s = pattern_device(h, f, &fallback);
+  if (s == CG_OK && fallback) s = pattern_host(h, f);
+  if (s == CG_OK) s = alloc_loop_arrays(h, f);
+  if (s != CG_OK) {
+    cgi::fsai_free(f);
+    return s;
+  }
+  h->fsai = f;
   return CG_OK;
 }
 

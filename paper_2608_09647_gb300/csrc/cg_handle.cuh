@@ -25,6 +25,7 @@ namespace cgi {
 void batch_free(BatchData* b);
 void fsai_free(FsaiData* f);
 void set_create_error(const std::string& msg);  // message of cg_last_error(NULL)
+cg_status ensure_offsets(cg_handle* h);         // cg_handle::offs_all, once (cg_api.cu)
 }  // namespace cgi
 
 // Device memory owned by a handle.  The internal off-diagonal matrices and
@@ -50,6 +51,13 @@ struct cg_handle {
   int32_t dia = 0;                  // sliced-diagonal layout (no column array)
   double dmin = 1.0, dmax = 1.0;    // range of A_ii (Jacobi)
   int32_t delta[kMaxDiag] = {};     // its diagonal offsets, ascending
+  // every distinct off-diagonal offset j - i of the CSR, ascending (loop
+  // layout, features of the learned factor); noffs_all = -1 when there are
+  // more than kOffsAll, kOffsUnknown before cgi::ensure_offsets
+  static constexpr int kOffsAll = 64;
+  static constexpr int32_t kOffsUnknown = -2;
+  int32_t noffs_all = kOffsUnknown;
+  int32_t offs_all[kOffsAll] = {};
   int32_t* delta_dev = nullptr;
   int32_t* soff = nullptr;
   uint32_t* lmask = nullptr;

@@ -90,29 +90,32 @@ __device__ void entry_features(const MlpArgs& M, int64_t e, bool upper_half, __n
     for (int f = a; f < a + 16; ++f) xr[f] = __float2bfloat16_rn(0.0f);
     return;
   }
+  // formed in fp32 (GB300 runs fp64 at 1/64 of the fp32 rate; a divide or a
+  // square root is a long fp64 sequence) and rounded to bf16, the network's
+  // input precision
   const int i = M.trow[e], j = M.tci[e];
-  const double di = M.diag[i], dj = M.diag[j];
-  double f[19];
+  const float si = sqrtf((float)M.diag[i]), sj = sqrtf((float)M.diag[j]);
+  float f[19];
   if (!upper_half) {
-    for (int k = 0; k < 19; ++k) f[k] = 0.0;
+    for (int k = 0; k < 19; ++k) f[k] = 0.0f;
     const int slot = offset_slot(M, j - i);  // always one of the first ntslots
-    if (slot >= 0 && slot < 8) f[slot] = 1.0;
-    f[8] = M.vals[M.tsrc[e]] / sqrt(di * dj);
-    f[9] = log(dj / di);
+    if (slot >= 0 && slot < 8) f[slot] = 1.0f;
+    f[8] = (float)M.vals[M.tsrc[e]] / (si * sj);
+    f[9] = logf((float)M.diag[j] / (float)M.diag[i]);
     for (int k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) {
       const int c = M.colind[k];
       const int s = offset_slot(M, c - i);
-      if (s >= 0) f[10 + s] = M.vals[k] / sqrt(di * M.diag[c]);
+      if (s >= 0) f[10 + s] = (float)M.vals[k] / (si * sqrtf((float)M.diag[c]));
     }
-    for (int k = 0; k < 19; ++k) xr[k] = __double2bfloat16(f[k]);
+    for (int k = 0; k < 19; ++k) xr[k] = __float2bfloat16_rn(f[k]);
   } else {
-    for (int k = 0; k < 9; ++k) f[k] = 0.0;
+    for (int k = 0; k < 9; ++k) f[k] = 0.0f;
     for (int k = M.rowptr[j]; k < M.rowptr[j + 1]; ++k) {
       const int c = M.colind[k];
       const int s = offset_slot(M, c - j);
-      if (s >= 0) f[s] = M.vals[k] / sqrt(dj * M.diag[c]);
+      if (s >= 0) f[s] = (float)M.vals[k] / (sj * sqrtf((float)M.diag[c]));
     }
-    for (int k = 0; k < 9; ++k) xr[19 + k] = __double2bfloat16(f[k]);
+    for (int k = 0; k < 9; ++k) xr[19 + k] = __float2bfloat16_rn(f[k]);
     xr[28] = __float2bfloat16_rn(1.0f);
     for (int k = 29; k < 32; ++k) xr[k] = __float2bfloat16_rn(0.0f);
   }
@@ -618,20 +621,14 @@ cg_status mlp_prepare(cg_handle* h) {
   if (s != CG_OK) return s;
   FsaiData* f = h->fsai;
   if (f->offs) return CG_OK;
-  const int64_t n = h->n, nnz = h->nnz;
-  std::vector<int32_t> ci((size_t)nnz);
-  if (nnz > 0) CGM_CUDA(h, cudaMemcpy(ci.data(), h->colind, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost));
-  std::vector<int32_t> offs;
-  const std::vector<int32_t>& rp = h->host_rowptr;
-  for (int64_t i = 0; i < n; ++i)
-    for (int k = rp[(size_t)i]; k < rp[(size_t)i + 1]; ++k) {
-      const int o = ci[(size_t)k] - (int)i;
-      if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
-        offs.push_back(o);
-        if ((int)offs.size() > kMaxOffs)
-          return mfail(h, CG_ERR_INVALID, "learned FSAI: the matrix has more than 9 distinct column offsets");
-      }
-    }
+  // the distinct offsets j - i: the off-diagonal set and the diagonal (every
+  // row has one: fsai_pattern checked it)
+  s = cgi::ensure_offsets(h);
+  if (s != CG_OK) return s;
+  if (h->noffs_all < 0 || h->noffs_all + 1 > kMaxOffs)
+    return mfail(h, CG_ERR_INVALID, "learned FSAI: the matrix has more than 9 distinct column offsets");
+  std::vector<int32_t> offs(h->offs_all, h->offs_all + h->noffs_all);
+  offs.push_back(0);
   std::sort(offs.begin(), offs.end());
   int nts = 0;
   for (int o : offs) nts += o <= 0;
@@ -669,6 +666,16 @@ unsigned mlp_grid(const cg_handle* h, int64_t ntril) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 4 * (int64_t)h->sm_count));
 }
 
+// Forward (inference) grid: every resident CTA (the feature gathers are
+// latency-bound; forward has no per-CTA partials to bound the grid).
+unsigned mlp_forward_grid(const cg_handle* h, int64_t ntril) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_forward_kernel, kMlpThreads, 0) != cudaSuccess)
+    per_sm = 4;
+  const int64_t tiles = (ntril + kTileE - 1) / kTileE;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)std::max(per_sm, 1) * h->sm_count));
+}
+
 }  // namespace
 
 extern "C" {
@@ -693,7 +700,7 @@ cg_status cg_fsai_load(cg_handle* h, const void* weights_bf16, int64_t bytes) {
   if (!f->params32) CGM_CUDA(h, cudaMalloc(&f->params32, sizeof(float) * kNParams));
   CGM_CUDA(h, cudaMemcpyAsync(f->params32, p32.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice, h->stream));
   const MlpArgs M = make_args(h, f->params32);
-  mlp_forward_kernel<<<mlp_grid(h, f->ntril), kMlpThreads, 0, h->stream>>>(M, nullptr, f->g);
+  mlp_forward_kernel<<<mlp_forward_grid(h, f->ntril), kMlpThreads, 0, h->stream>>>(M, nullptr, f->g);
   CGM_CUDA(h, cudaGetLastError());
   CGM_CUDA(h, cudaStreamSynchronize(h->stream));  // p32 is host memory of this call
   return cgi::fsai_commit(h, 2);

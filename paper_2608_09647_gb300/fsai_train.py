@@ -70,6 +70,13 @@ class Problem:
                 out.append(r)
         return torch.stack(out) if out else None
 
+    def fresh(self):
+        """Another handle on the same device matrix and right-hand side (no factor)."""
+        P = Problem.__new__(Problem)
+        P.A, P.dev, P.b, P.resid = self.A, self.dev, self.b, self.resid
+        P.h = cg_create(self.A.n, *self.dev)
+        return P
+
     def close(self):
         cg_destroy(self.h)
 
@@ -122,7 +129,8 @@ def solve_stats(P, precond, tol=1e-8, maxit=100000, precision=CG_PREC_FP32_IR, r
 def compare(problems, params, tol=1e-8, precision=CG_PREC_FP32_IR, reps=2):
     """Per matrix: Jacobi, classic FSAI and learned FSAI iterations, solve times
     (device time of the solve launch) and factor setup times (host wall time of
-    cg_fsai_classic / cg_fsai_load, which synchronise)."""
+    cg_fsai_classic / cg_fsai_load, which synchronise), each factor on a handle of
+    its own so that both setups include the pattern build."""
     rows = []
     params = params.detach().cpu().numpy() if hasattr(params, "detach") else params
     for P in problems:
@@ -136,12 +144,14 @@ def compare(problems, params, tol=1e-8, precision=CG_PREC_FP32_IR, reps=2):
             raise CGError(-1, cg_last_error(P.h))
         r["classic_setup_s"] = time.perf_counter() - t0
         r["classic_iters"], r["classic_s"], _, _ = solve_stats(P, CG_PRECOND_FSAI, tol, precision=precision, reps=reps)
+        L = P.fresh()
         t0 = time.perf_counter()
-        if cg_fsai_load(P.h, params) != CG_OK:
-            raise CGError(-1, cg_last_error(P.h))
+        if cg_fsai_load(L.h, params) != CG_OK:
+            raise CGError(-1, cg_last_error(L.h))
         r["learned_setup_s"] = time.perf_counter() - t0
-        r["learned_iters"], r["learned_s"], _, used = solve_stats(P, CG_PRECOND_FSAI, tol, precision=precision,
+        r["learned_iters"], r["learned_s"], _, used = solve_stats(L, CG_PRECOND_FSAI, tol, precision=precision,
                                                                   reps=reps)
+        L.close()
         assert used == CG_PRECOND_FSAI
         rows.append(r)
     return rows

@@ -245,3 +245,38 @@ def test_fsai_unrolled_graph_equals_while_graph(precision):
         out[mode] = (x.cpu().numpy(), it, info["restarts"], rel)
     assert np.array_equal(out[2][0], out[3][0])
     assert out[2][1:] == out[3][1:]
+
+
+def with_explicit_zero(A, i, j):
+    """A copy of A with an explicit zero stored at (i, j), (i, j) not yet stored."""
+    cols = A.colind[A.rowptr[i]:A.rowptr[i + 1]]
+    assert j not in cols
+    at = A.rowptr[i] + int(np.searchsorted(cols, j))
+    rowptr = A.rowptr.copy()
+    rowptr[i + 1:] += 1
+    colind = np.insert(A.colind, at, j).astype(np.int32)
+    vals = np.insert(A.vals, at, 0.0)
+    return gen.CSR(A.n, rowptr, colind, vals, A.name + "_unsym")
+
+
+def test_pattern_of_a_structurally_unsymmetric_matrix():
+    """An explicit zero stored below the diagonal without its mirror makes the stored
+    structure unsymmetric, so column j of tril(A) is no longer the upper half of row j
+    and the pattern is built on the host.  The classic factor (whose pattern includes
+    the stored zero) must match the oracle, and the preconditioned solve converge like
+    the oracle's."""
+    A = with_explicit_zero(gen.lap2d(12), 40, 3)
+    h = handle(A)
+    assert cg.cg_fsai_classic(h) == cg.CG_OK, cg.cg_last_error(h)
+    st, g, kind = cg.cg_fsai_get_factor(h)
+    ref = fsai.classic(A)
+    assert g.numel() == ref.size == fsai.tril(A)[1].size
+    g = g.cpu().numpy()
+    assert np.max(np.abs(g - ref) / np.maximum(np.abs(ref), 1e-300)) <= 1e-10
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    st, it, rel = cg.cg_solve(h, bd, x, 1e-10, 5000, cg.CG_PRECOND_FSAI, cg.CG_PREC_FP64)
+    r = fsai.pcg(A, ref, b, tol=1e-10, maxit=5000)
+    assert st == cg.CG_OK and abs(it - r.iters) <= iters_band(r.iters)
+    assert oracle.true_relres(A, b, x.cpu().numpy()) <= 1e-10 * (1 + 1e-6)
