@@ -96,6 +96,7 @@ def load_peaks():
 KERNEL_SOURCES = {
     "single": ("cg_device.cuh", "cg_kernels.cuh", "cg_graph.cuh", "cg_api.cu"),
     "batch": ("cg_device.cuh", "cg_kernels.cuh", "cg_batch.cu"),
+    "fsai": ("cg_device.cuh", "cg_kernels.cuh", "cg_graph.cuh", "cg_fsai.cu", "cg_fsai.cuh"),
 }
 
 
@@ -630,7 +631,7 @@ def main():
     bpi = kern_bytes / max(1, sum(iters))  # the library's model for this preconditioner
     form = {1: "persistent", 2: "graph", 3: "unrolled"}.get(infos[0][2]["loop_form"], "?")
     launches = sum(inf["kernel_launches"] for _, _, inf in infos)
-    tr = ncu_traffic(args.workload)
+    tr = ncu_traffic(args.workload, "fsai" if precond_s.startswith("fsai") else "single")
     traffic = None
     if tr:
         traffic = int(tr["dram_bytes_per_iter"] * statistics.mean(iters))
