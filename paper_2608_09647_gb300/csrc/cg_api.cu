@@ -655,7 +655,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   return CG_OK;
 }
 
-constexpr int64_t kGraphMinRows = 1 << 20;  // auto mode: graph loop from this many rows
+constexpr int64_t kGraphMinRows = 1 << 18;  // auto mode: graph loop from this many rows (fp64)
 constexpr int kUnrollIters = 8;               // iterations per launch of the unrolled form
 
 // fp64 solve through the graph form of the loop; restarts (true residual

@@ -36,11 +36,17 @@ struct GState {
   double rho_k;        // reliable updates: r.z before the last step of the inner solve
   double beta0;        // reliable updates: carry factor of the next inner solve's p
   int finished;        // refinement: the outer loop has stopped (host test of the unrolled form)
-  // FSAI refinement graph: scalars formed once by the producing kernel's last CTA
+  // scalars formed once by the last CTA of the kernel that reduces them
   double alpha;        // rho / p.q of the current iteration
   double beta;         // rho' / rho
-  int xflush;          // the inner solve has ended: x64 += d before the next outer step
+  double rho1, rr1;    // rho' and r.r of the new residual (committed by the x/p pass)
+  int want_rr;         // Jacobi: the r update also forms r.D r
+  int need_rr;         // Jacobi: g_rr must form the exact r.D r before the test
+  int fl;              // the loop ends after this iteration | converged << 1
+  int xflush;          // FSAI refinement: the inner solve has ended, x64 += d next
   unsigned ctr_q;      // arrivals of the SpMV launch (last-CTA election)
+  unsigned ctr_r;      // arrivals of the r-update launch
+  unsigned ctr_rr;     // arrivals of the r.D r launch
 };
 
 struct GArgs {
@@ -110,68 +116,82 @@ __global__ void g_start64(GArgs a) {
   if constexpr (COND) cudaGraphSetConditional(a.h, status == kRunning ? 1u : 0u);
 }
 
-// a1: q = A^ p, partial p.q.  W > 0: the matrix has uniform slices of width W
-// (chosen on the host, so each width gets its own register budget).
+// a1: q = A^ p, p.q.  W > 0: the matrix has uniform slices of width W (chosen
+// on the host, so each width gets its own register budget).  The last CTA
+// forms alpha = rho / p.q, the breakdown / non-finite test and whether the r
+// update must form r.D r, once for the next kernels.
 template <typename T, bool JAC, int W, bool DIA>
 __global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
   const SolveParams& P = a.P;
-  if (a.gs->status != kRunning) return;
+  GState* gs = a.gs;
+  if (gs->status != kRunning) return;
   Grid g = graph_grid();
   const Sell<T>& S = sell_of<T>(P);
   const LoopVecs<T>& V = vecs_of<T>(P);
-  double v[1];
+  double v[1], pq[1];
   if constexpr (W > 0) v[0] = spmv_phase_w<T, JAC, W, DIA>(S, V.p, V.q, g);
   else v[0] = spmv_phase<T, JAC>(S, V.p, V.q, g);
-  publish<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g);
+  if (!publish_last<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g, &gs->ctr_q, pq)) return;
+  if (threadIdx.x == 0) {
+    const double rho = gs->rho;
+    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
+    gs->alpha = rho / pq[0];
+    gs->want_rr = JAC && rr_wanted(S, rho, gs->stop_abs * gs->stop_abs);
+    if (st) gs->status = st;
+  }
 }
 
-// a2: alpha = rho / p.q (breakdown / non-finite stop the loop); r^ -= alpha q;
-// partials (r^.r^, r.r).
+// The stopping decision for r.r = rr after iteration k1: fl = done | conv << 1.
+__device__ __forceinline__ int stop_flags(double rr, double stop_abs, int k1, int maxit) {
+  const bool conv = sqrt(rr) <= stop_abs;
+  return (conv || k1 >= maxit ? 1 : 0) | (conv ? 2 : 0);
+}
+
+// a2: r^ -= alpha q; partials (r^.r^, r.r when wanted).  The last CTA forms
+// beta and the test (Jacobi with a varying diagonal: from the bound
+// dmin rho <= r.D r <= dmax rho, or it leaves the exact r.D r to g_rr).
 template <typename T, bool JAC>
 __global__ void __launch_bounds__(kBlock) g_upd_r(GArgs a) {
   const SolveParams& P = a.P;
-  if (a.gs->status != kRunning) return;
+  GState* gs = a.gs;
+  if (gs->status != kRunning) return;
   Grid g = graph_grid();
   const Sell<T>& S = sell_of<T>(P);
   const LoopVecs<T>& V = vecs_of<T>(P);
-  double pq[1];
-  grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
-  // the scalars once per CTA (fp64 divisions and tests in every thread would
-  // load GB300's narrow fp64 pipe), shared through shared memory
-  __shared__ double s_alpha;
-  __shared__ int s_stop, s_want;
-  if (threadIdx.x == 0) {
-    const double rho = a.gs->rho;
-    const int st = (!isfinite(pq[0]) || !isfinite(rho)) ? kNumeric : (pq[0] <= 0.0 ? kBreakdown : 0);
-    if (st && g.cta == 0) a.gs->status = st;
-    s_stop = st;
-    s_alpha = rho / pq[0];
-    s_want = JAC && rr_wanted(S, rho, a.gs->stop_abs * a.gs->stop_abs);
-  }
-  __syncthreads();
-  if (s_stop) return;
-  const T alpha = (T)s_alpha;
-  const bool want_rr = s_want != 0;
-  double v[2] = {0.0, 0.0};
+  const T alpha = (T)gs->alpha;
+  const bool want_rr = gs->want_rr != 0;
+  double v[2] = {0.0, 0.0}, s2[2];
   update_r_phase<T, JAC>(S, V, alpha, want_rr, v[0], v[1], g);
-  publish<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g);
+  if (!publish_last<2>(v, P.part + kSlotUpd * (size_t)P.pstride, g, &gs->ctr_r, s2)) return;
+  if (threadIdx.x == 0) {
+    const double rho = gs->rho;
+    const double stop2 = gs->stop_abs * gs->stop_abs;
+    double rr = s2[1];
+    const bool need = JAC && !want_rr && rr_bound_test(S, s2[0], stop2, &rr) < 0;
+    gs->beta = s2[0] / rho;
+    gs->rho1 = s2[0];
+    gs->rr1 = rr;
+    gs->need_rr = need;
+    if (!need) gs->fl = stop_flags(rr, gs->stop_abs, gs->k + 1, P.maxit);
+  }
 }
 
 // Jacobi with a varying diagonal only: when r.r was skipped and the new rho
-// falls into the band where it does not decide the test, compute r.r.
+// falls into the band where it does not decide the test, compute r.r; the
+// last CTA takes the test.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) g_rr(GArgs a) {
   const SolveParams& P = a.P;
-  if (a.gs->status != kRunning) return;
+  GState* gs = a.gs;
+  if (gs->status != kRunning || !gs->need_rr) return;
   Grid g = graph_grid();
   const Sell<T>& S = sell_of<T>(P);
-  const double stop2 = a.gs->stop_abs * a.gs->stop_abs;
-  if (rr_wanted(S, a.gs->rho, stop2)) return;
-  double s2[2], rr;
-  grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, a.G_upd, s2);
-  if (rr_bound_test(S, s2[0], stop2, &rr) >= 0) return;
-  double v[1] = {rr_phase<T>(S, vecs_of<T>(P), g)};
-  publish<1>(v, P.part + kSlotRr * (size_t)P.pstride, g);
+  double v[1] = {rr_phase<T>(S, vecs_of<T>(P), g)}, rr[1];
+  if (!publish_last<1>(v, P.part + kSlotRr * (size_t)P.pstride, g, &gs->ctr_rr, rr)) return;
+  if (threadIdx.x == 0) {
+    gs->rr1 = rr[0];
+    gs->fl = stop_flags(rr[0], gs->stop_abs, gs->k + 1, P.maxit);
+  }
 }
 
 // a3 + a4: beta, convergence; x^ += alpha p and p = r^ + beta p, or on the
@@ -185,43 +205,19 @@ __global__ void __launch_bounds__(kBlock) g_upd_xp(GArgs a) {
   const LoopVecs<T>& V = vecs_of<T>(P);
   GState* gs = a.gs;
   if (!COND && gs->status != kRunning) return;  // unrolled form: loop already over
-  const bool failed = gs->status != kRunning;  // set by g_upd_r (breakdown / numeric)
+  const bool failed = gs->status != kRunning;  // set by g_spmv (breakdown / numeric)
   double rho1 = 0.0, rr1 = 0.0;
   bool done = true, conv = false;
   const int k1 = gs->k + 1;
   if (!failed) {
-    double pq[1], s2[2];
-    grid_sum<1>(P.part + kSlotPQ * (size_t)P.pstride, a.G_spmv, pq);
-    grid_sum<2>(P.part + kSlotUpd * (size_t)P.pstride, a.G_upd, s2);
-    // scalars once per CTA, shared (see g_upd_r)
-    __shared__ double s_sc[4];  // alpha, beta, rr1
-    __shared__ int s_fl[2];     // exact r.r from g_rr needed; done | conv << 1
-    if (threadIdx.x == 0) {
-      const double rho = gs->rho;
-      const double stop2 = gs->stop_abs * gs->stop_abs;
-      double rr = s2[1];
-      s_sc[0] = rho / pq[0];
-      s_sc[1] = s2[0] / rho;
-      s_fl[0] = JAC && !rr_wanted(S, rho, stop2) && rr_bound_test(S, s2[0], stop2, &rr) < 0;
-      s_sc[2] = rr;
-    }
-    __syncthreads();
-    if (s_fl[0]) {  // uniform across the CTA
-      double v3[1];  // written by g_rr
-      grid_sum<1>(P.part + kSlotRr * (size_t)P.pstride, a.G_upd, v3);
-      if (threadIdx.x == 0) s_sc[2] = v3[0];
-    }
-    if (threadIdx.x == 0) {
-      const bool c = sqrt(s_sc[2]) <= gs->stop_abs;
-      s_fl[1] = (c || k1 >= P.maxit ? 1 : 0) | (c ? 2 : 0);
-    }
-    __syncthreads();
-    const T alpha = (T)s_sc[0];
-    const T beta = (T)s_sc[1];
-    rho1 = s2[0];
-    rr1 = s_sc[2];
-    conv = (s_fl[1] & 2) != 0;
-    done = (s_fl[1] & 1) != 0;
+    // the scalars the previous kernels' last CTAs formed
+    const T alpha = (T)gs->alpha;
+    const T beta = (T)gs->beta;
+    const int fl = gs->fl;
+    rho1 = gs->rho1;
+    rr1 = gs->rr1;
+    conv = (fl & 2) != 0;
+    done = (fl & 1) != 0;
     double* out = P.x;
     if (done) update_xp_phase<T, JAC, true, OUT_ADD>(S, V, alpha, beta, out, g);
     else update_xp_phase<T, JAC, false, OUT_ADD>(S, V, alpha, beta, out, g);
