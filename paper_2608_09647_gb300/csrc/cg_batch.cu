@@ -207,13 +207,17 @@ __device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int sta
 // One phase over its list of reduction groups [0, T).  CTA c takes the
 // contiguous chunk [c T / G, (c+1) T / G), which spans few systems.  At the
 // start of each system's segment begin(sys) loads the system's scalars and
-// says whether its sums are wanted.  For every row i of a group, row(i, acc)
-// does the row's work and adds its NV contributions to the thread's
-// accumulators; the group's sums are then reduced per warp (xor tree) and
-// stored.  Leaving a segment, the CTA adds its group count to the system's
+// says whether its sums are wanted.  For every row i of a group, row(i) does
+// the row's loads and arithmetic and returns its commit, which stores the
+// results and adds the row's NV contributions to the thread's accumulators.
+// A thread's rows go in groups of ROWS (4, 2 or 1, by the variant's register
+// budget), every row's loads in flight before the first commit (a store ahead
+// of the next row's loads would serialise them); the accumulation order stays
+// the row order.  The group's sums are then reduced
+// per warp (xor tree) and stored.  Leaving a segment, the CTA adds its group count to the system's
 // counter; the CTA that completes the count sums the system's partials in
 // (group, warp) order, independent of G, and calls done(sys, sums) in thread 0.
-template <int NV, class Begin, class Row, class Done>
+template <int NV, int ROWS, class Begin, class Row, class Done>
 __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
                                           Begin begin, Row row, Done done) {
   __shared__ int s_last;
@@ -231,8 +235,28 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
       double acc[NV > 0 ? NV : 1];
 #pragma unroll
       for (int k = 0; k < (NV > 0 ? NV : 1); ++k) acc[k] = 0.0;
-#pragma unroll 4
-      for (int gt = t0; gt < t1; ++gt) row(gt * kTile + t, acc);
+      int gt = t0;
+      if constexpr (ROWS >= 4) {
+        for (; gt + 3 < t1; gt += 4) {
+          const auto c0 = row(gt * kTile + t);
+          const auto c1 = row((gt + 1) * kTile + t);
+          const auto c2 = row((gt + 2) * kTile + t);
+          const auto c3 = row((gt + 3) * kTile + t);
+          c0(acc);
+          c1(acc);
+          c2(acc);
+          c3(acc);
+        }
+      }
+      if constexpr (ROWS >= 2) {
+        for (; gt + 1 < t1; gt += 2) {
+          const auto c0 = row(gt * kTile + t);
+          const auto c1 = row((gt + 1) * kTile + t);
+          c0(acc);
+          c1(acc);
+        }
+      }
+      for (; gt < t1; ++gt) row(gt * kTile + t)(acc);
       if (NV > 0 && sums) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -271,6 +295,8 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
 // MINB: resident CTAs per SM the registers are budgeted for (an autotuner choice).
 template <bool JAC, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) {
+  // rows in flight per thread within the register budget of MINB CTAs per SM
+  constexpr int kRows = MINB <= 3 ? 4 : (MINB == 4 ? 2 : 1);
   __shared__ int s_pref[kMaxBatch];
   __shared__ int s_scan[kWarps];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
@@ -290,19 +316,21 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     int T = build_list(P, kMaskR, seq, s_pref, s_scan, &alive);
     if (!alive) break;
     if (T > 0) {
-      run_phase<3>(
+      run_phase<3, kRows>(
           P, s_pref, T, g, [&](int) { return true; },
-          [&](int i, double* acc) {
+          [&](int i) {
             const double xi = xh[i];
             const double ri_ax = row_spmv(P, xh, i, JAC ? xi : __ldg(dg + i) * xi);
             const double bi = bh[i];
             const double ri = bi - ri_ax;
-            r[i] = ri;
-            p[i] = ri;
             const double d = JAC ? __ldg(dg + i) : 1.0;
-            acc[0] = fma(ri, ri, acc[0]);      // r^.r^ = r.z
-            acc[1] = fma(d * ri, ri, acc[1]);  // r.r
-            acc[2] = fma(d * bi, bi, acc[2]);  // b.b
+            return [=](double* acc) {
+              r[i] = ri;
+              p[i] = ri;
+              acc[0] = fma(ri, ri, acc[0]);      // r^.r^ = r.z
+              acc[1] = fma(d * ri, ri, acc[1]);  // r.r
+              acc[2] = fma(d * bi, bi, acc[2]);  // b.b
+            };
           },
           [&](int sys, const double* sm) {
             const bool first = P.bb[sys] < 0.0;
@@ -344,13 +372,15 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     ++seq;
     T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
     if (T == 0) continue;
-    run_phase<1>(
+    run_phase<1, kRows>(
         P, s_pref, T, g, [&](int) { return true; },
-        [&](int i, double* acc) {
+        [&](int i) {
           const double pi = p[i];
           const double qi = row_spmv(P, p, i, JAC ? pi : __ldg(dg + i) * pi);
-          q[i] = qi;
-          acc[0] = fma(pi, qi, acc[0]);
+          return [=](double* acc) {
+            q[i] = qi;
+            acc[0] = fma(pi, qi, acc[0]);
+          };
         },
         [&](int sys, const double* sm) {
           const double rho = P.rho[sys];
@@ -368,18 +398,22 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     // ---- B: r -= alpha q, rho' = r^.r^, r.r when near the stopping band, beta, test
     ++seq;
     T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
-    run_phase<2>(
+    run_phase<2, kRows>(
         P, s_pref, T, g,
         [&](int sys) {
           c_alpha = P.alpha[sys];
           c_flag = JAC && P.wrr[sys];
           return true;
         },
-        [&](int i, double* acc) {
+        [&](int i) {
           const double ri = fma(-c_alpha, q[i], r[i]);
-          r[i] = ri;
-          acc[0] = fma(ri, ri, acc[0]);
-          if (c_flag) acc[1] = fma(__ldg(dg + i) * ri, ri, acc[1]);
+          const double di = c_flag ? __ldg(dg + i) : 0.0;
+          const bool flag = c_flag;
+          return [=](double* acc) {
+            r[i] = ri;
+            acc[0] = fma(ri, ri, acc[0]);
+            if (flag) acc[1] = fma(di * ri, ri, acc[1]);
+          };
         },
         [&](int sys, const double* sm) {
           const double rho = sm[0];
@@ -409,7 +443,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     // ---- C: x += alpha p; p = r + beta p unless the loop ended; pending r.D r
     ++seq;
     T = build_list(P, kMaskC, seq, s_pref, s_scan, &alive);
-    run_phase<1>(
+    run_phase<1, kRows>(
         P, s_pref, T, g,
         [&](int sys) {
           const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
@@ -419,12 +453,18 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
           c_sum = stg == kStRrPending;
           return c_sum;
         },
-        [&](int i, double* acc) {
+        [&](int i) {
           const double pi = p[i];
-          xh[i] = fma(c_alpha, pi, xh[i]);
+          const double xn = fma(c_alpha, pi, xh[i]);
           const double ri = r[i];
-          if (c_flag) p[i] = fma(c_beta, pi, ri);
-          if (JAC && c_sum) acc[0] = fma(__ldg(dg + i) * ri, ri, acc[0]);
+          const double pn = fma(c_beta, pi, ri);
+          const bool keep_p = c_flag, sum = JAC && c_sum;
+          const double di = sum ? __ldg(dg + i) : 0.0;
+          return [=](double* acc) {
+            xh[i] = xn;
+            if (keep_p) p[i] = pn;
+            if (sum) acc[0] = fma(di * ri, ri, acc[0]);
+          };
         },
         [&](int sys, const double* sm) {
           P.rr[sys] = sm[0];
