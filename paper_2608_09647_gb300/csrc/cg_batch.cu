@@ -62,6 +62,7 @@ struct BatchParams {
   const int32_t* __restrict__ ntile;   // tiles of each system
   const int32_t* __restrict__ gstart;  // first reduction group of each system
   const int32_t* __restrict__ ngroup;  // reduction groups of each system
+  const int32_t* __restrict__ wcost;   // SpMV-phase cost of a row of each system (load balance)
   const double* __restrict__ dmin;     // smallest A_ii of each system
   const int32_t* __restrict__ soff;    // slice offsets (units of 32 entries)
   const int32_t* __restrict__ col;     // global (concatenated) column of each entry
@@ -85,10 +86,13 @@ __device__ __forceinline__ int eff_stage(unsigned long long w, unsigned seq) {
   return ((unsigned)(w >> 16) == seq) ? (int)((w >> 8) & 0xff) : (int)(w & 0xff);
 }
 
-// Exclusive prefix sum (in s_pref) of the reduction groups of the systems
-// whose stage, as seen in phase seq, is in `mask`; returns their total.
+// Exclusive prefix sum (in s_pref) of the work units of the systems whose
+// stage, as seen in phase seq, is in `mask` (a unit per reduction group, or
+// WEIGHTED: wcost units per group, the SpMV phases' row cost); returns their
+// total.
 // *alive gets whether any system is still unfinished.  Thread t owns a
 // contiguous run of systems; the runs' totals are scanned with warp shuffles.
+template <bool WEIGHTED>
 __device__ int build_list(const BatchParams& P, unsigned mask, unsigned seq, int* s_pref, int* s_warp,
                           bool* alive) {
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -97,7 +101,7 @@ __device__ int build_list(const BatchParams& P, unsigned mask, unsigned seq, int
   int c = 0, live = 0;
   for (int s = s0; s < s1; ++s) {
     const unsigned sbit = 1u << eff_stage(__ldcg(P.sstate + s), seq);
-    const int cs = (sbit & mask) ? P.ngroup[s] : 0;
+    const int cs = (sbit & mask) ? P.ngroup[s] * (WEIGHTED ? P.wcost[s] : 1) : 0;
     live |= (sbit & kMaskAlive) != 0;
     s_pref[s] = cs;
     c += cs;
@@ -217,7 +221,7 @@ __device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int sta
 // per warp (xor tree) and stored.  Leaving a segment, the CTA adds its group count to the system's
 // counter; the CTA that completes the count sums the system's partials in
 // (group, warp) order, independent of G, and calls done(sys, sums) in thread 0.
-template <int NV, int ROWS, class Begin, class Row, class Done>
+template <int NV, int ROWS, bool WEIGHTED, class Begin, class Row, class Done>
 __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
                                           Begin begin, Row row, Done done) {
   __shared__ int s_last;
@@ -226,11 +230,19 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
   int j = (int)((int64_t)T * g.cta / g.G);
   while (j < j1) {
     const int sys = system_of(P, s_pref, j);
-    const int je = min(j1, s_pref[sys] + P.ngroup[sys]);  // end of this system's segment
+    // this CTA's groups of sys: those whose first unit lies in [j, j1)
+    const int w = WEIGHTED ? P.wcost[sys] : 1;
+    const int base = s_pref[sys];
+    const int g0 = (j - base + w - 1) / w;
+    const int g1 = min(P.ngroup[sys], (j1 - base + w - 1) / w);
+    const int next = base + P.ngroup[sys] * w;  // the next system's first unit
+    if (g0 >= g1) {
+      j = min(j1, next);
+      continue;
+    }
     const bool sums = begin(sys);
     const int tend = P.tstart[sys] + P.ntile[sys];
-    for (int jj = j; jj < je; ++jj) {
-      const int grp = jj - s_pref[sys];
+    for (int grp = g0; grp < g1; ++grp) {
       const int t0 = P.tstart[sys] + grp * kGroup, t1 = min(t0 + kGroup, tend);
       double acc[NV > 0 ? NV : 1];
 #pragma unroll
@@ -274,7 +286,7 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
       if (lane == 0) __threadfence();  // partials visible before the count
       __syncthreads();
       if (t == 0) {
-        const unsigned add = (unsigned)(je - j);
+        const unsigned add = (unsigned)(g1 - g0);
         const unsigned prev = atomicAdd(P.cnt + sys, add);
         const int last = prev + add == (unsigned)P.ngroup[sys];
         if (last) P.cnt[sys] = 0u;  // reset for the next phase (after its barrier)
@@ -288,7 +300,7 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
         if (t == 0) done(sys, sm);
       }
     }
-    j = je;
+    j = min(j1, next);
   }
 }
 
@@ -313,10 +325,10 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     // ---- R: residual of the stage 0 / 3 systems, their test, (re)start
     ++seq;
     bool alive = false;
-    int T = build_list(P, kMaskR, seq, s_pref, s_scan, &alive);
+    int T = build_list<true>(P, kMaskR, seq, s_pref, s_scan, &alive);
     if (!alive) break;
     if (T > 0) {
-      run_phase<3, kRows>(
+      run_phase<3, kRows, true>(
           P, s_pref, T, g, [&](int) { return true; },
           [&](int i) {
             const double xi = xh[i];
@@ -370,9 +382,9 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     }
     // ---- A: q = A p, alpha
     ++seq;
-    T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    T = build_list<true>(P, kMaskAB, seq, s_pref, s_scan, &alive);
     if (T == 0) continue;
-    run_phase<1, kRows>(
+    run_phase<1, kRows, true>(
         P, s_pref, T, g, [&](int) { return true; },
         [&](int i) {
           const double pi = p[i];
@@ -397,8 +409,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     if (!g.sync()) return;
     // ---- B: r -= alpha q, rho' = r^.r^, r.r when near the stopping band, beta, test
     ++seq;
-    T = build_list(P, kMaskAB, seq, s_pref, s_scan, &alive);
-    run_phase<2, kRows>(
+    T = build_list<false>(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    run_phase<2, kRows, false>(
         P, s_pref, T, g,
         [&](int sys) {
           c_alpha = P.alpha[sys];
@@ -442,8 +454,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     if (!g.sync()) return;
     // ---- C: x += alpha p; p = r + beta p unless the loop ended; pending r.D r
     ++seq;
-    T = build_list(P, kMaskC, seq, s_pref, s_scan, &alive);
-    run_phase<1, kRows>(
+    T = build_list<false>(P, kMaskC, seq, s_pref, s_scan, &alive);
+    run_phase<1, kRows, false>(
         P, s_pref, T, g,
         [&](int sys) {
           const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
@@ -607,7 +619,7 @@ struct BatchData {
   int ntiles = 0, nslices = 0;
   int64_t entries = 0;             // slice entries (multiple of 32)
   int32_t *d_tstart = nullptr, *d_ntile = nullptr, *soff = nullptr, *col = nullptr;
-  int32_t *d_gstart = nullptr, *d_ngroup = nullptr;
+  int32_t *d_gstart = nullptr, *d_ngroup = nullptr, *d_wcost = nullptr;
   int ngroups = 0;                 // reduction groups in all
   double* d_dmin = nullptr;        // smallest A_ii per system
   int64_t *d_n = nullptr, *d_r0 = nullptr;
@@ -652,7 +664,7 @@ void cgi::batch_free(BatchData* b) {
                  b->val[1],   b->dg,      b->dsq,      b->disq,   b->r,    b->p,      b->q,
                  b->xh,       b->bh,      b->rho,      b->rr,     b->bb,   b->alpha,  b->beta,
                  b->relres,   b->k,       b->restarts, b->status, b->zero, b->sstate, b->cnt,
-                 b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr};
+                 b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr, b->d_wcost};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
@@ -709,6 +721,7 @@ BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
   P.ntile = B->d_ntile;
   P.gstart = B->d_gstart;
   P.ngroup = B->d_ngroup;
+  P.wcost = B->d_wcost;
   P.dmin = B->d_dmin;
   P.wrr = B->wrr;
   P.soff = B->soff;
@@ -977,7 +990,7 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
     CGB_CREATE(cudaMalloc(v, sizeof(double) * ns));
   for (int** v : {&B->k, &B->restarts, &B->status, &B->zero, &B->wrr}) CGB_CREATE(cudaMalloc(v, sizeof(int) * ns));
   {
-    std::vector<int32_t> gst(ns), ngr(ns);
+    std::vector<int32_t> gst(ns), ngr(ns), wc(ns);
     std::vector<double> dmin(ns);
     int groups = 0;
     for (size_t s = 0; s < ns; ++s) {
@@ -985,6 +998,13 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
       ngr[s] = (B->ntile[s] + kGroup - 1) / kGroup;
       groups += ngr[s];
       dmin[s] = B->sys[s]->jacobi_ok ? B->sys[s]->dmin : 1.0;
+      // SpMV-phase cost of a row relative to a vector phase's: ~12 bytes per
+      // stored entry (W of them, padding included) and ~24 of vectors, in
+      // units of 24 bytes, rounded up
+      const int64_t sl0 = (int64_t)B->tstart[s] * kWarps, sl1 = sl0 + (int64_t)B->ntile[s] * kWarps;
+      const int64_t wsum = soff[(size_t)sl1] - soff[(size_t)sl0];
+      const int64_t wavg = (wsum + (sl1 - sl0) - 1) / std::max<int64_t>(sl1 - sl0, 1);
+      wc[s] = (int32_t)std::max<int64_t>(1, (wavg + 3) / 2);
     }
     B->ngroups = groups;
     CGB_CREATE(cudaMalloc(&B->d_gstart, sizeof(int32_t) * ns));
@@ -993,6 +1013,8 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
     CGB_CREATE(cudaMemcpy(B->d_gstart, gst.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
     CGB_CREATE(cudaMemcpy(B->d_ngroup, ngr.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
     CGB_CREATE(cudaMemcpy(B->d_dmin, dmin.data(), sizeof(double) * ns, cudaMemcpyHostToDevice));
+    CGB_CREATE(cudaMalloc(&B->d_wcost, sizeof(int32_t) * ns));
+    CGB_CREATE(cudaMemcpy(B->d_wcost, wc.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
   }
   CGB_CREATE(cudaMalloc(&B->sstate, sizeof(unsigned long long) * ns));
   CGB_CREATE(cudaMalloc(&B->cnt, sizeof(unsigned) * ns));
