@@ -990,7 +990,7 @@ void cgi::fsai_free(FsaiData* f) {
   void* dev[] = {f->trp,   f->tci,    f->tsrc,   f->g,      f->gsrc,  f->gcol,  f->gval64, f->gval32,
                  f->gtsrc, f->gtcol,  f->gtval64, f->gtval32, f->r0,   f->r1,    f->t,      f->r0_32,
                  f->r1_32, f->t_32,   f->x_32,   f->offs,   f->work,  f->dout,  f->gpart,  f->mlp_o,
-                 f->params32, f->trow, f->rpart, f->tslot};
+                 f->params32, f->trow, f->rpart, f->tslot, f->a32,    f->d32,   f->rs32,  f->rs64};
   for (void* p : dev)
     if (p) cudaFree(p);
   destroy_fsai_graph(f);

@@ -37,6 +37,10 @@ struct FsaiData {
   float* dout = nullptr;           // dLoss/do per tril entry
   float* gpart = nullptr;          // per-CTA partial parameter gradients
   float* mlp_o = nullptr;          // MLP output per tril entry
+  float* a32 = nullptr;            // A's values in fp32 (feature inputs)
+  float* d32 = nullptr;            // A_ii in fp32
+  float* rs32 = nullptr;           // 1 / sqrt(A_ii) in fp32
+  double* rs64 = nullptr;          // 1 / sqrt(A_ii) in fp64 (G from the outputs)
   float* params32 = nullptr;       // parameters given to cg_fsai_load (device, fp32)
   // graph forms of the fp32 refinement loop: one graph with nested WHILE
   // nodes, or (unrolled) an outer-step graph, an 8-iteration graph and an

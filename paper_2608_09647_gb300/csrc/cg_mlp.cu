@@ -53,6 +53,9 @@ struct MlpArgs {
   const int32_t* __restrict__ tci;       // column of each tril entry
   const int32_t* __restrict__ tsrc;      // index of each tril entry in A's arrays
   const float* __restrict__ params;      // fp32 parameters (rounded to bf16 on load)
+  const float* __restrict__ a32;         // A's values, A_ii and 1 / sqrt(A_ii) in fp32
+  const float* __restrict__ d32;
+  const float* __restrict__ rs32;
   int offs[kMaxOffs];
   int noffs, ntslots;
   double c0;
@@ -90,22 +93,22 @@ __device__ void entry_features(const MlpArgs& M, int64_t e, bool upper_half, __n
     for (int f = a; f < a + 16; ++f) xr[f] = __float2bfloat16_rn(0.0f);
     return;
   }
-  // formed in fp32 (GB300 runs fp64 at 1/64 of the fp32 rate; a divide or a
-  // square root is a long fp64 sequence) and rounded to bf16, the network's
-  // input precision
+  // formed in fp32 from fp32 copies of A's values and diagonal (GB300 runs
+  // fp64, conversions included, at 1/64 of the fp32 rate) and rounded to
+  // bf16, the network's input precision
   const int i = M.trow[e], j = M.tci[e];
-  const float si = sqrtf((float)M.diag[i]), sj = sqrtf((float)M.diag[j]);
+  const float si = M.rs32[i], sj = M.rs32[j];
   float f[19];
   if (!upper_half) {
     for (int k = 0; k < 19; ++k) f[k] = 0.0f;
     const int slot = offset_slot(M, j - i);  // always one of the first ntslots
     if (slot >= 0 && slot < 8) f[slot] = 1.0f;
-    f[8] = (float)M.vals[M.tsrc[e]] / (si * sj);
-    f[9] = logf((float)M.diag[j] / (float)M.diag[i]);
+    f[8] = M.a32[M.tsrc[e]] * si * sj;
+    f[9] = logf(M.d32[j] / M.d32[i]);
     for (int k = M.rowptr[i]; k < M.rowptr[i + 1]; ++k) {
       const int c = M.colind[k];
       const int s = offset_slot(M, c - i);
-      if (s >= 0) f[10 + s] = (float)M.vals[k] / (si * sqrtf((float)M.diag[c]));
+      if (s >= 0) f[10 + s] = M.a32[k] * si * M.rs32[c];
     }
     for (int k = 0; k < 19; ++k) xr[k] = __float2bfloat16_rn(f[k]);
   } else {
@@ -113,7 +116,7 @@ __device__ void entry_features(const MlpArgs& M, int64_t e, bool upper_half, __n
     for (int k = M.rowptr[j]; k < M.rowptr[j + 1]; ++k) {
       const int c = M.colind[k];
       const int s = offset_slot(M, c - j);
-      if (s >= 0) f[s] = (float)M.vals[k] / (sj * sqrtf((float)M.diag[c]));
+      if (s >= 0) f[s] = M.a32[k] * sj * M.rs32[c];
     }
     for (int k = 0; k < 9; ++k) xr[19 + k] = __float2bfloat16_rn(f[k]);
     xr[28] = __float2bfloat16_rn(1.0f);
@@ -222,9 +225,9 @@ __device__ __forceinline__ double sigmoid_d(double x) {
   return x >= 0.0 ? 1.0 / (1.0 + exp(-x)) : exp(x) / (1.0 + exp(x));
 }
 
-// Inference / training forward: o of every tril entry (and G when g != null).
-__global__ void __launch_bounds__(kMlpThreads) mlp_forward_kernel(MlpArgs M, float* __restrict__ o_out,
-                                                                    double* __restrict__ g_out) {
+// Inference / training forward: the output o of every tril entry (G from o in
+// g_diag_kernel / g_offdiag_kernel).
+__global__ void __launch_bounds__(kMlpThreads) mlp_forward_kernel(MlpArgs M, float* __restrict__ o_out) {
   __shared__ __align__(16) SmemW S;
   __shared__ __align__(16) __nv_bfloat16 xs[4][16 * kW1S];  // 32-bit fragment loads need 4-byte alignment
   load_weights(M, S, nullptr);
@@ -240,14 +243,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_forward_kernel(MlpArgs M, flo
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t e = wb + g + 8 * h;
-        if (e < M.ntril) {
-          const float o = F.o[h];
-          if (o_out) o_out[e] = o;
-          if (g_out) {
-            const int i = M.trow[e], j = M.tci[e];
-            g_out[e] = i == j ? softplus_d((double)o + M.c0) / sqrt(M.diag[i]) : (double)o / sqrt(M.diag[j]);
-          }
-        }
+        if (e < M.ntril) o_out[e] = F.o[h];
       }
     }
     __syncwarp();
@@ -566,22 +562,51 @@ __global__ void resid_grad_kernel(int64_t ntril, const int32_t* __restrict__ tro
 
 // dLoss/do = dLoss/dG dG/do.
 __global__ void dout_kernel(int64_t ntril, const int32_t* __restrict__ trow, const int32_t* __restrict__ tci,
-                            const double* __restrict__ diag, const float* __restrict__ o,
+                            const double* __restrict__ rs64, const float* __restrict__ o,
                             const double* __restrict__ dg, double c0, float* __restrict__ dout) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ntril; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = trow[e], j = tci[e];
-    const double d = i == j ? sigmoid_d((double)o[e] + c0) / sqrt(diag[i]) : 1.0 / sqrt(diag[j]);
+    const double d = i == j ? sigmoid_d((double)o[e] + c0) * rs64[i] : rs64[j];
     dout[e] = (float)(dg[e] * d);
   }
 }
 
-// G from the outputs (training forward).
-__global__ void g_from_o_kernel(int64_t ntril, const int32_t* __restrict__ trow, const int32_t* __restrict__ tci,
-                                const double* __restrict__ diag, const float* __restrict__ o, double c0,
-                                double* __restrict__ g) {
+// fp32 copies of A's values and diagonal and 1 / sqrt(A_ii) in both
+// precisions, once per call (the MLP's feature inputs and G's scaling).
+__global__ void mlp_inputs_kernel(int64_t n, int64_t nnz, const double* __restrict__ vals,
+                                  const double* __restrict__ diag, float* __restrict__ a32, float* __restrict__ d32,
+                                  float* __restrict__ rs32, double* __restrict__ rs64) {
+  const int64_t m = nnz > n ? nnz : n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < nnz) a32[k] = (float)vals[k];
+    if (k < n) {
+      const float d = (float)diag[k];
+      d32[k] = d;
+      rs32[k] = 1.0f / sqrtf(d);
+      rs64[k] = 1.0 / sqrt(diag[k]);
+    }
+  }
+}
+
+// G from the outputs (F5), diagonal entries: thread per row (the diagonal is
+// the last tril entry of its row), G_ii = softplus(o + c0) / sqrt(A_ii) in
+// fp64, so a zero output gives Jacobi's D^-1/2 to rounding.
+__global__ void g_diag_kernel(int64_t n, const int32_t* __restrict__ trp, const double* __restrict__ rs64,
+                              const float* __restrict__ o, double c0, double* __restrict__ g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int e = trp[i + 1] - 1;
+    g[e] = softplus_d((double)o[e] + c0) * rs64[i];
+  }
+}
+
+// Off-diagonal entries, thread per entry: G_ij = o / sqrt(A_jj) (the diagonal
+// ones are g_diag_kernel's; separate kernels keep warps from running both).
+__global__ void g_offdiag_kernel(int64_t ntril, const int32_t* __restrict__ trow, const int32_t* __restrict__ tci,
+                                 const double* __restrict__ rs64, const float* __restrict__ o,
+                                 double* __restrict__ g) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ntril; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = trow[e], j = tci[e];
-    g[e] = i == j ? softplus_d((double)o[e] + c0) / sqrt(diag[i]) : (double)o[e] / sqrt(diag[j]);
+    if (i != j) g[e] = (double)o[e] * rs64[j];
   }
 }
 
@@ -634,6 +659,12 @@ cg_status mlp_prepare(cg_handle* h) {
   for (int o : offs) nts += o <= 0;
   if (nts > 8) return mfail(h, CG_ERR_INVALID, "learned FSAI: more than 8 offsets in tril(A)");
   CGM_CUDA(h, cudaMalloc(&f->offs, sizeof(int32_t) * kMaxOffs));
+  const size_t nv = (size_t)std::max<int64_t>(h->n, 1);
+  CGM_CUDA(h, cudaMalloc(&f->a32, sizeof(float) * (size_t)std::max<int64_t>(h->nnz, 1)));
+  CGM_CUDA(h, cudaMalloc(&f->d32, sizeof(float) * nv));
+  CGM_CUDA(h, cudaMalloc(&f->rs32, sizeof(float) * nv));
+  CGM_CUDA(h, cudaMalloc(&f->rs64, sizeof(double) * nv));
+  if (!f->mlp_o) CGM_CUDA(h, cudaMalloc(&f->mlp_o, sizeof(float) * (size_t)std::max<int64_t>(f->ntril, 1)));
   f->noffs = (int)offs.size();
   f->ntslots = nts;
   for (int k = 0; k < f->noffs; ++k) f->host_offs[k] = offs[(size_t)k];
@@ -654,6 +685,9 @@ MlpArgs make_args(const cg_handle* h, const float* params) {
   M.tci = f->tci;
   M.tsrc = f->tsrc;
   M.params = params;
+  M.a32 = f->a32;
+  M.d32 = f->d32;
+  M.rs32 = f->rs32;
   for (int k = 0; k < kMaxOffs; ++k) M.offs[k] = k < f->noffs ? f->host_offs[k] : 0;
   M.noffs = f->noffs;
   M.ntslots = f->ntslots;
@@ -700,7 +734,12 @@ cg_status cg_fsai_load(cg_handle* h, const void* weights_bf16, int64_t bytes) {
   if (!f->params32) CGM_CUDA(h, cudaMalloc(&f->params32, sizeof(float) * kNParams));
   CGM_CUDA(h, cudaMemcpyAsync(f->params32, p32.data(), sizeof(float) * kNParams, cudaMemcpyHostToDevice, h->stream));
   const MlpArgs M = make_args(h, f->params32);
-  mlp_forward_kernel<<<mlp_forward_grid(h, f->ntril), kMlpThreads, 0, h->stream>>>(M, nullptr, f->g);
+  const int64_t n = h->n, nt = f->ntril;
+  mlp_inputs_kernel<<<blocks_for(std::max(n, h->nnz)), 256, 0, h->stream>>>(n, h->nnz, h->vals, h->diag, f->a32,
+                                                                            f->d32, f->rs32, f->rs64);
+  mlp_forward_kernel<<<mlp_forward_grid(h, nt), kMlpThreads, 0, h->stream>>>(M, f->mlp_o);
+  g_diag_kernel<<<blocks_for(n), 256, 0, h->stream>>>(n, f->trp, f->rs64, f->mlp_o, M.c0, f->g);
+  g_offdiag_kernel<<<blocks_for(nt), 256, 0, h->stream>>>(nt, f->trow, f->tci, f->rs64, f->mlp_o, f->g);
   CGM_CUDA(h, cudaGetLastError());
   CGM_CUDA(h, cudaStreamSynchronize(h->stream));  // p32 is host memory of this call
   return cgi::fsai_commit(h, 2);
@@ -722,7 +761,6 @@ cg_status cg_fsai_loss_grad(cg_handle* h, const float* params, float* grad, cons
     CGM_CUDA(h, cudaMalloc(&f->work, sizeof(double) * (6 * (size_t)n + 2 * (size_t)nt)));
     CGM_CUDA(h, cudaMalloc(&f->rpart, sizeof(double) * (8192 * 2 + 16)));
     CGM_CUDA(h, cudaMalloc(&f->dout, sizeof(float) * (size_t)nt));
-    CGM_CUDA(h, cudaMalloc(&f->mlp_o, sizeof(float) * (size_t)nt));
     CGM_CUDA(h, cudaMalloc(&f->gpart, sizeof(float) * (size_t)(4 * h->sm_count) * kNParams));
     CGM_CUDA(h, cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)sizeof(SmemB)));
@@ -738,8 +776,11 @@ cg_status cg_fsai_loss_grad(cg_handle* h, const float* params, float* grad, cons
   double* sums = f->rpart + 8192 * 2;  // [0] quad, [1] log-diag, [2] r.r, [3..] residual losses
   const MlpArgs M = make_args(h, params);
   const cudaStream_t st = h->stream;
-  mlp_forward_kernel<<<mg, kMlpThreads, 0, st>>>(M, f->mlp_o, nullptr);
-  g_from_o_kernel<<<blocks_for(nt), 256, 0, st>>>(nt, f->trow, f->tci, h->diag, f->mlp_o, M.c0, gl);
+  mlp_inputs_kernel<<<blocks_for(std::max(n, h->nnz)), 256, 0, st>>>(n, h->nnz, h->vals, h->diag, f->a32, f->d32,
+                                                                     f->rs32, f->rs64);
+  mlp_forward_kernel<<<mg, kMlpThreads, 0, st>>>(M, f->mlp_o);
+  g_diag_kernel<<<blocks_for(n), 256, 0, st>>>(n, f->trp, f->rs64, f->mlp_o, M.c0, gl);
+  g_offdiag_kernel<<<blocks_for(nt), 256, 0, st>>>(nt, f->trow, f->tci, f->rs64, f->mlp_o, gl);
   kaporin_rows_kernel<<<rb, kRed, 0, st>>>(n, h->rowptr, h->colind, h->vals, f->trp, f->tci, gl, gag, f->rpart);
   sum_parts_kernel<<<1, 32, 0, st>>>(f->rpart, (int)rb, 2, sums);
   kaporin_grad_kernel<<<blocks_for(nt), 256, 0, st>>>(n, f->trow, f->tci, f->trp, gl, gag, sums, nt, dgv);
@@ -760,7 +801,7 @@ cg_status cg_fsai_loss_grad(cg_handle* h, const float* params, float* grad, cons
     CGM_CUDA(h, cudaStreamSynchronize(st));  // sums[2..3] are reused by the next vector
     rloss[(size_t)k] = er[0] / er[1];
   }
-  dout_kernel<<<blocks_for(nt), 256, 0, st>>>(nt, f->trow, f->tci, h->diag, f->mlp_o, dgv, M.c0, f->dout);
+  dout_kernel<<<blocks_for(nt), 256, 0, st>>>(nt, f->trow, f->tci, f->rs64, f->mlp_o, dgv, M.c0, f->dout);
   mlp_backward_kernel<<<mg, kMlpThreads, sizeof(SmemB), st>>>(M, f->dout, f->gpart);
   reduce_parts_kernel<<<blocks_for(kNParams), 256, 0, st>>>(f->gpart, (int)mg, grad);
   CGM_CUDA(h, cudaGetLastError());
