@@ -45,6 +45,7 @@ constexpr int kTile = kBlock;        // rows per tile (kWarps slices, one per wa
 constexpr int kGroup = 8;            // tiles per reduction group (2048 rows)
 constexpr int kMaxBatch = CG_BATCH_MAX_SYSTEMS;
 constexpr int kNP = 4;               // partial sums per (group, warp)
+constexpr int kBatchDiag = 8;        // offsets of a system in the diagonal layout, at most
 constexpr int kStRunning = 100;      // status of a system still being solved
 constexpr int kMaxCand = 8;          // autotuner candidates
 constexpr double kRrMarginB = 64.0;  // r.D r is computed while dmin r^.r^ <= 64 stop^2
@@ -63,6 +64,8 @@ struct BatchParams {
   const int32_t* __restrict__ gstart;  // first reduction group of each system
   const int32_t* __restrict__ ngroup;  // reduction groups of each system
   const int32_t* __restrict__ wcost;   // SpMV-phase cost of a row of each system (load balance)
+  const int32_t* __restrict__ sdia;    // offsets of each system in the diagonal layout (0: sliced ELL)
+  const int32_t* __restrict__ sdelta;  // those offsets, kBatchDiag per system
   const double* __restrict__ dmin;     // smallest A_ii of each system
   const int32_t* __restrict__ soff;    // slice offsets (units of 32 entries)
   const int32_t* __restrict__ col;     // global (concatenated) column of each entry
@@ -162,11 +165,42 @@ __device__ __forceinline__ double slice_row(const int32_t* __restrict__ cp, cons
   return acc;
 }
 
+// The system a CTA's current segment belongs to, as row_spmv needs it
+// (shared memory, written by run_phase at the start of each segment).
+struct SegInfo {
+  int nd;              // offsets of the diagonal layout (0: sliced ELL)
+  int lo, hi;          // the system's first and last concatenated rows
+  int delta[kBatchDiag];
+};
+
+// Diagonal layout: column i + delta[m], clamped into the system's own rows
+// (the value is 0 there, and no other system's vector is read).
+template <int W>
+__device__ __forceinline__ double slice_row_dia(const double* __restrict__ vp, const double* __restrict__ v,
+                                                int i, const SegInfo& sg, double acc) {
+  double a[W], x[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) {
+    a[m] = ld_stream(vp + m * 32);
+    x[m] = v[min(max(i + sg.delta[m], sg.lo), sg.hi)];
+  }
+#pragma unroll
+  for (int m = 0; m < W; ++m) acc = fma(a[m], x[m], acc);
+  return acc;
+}
+
 __device__ __forceinline__ double row_spmv(const BatchParams& P, const double* __restrict__ v, int i,
-                                           double acc) {
+                                           double acc, const SegInfo& sg) {
   const int sl = i >> 5, lane = i & 31;
   const int o0 = __ldg(P.soff + sl);
   const int w = __ldg(P.soff + sl + 1) - o0;
+  if (sg.nd) {
+    const double* vp = P.val + (int64_t)o0 * 32 + lane;
+    if (w == 8) return slice_row_dia<8>(vp, v, i, sg, acc);
+    if (w == 4) return slice_row_dia<4>(vp, v, i, sg, acc);
+    for (int m = 0; m < w; ++m) acc = fma(ld_stream(vp + m * 32), v[min(max(i + sg.delta[m], sg.lo), sg.hi)], acc);
+    return acc;
+  }
   const int32_t* cp = P.col + (int64_t)o0 * 32 + lane;
   const double* vp = P.val + (int64_t)o0 * 32 + lane;
   if (w == 8) return slice_row<8>(cp, vp, v, acc);
@@ -223,7 +257,7 @@ __device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int sta
 // (group, warp) order, independent of G, and calls done(sys, sums) in thread 0.
 template <int NV, int ROWS, bool WEIGHTED, class Begin, class Row, class Done>
 __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
-                                          Begin begin, Row row, Done done) {
+                                          SegInfo& seg, Begin begin, Row row, Done done) {
   __shared__ int s_last;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int j1 = (int)((int64_t)T * (g.cta + 1) / g.G);
@@ -240,6 +274,14 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
       j = min(j1, next);
       continue;
     }
+    if (t == 0) {
+      seg.nd = P.sdia[sys];
+      seg.lo = P.tstart[sys] * kTile;
+      seg.hi = seg.lo + P.ntile[sys] * kTile - 1;
+#pragma unroll
+      for (int m = 0; m < kBatchDiag; ++m) seg.delta[m] = P.sdelta[sys * kBatchDiag + m];
+    }
+    __syncthreads();
     const bool sums = begin(sys);
     const int tend = P.tstart[sys] + P.ntile[sys];
     for (int grp = g0; grp < g1; ++grp) {
@@ -300,6 +342,7 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
         if (t == 0) done(sys, sm);
       }
     }
+    __syncthreads();  // every thread is done with seg before the next segment's
     j = min(j1, next);
   }
 }
@@ -311,6 +354,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
   constexpr int kRows = MINB <= 3 ? 4 : (MINB == 4 ? 2 : 1);
   __shared__ int s_pref[kMaxBatch];
   __shared__ int s_scan[kWarps];
+  __shared__ SegInfo s_seg;
   Grid g(P.st, P.timeout_ns, P.skip_seq);
   double* __restrict__ r = P.r;
   double* __restrict__ p = P.p;
@@ -329,10 +373,10 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     if (!alive) break;
     if (T > 0) {
       run_phase<3, kRows, true>(
-          P, s_pref, T, g, [&](int) { return true; },
+          P, s_pref, T, g, s_seg, [&](int) { return true; },
           [&](int i) {
             const double xi = xh[i];
-            const double ri_ax = row_spmv(P, xh, i, JAC ? xi : __ldg(dg + i) * xi);
+            const double ri_ax = row_spmv(P, xh, i, JAC ? xi : __ldg(dg + i) * xi, s_seg);
             const double bi = bh[i];
             const double ri = bi - ri_ax;
             const double d = JAC ? __ldg(dg + i) : 1.0;
@@ -385,10 +429,10 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     T = build_list<true>(P, kMaskAB, seq, s_pref, s_scan, &alive);
     if (T == 0) continue;
     run_phase<1, kRows, true>(
-        P, s_pref, T, g, [&](int) { return true; },
+        P, s_pref, T, g, s_seg, [&](int) { return true; },
         [&](int i) {
           const double pi = p[i];
-          const double qi = row_spmv(P, p, i, JAC ? pi : __ldg(dg + i) * pi);
+          const double qi = row_spmv(P, p, i, JAC ? pi : __ldg(dg + i) * pi, s_seg);
           return [=](double* acc) {
             q[i] = qi;
             acc[0] = fma(pi, qi, acc[0]);
@@ -411,7 +455,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     ++seq;
     T = build_list<false>(P, kMaskAB, seq, s_pref, s_scan, &alive);
     run_phase<2, kRows, false>(
-        P, s_pref, T, g,
+        P, s_pref, T, g, s_seg,
         [&](int sys) {
           c_alpha = P.alpha[sys];
           c_flag = JAC && P.wrr[sys];
@@ -456,7 +500,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     ++seq;
     T = build_list<false>(P, kMaskC, seq, s_pref, s_scan, &alive);
     run_phase<1, kRows, false>(
-        P, s_pref, T, g,
+        P, s_pref, T, g, s_seg,
         [&](int sys) {
           const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
           c_alpha = P.alpha[sys];
@@ -573,6 +617,41 @@ __global__ void batch_fill_kernel(int64_t n, int64_t npad, int64_t r0, int64_t s
   }
 }
 
+// The diagonal layout of one system (thread per padded row): slot m of row i
+// holds the sum of the row's entries in column i + delta[m] (0 where there is
+// none, and on padding rows), scaled as batch_fill_kernel does.
+struct BatchDelta {
+  int nd;
+  int d[kBatchDiag];
+};
+template <bool SCALE>
+__global__ void batch_fill_dia_kernel(int64_t n, int64_t npad, int64_t sl0, const int32_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ colind, const double* __restrict__ vals,
+                                      const double* __restrict__ ldisq, const int32_t* __restrict__ soff,
+                                      BatchDelta bd, double* val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = (int64_t)soff[sl0 + (i >> 5)] * 32 + (i & 31);
+    double v[kBatchDiag];
+#pragma unroll
+    for (int m = 0; m < kBatchDiag; ++m) v[m] = 0.0;
+    if (i < n) {
+      const double si = SCALE ? ldisq[i] : 1.0;
+      for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+        const int c = colind[k];
+        if ((int64_t)c == i) continue;
+        const int o = (int)(c - i);
+#pragma unroll
+        for (int m = 0; m < kBatchDiag; ++m)
+          if (m < bd.nd && bd.d[m] == o) v[m] += SCALE ? vals[k] * (si * ldisq[c]) : vals[k];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < kBatchDiag; ++m)
+      if (m < bd.nd) val[base + (int64_t)m * 32] = v[m];
+  }
+}
+
 // Diagonal vectors of one system at its rows of the concatenation: A_ii,
 // sqrt(A_ii), 1/sqrt(A_ii) (1 on padding rows and where A_ii <= 0, which
 // only the unpreconditioned solve accepts).
@@ -620,6 +699,8 @@ struct BatchData {
   int64_t entries = 0;             // slice entries (multiple of 32)
   int32_t *d_tstart = nullptr, *d_ntile = nullptr, *soff = nullptr, *col = nullptr;
   int32_t *d_gstart = nullptr, *d_ngroup = nullptr, *d_wcost = nullptr;
+  std::vector<int32_t> sdia, sdelta;  // diagonal layout of each system and its offsets (kBatchDiag each)
+  int32_t *d_sdia = nullptr, *d_sdelta = nullptr;
   int ngroups = 0;                 // reduction groups in all
   double* d_dmin = nullptr;        // smallest A_ii per system
   int64_t *d_n = nullptr, *d_r0 = nullptr;
@@ -664,7 +745,8 @@ void cgi::batch_free(BatchData* b) {
                  b->val[1],   b->dg,      b->dsq,      b->disq,   b->r,    b->p,      b->q,
                  b->xh,       b->bh,      b->rho,      b->rr,     b->bb,   b->alpha,  b->beta,
                  b->relres,   b->k,       b->restarts, b->status, b->zero, b->sstate, b->cnt,
-                 b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr, b->d_wcost};
+                 b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr, b->d_wcost,
+                 b->d_sdia,   b->d_sdelta};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
@@ -701,6 +783,18 @@ cg_status ensure_batch_vals(cg_handle* h, bool jac) {
     const int64_t r0 = B->r0[(size_t)s];
     const int64_t sl0 = (int64_t)B->tstart[(size_t)s] * kWarps;
     int32_t* col = write_col ? B->col : nullptr;
+    if (B->sdia[(size_t)s]) {
+      BatchDelta bd{};
+      bd.nd = B->sdia[(size_t)s];
+      for (int m = 0; m < kBatchDiag; ++m) bd.d[m] = B->sdelta[(size_t)s * kBatchDiag + m];
+      if (jac)
+        batch_fill_dia_kernel<true><<<blocks_for(npad), 256, 0, h->stream>>>(
+            hs->n, npad, sl0, hs->rowptr, hs->colind, hs->vals, B->disq + r0, B->soff, bd, B->val[jac]);
+      else
+        batch_fill_dia_kernel<false><<<blocks_for(npad), 256, 0, h->stream>>>(
+            hs->n, npad, sl0, hs->rowptr, hs->colind, hs->vals, B->disq + r0, B->soff, bd, B->val[jac]);
+      continue;
+    }
     if (jac)
       batch_fill_kernel<true><<<blocks_for(npad), 256, 0, h->stream>>>(
           hs->n, npad, r0, sl0, hs->rowptr, hs->colind, hs->vals, B->disq + r0, B->soff, col, B->val[jac]);
@@ -722,6 +816,8 @@ BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
   P.gstart = B->d_gstart;
   P.ngroup = B->d_ngroup;
   P.wcost = B->d_wcost;
+  P.sdia = B->d_sdia;
+  P.sdelta = B->d_sdelta;
   P.dmin = B->d_dmin;
   P.wrr = B->wrr;
   P.soff = B->soff;
@@ -952,11 +1048,29 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
   B->nslices = (int)(tiles * kWarps);
   h->n = rows;
   h->nnz = nnz;
-  // slice widths: the longest off-diagonal row of each 32-row slice
+  // layout of each system: diagonal (stencils: every off-diagonal entry on one
+  // of at most kBatchDiag offsets; a slot per offset, no column array read)
+  // or sliced ELL; slice widths: the offsets, or the longest off-diagonal row
+  // of each 32-row slice
+  B->sdia.assign((size_t)nsys, 0);
+  B->sdelta.assign((size_t)nsys * kBatchDiag, 0);
   std::vector<int32_t> soff((size_t)B->nslices + 1, 0);
   int64_t off = 0;
   for (int s = 0; s < nsys; ++s) {
-    const cg_handle* hs = B->sys[(size_t)s];
+    cg_handle* hs = B->sys[(size_t)s];
+    const cg_status so = cgi::ensure_offsets(hs);
+    if (so != CG_OK) return bail(bfail(h, so, "cg_batch_create: system " + std::to_string(s) + ": " + hs->err));
+    if (hs->noffs_all >= 1 && hs->noffs_all <= kBatchDiag) {
+      B->sdia[(size_t)s] = hs->noffs_all;
+      for (int m = 0; m < hs->noffs_all; ++m) B->sdelta[(size_t)s * kBatchDiag + m] = hs->offs_all[m];
+      const int nsl = B->ntile[(size_t)s] * kWarps;
+      for (int j = 0; j < nsl; ++j) {
+        off += hs->noffs_all;
+        soff[(size_t)B->tstart[(size_t)s] * kWarps + j + 1] = (int32_t)off;
+      }
+      if (off * 32 >= INT32_MAX) return bail(bfail(h, CG_ERR_INVALID, "cg_batch_create: matrices too large"));
+      continue;
+    }
     std::vector<int32_t> nd((size_t)hs->n);
     CGB_CREATE(cudaMemcpy(nd.data(), hs->ndiag, sizeof(int32_t) * (size_t)hs->n, cudaMemcpyDeviceToHost));
     const std::vector<int32_t>& rp = hs->host_rowptr;
@@ -975,7 +1089,8 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
   const size_t nv = (size_t)rows, ns = (size_t)nsys;
   CGB_CREATE(cudaMalloc(&B->soff, sizeof(int32_t) * soff.size()));
   CGB_CREATE(cudaMemcpy(B->soff, soff.data(), sizeof(int32_t) * soff.size(), cudaMemcpyHostToDevice));
-  CGB_CREATE(cudaMalloc(&B->col, sizeof(int32_t) * (size_t)std::max<int64_t>(B->entries, 32)));
+  const bool any_ell = std::count(B->sdia.begin(), B->sdia.end(), 0) > 0;
+  CGB_CREATE(cudaMalloc(&B->col, sizeof(int32_t) * (size_t)std::max<int64_t>(any_ell ? B->entries : 0, 32)));
   CGB_CREATE(cudaMalloc(&B->d_tstart, sizeof(int32_t) * ns));
   CGB_CREATE(cudaMalloc(&B->d_ntile, sizeof(int32_t) * ns));
   CGB_CREATE(cudaMalloc(&B->d_n, sizeof(int64_t) * ns));
@@ -1004,7 +1119,8 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
       const int64_t sl0 = (int64_t)B->tstart[s] * kWarps, sl1 = sl0 + (int64_t)B->ntile[s] * kWarps;
       const int64_t wsum = soff[(size_t)sl1] - soff[(size_t)sl0];
       const int64_t wavg = (wsum + (sl1 - sl0) - 1) / std::max<int64_t>(sl1 - sl0, 1);
-      wc[s] = (int32_t)std::max<int64_t>(1, (wavg + 3) / 2);
+      // diagonal layout: ~8 bytes per entry (no column), else ~12
+      wc[s] = (int32_t)std::max<int64_t>(1, B->sdia[s] ? (wavg + 5) / 3 : (wavg + 3) / 2);
     }
     B->ngroups = groups;
     CGB_CREATE(cudaMalloc(&B->d_gstart, sizeof(int32_t) * ns));
@@ -1015,6 +1131,11 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
     CGB_CREATE(cudaMemcpy(B->d_dmin, dmin.data(), sizeof(double) * ns, cudaMemcpyHostToDevice));
     CGB_CREATE(cudaMalloc(&B->d_wcost, sizeof(int32_t) * ns));
     CGB_CREATE(cudaMemcpy(B->d_wcost, wc.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+    CGB_CREATE(cudaMalloc(&B->d_sdia, sizeof(int32_t) * ns));
+    CGB_CREATE(cudaMemcpy(B->d_sdia, B->sdia.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice));
+    CGB_CREATE(cudaMalloc(&B->d_sdelta, sizeof(int32_t) * ns * kBatchDiag));
+    CGB_CREATE(cudaMemcpy(B->d_sdelta, B->sdelta.data(), sizeof(int32_t) * ns * kBatchDiag,
+                          cudaMemcpyHostToDevice));
   }
   CGB_CREATE(cudaMalloc(&B->sstate, sizeof(unsigned long long) * ns));
   CGB_CREATE(cudaMalloc(&B->cnt, sizeof(unsigned) * ns));
