@@ -226,6 +226,24 @@ def time_oracle_sample(A, b, precond, precision, tol, budget_s):
         m = max(m * 2, int(m * (budget_s / 3) / max(dt, 1e-3)))
 
 
+def max_over_ranks(x, world, device=None):
+    """x from every rank reduced to its maximum (the job's time is its slowest
+    rank's); x itself with one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, t_max_s):
+    """Whole-job units per second: every rank processes `steps` units in the
+    slowest rank's time."""
+    return world * steps / t_max_s
+
+
 def run_reference(args):
     """The oracle as the reference arm: rank 0 times bounded samples on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -395,13 +413,9 @@ def run_batch(args, world, rank, dev, torch, cg):
             infos.append(step())
         ev1.record()
         barrier()
-    t_max = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([t_max], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_per_step = t_max / args.steps
-    value = world * args.steps / (t_max / 1e3)
+    value = job_throughput(world, args.steps, t_max / 1e3)
     its = infos[0][0]
     relres = max(max(r) for _, r, _ in infos)
     kern_ms = sum(inf["kernel_ms"] for _, _, inf in infos)
@@ -431,12 +445,8 @@ def run_batch(args, world, rank, dev, torch, cg):
             xh.copy_(x_flat, non_blocking=True)
             torch.cuda.current_stream().synchronize()
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * args.steps / e2e_s, "unit": "batches/s",
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_throughput(world, args.steps, e2e_s), "unit": "batches/s",
                "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot}
 
     # the same systems solved one after another by cg_solve (plain FP64 Jacobi-PCG,
@@ -612,13 +622,9 @@ def main():
         ev1.record()
         barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    t_max = elapsed_ms
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(elapsed_ms, world, dev)
     ms_per_step = t_max / args.steps
-    value = world * args.steps / (t_max / 1e3)
+    value = job_throughput(world, args.steps, t_max / 1e3)
 
     iters = [i for i, _, _ in infos]
     relres = max(r for _, r, _ in infos)
@@ -650,12 +656,8 @@ def main():
             if st != cg.CG_OK:
                 raise RuntimeError(f"host solve failed: {cg.status_string(st)}")
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s",
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_throughput(world, args.steps, e2e_s), "unit": "solves/s",
                "h2d_bytes_per_step": 16 * A.n, "d2h_bytes_per_step": 8 * A.n}
 
     # the caller-CSR SpMV (cg_spmv) against cuSPARSE through torch's CSR tensor, the

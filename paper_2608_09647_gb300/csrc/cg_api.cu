@@ -525,7 +525,7 @@ const void* spmv_kernel_w(int uw) {
     case 4: return (const void*)g_spmv<T, JAC, 4, DIA>;
     case 6: return (const void*)g_spmv<T, JAC, 6, DIA>;
     case 8: return (const void*)g_spmv<T, JAC, 8, DIA>;
-    case 26: return DIA ? (const void*)g_spmv<T, JAC, 26, true> : (const void*)g_spmv<T, JAC, 0, false>;
+    case 26: return DIA ? (const void*)g_spmv_wide<T, JAC, 26, true> : (const void*)g_spmv<T, JAC, 0, false>;
     default: return (const void*)g_spmv<T, JAC, 0, false>;
   }
 }

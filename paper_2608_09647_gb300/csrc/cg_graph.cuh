@@ -121,7 +121,7 @@ __global__ void g_start64(GArgs a) {
 // forms alpha = rho / p.q, the breakdown / non-finite test and whether the r
 // update must form r.D r, once for the next kernels.
 template <typename T, bool JAC, int W, bool DIA>
-__global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
+__device__ __forceinline__ void spmv_body(const GArgs& a) {
   const SolveParams& P = a.P;
   GState* gs = a.gs;
   if (gs->status != kRunning) return;
@@ -139,6 +139,19 @@ __global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
     gs->want_rr = JAC && rr_wanted(S, rho, gs->stop_abs * gs->stop_abs);
     if (st) gs->status = st;
   }
+}
+
+template <typename T, bool JAC, int W, bool DIA>
+__global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
+  spmv_body<T, JAC, W, DIA>(a);
+}
+
+// Wide uniform slices (W > 16) with a budget of 4 resident CTAs per SM: a
+// 26-diagonal row keeps half its loads in flight only with ~64 registers
+// (left to itself the compiler chose 48 and the loop waited on memory).
+template <typename T, bool JAC, int W, bool DIA>
+__global__ void __launch_bounds__(kBlock, 4) g_spmv_wide(GArgs a) {
+  spmv_body<T, JAC, W, DIA>(a);
 }
 
 // The stopping decision for r.r = rr after iteration k1: fl = done | conv << 1.

@@ -293,3 +293,29 @@ def test_sudden_convergence_takes_the_exact_stopping_test():
         assert res[1][s] == ref.iters, (A.name, res[1][s], ref.iters)
     assert res[1][0] == 1 and res[1][1] == 2
     check_against_oracle(systems, bs, res, 1e-10, 100, cg.CG_PRECOND_JACOBI)
+
+
+def test_a_breakdown_in_the_diagonal_layout_stays_in_its_system():
+    """Stencil members use the diagonal layout, whose gathers are clamped into the
+    member's own rows.  An indefinite 5-point member (the Laplacian shifted by -3 I)
+    that breaks down between healthy 5- and 9-point members gets the oracle's status,
+    and the healthy members' results are bit for bit those of a batch without it."""
+    good = [gen.lap2d(24, 5, 1.0), gen.lap2d(31, 9, 0.05), gen.lap2d(17, 5, 0.2)]
+    L = gen.lap2d(20, 5, 1.0)
+    vals = L.vals.copy()
+    rows = np.repeat(np.arange(L.n), np.diff(L.rowptr))
+    vals[L.colind == rows] -= 3.0
+    bad = gen.CSR(L.n, L.rowptr, L.colind, vals, "shifted_lap2d")
+    bs_good = rhs(good, 40)
+    b_bad = oracle.spmv(bad, gen.xstar(bad.n, 7))
+    maxit = 2000
+    res_mixed = Batch([good[0], bad, good[1], good[2]]).solve(
+        [bs_good[0], b_bad, bs_good[1], bs_good[2]], 1e-9, maxit, cg.CG_PRECOND_NONE)
+    res_good = Batch(good).solve(bs_good, 1e-9, maxit, cg.CG_PRECOND_NONE)
+    ref_bad = oracle.pcg(bad, b_bad, tol=1e-9, maxit=maxit, precond=0)
+    assert ref_bad.status in (cg.CG_ERR_BREAKDOWN, cg.CG_NOT_CONVERGED)
+    assert res_mixed[4][1]["status"] == ref_bad.status
+    for k, s in enumerate((0, 2, 3)):
+        assert res_mixed[4][s]["status"] == cg.CG_OK
+        assert res_mixed[1][s] == res_good[1][k]
+        assert np.array_equal(res_mixed[3][s], res_good[3][k])
