@@ -12,8 +12,7 @@ constexpr int kWarps = kBlock / 32;
 
 // Device status words of one persistent launch (zeroed before each launch).
 struct DevState {
-  unsigned bar_count;    // arrivals at the current grid barrier
-  unsigned bar_gen;      // barrier generation, bumped by the last arriver
+  unsigned long long bar_arrivals;  // grid-barrier arrivals of this launch (only grows)
   int abort;             // set by any CTA that gave up; every CTA then leaves
   int status;            // cg_status of the solve
   int iters;
@@ -31,26 +30,21 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
   return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Add without a returned value, ordered after this thread's earlier writes.
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed_s32(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
 }
 
 // Grid-wide barrier for a co-resident (cooperatively launched) grid.  Every
@@ -69,28 +63,27 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks, uin
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    // barrier seq of this launch is complete when the arrivals reach
+    // seq * nblocks: each CTA adds 1 with release order (its partials are
+    // visible first) and waits for the total with acquire loads; there is no
+    // last arriver to wait for and no reset
     int ok = 1;
-    const unsigned gen = ld_acquire_u32(&st->bar_gen);
+    const unsigned long long target = (unsigned long long)seq * nblocks;
     const bool skip = (skip_seq != 0u && seq == skip_seq && blockIdx.x == 0);
-    unsigned prev = skip ? 0u : atom_add_acq_rel_u32(&st->bar_count, 1u);
-    if (!skip && prev == nblocks - 1) {
-      atomicExch(&st->bar_count, 0u);
-      st_release_u32(&st->bar_gen, gen + 1u);
-    } else {
-      const uint64_t t0 = global_timer_ns();
-      unsigned spins = 0;
-      while (ld_acquire_u32(&st->bar_gen) == gen) {
-        if (ld_relaxed_s32(&st->abort) != 0) { ok = 0; break; }
-        if (((++spins) & 15u) == 0u && global_timer_ns() - t0 > timeout_ns) {
-          if (atomicCAS(&st->abort, 0, 1) == 0) {
-            st->err_cta = (int)blockIdx.x;
-            st->err_barrier = (int)seq;
-          }
-          ok = 0;
-          break;
+    if (!skip) red_release_add_u64(&st->bar_arrivals, 1ull);
+    const uint64_t t0 = global_timer_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u64(&st->bar_arrivals) < target) {
+      if (ld_relaxed_s32(&st->abort) != 0) { ok = 0; break; }
+      if (((++spins) & 15u) == 0u && global_timer_ns() - t0 > timeout_ns) {
+        if (atomicCAS(&st->abort, 0, 1) == 0) {
+          st->err_cta = (int)blockIdx.x;
+          st->err_barrier = (int)seq;
         }
-        __nanosleep(32);
+        ok = 0;
+        break;
       }
+      __nanosleep(32);
     }
     s_ok = ok;
   }
