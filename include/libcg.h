@@ -74,7 +74,7 @@ typedef enum {
                                      (1-based; 0 = off), so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
   CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: graph from 2^18 rows;
-                                     fp32 FSAI refinement: graph from 2^20 rows; else persistent),
+                                     fp32 FSAI refinement: graph from 2^21 rows; else persistent),
                                      1 one persistent cooperative launch, 2 CUDA graph with a
                                      device-side WHILE node (nested WHILE nodes for fp32
                                      refinement), 3 graphs of 8 unrolled iterations relaunched by

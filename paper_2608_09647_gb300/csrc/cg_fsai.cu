@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
 // last CTA of a reducing kernel sums its fixed-order partials once and stores
 // the scalars for the next kernel, so no CTA waits on a reduction at its start.
 constexpr int kSlotT = kSlotRes + 3;  // t.t of the start pass
-constexpr int64_t kFsaiGraphMinRows = 1 << 20;  // auto loop form: graph from here (fp32 inner)
+constexpr int64_t kFsaiGraphMinRows = 1 << 21;  // auto loop form: graph from here (fp32 inner)
 constexpr int kFsaiUnroll = 8;                   // inner iterations per graph of the unrolled form
 constexpr int kFsaiOuterKernels = 6;             // kernels of one outer step
 // Residency of the graph form's phase kernels: 4 CTAs (32 warps) per SM keeps

@@ -195,7 +195,7 @@ def test_fsai_rejects_unsuitable_matrices():
 def test_fsai_refinement_loop_forms_match_oracle(name, make, mode, precision):
     """The loop forms of the fp32 FSAI refinement (the persistent kernel, the graph of
     phase kernels under WHILE nodes, and the same kernels in unrolled graphs relaunched by
-    the host) against the oracle; the automatic choice is the graph form from 2^20 rows."""
+    the host) against the oracle; the automatic choice is the graph form from 2^21 rows."""
     A = make()
     g = fsai.classic(A)
     b = oracle.spmv(A, gen.xstar(A.n, 9))
@@ -217,12 +217,12 @@ def test_fsai_refinement_loop_forms_match_oracle(name, make, mode, precision):
     xs = x.cpu().numpy()
     assert oracle.true_relres(A, b, xs) <= tol * (1 + 1e-6)
     assert abs(rel - oracle.true_relres(A, b, xs)) <= 1e-6 * rel + 1e-15
-    # auto picks the graph form from 2^20 rows
+    # auto picks the graph form from 2^21 rows
     h2 = handle(A)
     assert cg.cg_fsai_set_factor(h2, torch.from_numpy(g).cuda()) == cg.CG_OK
     x2 = torch.zeros_like(bd)
     assert cg.cg_solve(h2, bd, x2, tol, 100000, cg.CG_PRECOND_FSAI, precision)[0] == cg.CG_OK
-    assert cg.cg_get_solve_info(h2)["loop_form"] == (2 if A.n >= 1 << 20 else 1)
+    assert cg.cg_get_solve_info(h2)["loop_form"] == (2 if A.n >= 1 << 21 else 1)
 
 
 @pytest.mark.parametrize("precision", [cg.CG_PREC_FP32_IR, cg.CG_PREC_FP32_RU], ids=["fp32_ir", "fp32_ru"])
