@@ -108,14 +108,17 @@ def kernel_source_sha(kind="single"):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, kind="single"):
+def ncu_traffic(workload, kind="single", loop_form=None):
     """DRAM bytes of the timed kernels from the committed ncu summary, if it was taken
-    from the current kernel sources (else None)."""
+    from the current kernel sources and, where it names one, in the loop form that
+    ran (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(workload)
     if not d or d.get("kernel_sha") != kernel_source_sha(kind):
+        return None
+    if loop_form is not None and d.get("loop_form", loop_form) != loop_form:
         return None
     return d
 
@@ -637,7 +640,7 @@ def main():
     bpi = kern_bytes / max(1, sum(iters))  # the library's model for this preconditioner
     form = {1: "persistent", 2: "graph", 3: "unrolled"}.get(infos[0][2]["loop_form"], "?")
     launches = sum(inf["kernel_launches"] for _, _, inf in infos)
-    tr = ncu_traffic(args.workload, "fsai" if precond_s.startswith("fsai") else "single")
+    tr = ncu_traffic(args.workload, "fsai" if precond_s.startswith("fsai") else "single", form)
     traffic = None
     if tr:
         traffic = int(tr["dram_bytes_per_iter"] * statistics.mean(iters))
