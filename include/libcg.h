@@ -95,8 +95,9 @@ typedef struct {
   int64_t bytes_moved;    /* modelled HBM bytes of the loop: iters x (12 nnz + 4(n+1) + 104 n)
                              (Jacobi; 88 n without; fp32 refinement 8 nnz + 4(n+1) + 52/44 n) */
   int64_t kernel_bytes_per_iter; /* bytes one iteration of this library's loop must move:
-                             its SELL-32 off-diagonal slices (12 B/entry fp64, 8 B fp32) plus
-                             88 n (Jacobi) / 80 n bytes of vectors (fp64; half that in fp32) */
+                             its off-diagonal slices (fp64: 8 B/entry in the diagonal layout,
+                             12 B with a column array; fp32: 4 / 8 B) plus 88 n (Jacobi) /
+                             80 n bytes of vectors (fp64; half that in fp32) */
   double phase_ms[6];     /* with CG_OPT_PHASE_TIMERS: CTA 0 time in the SpMV, r-update and
                              x/p-update phases, each followed by its grid-barrier wait */
   int32_t loop_form;      /* CG_OPT_LOOP_MODE form that ran: 1 persistent, 2 graph WHILE, 3 unrolled */
@@ -174,7 +175,9 @@ const char* cg_status_string(int32_t status);
  * vals[s] (host arrays of DEVICE pointers) its CSR, validated as in
  * cg_create and borrowed until cg_destroy.  The handle concatenates the
  * systems into one block-diagonal matrix in 256-row tiles (so it holds a
- * second copy of all matrices) and serves cg_solve_batch,
+ * second copy of all matrices: a system whose off-diagonal entries lie on at
+ * most 8 offsets by diagonal, the others as sliced ELL) and serves
+ * cg_solve_batch,
  * cg_batch_get_system, cg_batch_get_tuning, cg_set_stream, cg_set_option,
  * cg_get_solve_info, cg_last_error and cg_destroy; the single-system calls
  * return CG_ERR_INVALID on it.  On failure *out = NULL and
@@ -228,7 +231,9 @@ cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* coun
  * factor belongs to the handle and is used by cg_solve(precond =
  * CG_PRECOND_FSAI) in both precisions (fp32 refinement: G rounded to fp32);
  * each iteration applies it as t = G r, z = G^T t (three grid barriers per
- * iteration, as with Jacobi).
+ * iteration, as with Jacobi).  The pattern of G and G^T is built once per
+ * handle, on the device when the CSR's structure is symmetric (else on the
+ * host); the factor calls synchronise the handle's stream.
  */
 
 /* Classic FSAI: per row i, solve A[P_i,P_i] y = e_i on the row's pattern P_i
