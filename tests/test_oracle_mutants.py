@@ -97,3 +97,53 @@ def test_mutant_is_caught(tmp_path, name):
     assert body.count(old) == 1, f"mutation site for {name} not unique"
     text = text[:a] + body.replace(old, new) + text[b:]
     assert not _pins_pass(_build_variant(tmp_path, text, name))
+
+
+# Mistakes in the FSAI application z = G^T (G r) (fsai_apply, the fp64 one): the second
+# factor applied untransposed (z = G G r, a transposed operand) or dropped (z = G r).
+FSAI_MUTANTS = {
+    "fsai_second_factor_untransposed": (
+        "    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) z[gci[k]] += gval[k] * t[i];",
+        "    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) z[i] += gval[k] * t[gci[k]];"),
+    "fsai_second_factor_dropped": (
+        "    for (int64_t k = grp[i]; k < grp[i + 1]; ++k) z[gci[k]] += gval[k] * t[i];",
+        "    z[i] = t[i];"),
+}
+
+
+def _fsai_pins_pass(lib) -> bool:
+    """The dense-pattern pin: classic FSAI of a dense SPD matrix (numpy, independent of
+    the C code) is the inverse Cholesky factor, so FSAI-PCG converges in one iteration."""
+    from oracle import fsai
+    saved = fsai._load
+    fsai._load = lambda: lib
+    try:
+        M = random_spd(12, 100.0, 3)
+        A = csr_from_scipy(M)
+        g = fsai.classic(A)
+        b = M @ np.ones(12)
+        s = fsai.pcg(A, g, b, tol=1e-12, maxit=50)
+        return s.status == oracle.OK and s.iters == 1 and np.allclose(s.x, np.ones(12), atol=1e-9)
+    finally:
+        fsai._load = saved
+
+
+def _fsai_apply_body(text):
+    a = text.index("static void fsai_apply(")
+    b = text.index("\n}\n", a) + 3
+    return a, b
+
+
+def test_unmutated_copy_passes_the_fsai_pin(tmp_path):
+    assert _fsai_pins_pass(_build_variant(tmp_path, open(oracle._SRC).read(), "clean_fsai"))
+
+
+@pytest.mark.parametrize("name", sorted(FSAI_MUTANTS))
+def test_fsai_mutant_is_caught(tmp_path, name):
+    old, new = FSAI_MUTANTS[name]
+    text = open(oracle._SRC).read()
+    a, b = _fsai_apply_body(text)
+    body = text[a:b]
+    assert body.count(old) == 1, f"mutation site for {name} not unique"
+    text = text[:a] + body.replace(old, new) + text[b:]
+    assert not _fsai_pins_pass(_build_variant(tmp_path, text, name))
