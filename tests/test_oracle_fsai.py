@@ -173,3 +173,28 @@ def test_fsai_refinement_reaches_tolerance():
     s = fsai.pcg_ir(A, g, b, tol=1e-10, tol_in=1e-4)
     assert s.status == oracle.OK and s.relres_true <= 1e-10
     assert oracle.true_relres(A, b, s.x) <= 1e-10
+
+
+def test_mlp_forward_by_hand():
+    """A network small enough to evaluate on paper (F4): every weight a bf16-exact
+    number.  Unit 0 of layer 1 reads feature 3 (x2), unit 1 reads feature 7 (x -1, bias
+    0.5); unit 0 of layer 2 is h1_0 + 3 h1_1 - 0.25 (an off-diagonal W2 entry, so a
+    transposed W2 reads the wrong unit), unit 5 is -h1_1 (never positive: only the
+    second ReLU keeps it out); o = 0.5 h2_0 + 4 h2_5 + 0.125."""
+    W1 = np.zeros((fsai.N_HID, fsai.N_IN)); b1 = np.zeros(fsai.N_HID)
+    W2 = np.zeros((fsai.N_HID, fsai.N_HID)); b2 = np.zeros(fsai.N_HID)
+    W3 = np.zeros(fsai.N_HID)
+    W1[0, 3], W1[1, 7], b1[1] = 2.0, -1.0, 0.5
+    W2[0, 0], W2[0, 1], b2[0], W2[5, 1] = 1.0, 3.0, -0.25, -1.0
+    W3[0], W3[5] = 0.5, 4.0
+    p = np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, [0.125]])
+    assert all(np.array_equal(u, v) for u, v in zip(fsai.unpack(p), (W1, b1, W2, b2, W3, 0.125)))
+    F = np.zeros((3, fsai.N_IN))
+    F[0, 3], F[0, 7] = 1.5, 0.25      # h1 = (3, 0.25); z2_0 = 3.5; z2_5 = -0.25
+    F[1, 3], F[1, 7] = -1.0, 2.0      # h1 = (0, 0): both first-layer units cut by the ReLU
+    F[2, 3], F[2, 7] = 0.25, -0.5     # h1 = (0.5, 1.0); z2_0 = 3.25; z2_5 = -1
+    F[:, 0] = 7.0                     # a feature no unit reads
+    want = np.array([0.5 * 3.5 + 0.125, 0.125, 0.5 * 3.25 + 0.125])
+    for rnd in (True, False):
+        o, _ = fsai.mlp_forward(p, F, round_bf16=rnd)
+        assert np.array_equal(o, want), (rnd, o, want)
