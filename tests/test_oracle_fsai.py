@@ -198,3 +198,22 @@ def test_mlp_forward_by_hand():
     for rnd in (True, False):
         o, _ = fsai.mlp_forward(p, F, round_bf16=rnd)
         assert np.array_equal(o, want), (rnd, o, want)
+
+
+def test_loss_terms_in_closed_form():
+    """The Jacobi factor G = D^-1/2 makes every g_i^T A g_i = 1, so the Kaporin term is
+    the mean of log A_ii (F6); the exact inverse factor of a dense SPD matrix makes
+    G^T G = A^-1, so A G^T G r = r and the residual term vanishes."""
+    A = gen.q1aniso(9, 1.5, 0.4, 0.05, 2)
+    d = A.to_scipy().diagonal()
+    trp, tci, _ = fsai.tril(A)
+    rows = np.repeat(np.arange(A.n), np.diff(trp))
+    gj = np.where(tci == rows, 1.0 / np.sqrt(d[rows]), 0.0)
+    L, _ = fsai.kaporin(A, gj)
+    assert abs(L - np.mean(np.log(d))) <= 1e-13 * abs(np.mean(np.log(d))) + 1e-14
+    M = random_spd(10, 4)
+    Ad = dense_csr(M, "dense10")
+    g = fsai.classic(Ad)
+    R = np.random.default_rng(3).standard_normal((3, 10))
+    LR, _ = fsai.residual_term(Ad, g, R)
+    assert LR <= 1e-24
