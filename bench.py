@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -100,11 +101,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """Source text without its comments and blank lines: editing a comment does not
+    change the kernels a traffic figure was measured on."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_sha(kind="single"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2608_09647_gb300", "csrc")
     for f in KERNEL_SOURCES[kind]:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -5,11 +5,14 @@
 // the schedule is shared.
 //
 // Layout.  The systems are concatenated into one block-diagonal loop matrix
-// in SELL-32 form (32-row slices stored column-major, the diagonal held apart
-// as a vector; with Jacobi the matrix is the scaled D^-1/2 A D^-1/2 of unit
-// diagonal).  Every system is padded to whole 256-row tiles (padding rows are
-// identity rows with b = x = 0), so no tile spans two systems.  One tile is
-// one CTA's unit of work: 8 warps, one slice each, lane = row.
+// of 32-row slices stored column-major (the diagonal held apart as a vector;
+// with Jacobi the matrix is the scaled D^-1/2 A D^-1/2 of unit diagonal): a
+// system whose off-diagonal entries lie on at most kBatchDiag offsets is
+// stored by diagonal (a slot per offset, the gather index clamped into the
+// system's own rows, no column array), the others as SELL-32 with global
+// columns.  Every system is padded to whole 256-row tiles (padding rows are
+// identity rows with b = x = 0), so no tile spans two systems; 8 tiles form a
+// 2048-row reduction group.
 //
 // Schedule.  Rounds of four phases separated by bounded grid barriers:
 //   R  r = b - A x for the systems that need it (start, after their loop,
@@ -18,15 +21,16 @@
 //   B  r -= alpha q, r.r and r.D r, beta and the recursive stopping test;
 //   C  x += alpha p, p = r + beta p.
 // A system's stage says which phases it takes part in: 0 residual pending,
-// 1 iterating, 2 done, 3 last x update pending (C, then R).  At the start of
-// each phase every CTA scans the stages, forms the prefix sum of the tiles of
-// the systems in that phase in shared memory and deals those tiles
-// round-robin, so finished systems cost nothing.  A system's sums are formed
-// by the CTA that completes its last tile of the phase, over the tiles'
-// partials in tile order, so they do not depend on the schedule.  A stage
-// change made during a phase carries that phase's number; a CTA that reads
-// the word in the same phase takes the stage from before the change, so all
-// CTAs deal the same tile list.
+// 1 iterating, 2 done, 3 last x update pending (C, then R), 4 r.D r pending.
+// At the start of each phase every CTA scans the stages, forms the prefix sum
+// of the work of the systems in that phase in shared memory (a unit per
+// group, or in the SpMV phases R and A a row-cost weight per group) and takes
+// a contiguous chunk of it, so finished systems cost nothing and a chunk
+// spans few systems.  A system's sums are formed by the CTA that completes
+// its last group of the phase, over (group, warp) partials in order, so they
+// do not depend on the schedule.  A stage change made during a phase carries
+// that phase's number; a CTA that reads the word in the same phase takes the
+// stage from before the change, so all CTAs deal the same list.
 #include <cuda_runtime.h>
 
 #include <algorithm>

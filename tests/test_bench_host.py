@@ -38,3 +38,18 @@ def test_committed_traffic_figures_name_their_sources():
     for name, e in d.items():
         assert name in bench.WORKLOADS
         assert e["sources"] and e["how"] and len(e["kernel_sha"]) == 16
+
+
+def test_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    import shutil
+    src = bench.os.path.join(bench.ROOT, "paper_2608_09647_gb300", "csrc")
+    dst = tmp_path / "paper_2608_09647_gb300" / "csrc"
+    shutil.copytree(src, dst)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    before = bench.kernel_source_sha("batch")
+    f = dst / "cg_batch.cu"
+    text = f.read_text()
+    f.write_text("// a new comment line\n" + text.replace("// Batched solves:", "/* reworded */ // Batched solves:", 1))
+    assert bench.kernel_source_sha("batch") == before
+    f.write_text(text.replace("constexpr int kNP = 4;", "constexpr int kNP = 5;", 1))
+    assert bench.kernel_source_sha("batch") != before
