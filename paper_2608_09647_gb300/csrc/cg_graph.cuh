@@ -1,16 +1,19 @@
 // The CG loop as a CUDA graph with a device-controlled WHILE node (large
 // systems).  Each phase of an iteration is its own high-occupancy kernel; a
-// kernel boundary is the grid-wide barrier, the scalars are re-formed by every
-// CTA from the fixed-order partial sums of the previous kernel, and the last
-// CTA of the x/p pass stores the loop state and sets the loop condition.  The
-// host launches one graph per solve and reads one status word back.
+// kernel boundary is the grid-wide barrier.  The last CTA of a reducing
+// kernel sums the fixed-order per-CTA partials once and stores the scalars
+// (alpha after the SpMV, beta and the stopping test after the r update) for
+// the next kernel; the last CTA of the x/p pass stores the loop state and sets
+// the loop condition.  The host launches one graph per solve and reads one
+// status word back.
 //
 //   prologue : q = A x | r = b - q, r^, p, x^, partials | start (1 CTA)
 //   WHILE    : q = A^ p, p.q | alpha, r^ -= alpha q, r.z, r.r | beta, x^/p
 //   epilogue : flush x on breakdown | q = A x | ||b - q||^2 | final (1 CTA)
 //
-// The phases are the same device functions as the persistent launch, so both
-// loop forms compute identical iterates for the same grid size.
+// The row work is the same device functions as the persistent launch; the
+// two forms sum the CTA partials in different fixed orders, so their iterates
+// agree to rounding (each form is deterministic on its own).
 #pragma once
 
 #include "cg_kernels.cuh"
