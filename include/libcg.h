@@ -132,8 +132,11 @@ cg_status cg_spmv(cg_handle* h, const double* x, double* y);
  * residual (tested before each SpMV, so iters counts SpMVs), then recomputes
  * the true residual in fp64; if that misses tol, restarts from x (residual
  * replacement) up to CG_OPT_MAX_RESTARTS times.  b = 0 gives x = 0, iters 0,
- * relres 0.  The whole loop is one persistent kernel launch with no host
- * round trip per iteration.  iters_out / relres_out (host, may be NULL)
+ * relres 0.  The loop runs either as one persistent cooperative launch or
+ * as one launch of a captured CUDA graph whose WHILE node the kernels
+ * themselves continue or end (CG_OPT_LOOP_MODE picks the form; auto takes
+ * the graph for large fp64 systems); either way there is no host round trip
+ * per iteration.  iters_out / relres_out (host, may be NULL)
  * receive the iteration count and the fp64 true relative residual.
  * Returns CG_OK, CG_NOT_CONVERGED or an error (x then holds the last iterate).
  */
@@ -148,6 +151,32 @@ cg_status cg_solve(cg_handle* h, const double* b, double* x, double tol, int32_t
 cg_status cg_solve_host(cg_handle* h, const double* b_host, double* x_host, double tol,
                         int32_t maxit, int32_t precond, int32_t precision, int32_t* iters_out,
                         double* relres_out);
+
+/*
+ * Build everything cg_solve(precond, precision) needs on this handle (the
+ * loop matrix in its sliced layout, scaled by D^-1/2 for Jacobi, the fp32
+ * copy for the refinement precisions, the work vectors), so that the first
+ * solve does no setup work.  Optional: cg_solve builds whatever is missing.
+ * Synchronous.  Errors as cg_solve's argument checks; CG_ERR_OOM when an
+ * allocation fails.
+ */
+cg_status cg_prepare(cg_handle* h, int32_t precond, int32_t precision);
+
+/*
+ * The solve loop's own SpMV kernel on its own: q = A^ p with A^ = D^-1/2 A
+ * D^-1/2 for CG_PRECOND_JACOBI and A otherwise (Sec. 3.1 SpMV on the loop
+ * matrix of Alg. 1), fused with the p.q reduction exactly as in each loop
+ * iteration of the graph form (the reduction's result stays on the device).
+ * p and q are DEVICE vectors of n doubles (CG_PREC_FP64) or n floats (the
+ * fp32 precisions), 16-byte aligned, not aliased.  The kernel is launched
+ * reps >= 1 times back to back on the handle's stream (after one tiny state
+ * kernel); the call does not block.  *bytes_out (host, may be NULL) gets the
+ * bytes one launch must move: the loop matrix entries (values, plus int32
+ * columns when the matrix is not in the diagonal layout), p read once, q
+ * written (and the stored diagonal without Jacobi).
+ */
+cg_status cg_loop_spmv(cg_handle* h, int32_t precond, int32_t precision, const void* p, void* q,
+                       int32_t reps, int64_t* bytes_out);
 
 /* Statistics of the last solve on h (host struct). */
 cg_status cg_get_solve_info(const cg_handle* h, cg_solve_info* out);
@@ -271,6 +300,12 @@ cg_status cg_fsai_get_factor(cg_handle* h, double* g_tril, int64_t* ntril, int32
 /* Compute the handle's factor with the MLP (inference).  weights_bf16: HOST
  * array of CG_MLP_PARAMS bfloat16 values (bytes = 2 * CG_MLP_PARAMS). */
 cg_status cg_fsai_load(cg_handle* h, const void* weights_bf16, int64_t bytes);
+
+/* cg_fsai_load from fp32 weights: weights is a HOST array of count =
+ * CG_MLP_PARAMS floats, rounded to bf16 (nearest, ties to even) by the
+ * library.  CG_ERR_INVALID for a wrong count, a NaN or infinite weight, or a
+ * finite weight that rounds beyond the largest bf16 value. */
+cg_status cg_fsai_load_f32(cg_handle* h, const float* weights, int64_t count);
 
 /*
  * Training loss of the MLP on the handle's matrix and its gradient.

@@ -30,8 +30,8 @@ EXPORTS = ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
            "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_destroy",
            "cg_last_error", "cg_status_string", "cg_solve_noalloc", "cg_batch_create",
            "cg_solve_batch", "cg_batch_get_system", "cg_batch_get_tuning", "cg_fsai_classic",
-           "cg_fsai_set_factor", "cg_fsai_get_factor", "cg_fsai_load", "cg_fsai_loss_grad",
-           "cg_adam_step")
+           "cg_fsai_set_factor", "cg_fsai_get_factor", "cg_fsai_load", "cg_fsai_load_f32",
+           "cg_fsai_loss_grad", "cg_adam_step", "cg_prepare", "cg_loop_spmv")
 CG_MLP_INPUTS, CG_MLP_HIDDEN, CG_MLP_PARAMS = 32, 64, 6337
 CG_NOALLOC_MAX_ROWS = 65536
 CG_BATCH_MAX_SYSTEMS = 4096
@@ -99,6 +99,9 @@ def load(build_if_missing: bool = True):
     lib.cg_fsai_set_factor.argtypes = [P, P]
     lib.cg_fsai_get_factor.argtypes = [P, P, pi64, pi32]
     lib.cg_fsai_load.argtypes = [P, P, i64]
+    lib.cg_fsai_load_f32.argtypes = [P, P, i64]
+    lib.cg_prepare.argtypes = [P, i32, i32]
+    lib.cg_loop_spmv.argtypes = [P, i32, i32, P, P, i32, pi64]
     lib.cg_fsai_loss_grad.argtypes = [P, P, P, P, i32, f64, pf64]
     f32 = ctypes.c_float
     lib.cg_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
@@ -106,7 +109,8 @@ def load(build_if_missing: bool = True):
     lib.cg_batch_get_system.argtypes = [P, i32, pi32, pi32, pi32, pf64]
     lib.cg_batch_get_tuning.argtypes = [P, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
     for name in ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
-                 "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info"):
+                 "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_fsai_load_f32", "cg_prepare",
+                 "cg_loop_spmv"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -122,12 +126,19 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _dptr(t, dtype, name):
+def _dptr(t, dtype, name, numel=None):
+    """Device pointer of a contiguous CUDA tensor of `dtype` on the current device
+    (and of `numel` elements when given); None stays None."""
     import torch
     if t is None:
         return None
     if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
         raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: tensor is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -158,8 +169,10 @@ def cg_create(n: int, rowptr, colind, vals) -> Handle:
     lib = load()
     out = ctypes.c_void_p()
     torch.cuda.current_stream().synchronize()
-    st = lib.cg_create(int(n), _dptr(rowptr, torch.int32, "rowptr"),
-                       _dptr(colind, torch.int32, "colind"), _dptr(vals, torch.float64, "vals"),
+    nnz = colind.numel() if colind is not None else 0
+    st = lib.cg_create(int(n), _dptr(rowptr, torch.int32, "rowptr", int(n) + 1),
+                       _dptr(colind, torch.int32, "colind"),
+                       _dptr(vals, torch.float64, "vals", nnz if vals is not None else None),
                        ctypes.byref(out))
     if st != CG_OK:
         raise CGError(st, lib.cg_last_error(None).decode())
@@ -183,7 +196,7 @@ def cg_spmv(h: Handle, x, y) -> int:
     import torch
     lib = load()
     lib.cg_set_stream(h.ptr, _stream_ptr())
-    return lib.cg_spmv(h.ptr, _dptr(x, torch.float64, "x"), _dptr(y, torch.float64, "y"))
+    return lib.cg_spmv(h.ptr, _dptr(x, torch.float64, "x", h.n), _dptr(y, torch.float64, "y", h.n))
 
 
 def cg_solve(h: Handle, b, x, tol: float = 1e-8, maxit: int = 1000,
@@ -195,7 +208,7 @@ def cg_solve(h: Handle, b, x, tol: float = 1e-8, maxit: int = 1000,
     lib.cg_set_stream(h.ptr, _stream_ptr())
     it = ctypes.c_int32(0)
     rel = ctypes.c_double(0.0)
-    st = lib.cg_solve(h.ptr, _dptr(b, torch.float64, "b"), _dptr(x, torch.float64, "x"),
+    st = lib.cg_solve(h.ptr, _dptr(b, torch.float64, "b", h.n), _dptr(x, torch.float64, "x", h.n),
                       float(tol), int(maxit), int(precond), int(precision), ctypes.byref(it),
                       ctypes.byref(rel))
     return st, it.value, rel.value
@@ -209,6 +222,8 @@ def cg_solve_host(h: Handle, b_host, x_host, tol: float = 1e-8, maxit: int = 100
     for t, name in ((b_host, "b_host"), (x_host, "x_host")):
         if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
             raise ValueError(f"{name}: expected a contiguous host float64 tensor")
+        if t.numel() != h.n:
+            raise ValueError(f"{name}: expected {h.n} elements, got {t.numel()}")
     lib = load()
     lib.cg_set_stream(h.ptr, _stream_ptr())
     it = ctypes.c_int32(0)
@@ -226,15 +241,38 @@ def cg_solve_noalloc(rowptr, colind, vals, b, x, tol: float = 1e-8, maxit: int =
     the current stream; x holds x0 on entry.  Returns (status, iters, relres_true)."""
     import torch
     n = rowptr.numel() - 1
+    nnz = colind.numel() if colind is not None else 0
     it = ctypes.c_int32(0)
     rel = ctypes.c_double(0.0)
-    st = load().cg_solve_noalloc(n, colind.numel() if colind is not None else 0,
-                                 _dptr(rowptr, torch.int32, "rowptr"),
+    st = load().cg_solve_noalloc(n, nnz, _dptr(rowptr, torch.int32, "rowptr"),
                                  _dptr(colind, torch.int32, "colind"),
-                                 _dptr(vals, torch.float64, "vals"), _dptr(b, torch.float64, "b"),
-                                 _dptr(x, torch.float64, "x"), float(tol), int(maxit),
+                                 _dptr(vals, torch.float64, "vals", nnz if vals is not None else None),
+                                 _dptr(b, torch.float64, "b", n), _dptr(x, torch.float64, "x", n),
+                                 float(tol), int(maxit),
                                  int(precond), _stream_ptr(), ctypes.byref(it), ctypes.byref(rel))
     return st, it.value, rel.value
+
+
+def cg_prepare(h: Handle, precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64) -> int:
+    """Build the loop matrix and work vectors a solve with (precond, precision) needs."""
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    return lib.cg_prepare(h.ptr, int(precond), int(precision))
+
+
+def cg_loop_spmv(h: Handle, p, q, precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64,
+                 reps: int = 1):
+    """q = A^ p with the solve loop's SpMV kernel, `reps` launches on the current stream
+    (A^ = D^-1/2 A D^-1/2 with Jacobi).  p, q: CUDA float64 (fp64) or float32 (fp32
+    precisions) tensors of n elements.  Returns (status, bytes one launch must move)."""
+    import torch
+    lib = load()
+    lib.cg_set_stream(h.ptr, _stream_ptr())
+    dt = torch.float64 if precision == CG_PREC_FP64 else torch.float32
+    nb = ctypes.c_int64(0)
+    st = lib.cg_loop_spmv(h.ptr, int(precond), int(precision), _dptr(p, dt, "p", h.n),
+                          _dptr(q, dt, "q", h.n), int(reps), ctypes.byref(nb))
+    return st, nb.value
 
 
 def cg_get_solve_info(h: Handle) -> dict:
@@ -359,26 +397,18 @@ def cg_fsai_get_factor(h: Handle):
     return st, g, kind.value
 
 
-def bf16_bits(params) -> "np.ndarray":
-    """fp32 values -> bfloat16 bit patterns (round to nearest even), the format of
-    cg_fsai_load's weights."""
-    import numpy as np
-    u = np.ascontiguousarray(params, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
-
-
 def cg_fsai_load(h: Handle, params) -> int:
     """Compute the handle's FSAI factor with the MLP; params: CG_MLP_PARAMS fp32 values
-    (host array or tensor), rounded to bf16 for the call."""
+    (host array or tensor), which the library rounds to bf16 (cg_fsai_load_f32)."""
     import numpy as np
     if hasattr(params, "detach"):
         params = params.detach().cpu().numpy()
-    bits = bf16_bits(np.asarray(params, dtype=np.float32))
-    if bits.size != CG_MLP_PARAMS:
+    w = np.ascontiguousarray(params, dtype=np.float32)
+    if w.size != CG_MLP_PARAMS:
         raise ValueError(f"expected {CG_MLP_PARAMS} parameters")
     lib = load()
     lib.cg_set_stream(h.ptr, _stream_ptr())
-    return lib.cg_fsai_load(h.ptr, ctypes.c_void_p(bits.ctypes.data), bits.nbytes)
+    return lib.cg_fsai_load_f32(h.ptr, ctypes.c_void_p(w.ctypes.data), w.size)
 
 
 def cg_fsai_loss_grad(h: Handle, params, grad, resid=None, lam: float = 0.1):

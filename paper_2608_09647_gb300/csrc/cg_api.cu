@@ -1022,37 +1022,19 @@ cg_status cg_spmv(cg_handle* h, const double* x, double* y) {
 
 namespace {
 
-// cg_solve after the preconditioner choice (FSAI only when the handle has a factor).
-cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32_t maxit, int32_t precond,
-                     int32_t precision, int32_t* iters_out, double* relres_out) {
-  h->last = cg_solve_info{};
-  if (!(tol >= 0.0) || maxit < 0) return fail(h, CG_ERR_INVALID, "cg_solve: tol < 0 or maxit < 0");
-  if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI && precond != CG_PRECOND_FSAI)
-    return fail(h, CG_ERR_INVALID, "cg_solve: unknown preconditioner");
-  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR && precision != CG_PREC_FP32_RU)
-    return fail(h, CG_ERR_INVALID, "cg_solve: unknown precision");
-  if (precond == CG_PRECOND_JACOBI && !h->jacobi_ok)
-    return fail(h, CG_ERR_INVALID, "cg_solve: Jacobi needs a positive diagonal in every row");
-  if (h->n == 0) {
-    if (iters_out) *iters_out = 0;
-    if (relres_out) *relres_out = 0.0;
-    return CG_OK;
-  }
-  if (!b || !x) return fail(h, CG_ERR_INVALID, "cg_solve: b or x is NULL");
-  if (!aligned16(b) || !aligned16(x)) return fail(h, CG_ERR_INVALID, "cg_solve: b and x must be 16-byte aligned");
-  if (b == x) return fail(h, CG_ERR_INVALID, "cg_solve: b and x alias");
-  const bool fsai = precond == CG_PRECOND_FSAI;
-  const bool jac = precond == CG_PRECOND_JACOBI;  // FSAI runs on the unscaled matrix
-  const bool fp64 = precision == CG_PREC_FP64;
-  const bool carry = precision == CG_PREC_FP32_RU;  // reliable updates: persistent form only
+// Loop matrix (scaled with Jacobi, unscaled otherwise) and work vectors for
+// one precision, built once per handle.
+cg_status prepare_impl(cg_handle* h, bool jac, bool fp64) {
   cg_status s = ensure_offdiag(h);
   if (s == CG_OK) s = ensure_vectors<double>(h, &h->r, &h->p, &h->q, &h->xh);
   if (s == CG_OK && fp64) s = ensure_vals<double>(h, &h->sval64[jac], &h->lval64[jac], jac);
   if (s == CG_OK && !fp64) s = ensure_vals<float>(h, &h->sval32[jac], &h->lval32[jac], jac);
   if (s == CG_OK && !fp64) s = ensure_vectors<float>(h, &h->r32, &h->p32, &h->q32, &h->xh32);
-  if (s != CG_OK) return s;
+  return s;
+}
 
-  const int G = auto_grid(h);
+SolveParams make_solve_params(const cg_handle* h, bool jac, const double* b, double* x, double tol,
+                              int32_t maxit, bool fp64, bool carry) {
   SolveParams P{};
   P.A = Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
   P.S64 = make_sell<double>(h, h->sval64[jac], h->lval64[jac], h->diag, h->disq);
@@ -1073,6 +1055,52 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
   P.timers = h->timers;
+  return P;
+}
+
+cg_status check_precond_precision(cg_handle* h, int32_t precond, int32_t precision, const char* who) {
+  if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI && precond != CG_PRECOND_FSAI)
+    return fail(h, CG_ERR_INVALID, std::string(who) + ": unknown preconditioner");
+  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR && precision != CG_PREC_FP32_RU)
+    return fail(h, CG_ERR_INVALID, std::string(who) + ": unknown precision");
+  if (precond == CG_PRECOND_JACOBI && !h->jacobi_ok)
+    return fail(h, CG_ERR_INVALID, std::string(who) + ": Jacobi needs a positive diagonal in every row");
+  return CG_OK;
+}
+
+// Loop state for stand-alone launches of the loop SpMV: iterating, rho = 1,
+// arrival counter clear (the kernel's last CTA forms alpha into this state).
+__global__ void loop_spmv_state_kernel(GState* gs) {
+  gs->status = kRunning;
+  gs->rho = 1.0;
+  gs->stop_abs = 0.0;
+  gs->ctr_q = 0u;
+}
+
+// cg_solve after the preconditioner choice (FSAI only when the handle has a factor).
+cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32_t maxit, int32_t precond,
+                     int32_t precision, int32_t* iters_out, double* relres_out) {
+  h->last = cg_solve_info{};
+  if (!(tol >= 0.0) || maxit < 0) return fail(h, CG_ERR_INVALID, "cg_solve: tol < 0 or maxit < 0");
+  const cg_status c = check_precond_precision(h, precond, precision, "cg_solve");
+  if (c != CG_OK) return c;
+  if (h->n == 0) {
+    if (iters_out) *iters_out = 0;
+    if (relres_out) *relres_out = 0.0;
+    return CG_OK;
+  }
+  if (!b || !x) return fail(h, CG_ERR_INVALID, "cg_solve: b or x is NULL");
+  if (!aligned16(b) || !aligned16(x)) return fail(h, CG_ERR_INVALID, "cg_solve: b and x must be 16-byte aligned");
+  if (b == x) return fail(h, CG_ERR_INVALID, "cg_solve: b and x alias");
+  const bool fsai = precond == CG_PRECOND_FSAI;
+  const bool jac = precond == CG_PRECOND_JACOBI;  // FSAI runs on the unscaled matrix
+  const bool fp64 = precision == CG_PREC_FP64;
+  const bool carry = precision == CG_PREC_FP32_RU;  // reliable updates: persistent form only
+  cg_status s = prepare_impl(h, jac, fp64);
+  if (s != CG_OK) return s;
+
+  const int G = auto_grid(h);
+  SolveParams P = make_solve_params(h, jac, b, x, tol, maxit, fp64, carry);
   if (fsai) return cgi::fsai_solve(h, P, fp64, carry, G, iters_out, relres_out);
   // auto: fp64 takes the graph form from kGraphMinRows rows; the refinement's
   // fp32 vector passes are short, so it stays in the persistent form
@@ -1162,6 +1190,65 @@ cg_status cg_solve_host(cg_handle* h, const double* b_host, double* x_host, doub
     CG_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   return s;
+}
+
+cg_status cg_prepare(cg_handle* h, int32_t precond, int32_t precision) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_prepare: batch handle");
+  const cg_status c = check_precond_precision(h, precond, precision, "cg_prepare");
+  if (c != CG_OK) return c;
+  if (h->n == 0) return CG_OK;
+  const bool fp64 = precision == CG_PREC_FP64;
+  cg_status s = prepare_impl(h, precond == CG_PRECOND_JACOBI, fp64);
+  // FSAI without a factor solves with Jacobi: build that variant too
+  if (s == CG_OK && precond == CG_PRECOND_FSAI && !(h->fsai && h->fsai->kind) && h->jacobi_ok)
+    s = prepare_impl(h, true, fp64);
+  return s;
+}
+
+cg_status cg_loop_spmv(cg_handle* h, int32_t precond, int32_t precision, const void* p, void* q, int32_t reps,
+                       int64_t* bytes_out) {
+  if (!h) return CG_ERR_INVALID;
+  if (h->batch) return fail(h, CG_ERR_INVALID, "cg_loop_spmv: batch handle");
+  const cg_status c = check_precond_precision(h, precond, precision, "cg_loop_spmv");
+  if (c != CG_OK) return c;
+  if (reps < 1) return fail(h, CG_ERR_INVALID, "cg_loop_spmv: reps < 1");
+  if (h->n == 0) {
+    if (bytes_out) *bytes_out = 0;
+    return CG_OK;
+  }
+  if (!p || !q || p == q) return fail(h, CG_ERR_INVALID, "cg_loop_spmv: p/q NULL or aliased");
+  if (!aligned16(p) || !aligned16(q)) return fail(h, CG_ERR_INVALID, "cg_loop_spmv: p and q must be 16-byte aligned");
+  const bool jac = precond == CG_PRECOND_JACOBI;
+  const bool fp64 = precision == CG_PREC_FP64;
+  cg_status s = prepare_impl(h, jac, fp64);
+  if (s != CG_OK) return s;
+  SolveParams P = make_solve_params(h, jac, nullptr, nullptr, 0.0, 0, fp64, false);
+  if (fp64) {
+    P.V64.p = static_cast<double*>(const_cast<void*>(p));
+    P.V64.q = static_cast<double*>(q);
+  } else {
+    P.V32.p = static_cast<float*>(const_cast<void*>(p));
+    P.V32.q = static_cast<float*>(q);
+  }
+  const void* f = fp64 ? spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac)
+                       : spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac);
+  const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f, h->sm_count), h->grid_part));
+  GArgs ga{P, h->gs, 0, 0, Gq, (unsigned)h->grid_graph};
+  void* args[] = {&ga};
+  loop_spmv_state_kernel<<<1, 1, 0, h->stream>>>(h->gs);
+  CG_CUDA(h, cudaGetLastError());
+  for (int r = 0; r < reps; ++r)
+    CG_CUDA(h, cudaLaunchKernel(f, dim3(Gq), dim3(kBlock), args, 0, h->stream));
+  if (bytes_out) {
+    // the entries of the loop matrix (8 B fp64 / 4 B fp32, plus a 4 B column
+    // without the diagonal layout), p read once, q written
+    const int64_t ent = h->sell_entries + h->nnz_long;
+    const int64_t vb = fp64 ? 8 : 4, cb = h->dia ? 0 : 4;
+    *bytes_out = (vb + cb) * ent + 4 * (int64_t)h->nlong + 2 * vb * h->n +
+                 (jac ? 0 : vb * h->n);  // the stored diagonal without Jacobi
+  }
+  return CG_OK;
 }
 
 cg_status cg_get_solve_info(const cg_handle* h, cg_solve_info* out) {

@@ -745,6 +745,28 @@ cg_status cg_fsai_load(cg_handle* h, const void* weights_bf16, int64_t bytes) {
   return cgi::fsai_commit(h, 2);
 }
 
+cg_status cg_fsai_load_f32(cg_handle* h, const float* weights, int64_t count) {
+  if (!h) return CG_ERR_INVALID;
+  if (!weights || count != kNParams)
+    return mfail(h, CG_ERR_INVALID, "cg_fsai_load_f32: expected " + std::to_string(kNParams) + " fp32 weights");
+  // fp32 -> bf16, round to nearest even on the bit pattern: add 0x7FFF plus the
+  // lowest kept bit, drop the 16 low bits.  Non-finite inputs are refused before
+  // rounding (the carry could turn a NaN payload into an infinity), and a finite
+  // value that rounds past the largest bf16 is refused after it.
+  std::vector<uint16_t> bits(kNParams);
+  for (int k = 0; k < kNParams; ++k) {
+    const float w = weights[k];
+    if (!std::isfinite(w)) return mfail(h, CG_ERR_INVALID, "cg_fsai_load_f32: non-finite weight " + std::to_string(k));
+    uint32_t u;
+    std::memcpy(&u, &w, sizeof(u));
+    const uint32_t r = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+    if ((r & 0x7F80u) == 0x7F80u)
+      return mfail(h, CG_ERR_INVALID, "cg_fsai_load_f32: weight " + std::to_string(k) + " overflows bf16");
+    bits[(size_t)k] = (uint16_t)r;
+  }
+  return cg_fsai_load(h, bits.data(), (int64_t)sizeof(uint16_t) * kNParams);
+}
+
 cg_status cg_fsai_loss_grad(cg_handle* h, const float* params, float* grad, const double* resid, int32_t nresid,
                             double lambda, double* loss_out) {
   if (!h) return CG_ERR_INVALID;

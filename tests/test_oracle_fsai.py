@@ -217,3 +217,101 @@ def test_loss_terms_in_closed_form():
     R = np.random.default_rng(3).standard_normal((3, 10))
     LR, _ = fsai.residual_term(Ad, g, R)
     assert LR <= 1e-24
+
+
+def hand_network():
+    """The network of test_mlp_forward_by_hand: bf16-exact weights."""
+    W1 = np.zeros((fsai.N_HID, fsai.N_IN)); b1 = np.zeros(fsai.N_HID)
+    W2 = np.zeros((fsai.N_HID, fsai.N_HID)); b2 = np.zeros(fsai.N_HID)
+    W3 = np.zeros(fsai.N_HID)
+    W1[0, 3], W1[1, 7], b1[1] = 2.0, -1.0, 0.5
+    W2[0, 0], W2[0, 1], b2[0], W2[5, 1] = 1.0, 3.0, -0.25, -1.0
+    W3[0], W3[5] = 0.5, 4.0
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, [0.125]])
+
+
+D_A = 1.0 + 3 * 2.0 ** -9        # dLoss/do of entry A: not a bf16 value (bf16(D_A) = 1 + 2^-7)
+
+
+def hand_backward_case():
+    """Two entries.  A: x3 = 1.5, x7 = 0.25, x0 = 7 -> z1 = (3, 0.25), z2_0 = 3.5,
+    z2_5 = -0.25 (masked; W3_5 = 4 would leak through a missing second-layer mask);
+    dout = D_A.  B: x3 = 1.5, x7 = 1 -> z1 = (3, -0.5) (unit 1 cut by the first ReLU,
+    yet it receives dh1_1 = 3 dz2_0 through W2[0, 1]), z2_0 = 2.75; dout = 1."""
+    F = np.zeros((2, fsai.N_IN))
+    F[0, 3], F[0, 7], F[0, 0] = 1.5, 0.25, 7.0
+    F[1, 3], F[1, 7] = 1.5, 1.0
+    return F, np.array([D_A, 1.0])
+
+
+def hand_backward_expected(rounded):
+    """The gradient worked by hand (F7).  Entry A: dz2_0 = 0.5 D_A = 0.5029296875, which
+    bf16 rounds to 0.50390625; dh1 = dz2r_0 (W2[0, 0], W2[0, 1]) = (0.50390625, 1.51171875);
+    dz1_1 = 1.51171875 needs 9 significant bits and rounds (tie, to even) to 1.515625.
+    Entry B: dz2_0 = 0.5, dz1 = (0.5, 0).  Weight gradients take the rounded dz,
+    bias gradients the unrounded ones; in fp64 mode nothing is rounded."""
+    W1 = np.zeros((fsai.N_HID, fsai.N_IN)); b1 = np.zeros(fsai.N_HID)
+    W2 = np.zeros((fsai.N_HID, fsai.N_HID)); b2 = np.zeros(fsai.N_HID)
+    W3 = np.zeros(fsai.N_HID)
+    dz2a = 0.50390625 if rounded else 0.5029296875       # weight-gradient input of entry A
+    dz1a = (0.50390625, 1.515625) if rounded else (0.5029296875, 1.5087890625)
+    W3[0] = 3.5 * D_A + 2.75                 # h2_0 dout summed over A and B
+    b3 = D_A + 1.0
+    W2[0, 0] = 3.0 * dz2a + 3.0 * 0.5        # dz2_0 h1_0
+    W2[0, 1] = 0.25 * dz2a                   # h1_1 = 0.25 in A, 0 in B
+    b2[0] = 0.5029296875 + 0.5
+    W1[0, 0], W1[1, 0] = 7.0 * dz1a[0], 7.0 * dz1a[1]
+    W1[0, 3] = 1.5 * dz1a[0] + 1.5 * 0.5
+    W1[0, 7] = 0.25 * dz1a[0] + 1.0 * 0.5
+    W1[1, 3], W1[1, 7] = 1.5 * dz1a[1], 0.25 * dz1a[1]
+    b1[0] = 0.50390625 + 0.5 if rounded else 0.5029296875 + 0.5
+    b1[1] = 1.51171875 if rounded else 1.5087890625
+    return np.concatenate([W1.ravel(), b1, W2.ravel(), b2, W3, [b3]])
+
+
+def backward_pin_holds(backward):
+    p = hand_network()
+    F, dout = hand_backward_case()
+    for rnd in (True, False):
+        o, cache = fsai.mlp_forward(p, F, round_bf16=rnd)
+        if not np.array_equal(o, [0.5 * 3.5 + 0.125, 0.5 * 2.75 + 0.125]):
+            return False
+        if not np.array_equal(backward(dout, cache), hand_backward_expected(rnd)):
+            return False
+    return True
+
+
+def test_mlp_backward_by_hand():
+    """F7 on a network evaluated by hand, in both precision modes: where dz2 and dz1 are
+    rounded to bf16 (before the weight-gradient products and before dh1 = dz2 W2), that
+    the bias gradients take the unrounded values, the ReLU masks of both layers and the
+    orientation of W2 in dh1."""
+    assert backward_pin_holds(fsai.mlp_backward)
+
+
+# Plausible mistakes in the backward pass, each planted in a copy of mlp_backward.
+# Moving a rounding to after a ReLU mask is not among them: the mask is 0 or 1, so the
+# two orders give the same bits.
+BACKWARD_MUTANTS = {
+    "dz1 from the unrounded dz2": ("dz1 = (dz2r @ W2)", "dz1 = (dz2 @ W2)"),
+    "dW2 from the unrounded dz2": ("dW2 = dz2r.T @ h1", "dW2 = dz2.T @ h1"),
+    "dW1 from the unrounded dz1": ("dW1 = dz1r.T @ X", "dW1 = dz1.T @ X"),
+    "db2 from the rounded dz2": ("db2 = dz2.sum(0)", "db2 = dz2r.sum(0)"),
+    "db1 from the rounded dz1": ("db1 = dz1.sum(0)", "db1 = dz1r.sum(0)"),
+    "W2 transposed in dh1": ("(dz2r @ W2)", "(dz2r @ W2.T)"),
+    "first-layer ReLU mask dropped": ("* (z1 > 0)", "* 1.0"),
+    "second-layer ReLU mask dropped": ("* (z2 > 0)", "* 1.0"),
+    "dz2 not rounded": ("dz2r = rnd(dz2)", "dz2r = dz2"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BACKWARD_MUTANTS))
+def test_backward_pin_catches_planted_mistakes(name):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fsai.mlp_backward))
+    old, new = BACKWARD_MUTANTS[name]
+    assert src.count(old) == 1, (name, old)
+    ns = dict(vars(fsai))
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    assert not backward_pin_holds(ns["mlp_backward"]), name

@@ -69,3 +69,45 @@ def test_noalloc_rejects_more_rows_than_its_scratch_holds():
     n = cg.CG_NOALLOC_MAX_ROWS + 1
     assert lib.cg_solve_noalloc(n, 0, None, None, None, None, None, 1e-8, 10, 0, None, None,
                                 None) == cg.CG_ERR_INVALID
+
+
+def raw_noalloc(n, nnz, rp, ci, va, b, x, precond):
+    """The C entry point itself, with the nnz the caller states (the binding would
+    take it from colind's length)."""
+    lib = cg.load()
+    it = cg.ctypes.c_int32(-1)
+    rel = cg.ctypes.c_double(-1.0)
+    st = lib.cg_solve_noalloc(n, nnz, rp.data_ptr(), ci.data_ptr(), va.data_ptr(), b.data_ptr(),
+                              x.data_ptr(), 1e-8, 500, precond,
+                              cg.ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                              cg.ctypes.byref(it), cg.ctypes.byref(rel))
+    torch.cuda.synchronize()
+    return st
+
+
+@pytest.mark.parametrize("fault", ["colind_equals_n", "rowptr_end_differs_from_nnz",
+                                   "jacobi_zero_diagonal"])
+def test_noalloc_refuses_a_malformed_csr_on_the_device_then_recovers(fault):
+    """The kernel checks the CSR before any indexed read (rowptr[0] = 0, rowptr[n] = nnz,
+    rows non-decreasing, colind in [0, n), a positive diagonal for Jacobi), so each of
+    these inputs is refused with CG_ERR_INVALID without touching memory outside the
+    buffers.  A valid solve right after must still agree with cg_solve: the shared
+    scratch and its result block carry nothing over from the refused call."""
+    A = gen.lap2d(24)
+    rp, ci, va = (t.clone() for t in to_device(A))
+    nnz = A.nnz
+    precond = cg.CG_PRECOND_NONE
+    if fault == "colind_equals_n":
+        ci[nnz // 2] = A.n
+    elif fault == "rowptr_end_differs_from_nnz":
+        nnz -= 1                       # the buffers keep their full length
+    else:
+        va[rp[5].item():rp[6].item()] = torch.where(ci[rp[5].item():rp[6].item()] == 5, 0.0,
+                                                    va[rp[5].item():rp[6].item()])
+        precond = cg.CG_PRECOND_JACOBI
+    b = torch.from_numpy(oracle.spmv(A, gen.xstar(A.n, 4))).cuda()
+    x = torch.zeros_like(b)
+    assert raw_noalloc(A.n, nnz, rp, ci, va, b, x, precond) == cg.CG_ERR_INVALID
+    B = gen.lap2d(30, 9, 0.2)
+    bb = oracle.spmv(B, gen.xstar(B.n, 5))
+    check_agrees(B, bb, 1e-8, 5000, cg.CG_PRECOND_JACOBI)
