@@ -23,19 +23,44 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 OK, NOT_CONVERGED, ERR_INVALID, ERR_BREAKDOWN, ERR_NUMERIC, ERR_OOM = 0, 1, -1, -2, -3, -6
 
 
+def _compile(lib, extra):
+    tmp = lib + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11", *extra,
+                    "-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, lib)
+
+
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (no FMA contraction, no arch-specific flags)."""
+    """Compile oracle.c with gcc (no FMA contraction, no arch-specific flags); the
+    OpenMP build used only to time the oracle on all host cores is attempted too."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
-                        "-o", tmp, _SRC, "-lm"], check=True)
-        os.replace(tmp, _LIB)
+        _compile(_LIB, [])
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        try:
+            _compile(_LIB_OMP, ["-fopenmp"])
+        except (subprocess.CalledProcessError, OSError):
+            pass  # no OpenMP runtime: the all-core timing leg reports itself unavailable
     return _LIB
+
+
+def openmp():
+    """The all-core build of the same oracle (row loops split over OpenMP threads, Sec.
+    3.3), for timing only: its reductions sum per thread, so it never judges results.
+    Returns (library, threads) or (None, 0) when no OpenMP build exists."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        if not os.path.exists(_LIB_OMP):
+            return None, 0
+        _lib_omp = _bind(ctypes.CDLL(_LIB_OMP))
+    return _lib_omp, int(_lib_omp.or_threads())
 
 
 class _Result(ctypes.Structure):
@@ -63,6 +88,8 @@ def _bind(lib):
     lib.or_pcg_ir.restype = ctypes.c_int
     lib.or_pcg_ru.argtypes = lib.or_pcg_ir.argtypes
     lib.or_pcg_ru.restype = ctypes.c_int
+    lib.or_threads.argtypes = []
+    lib.or_threads.restype = ctypes.c_int
     return lib
 
 
@@ -123,17 +150,18 @@ def jacobi_dinv(A) -> np.ndarray:
 
 
 def pcg(A, b, x0=None, tol=1e-8, maxit=1000, precond=1, max_restarts=3,
-        p_hist_k=0, res_hist=False) -> Solve:
+        p_hist_k=0, res_hist=False, lib=None) -> Solve:
     """(Jacobi-preconditioned) CG, Alg. 1 with readings R1-R5 (see oracle.c).
 
-    precond: 0 = none (the paper's unpreconditioned CG), 1 = Jacobi."""
+    precond: 0 = none (the paper's unpreconditioned CG), 1 = Jacobi.  lib: another build
+    of the oracle (openmp()[0], for timing on all cores); default the checker build."""
     n, rp, ci, va = _csr(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     ph = np.zeros((p_hist_k, n)) if p_hist_k else None
     rh = np.full(maxit + 1, np.nan) if res_hist else None
     res = _Result()
-    _load().or_pcg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, maxit, precond,
+    (lib or _load()).or_pcg(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), tol, maxit, precond,
                    max_restarts, _p(ph), p_hist_k, _p(rh), ctypes.byref(res))
     if rh is not None:
         rh = rh[: res.iters + 1]

@@ -38,9 +38,19 @@
  *      instead of p = z', so the Krylov information is not thrown away.
  * Sums run in index order.  Compiled with -ffp-contract=off so no fused
  * multiply-add changes the rounding.
+ *
+ * The row and vector loops of the fp64 SpMV and (Jacobi-)PCG carry OpenMP
+ * row-split pragmas, the form of the paper's CPU runs (Sec. 3.3).  The
+ * checker build (no -fopenmp) ignores them and stays sequential, in index
+ * order; a second build with -fopenmp exists only to time the same loops on
+ * all host cores (its reductions then sum per thread, so its rounding differs
+ * and it is never used to judge results).
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -59,6 +69,7 @@ typedef struct {
 /* y = A x, row by row, terms in storage order (Sec. 3.1) */
 void or_spmv(int64_t n, const int32_t* rowptr, const int32_t* colind, const double* vals,
              const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += vals[k] * x[colind[k]];
@@ -68,14 +79,25 @@ void or_spmv(int64_t n, const int32_t* rowptr, const int32_t* colind, const doub
 
 double or_dot(int64_t n, const double* a, const double* b) {
   double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
   for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
+}
+
+/* Threads the row loops use: 1 in the checker build. */
+int or_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* ||b - A x||_2 / ||b||_2, 0 when b = 0 (Sec. 3.1, recomputed residual) */
 double or_true_relres(int64_t n, const int32_t* rowptr, const int32_t* colind,
                       const double* vals, const double* b, const double* x) {
   double rr = 0.0, bb = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : rr, bb)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += vals[k] * x[colind[k]];
@@ -143,8 +165,11 @@ int or_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, const double
   for (;;) {
     /* r = b - A x, z = M^-1 r, p = z, rho = r.z */
     or_spmv(n, rowptr, colind, vals, x, q);
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) z[i] = precond ? r[i] * dinv[i] : r[i];
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) p[i] = z[i];
     double rho = or_dot(n, r, z);
     rr = or_dot(n, r, r);
@@ -159,13 +184,17 @@ int or_pcg(int64_t n, const int32_t* rowptr, const int32_t* colind, const double
       if (!isfinite(pq) || !isfinite(rho)) { status = OR_ERR_NUMERIC; stop = 1; break; }
       if (pq <= 0.0) { status = OR_ERR_BREAKDOWN; stop = 1; break; } /* R4 */
       const double alpha = rho / pq;
+      #pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+      #pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+      #pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) z[i] = precond ? r[i] * dinv[i] : r[i];
       const double rho_new = or_dot(n, r, z);
       rr = or_dot(n, r, r);
       const double beta = rho_new / rho;
       rho = rho_new;
+      #pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
       ++k;
     }

@@ -145,10 +145,17 @@ def _dptr(t, dtype, name, numel=None):
 class Handle:
     """Owns a cg_handle; keeps the borrowed CSR tensors alive until destroyed."""
 
-    def __init__(self, ptr, n, keep):
+    def __init__(self, ptr, n, keep, batch=False):
         self._ptr = ptr
         self.n = n
         self._keep = keep
+        self.batch = batch
+
+    @property
+    def vec_len(self):
+        """Length single-system vectors must have (None on a batch handle, which the
+        library itself refuses for single-system calls)."""
+        return None if self.batch else self.n
 
     @property
     def ptr(self):
@@ -196,7 +203,8 @@ def cg_spmv(h: Handle, x, y) -> int:
     import torch
     lib = load()
     lib.cg_set_stream(h.ptr, _stream_ptr())
-    return lib.cg_spmv(h.ptr, _dptr(x, torch.float64, "x", h.n), _dptr(y, torch.float64, "y", h.n))
+    return lib.cg_spmv(h.ptr, _dptr(x, torch.float64, "x", h.vec_len),
+                       _dptr(y, torch.float64, "y", h.vec_len))
 
 
 def cg_solve(h: Handle, b, x, tol: float = 1e-8, maxit: int = 1000,
@@ -208,7 +216,8 @@ def cg_solve(h: Handle, b, x, tol: float = 1e-8, maxit: int = 1000,
     lib.cg_set_stream(h.ptr, _stream_ptr())
     it = ctypes.c_int32(0)
     rel = ctypes.c_double(0.0)
-    st = lib.cg_solve(h.ptr, _dptr(b, torch.float64, "b", h.n), _dptr(x, torch.float64, "x", h.n),
+    st = lib.cg_solve(h.ptr, _dptr(b, torch.float64, "b", h.vec_len),
+                      _dptr(x, torch.float64, "x", h.vec_len),
                       float(tol), int(maxit), int(precond), int(precision), ctypes.byref(it),
                       ctypes.byref(rel))
     return st, it.value, rel.value
@@ -222,7 +231,7 @@ def cg_solve_host(h: Handle, b_host, x_host, tol: float = 1e-8, maxit: int = 100
     for t, name in ((b_host, "b_host"), (x_host, "x_host")):
         if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
             raise ValueError(f"{name}: expected a contiguous host float64 tensor")
-        if t.numel() != h.n:
+        if h.vec_len is not None and t.numel() != h.vec_len:
             raise ValueError(f"{name}: expected {h.n} elements, got {t.numel()}")
     lib = load()
     lib.cg_set_stream(h.ptr, _stream_ptr())
@@ -270,8 +279,8 @@ def cg_loop_spmv(h: Handle, p, q, precond: int = CG_PRECOND_JACOBI, precision: i
     lib.cg_set_stream(h.ptr, _stream_ptr())
     dt = torch.float64 if precision == CG_PREC_FP64 else torch.float32
     nb = ctypes.c_int64(0)
-    st = lib.cg_loop_spmv(h.ptr, int(precond), int(precision), _dptr(p, dt, "p", h.n),
-                          _dptr(q, dt, "q", h.n), int(reps), ctypes.byref(nb))
+    st = lib.cg_loop_spmv(h.ptr, int(precond), int(precision), _dptr(p, dt, "p", h.vec_len),
+                          _dptr(q, dt, "q", h.vec_len), int(reps), ctypes.byref(nb))
     return st, nb.value
 
 
@@ -324,7 +333,7 @@ def cg_batch_create(rowptrs, colinds, valss) -> Handle:
     if st != CG_OK:
         raise CGError(st, lib.cg_last_error(None).decode())
     return Handle(out, sum(int(r.numel()) - 1 for r in rowptrs),
-                  (list(rowptrs), list(colinds), list(valss)))
+                  (list(rowptrs), list(colinds), list(valss)), batch=True)
 
 
 def cg_solve_batch(h: Handle, bs, xs, tol: float = 1e-8, maxit: int = 1000,
