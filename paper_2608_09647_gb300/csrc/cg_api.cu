@@ -221,7 +221,7 @@ unsigned grid_for(int64_t items) {
 }
 
 // Cut rows into row blocks: greedily extend a block while it stays within
-// kCap nonzeros and kBlock rows; a row longer than kCap gets a block alone.
+// kCapV nonzeros and kBlock rows; a row longer than kCapV gets a block alone.
 std::vector<int32_t> build_row_blocks(const int32_t* rowptr, int64_t n, int64_t* long_rows) {
   std::vector<int32_t> rb;
   rb.reserve((size_t)(n / 64 + 2));
@@ -230,14 +230,14 @@ std::vector<int32_t> build_row_blocks(const int32_t* rowptr, int64_t n, int64_t*
   while (r < n) {
     const int64_t start = r;
     const int64_t len0 = rowptr[r + 1] - rowptr[r];
-    if (len0 > kCap) {
+    if (len0 > kCapV) {
       ++r;
       ++longs;
     } else {
       int64_t nk = 0;
       while (r < n && r - start < kBlock) {
         const int64_t len = rowptr[r + 1] - rowptr[r];
-        if (nk + len > kCap) break;
+        if (nk + len > kCapV) break;
         nk += len;
         ++r;
       }
@@ -254,6 +254,22 @@ int max_coresident(K kernel, int sm_count) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess)
     return 0;
   return per_sm * sm_count;
+}
+
+// The caller's CSR for the SpMV kernels; 16-byte loads when both arrays allow them.
+Csr<double> make_csr(const cg_handle* h) {
+  return Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb,
+                     (aligned16(h->colind) && aligned16(h->vals)) ? 1 : 0};
+}
+
+// Grid of the stand-alone caller-CSR SpMV: every resident CTA, each taking row
+// blocks round-robin.
+unsigned spmv_grid(const cg_handle* h) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spmv_kernel<double>, kBlock, 0) != cudaSuccess ||
+      per_sm <= 0)
+    per_sm = 4;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(h->nrb, (int64_t)per_sm * h->sm_count));
 }
 
 int auto_grid(const cg_handle* h) {
@@ -575,7 +591,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   Csr<double> A = P.A;
   const double* x = P.x;
   double* q = P.V64.q;
-  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  const unsigned Gs = spmv_grid(h);
   void* a_spmv[] = {&A, &x, &q};
   void* a_ga[] = {&ga};
   const void* f_r = jac ? (const void*)g_upd_r<double, true> : (const void*)g_upd_r<double, false>;
@@ -748,7 +764,7 @@ cg_status build_graph_ir(cg_handle* h, const SolveParams& P, bool jac) {
   Csr<double> A = P.A;
   const double* x = P.x;
   double* q = P.V64.q;
-  const unsigned Gs = (unsigned)std::min<int64_t>(std::max<int32_t>(h->nrb, 1), (int64_t)h->sm_count * 64);
+  const unsigned Gs = spmv_grid(h);
   void* a_spmv[] = {&A, &x, &q};
   void* a_ga[] = {&ga};
   const bool with_rr = jac && h->dmin != h->dmax;
@@ -1011,9 +1027,8 @@ cg_status cg_spmv(cg_handle* h, const double* x, double* y) {
   if (h->batch) return fail(h, CG_ERR_INVALID, "cg_spmv: batch handle (use cg_solve_batch)");
   if (h->n == 0) return CG_OK;
   if (!x || !y || x == y) return fail(h, CG_ERR_INVALID, "cg_spmv: x/y NULL or aliased");
-  Csr<double> A{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
-  const unsigned grid = (unsigned)std::min<int64_t>(h->nrb, (int64_t)h->sm_count * 64);
-  spmv_kernel<double><<<grid, kBlock, 0, h->stream>>>(A, x, y);
+  const Csr<double> A = make_csr(h);
+  spmv_kernel<double><<<spmv_grid(h), kBlock, 0, h->stream>>>(A, x, y);
   CG_CUDA(h, cudaGetLastError());
   return CG_OK;
 }
@@ -1036,7 +1051,7 @@ cg_status prepare_impl(cg_handle* h, bool jac, bool fp64) {
 SolveParams make_solve_params(const cg_handle* h, bool jac, const double* b, double* x, double tol,
                               int32_t maxit, bool fp64, bool carry) {
   SolveParams P{};
-  P.A = Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb};
+  P.A = make_csr(h);
   P.S64 = make_sell<double>(h, h->sval64[jac], h->lval64[jac], h->diag, h->disq);
   P.S32 = make_sell<float>(h, h->sval32[jac], h->lval32[jac], h->diag32, h->disq32);
   P.V64 = LoopVecs<double>{h->r, h->p, h->q, h->xh};

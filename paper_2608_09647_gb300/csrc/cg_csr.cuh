@@ -1,0 +1,194 @@
+// SpMV on the caller's CSR matrix (Sec. 3.1: y_i = sum_k vals[k] x[colind[k]]
+// over row i's stored entries): cg_spmv, the residuals b - A x of the graph
+// form, and the once-per-solve true residual of the persistent kernels.
+//
+// The rows are cut on the host into row blocks of at most kCapV nonzeros and
+// kBlock rows; a row with more than kCapV nonzeros is a block of its own (a
+// "long" block, which the CTA strides over and reduces).  Two forms:
+//
+//  * spmv_rowblock_fma (the stand-alone kernel): the block's nonzeros are read
+//    with 16-byte loads (four column indices, two pairs of values) starting at
+//    the 16-byte boundary at or below the block's first nonzero, each value is
+//    staged in shared memory beside its gathered x, and one thread per row
+//    sums val * x over the row in storage order with fused multiply-adds: one
+//    fp64 FMA per nonzero.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
+//    so a separate multiply and add per nonzero (two fp64 instructions) makes a
+//    7-point SpMV pipe-bound; with one FMA the kernel is HBM-bound.
+//  * spmv_rowblock (inside the persistent solver kernels, twice per solve):
+//    products rounded, then summed in storage order, the oracle's arithmetic
+//    exactly, staged in a smaller shared buffer so the persistent kernels keep
+//    their occupancy.
+#pragma once
+
+#include "cg_device.cuh"
+
+namespace cg {
+
+constexpr int kCap = 2048;                 // shared staging of one row block (persistent kernels)
+constexpr int kCapV = kCap - 4;            // nonzeros of a row block: its 16-byte window fits kCap
+constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
+
+// CSR matrix view plus its row-block schedule.  Row block b covers rows
+// [rb[b], rb[b+1]).  vec != 0: colind and vals start on 16-byte boundaries, so
+// the 16-byte loads of spmv_rowblock_fma are allowed.
+template <typename T>
+struct Csr {
+  int64_t n;
+  const int32_t* __restrict__ rowptr;
+  const int32_t* __restrict__ colind;
+  const T* __restrict__ vals;
+  const int32_t* __restrict__ rb;
+  int32_t nrb;
+  int32_t vec;
+};
+
+// One row block of y = A x, the oracle's arithmetic: stream blocks sum each row
+// in storage order over rounded products, so fp64 results match it bit for
+// bit; long rows use a strided multiply-add and a fixed tree.
+template <typename T>
+__device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y, int b, T* s_prod) {
+  const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
+  const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
+  const int nk = k1 - k0;
+  const int t = threadIdx.x;
+  if (nk > kCap) {  // long row (r1 == r0 + 1 by construction)
+    T acc = T(0);
+    for (int k = k0 + t; k < k1; k += kBlock) acc += __ldg(A.vals + k) * x[__ldg(A.colind + k)];
+    double v[1] = {(double)acc};
+    block_sum<1>(v);
+    if (t == 0) y[r0] = (T)v[0];
+    return;
+  }
+  T prod[kPerThread];
+  int col[kPerThread];
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int k = t + j * kBlock;
+    if (k < nk) {
+      col[j] = __ldg(A.colind + k0 + k);
+      prod[j] = __ldg(A.vals + k0 + k);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int k = t + j * kBlock;
+    if (k < nk) prod[j] = prod[j] * x[col[j]];
+  }
+#pragma unroll
+  for (int j = 0; j < kPerThread; ++j) {
+    const int k = t + j * kBlock;
+    if (k < nk) s_prod[k] = prod[j];
+  }
+  __syncthreads();
+  const int i = r0 + t;
+  if (i < r1) {
+    const int a = __ldg(A.rowptr + i) - k0, e = __ldg(A.rowptr + i + 1) - k0;
+    T s = T(0);
+    for (int k = a; k < e; ++k) s += s_prod[k];
+    y[i] = s;
+  }
+  __syncthreads();  // s_prod is reused by the next row block
+}
+
+// A row block's 16-byte window holds at most kCapV + 3 nonzeros: two quads
+// (four nonzeros on a 16-byte boundary) per thread.
+constexpr int kQuadPasses = 2;
+static_assert((kCapV + 3 + 3) / 4 <= kQuadPasses * kBlock, "a row block's window exceeds two quads per thread");
+
+// One row block of y = A x with one fused multiply-add per nonzero (header
+// comment).  s_vx holds (val, x[col]) of the block's nonzeros in storage order.
+__device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const double* __restrict__ x,
+                                                  double* __restrict__ y, int b, double2* s_vx) {
+  const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
+  const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
+  const int t = threadIdx.x;
+  if (k1 - k0 > kCapV) {  // long row (r1 == r0 + 1 by construction): strided FMA, fixed tree
+    double acc = 0.0;
+    for (int k = k0 + t; k < k1; k += kBlock) acc = fma(__ldg(A.vals + k), __ldg(x + __ldg(A.colind + k)), acc);
+    double v[1] = {acc};
+    block_sum<1>(v);
+    if (t == 0) y[r0] = v[0];
+    return;
+  }
+  // every load of the block is issued before the first gather, every gather
+  // before the first shared-memory store
+  const int a0 = A.vec ? (k0 & ~3) : k0;
+  const int nq = (k1 - a0 + 3) >> 2;
+  int c[kQuadPasses][4];
+  double v[kQuadPasses][4];
+#pragma unroll
+  for (int j = 0; j < kQuadPasses; ++j) {
+    const int k = a0 + 4 * (t + j * kBlock);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[j][u] = 0;
+      v[j][u] = 0.0;
+    }
+    if (t + j * kBlock >= nq) continue;
+    if (A.vec && k + 4 <= k1) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(A.colind + k));
+      const double2 v01 = __ldg(reinterpret_cast<const double2*>(A.vals + k));
+      const double2 v23 = __ldg(reinterpret_cast<const double2*>(A.vals + k + 2));
+      c[j][0] = c4.x;
+      c[j][1] = c4.y;
+      c[j][2] = c4.z;
+      c[j][3] = c4.w;
+      v[j][0] = v01.x;
+      v[j][1] = v01.y;
+      v[j][2] = v23.x;
+      v[j][3] = v23.y;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = k + u;
+        if (kk >= k0 && kk < k1) {
+          c[j][u] = __ldg(A.colind + kk);
+          v[j][u] = __ldg(A.vals + kk);
+        }
+      }
+    }
+  }
+  double xg[kQuadPasses][4];
+#pragma unroll
+  for (int j = 0; j < kQuadPasses; ++j) {
+    const int k = a0 + 4 * (t + j * kBlock);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u;
+      xg[j][u] = (t + j * kBlock < nq && kk >= k0 && kk < k1) ? __ldg(x + c[j][u]) : 0.0;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kQuadPasses; ++j) {
+    const int k = a0 + 4 * (t + j * kBlock);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u;
+      if (t + j * kBlock < nq && kk >= k0 && kk < k1) s_vx[kk - k0] = make_double2(v[j][u], xg[j][u]);
+    }
+  }
+  __syncthreads();
+  const int i = r0 + t;
+  if (i < r1) {
+    const int a = __ldg(A.rowptr + i) - k0, e = __ldg(A.rowptr + i + 1) - k0;
+    double s = 0.0;
+    for (int k = a; k < e; ++k) {
+      const double2 p = s_vx[k];
+      s = fma(p.x, p.y, s);
+    }
+    y[i] = s;
+  }
+  __syncthreads();  // s_vx is reused by the next row block
+}
+
+// Stand-alone y = A x over all row blocks (cg_spmv, the graph form's residuals);
+// CTAs take blocks round-robin, so the grid works on one band of rows at a time
+// and the gathers of neighbouring rows meet in L2.  fp64 only.
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(Csr<T> A, const T* x, T* y) {
+  static_assert(sizeof(T) == sizeof(double), "the stand-alone caller-CSR SpMV is fp64");
+  __shared__ double2 s_vx[kCapV];
+  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock_fma(A, x, y, b, s_vx);
+}
+
+}  // namespace cg

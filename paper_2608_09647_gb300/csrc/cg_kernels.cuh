@@ -32,91 +32,15 @@
 //    slices and are summed by a warp each from a compact CSR.
 #pragma once
 
-#include "cg_device.cuh"
+#include "cg_csr.cuh"
 
 namespace cg {
 
-constexpr int kCap = 2048;                 // nonzeros of one caller-CSR row block
-constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
 constexpr int kLongRow = 128;              // off-diagonal entries above which a row leaves SELL
 constexpr int kUnroll = 8;                 // slice columns whose loads are issued together
 constexpr double kIrTolInner = 1e-4;       // default inner tolerance: refinement (restarting)
 constexpr double kRuTolInner = 1e-1;       // default update threshold: reliable updates
 constexpr int kMaxDiag = 32;               // most distinct offsets of the diagonal (DIA) layout
-
-// --------------------------------------------------------------------------
-// Plain CSR (the caller's matrix): cg_spmv and the fp64 true residual
-// --------------------------------------------------------------------------
-
-// CSR matrix view plus its row-block schedule.  Row block b covers rows
-// [rb[b], rb[b+1]); it holds either <= kCap nonzeros and <= kBlock rows
-// ("stream" block: products staged in shared memory, one thread per row), or
-// exactly one row with more than kCap nonzeros ("long" block: the CTA strides
-// over the row and reduces).
-template <typename T>
-struct Csr {
-  int64_t n;
-  const int32_t* __restrict__ rowptr;
-  const int32_t* __restrict__ colind;
-  const T* __restrict__ vals;
-  const int32_t* __restrict__ rb;
-  int32_t nrb;
-};
-
-// One row block of y = A x.  Stream blocks sum each row in storage order over
-// rounded products, the oracle's order, so fp64 results match it bit for
-// bit; long rows use a strided fused multiply-add and a fixed tree.
-template <typename T>
-__device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y, int b, T* s_prod) {
-  const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
-  const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
-  const int nk = k1 - k0;
-  const int t = threadIdx.x;
-  if (nk > kCap) {  // long row (r1 == r0 + 1 by construction)
-    T acc = T(0);
-    for (int k = k0 + t; k < k1; k += kBlock) acc += __ldg(A.vals + k) * x[__ldg(A.colind + k)];
-    double v[1] = {(double)acc};
-    block_sum<1>(v);
-    if (t == 0) y[r0] = (T)v[0];
-    return;
-  }
-  T prod[kPerThread];
-  int col[kPerThread];
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) {
-      col[j] = __ldg(A.colind + k0 + k);
-      prod[j] = __ldg(A.vals + k0 + k);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) prod[j] = prod[j] * x[col[j]];
-  }
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) s_prod[k] = prod[j];
-  }
-  __syncthreads();
-  const int i = r0 + t;
-  if (i < r1) {
-    const int a = __ldg(A.rowptr + i) - k0, e = __ldg(A.rowptr + i + 1) - k0;
-    T s = T(0);
-    for (int k = a; k < e; ++k) s += s_prod[k];
-    y[i] = s;
-  }
-  __syncthreads();  // s_prod is reused by the next row block
-}
-
-// Stand-alone y = A x over all row blocks (cg_spmv).
-template <typename T>
-__global__ void __launch_bounds__(kBlock) spmv_kernel(Csr<T> A, const T* x, T* y) {
-  __shared__ T s_prod[kCap];
-  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock<T>(A, x, y, b, s_prod);
-}
 
 // --------------------------------------------------------------------------
 // Persistent solver launch
