@@ -87,20 +87,30 @@ WORKLOADS = {
                                  "the same matrix, plain FP64 Jacobi-PCG to 1e-8"),
     "q1aniso_1024_learned_fp64": ("q1aniso", Q1_1024, "fsai_learned", "fp64", 1e-8, 200000,
                                   "the same matrix, learned FSAI, FP64 PCG to 1e-8"),
+    "graph_spd_12m": ("graph_spd", {"n": 12_000_000, "dmax": 600, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
+                      "general sparse SPD (graph Laplacian, power-law degrees 1-223 nonzeros per row, "
+                      "70 % local / 30 % random couplings), n = 12M, nnz = 71M; FP64 Jacobi-PCG to 1e-8 "
+                      "(the sliced-ELL loop layout with long rows)"),
+    "graph_spd_2m": ("graph_spd", {"n": 2_000_000, "dmax": 600, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
+                     "the same family at n = 2M (profiling size)"),
     "batch64": ("batch", {"count": 64, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                 "the first 64 systems of the 512-system batch (profiling size)"),
     "batch512": ("batch", {"count": 512, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                  "512 systems in one launch: 2-D 5-/9-point anisotropic Laplacians, side uniform "
                  "in [32, 512], eps log-uniform in [1e-3, 1]; FP64 Jacobi-PCG to 1e-8 each"),
+    "batch512_fp32": ("batch", {"count": 512, "seed": 0}, "jacobi", "fp32_ru", 1e-8, 20000,
+                      "the same 512 systems in one launch, FP32 Jacobi-PCG with FP64 reliable "
+                      "updates to 1e-8 each"),
 }
 BATCH_GOLDEN = os.path.join(ROOT, "tests", "golden", "batch512_oracle.json")
 
 # Configurations timed beside the default workload (one rank): (label, workload,
 # steps) and the pairs compared on the same GPU (faster form, plain fp64 form).
 EXTRAS = ("poisson2d_64", "diffusion27_160_ru", "diffusion27_160_fp64", "q1aniso_1024_learned_ru",
-          "q1aniso_1024_jacobi_fp64", "batch512")
+          "q1aniso_1024_jacobi_fp64", "batch512", "batch512_fp32", "graph_spd_12m")
 EXTRA_PAIRS = (("diffusion27_160_ru", "diffusion27_160_fp64"),
-               ("q1aniso_1024_learned_ru", "q1aniso_1024_jacobi_fp64"))
+               ("q1aniso_1024_learned_ru", "q1aniso_1024_jacobi_fp64"),
+               ("batch512_fp32", "batch512"))
 
 
 def bytes_per_iter(n, nnz, precond, precision):
@@ -474,6 +484,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
     """The batched workload: every system of the batch in one cg_solve_batch per step."""
     _, kw, precond_s, precision_s, tol, maxit, desc = WORKLOADS[workload]
     precond = cg.CG_PRECOND_JACOBI if precond_s == "jacobi" else cg.CG_PRECOND_NONE
+    precision = {"fp64": cg.CG_PREC_FP64, "fp32_ir": cg.CG_PREC_FP32_IR, "fp32_ru": cg.CG_PREC_FP32_RU}[precision_s]
     params, systems = batch_systems(workload)
     import numpy as np
     import cgproblems as gen
@@ -501,7 +512,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
 
     def step():
         x_flat.zero_()
-        st, its, rels = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond)
+        st, its, rels = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond, precision)
         if st != cg.CG_OK:
             raise RuntimeError(f"batch solve failed: {cg.status_string(st)} {cg.cg_last_error(h)}")
         return its, rels, cg.cg_get_solve_info(h)
@@ -511,7 +522,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
     first_ms = (time.perf_counter() - t0) * 1e3
     for _ in range(max(0, warmup - 1)):
         step()
-    tuning = cg.cg_batch_get_tuning(h, precond)
+    tuning = cg.cg_batch_get_tuning(h, precond, precision)
 
     infos = []
     _barrier(world, torch)
@@ -537,7 +548,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
     # DRAM bytes of one launch from the committed ncu capture (a smaller batch, scaled by
     # the row-iterations processed), while the kernel sources are unchanged
     row_iters = int(sum(n_i * k_i for n_i, k_i in zip(ns, its)))
-    tr = ncu_traffic(workload, "batch")
+    tr = ncu_traffic(workload, "batch") if precision_s == "fp64" else None
     traffic = int(tr["dram_bytes_per_row_iter"] * row_iters) if tr else None
     # this kernel's own bytes: the row-iterations it performs times its bytes per row
     # and iteration as ncu measured them are the traffic; the design's algorithmic
@@ -554,7 +565,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
         for _ in range(steps):
             b_flat.copy_(bh, non_blocking=True)
             x_flat.copy_(x0h, non_blocking=True)
-            st, _, _ = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond)
+            st, _, _ = cg.cg_solve_batch(h, bs, xs, tol, maxit, precond, precision)
             if st != cg.CG_OK:
                 raise RuntimeError(f"batch solve failed: {cg.status_string(st)}")
             xh.copy_(x_flat, non_blocking=True)
@@ -567,7 +578,7 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
     # the same systems solved one after another by cg_solve (plain FP64 Jacobi-PCG,
     # one launch per system), for comparison on the same GPU
     seq = None
-    if not args.no_sequential:
+    if not args.no_sequential and precision_s == "fp64":
         handles = [cg.cg_create(A.n, *c) for A, c in zip(systems, dev_csr)]
         bsq = [b.clone() for b in bs]  # own (16-byte aligned) vectors per system
         xsq = [torch.zeros_like(b) for b in bsq]
@@ -604,8 +615,10 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
         "metric": "batched PCG time to 1e-8 rel. residual, all systems (batches/s)",
         "value": value, "unit": "batches/s", "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if precision_s == "fp64" else "f32+f64",
+        "data": "synthetic",
         "config": {"workload": workload, "description": desc, "systems": len(systems),
+                   "precision": precision_s,
                    "rows": ntot, "nnz": int(sum(A.nnz for A in systems)), "tol": tol,
                    "iters_max": max(its), "iters_sum": int(sum(its)), "row_iterations": row_iters,
                    "relres_true_max": relres, "parallelism": f"replicas{world}",
@@ -622,7 +635,9 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
                      "timed_unit": "one batched solve: the persistent batch kernel (whole launch)",
                      "loop_form": form,
                      "achieved_survey_model": achieved, "frac_survey_model": achieved / peak,
-                     "bytes_model": "sum over systems of iters x (12 nnz + 4 (n+1) + 104 n)"},
+                     "bytes_model": ("sum over systems of iters x (12 nnz + 4 (n+1) + 104 n)"
+                                     if precision_s == "fp64" else
+                                     "sum over systems of inner iters x (8 nnz + 4 (n+1) + 52 n)")},
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks.summary(),
@@ -769,7 +784,7 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
                             "nor the diagonal in the loop"}
 
     dom = None
-    if full and not args.no_dominant and not precond_s.startswith("fsai"):
+    if not args.no_dominant and not precond_s.startswith("fsai"):
         dom = dominant_kernel(h, A, precond, precision, torch, cg, dev, peak, fma_peak)
     if dom is not None:
         trd = ncu_traffic(workload + ":g_spmv", "single")
@@ -907,6 +922,9 @@ def run_extras(args, dev, torch, cg):
         if "loop" in r:
             e["loop"] = {k: r["loop"][k] for k in ("achieved_gbs", "frac", "iter_us", "loop_form",
                                                     "frac_survey_model")}
+            if "ms_per_launch" in r["roofline"]:
+                e["dominant_kernel"] = {k: r["roofline"].get(k) for k in ("kernel", "achieved", "frac",
+                                                                          "ms_per_launch", "fp64_pipe")}
         else:
             e["roofline"] = {k: r["roofline"][k] for k in ("achieved", "frac", "frac_survey_model",
                                                             "traffic")}

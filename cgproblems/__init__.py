@@ -13,6 +13,7 @@ are not reproduced; these synthetic families stand in for them):
 * ``diff3d27(N, s)``   3-D 27-point graph Laplacian, per-edge lognormal weights.
 * ``lap2d(N, p, eps)`` anisotropic 5-/9-point 2-D Laplacians (batched solves).
 * ``q1aniso(...)``     rotated-anisotropy Q1 finite elements (learned FSAI).
+* ``graph_spd(n)``     general sparse SPD: graph Laplacian with power-law degrees.
 * ``xstar(n, seed)``   exact solution, uniform in [-1, 1).
 """
 from __future__ import annotations
@@ -60,9 +61,12 @@ def _load():
         lib.gen_diff3d27_fill.argtypes = [i64, f64, u64, P, P, P]
         lib.gen_q1aniso_size.argtypes = [i64, pi64, pi64]
         lib.gen_q1aniso_fill.argtypes = [i64, f64, f64, f64, u64, P, P, P]
+        lib.gen_graph_spd_size.argtypes = [i64, i32, u64, pi64, pi64]
+        lib.gen_graph_spd_fill.argtypes = [i64, i32, u64, P, P, P]
         for name in ("gen_uniform_pm1", "gen_lap2d_size", "gen_lap2d_fill", "gen_lap3d7_size",
                      "gen_lap3d7_fill", "gen_diff3d27_size", "gen_diff3d27_fill",
-                     "gen_q1aniso_size", "gen_q1aniso_fill"):
+                     "gen_q1aniso_size", "gen_q1aniso_fill", "gen_graph_spd_size",
+                     "gen_graph_spd_fill"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -134,6 +138,16 @@ def q1aniso(s: int, sigma_a: float, theta: float, eps: float, seed: int) -> CSR:
     return _build("gen_q1aniso_size", "gen_q1aniso_fill", (s,),
                   (s, float(sigma_a), float(theta), float(eps), seed),
                   f"q1aniso_s{s}_seed{seed}")
+
+
+def graph_spd(n: int, dmax: int = 600, seed: int = 0) -> CSR:
+    """General sparse SPD matrix (no stencil structure): a weighted graph Laplacian with
+    power-law degrees (a row emits up to dmax/2 couplings, most rows have 2-6 neighbours, a
+    few hundred), 70 % of the couplings within 64 rows and 30 % to uniformly random rows,
+    diagonal (1 + s_i) times the row's coupling sum with s_i log-uniform in [1e-4, 1e-3]
+    (1 for a row without couplings)."""
+    return _build("gen_graph_spd_size", "gen_graph_spd_fill", (n, dmax, seed), (n, dmax, seed),
+                  f"graph_spd_n{n}_d{dmax}_seed{seed}")
 
 
 def xstar(n: int, seed: int) -> np.ndarray:

@@ -25,6 +25,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #define GOLDEN 0x9E3779B97F4A7C15ULL
@@ -312,4 +313,131 @@ int gen_q1aniso_fill(int64_t s, double sigma_a, double theta, double eps, uint64
       rowptr[y * s + x + 1] = (int32_t)k;
     }
   return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* General sparse SPD matrix: a weighted graph Laplacian with power-law  */
+/* degrees, plus a small diagonal shift                                 */
+/* ------------------------------------------------------------------ */
+/* Row i emits h_i = ceil(d_i / 2) edges, d_i = min(dmax, floor(2 u^(-1/1.6)))
+ * (a Pareto tail: most rows have 2-6 neighbours, a few hundreds), to partners
+ * j that are local (|j - i| <= 64) with probability 0.7 and uniform over all
+ * rows otherwise; edge weight w = 0.5 + u.  Every edge couples both of its
+ * rows (A_ij = A_ji = -w, duplicates summed), and A_ii = (1 + s_i) sum_j w_ij
+ * with s_i = 10^(-4 + u) (the shift makes the Laplacian definite; a row left
+ * without couplings gets A_ii = 1; the diagonal is always stored).  Columns are sorted within each row.  Counter
+ * layout of the stream: row i uses counters i * 1024 + c, c < 1024. */
+static int gspd_half_degree(int64_t i, int32_t dmax, uint64_t seed) {
+  const double u = u01_open0(seed, (uint64_t)i * 1024 + 1023);
+  double d = floor(2.0 * pow(u, -1.0 / 1.6));
+  if (d > (double)dmax) d = (double)dmax;
+  return (int)((d + 1.0) / 2.0);
+}
+
+/* partner of edge e of row i (i itself means no edge) */
+static int64_t gspd_partner(int64_t i, int e, int64_t n, uint64_t seed) {
+  const uint64_t c = (uint64_t)i * 1024 + 3 * (uint64_t)e;
+  int64_t j;
+  if (u01(seed, c) < 0.7)
+    j = i + (int64_t)floor((2.0 * u01(seed, c + 1) - 1.0) * 64.5);
+  else
+    j = (int64_t)floor(u01(seed, c + 1) * (double)n);
+  return (j < 0 || j >= n) ? i : j;
+}
+
+static int64_t graph_spd_build(int64_t n, int32_t dmax, uint64_t seed, int32_t* rowptr, int32_t* colind,
+                               double* vals) {
+  if (n <= 0 || n >= INT32_MAX || dmax < 2 || dmax > 600) return -1;
+  int32_t* cnt = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  if (!cnt) return -1;
+  /* pass 1: row lengths before merging */
+  for (int64_t i = 0; i < n; ++i) {
+    const int h = gspd_half_degree(i, dmax, seed);
+    for (int e = 0; e < h; ++e) {
+      const int64_t j = gspd_partner(i, e, n, seed);
+      if (j == i) continue;
+      ++cnt[i];
+      ++cnt[j];
+    }
+  }
+  int64_t* start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  if (!start) { free(cnt); return -1; }
+  start[0] = 0;
+  for (int64_t i = 0; i < n; ++i) start[i + 1] = start[i] + cnt[i] + 1; /* + the diagonal */
+  const int64_t total = start[n];
+  int32_t* col = (int32_t*)malloc(sizeof(int32_t) * (size_t)total);
+  double* w = (double*)malloc(sizeof(double) * (size_t)total);
+  if (!col || !w) { free(cnt); free(start); free(col); free(w); return -1; }
+  /* pass 2: both directions of every edge */
+  for (int64_t i = 0; i < n; ++i) cnt[i] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int h = gspd_half_degree(i, dmax, seed);
+    for (int e = 0; e < h; ++e) {
+      const int64_t j = gspd_partner(i, e, n, seed);
+      if (j == i) continue;
+      const double we = 0.5 + u01(seed, (uint64_t)i * 1024 + 3 * (uint64_t)e + 2);
+      int64_t p = start[i] + cnt[i]++;
+      col[p] = (int32_t)j;
+      w[p] = we;
+      p = start[j] + cnt[j]++;
+      col[p] = (int32_t)i;
+      w[p] = we;
+    }
+  }
+  /* per row: the diagonal slot, sort by column, merge duplicates, emit */
+  int64_t nnz = 0;
+  if (rowptr) rowptr[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t a = start[i];
+    int64_t e = a + cnt[i];
+    col[e] = (int32_t)i;
+    w[e] = 0.0;
+    ++e;
+    for (int64_t k = a + 1; k < e; ++k) { /* insertion sort by column */
+      const int32_t ck = col[k];
+      const double wk = w[k];
+      int64_t m = k - 1;
+      while (m >= a && col[m] > ck) {
+        col[m + 1] = col[m];
+        w[m + 1] = w[m];
+        --m;
+      }
+      col[m + 1] = ck;
+      w[m + 1] = wk;
+    }
+    double wsum = 0.0;
+    for (int64_t k = a; k < e; ++k) wsum += w[k];
+    const double shift = pow(10.0, -4.0 + u01(seed, (uint64_t)i * 1024 + 1022));
+    for (int64_t k = a; k < e;) {
+      int64_t m = k;
+      double ws = 0.0;
+      while (m < e && col[m] == col[k]) ws += w[m++];
+      if (colind) {
+        colind[nnz] = col[k];
+        vals[nnz] = col[k] == (int32_t)i ? (wsum > 0.0 ? (1.0 + shift) * wsum : 1.0) : -ws;
+      }
+      ++nnz;
+      k = m;
+    }
+    if (rowptr) rowptr[i + 1] = (int32_t)nnz;
+    if (nnz >= INT32_MAX) { nnz = -1; break; }
+  }
+  free(cnt);
+  free(start);
+  free(col);
+  free(w);
+  return nnz;
+}
+
+int gen_graph_spd_size(int64_t n, int32_t dmax, uint64_t seed, int64_t* n_out, int64_t* nnz) {
+  const int64_t z = graph_spd_build(n, dmax, seed, NULL, NULL, NULL);
+  if (z < 0) return -1;
+  *n_out = n;
+  *nnz = z;
+  return 0;
+}
+
+int gen_graph_spd_fill(int64_t n, int32_t dmax, uint64_t seed, int32_t* rowptr, int32_t* colind,
+                       double* vals) {
+  return graph_spd_build(n, dmax, seed, rowptr, colind, vals) < 0 ? -1 : 0;
 }

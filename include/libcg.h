@@ -217,24 +217,29 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
                           cg_handle** out);
 
 /*
- * Solve every system of a batch handle, each exactly as cg_solve would in
- * fp64 (Alg. 1 with the same stopping rule, fp64 true-residual test and
- * restarts; precision must be CG_PREC_FP64).  b[s] and x[s] (host arrays of
- * DEVICE pointers, length n[s]) are system s's rhs and initial guess /
- * solution.  One persistent cooperative kernel, captured with its gather and
- * scatter kernels in a CUDA graph (CG_OPT_LOOP_MODE 1: direct launch),
- * iterates all systems; a converged system drops out of the tile schedule.
- * The kernel variant (registers budgeted for 3, 4 or 5 resident CTAs per
- * SM) and grid size come from an autotuner that times short trial solves of
- * these systems at the first solve of each preconditioner (x is not touched
- * by the trials; the choice is kept in the handle); CG_OPT_GRID_CTAS > 0
- * forces the grid instead.  iters[s] and relres[s] (host,
- * may be NULL) receive each system's iterations and fp64 true relative
- * residual.  Returns the most severe error of any system, else
- * CG_NOT_CONVERGED if any system missed tol, else CG_OK; per-system results
- * via cg_batch_get_system.  cg_get_solve_info reports the largest iteration
- * count and residual, the grid, the device time and the modelled bytes
- * summed over systems.
+ * Solve every system of a batch handle, each exactly as cg_solve would alone
+ * (Alg. 1 with the same stopping rule, fp64 true-residual test and restarts).
+ * precision: CG_PREC_FP64; CG_PREC_FP32_IR (fp32 inner PCG on the fp32 loop
+ * matrix, fp64 residual, x += d and test per refinement step, inner tolerance
+ * CG_OPT_IR_TOL_INNER, default 1e-4); CG_PREC_FP32_RU (the same with the
+ * search direction carried over each fp64 update, default inner drop 0.1);
+ * CG_OPT_IR_MAX_OUTER caps the refinement steps of each system.  b[s] and
+ * x[s] (host arrays of DEVICE pointers, length n[s]) are system s's rhs and
+ * initial guess / solution.  One persistent cooperative kernel, captured with
+ * its gather and scatter kernels in a CUDA graph (CG_OPT_LOOP_MODE 1: direct
+ * launch), iterates all systems; a converged system drops out of the tile
+ * schedule.  The kernel variant (registers budgeted for 3, 4 or 5 resident
+ * CTAs per SM) and grid size come from an autotuner that times short trial
+ * solves of these systems at the first solve of each (preconditioner,
+ * precision kind) (x is not touched by the trials; the choice is kept in the
+ * handle); CG_OPT_GRID_CTAS > 0 forces the grid instead.  iters[s] and
+ * relres[s] (host, may be NULL) receive each system's iterations (fp64 PCG
+ * steps, or inner fp32 steps in all) and fp64 true relative residual.
+ * Returns the most severe error of any system, else CG_NOT_CONVERGED if any
+ * system missed tol, else CG_OK; per-system results via cg_batch_get_system
+ * (restarts = residual replacements in fp64, refinement steps / updates in
+ * fp32).  cg_get_solve_info reports the largest iteration count and residual,
+ * the grid, the device time and the modelled bytes summed over systems.
  */
 cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x, double tol,
                          int32_t maxit, int32_t precond, int32_t precision, int32_t* iters,
@@ -245,12 +250,13 @@ cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x,
 cg_status cg_batch_get_system(const cg_handle* h, int32_t s, int32_t* status, int32_t* iters,
                               int32_t* restarts, double* relres);
 
-/* The autotuner's record for a preconditioner: *count candidates (kernel
- * variant = resident CTAs per SM its registers are budgeted for, grid size)
- * with their trial times in ms (arrays of at least 8 entries, may be NULL),
- * and the index of the chosen candidate (-1 before the first autotuned solve). */
-cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* count, int32_t* grids,
-                              int32_t* ctas_per_sm, float* ms, int32_t* chosen);
+/* The autotuner's record for a preconditioner and precision (both fp32
+ * precisions share one record): *count candidates (kernel variant = resident
+ * CTAs per SM its registers are budgeted for, grid size) with their trial
+ * times in ms (arrays of at least 8 entries, may be NULL), and the index of
+ * the chosen candidate (-1 before the first autotuned solve). */
+cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t precision, int32_t* count,
+                              int32_t* grids, int32_t* ctas_per_sm, float* ms, int32_t* chosen);
 
 /*
  * FSAI preconditioner M^-1 = G^T G (Kolotilina & Yeremin 1993; not in the

@@ -107,7 +107,7 @@ def load(build_if_missing: bool = True):
     lib.cg_adam_step.argtypes = [P, P, P, P, i64, f32, f32, f32, f32, i32, P]
     lib.cg_solve_batch.argtypes = [P, P, P, f64, i32, i32, i32, pi32, pf64]
     lib.cg_batch_get_system.argtypes = [P, i32, pi32, pi32, pi32, pf64]
-    lib.cg_batch_get_tuning.argtypes = [P, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
+    lib.cg_batch_get_tuning.argtypes = [P, i32, i32, pi32, pi32, pi32, ctypes.POINTER(ctypes.c_float), pi32]
     for name in ("cg_create", "cg_set_stream", "cg_set_option", "cg_spmv", "cg_solve",
                  "cg_solve_host", "cg_get_solve_info", "cg_get_matrix_info", "cg_fsai_load_f32", "cg_prepare",
                  "cg_loop_spmv"):
@@ -363,12 +363,12 @@ def cg_batch_get_system(h: Handle, s: int) -> dict:
     return {"status": st.value, "iters": it.value, "restarts": rs.value, "relres": rel.value}
 
 
-def cg_batch_get_tuning(h: Handle, precond: int = CG_PRECOND_JACOBI) -> dict:
+def cg_batch_get_tuning(h: Handle, precond: int = CG_PRECOND_JACOBI, precision: int = CG_PREC_FP64) -> dict:
     cnt, chosen = ctypes.c_int32(), ctypes.c_int32()
     grids = (ctypes.c_int32 * 8)()
     per_sm = (ctypes.c_int32 * 8)()
     ms = (ctypes.c_float * 8)()
-    r = load().cg_batch_get_tuning(h.ptr, int(precond), ctypes.byref(cnt), grids, per_sm, ms,
+    r = load().cg_batch_get_tuning(h.ptr, int(precond), int(precision), ctypes.byref(cnt), grids, per_sm, ms,
                                    ctypes.byref(chosen))
     if r != CG_OK:
         raise CGError(r, cg_last_error(h))

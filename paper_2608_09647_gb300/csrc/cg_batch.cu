@@ -87,6 +87,15 @@ struct BatchParams {
   DevState* st;
   uint64_t timeout_ns;
   unsigned skip_seq;
+  // fp32 inner solves with fp64 refinement (batch_ir_kernel only)
+  const float* __restrict__ val32;     // the loop matrix values rounded to fp32
+  float *r32, *p32, *q32, *d32;        // inner residual, direction, A p, correction d
+  double* rho_k;                       // r.z before the last step of the inner solve
+  double* beta0;                       // carry factor of the inner solve being started
+  double* stopin;                      // inner stopping threshold tol_in ||r32|| (true norm)
+  int* start;                          // 1: the A and B phases begin an inner solve
+  double tol_in;
+  int max_outer, carry;
 };
 
 __device__ __forceinline__ int eff_stage(unsigned long long w, unsigned seq) {
@@ -214,6 +223,67 @@ __device__ __forceinline__ double row_spmv(const BatchParams& P, const double* _
       acc = slice_row<4>(cp + m0 * 32, vp + m0 * 32, v, acc);
     } else {
       for (int m = m0; m < w; ++m) acc = fma(ld_stream(vp + m * 32), v[ld_stream(cp + m * 32)], acc);
+    }
+  }
+  return acc;
+}
+
+// The same row sum for any value type TV, accumulator TA and gathered vector:
+// gx(j) gives the vector's entry j (the fp32 inner solves gather r + beta0 p on
+// the first iteration of an inner solve without storing that vector first).
+template <int W, typename TV, typename TA, class Gx>
+__device__ __forceinline__ TA slice_row_g(const int32_t* __restrict__ cp, const TV* __restrict__ vp, Gx gx,
+                                          TA acc) {
+  int c[W];
+  TV a[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) {
+    c[m] = ld_stream(cp + m * 32);
+    a[m] = ld_stream(vp + m * 32);
+  }
+  TA x[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) x[m] = gx(c[m]);
+#pragma unroll
+  for (int m = 0; m < W; ++m) acc = fma((TA)a[m], x[m], acc);
+  return acc;
+}
+
+template <int W, typename TV, typename TA, class Gx>
+__device__ __forceinline__ TA slice_row_dia_g(const TV* __restrict__ vp, Gx gx, int i, const SegInfo& sg, TA acc) {
+  TV a[W];
+  TA x[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) {
+    a[m] = ld_stream(vp + m * 32);
+    x[m] = gx(min(max(i + sg.delta[m], sg.lo), sg.hi));
+  }
+#pragma unroll
+  for (int m = 0; m < W; ++m) acc = fma((TA)a[m], x[m], acc);
+  return acc;
+}
+
+template <typename TV, typename TA, class Gx>
+__device__ __forceinline__ TA row_spmv_g(const BatchParams& P, const TV* __restrict__ val, int i, TA acc,
+                                         const SegInfo& sg, Gx gx) {
+  const int sl = i >> 5, lane = i & 31;
+  const int o0 = __ldg(P.soff + sl);
+  const int w = __ldg(P.soff + sl + 1) - o0;
+  const TV* vp = val + (int64_t)o0 * 32 + lane;
+  if (sg.nd) {
+    if (w == 8) return slice_row_dia_g<8, TV, TA>(vp, gx, i, sg, acc);
+    if (w == 4) return slice_row_dia_g<4, TV, TA>(vp, gx, i, sg, acc);
+    for (int m = 0; m < w; ++m) acc = fma((TA)ld_stream(vp + m * 32), gx(min(max(i + sg.delta[m], sg.lo), sg.hi)), acc);
+    return acc;
+  }
+  const int32_t* cp = P.col + (int64_t)o0 * 32 + lane;
+  if (w == 8) return slice_row_g<8, TV, TA>(cp, vp, gx, acc);
+  if (w == 4) return slice_row_g<4, TV, TA>(cp, vp, gx, acc);
+  for (int m0 = 0; m0 < w; m0 += 4) {
+    if (m0 + 4 <= w) {
+      acc = slice_row_g<4, TV, TA>(cp + m0 * 32, vp + m0 * 32, gx, acc);
+    } else {
+      for (int m = m0; m < w; ++m) acc = fma((TA)ld_stream(vp + m * 32), gx(ld_stream(cp + m * 32)), acc);
     }
   }
   return acc;
@@ -536,6 +606,261 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
   }
 }
 
+// fp32 inner solves with fp64 refinement (readings R6 and R8 per system).
+// Stages beyond the fp64 kernel's: 5 = the step's x/p update is still due (C,
+// then iterating), 6 = the inner solve's last update is still due (C, then R).
+constexpr int kStCOnly = 5, kStFinalDue = 6;
+constexpr unsigned kMaskC32 = (1u << kStIter) | (1u << kStLastX) | (1u << kStRrPending) | (1u << kStCOnly) |
+                              (1u << kStFinalDue);
+
+// Every system solved as the single-system refinement solves it: R forms the
+// fp64 residual r = b^ - A^ x^ with the fp64 loop matrix, takes the true-residual
+// test and starts an inner solve on r32 = fl32(r) (d = 0; with reliable updates,
+// P.carry, the search direction carries over: p = r32 + (r32.r32 / rho_k) p_k);
+// A, B, C are the inner fp32 PCG on the fp32 loop matrix, sums in fp64, until
+// the inner residual has dropped by tol_in; the inner solve's last C phase adds
+// fl64(d + alpha p) to x^ and hands the system back to R.  The carried direction
+// is never stored before its first use: A gathers r + beta0 p at neighbouring
+// rows, and B writes p = r + beta0 p for its own rows before it updates r.
+template <bool JAC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) batch_ir_kernel(BatchParams P) {
+  constexpr int kRows = MINB <= 3 ? 4 : (MINB == 4 ? 2 : 1);
+  __shared__ int s_pref[kMaxBatch];
+  __shared__ int s_scan[kWarps];
+  __shared__ SegInfo s_seg;
+  Grid g(P.st, P.timeout_ns, P.skip_seq);
+  float* __restrict__ r = P.r32;
+  float* __restrict__ p = P.p32;
+  float* __restrict__ q = P.q32;
+  float* __restrict__ d = P.d32;
+  double* __restrict__ xh = P.xh;
+  const double* __restrict__ bh = P.bh;
+  const double* __restrict__ dg = P.dg;
+  float c_alpha = 0.0f, c_beta = 0.0f, c_beta0 = 0.0f;
+  bool c_flag = false, c_start = false;
+  int c_mode = 0;  // C phase: 0 update, 1 last update of the inner solve, 2 r.D r only
+  unsigned seq = 0;
+  for (;;) {
+    // ---- R: fp64 residual, true-residual test, start of an inner solve
+    ++seq;
+    bool alive = false;
+    int T = build_list<true>(P, kMaskR, seq, s_pref, s_scan, &alive);
+    if (!alive) break;
+    if (T > 0) {
+      run_phase<4, kRows, true>(
+          P, s_pref, T, g, s_seg, [&](int) { return true; },
+          [&](int i) {
+            const double xi = xh[i];
+            const double ax = row_spmv(P, xh, i, JAC ? xi : __ldg(dg + i) * xi, s_seg);
+            const double bi = bh[i];
+            const double ri = bi - ax;
+            const float r32 = (float)ri;
+            const double dd = JAC ? __ldg(dg + i) : 1.0;
+            return [=](double* acc) {
+              r[i] = r32;
+              d[i] = 0.0f;
+              const double rs = (double)r32;
+              acc[0] = fma(rs, rs, acc[0]);       // r32.r32: the inner rho
+              acc[1] = fma(dd * rs, rs, acc[1]);  // r32.D r32: the inner solve's reference norm
+              acc[2] = fma(dd * ri, ri, acc[2]);  // fp64 r.r
+              acc[3] = fma(dd * bi, bi, acc[3]);  // b.b
+            };
+          },
+          [&](int sys, const double* sm) {
+            const bool first = P.bb[sys] < 0.0;
+            if (first) P.bb[sys] = sm[3];
+            const double bb = P.bb[sys];
+            const double rel = bb > 0.0 ? sqrt(sm[2]) / sqrt(bb) : 0.0;
+            P.relres[sys] = rel;
+            int st = P.status[sys], next = kStDone;
+            if (bb == 0.0) {
+              st = kOk;
+              P.zero[sys] = 1;
+            } else if (st == kBreakdown || st == kNumeric) {
+              // keep: the residual was only wanted for the report
+            } else if (!isfinite(rel)) {
+              st = kNumeric;
+            } else if (rel <= P.tol) {
+              st = kOk;
+            } else if (P.k[sys] >= P.maxit || P.restarts[sys] >= P.max_outer || !(sm[0] > 0.0)) {
+              st = kNotConverged;  // out of iterations or updates (or r32 underflowed to 0)
+            } else {
+              const double rho = sm[0];
+              P.beta0[sys] = (P.carry && P.rho_k[sys] > 0.0) ? rho / P.rho_k[sys] : 0.0;
+              P.rho[sys] = rho;
+              P.rr[sys] = sm[1];
+              const double stop = P.tol_in * sqrt(sm[1]);
+              P.stopin[sys] = stop;
+              P.wrr[sys] = JAC && P.dmin[sys] * rho <= kRrMarginB * stop * stop;
+              P.start[sys] = 1;
+              P.restarts[sys] += 1;  // inner solves started (refinement steps / updates)
+              st = kStRunning;
+              next = kStIter;
+            }
+            P.status[sys] = st;
+            set_stage(P, sys, next, seq);
+          });
+      if (!g.sync()) return;
+    }
+    // ---- A: q = A p (the first step of an inner solve: p = r + beta0 p gathered), alpha
+    ++seq;
+    T = build_list<true>(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    if (T == 0) continue;
+    run_phase<1, kRows, true>(
+        P, s_pref, T, g, s_seg,
+        [&](int sys) {
+          c_start = P.start[sys] != 0;
+          c_beta0 = (float)P.beta0[sys];
+          return true;
+        },
+        [&](int i) {
+          float pi, qi;
+          const float dgi = JAC ? 1.0f : (float)__ldg(dg + i);
+          if (c_start && c_beta0 != 0.0f) {
+            const float b0 = c_beta0;
+            auto gx = [=](int j) { return fmaf(b0, p[j], r[j]); };
+            pi = gx(i);
+            qi = row_spmv_g<float, float>(P, P.val32, i, dgi * pi, s_seg, gx);
+          } else if (c_start) {
+            auto gx = [=](int j) { return r[j]; };
+            pi = r[i];
+            qi = row_spmv_g<float, float>(P, P.val32, i, dgi * pi, s_seg, gx);
+          } else {
+            auto gx = [=](int j) { return p[j]; };
+            pi = p[i];
+            qi = row_spmv_g<float, float>(P, P.val32, i, dgi * pi, s_seg, gx);
+          }
+          return [=](double* acc) {
+            q[i] = qi;
+            acc[0] = fma((double)pi, (double)qi, acc[0]);
+          };
+        },
+        [&](int sys, const double* sm) {
+          const double rho = P.rho[sys];
+          if (!isfinite(sm[0]) || !isfinite(rho) || sm[0] <= 0.0) {
+            // x^ gets the inner iterate so far (d), then R reports its true residual
+            P.status[sys] = (!isfinite(sm[0]) || !isfinite(rho)) ? kNumeric : kBreakdown;
+            P.alpha[sys] = 0.0;
+            set_stage(P, sys, kStLastX, seq);
+          } else {
+            P.alpha[sys] = rho / sm[0];
+          }
+        });
+    if (!g.sync()) return;
+    // ---- B: p = r + beta0 p at the start of an inner solve; r -= alpha q, rho', r.D r near
+    //      the band, beta, the inner test
+    ++seq;
+    T = build_list<false>(P, kMaskAB, seq, s_pref, s_scan, &alive);
+    run_phase<2, kRows, false>(
+        P, s_pref, T, g, s_seg,
+        [&](int sys) {
+          c_alpha = (float)P.alpha[sys];
+          c_flag = JAC && P.wrr[sys];
+          c_start = P.start[sys] != 0;
+          c_beta0 = (float)P.beta0[sys];
+          return true;
+        },
+        [&](int i) {
+          const float r0 = r[i];
+          const float ri = fmaf(-c_alpha, q[i], r0);
+          const bool st = c_start;
+          const float pn = st ? (c_beta0 != 0.0f ? fmaf(c_beta0, p[i], r0) : r0) : 0.0f;
+          const double di = c_flag ? __ldg(dg + i) : 0.0;
+          const bool flag = c_flag;
+          return [=](double* acc) {
+            r[i] = ri;
+            if (st) p[i] = pn;
+            const double rd = (double)ri;
+            acc[0] = fma(rd, rd, acc[0]);
+            if (flag) acc[1] = fma(di * rd, rd, acc[1]);
+          };
+        },
+        [&](int sys, const double* sm) {
+          P.start[sys] = 0;
+          const double rho = sm[0];
+          P.beta[sys] = rho / P.rho[sys];
+          P.rho_k[sys] = P.rho[sys];  // r.z of the step just taken (the carry's denominator)
+          P.rho[sys] = rho;
+          const int k = P.k[sys] + 1;
+          P.k[sys] = k;
+          const double stop = P.stopin[sys];
+          bool conv;
+          if (!JAC || P.wrr[sys]) {
+            const double rr = JAC ? sm[1] : rho;
+            P.rr[sys] = rr;
+            conv = sqrt(rr) <= stop;
+          } else {
+            conv = false;  // r.D r >= dmin r^.r^: above the band the test fails for sure
+            if (P.dmin[sys] * rho <= stop * stop) {
+              P.wrr[sys] = 1;
+              set_stage(P, sys, kStRrPending, seq);  // exact r.D r in phase C, no update yet
+              return;
+            }
+          }
+          if (JAC) P.wrr[sys] = P.dmin[sys] * rho <= kRrMarginB * stop * stop;
+          if (conv || k >= P.maxit) set_stage(P, sys, kStLastX, seq);
+        });
+    if (!g.sync()) return;
+    // ---- C: d += alpha p, p = r + beta p; the inner solve's last update x^ += fl64(d + alpha p)
+    //      (p stays the last direction); a pending exact r.D r
+    ++seq;
+    T = build_list<false>(P, kMaskC32, seq, s_pref, s_scan, &alive);
+    run_phase<1, kRows, false>(
+        P, s_pref, T, g, s_seg,
+        [&](int sys) {
+          const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
+          c_alpha = (float)P.alpha[sys];
+          c_beta = (float)P.beta[sys];
+          c_mode = (stg == kStLastX || stg == kStFinalDue) ? 1 : (stg == kStRrPending ? 2 : 0);
+          // sums (and so done()) for the r.D r pass and to move the deferred stages on
+          return stg == kStRrPending || stg == kStCOnly || stg == kStFinalDue;
+        },
+        [&](int i) {
+          const int mode = c_mode;
+          // alpha = 0 (a breakdown at an inner solve's first step): p is not read
+          const float pi = (mode != 2 && c_alpha != 0.0f) ? p[i] : 0.0f;
+          const float di = mode != 2 ? d[i] : 0.0f;
+          const float ri = mode != 1 ? r[i] : 0.0f;
+          const double xo = mode == 1 ? xh[i] : 0.0;
+          const float dn = fmaf(c_alpha, pi, di);
+          const float pn = fmaf(c_beta, pi, ri);
+          const double dgi = (JAC && mode == 2) ? __ldg(dg + i) : 0.0;
+          return [=](double* acc) {
+            if (mode == 0) {
+              d[i] = dn;
+              p[i] = pn;
+            } else if (mode == 1) {
+              xh[i] = xo + (double)dn;
+            } else {
+              const double rd = (double)ri;
+              acc[0] = fma(JAC ? dgi * rd : rd, rd, acc[0]);
+            }
+          };
+        },
+        [&](int sys, const double* sm) {
+          const int stg = eff_stage(__ldcg(P.sstate + sys), seq);
+          if (stg == kStRrPending) {
+            P.rr[sys] = sm[0];
+            const bool conv = sqrt(sm[0]) <= P.stopin[sys];
+            set_stage(P, sys, conv || P.k[sys] >= P.maxit ? kStFinalDue : kStCOnly, seq);
+          } else if (stg == kStCOnly) {
+            set_stage(P, sys, kStIter, seq);
+          } else {  // kStFinalDue: the last update is done, the fp64 residual is next
+            set_stage(P, sys, kStLastX, seq);
+          }
+        });
+    if (!g.sync()) return;
+  }
+}
+
+// Inner-solve state of every system at the start of an fp32 solve (no direction to carry yet).
+__global__ void batch_init_f32_kernel(int nsys, double* rho_k, int* start) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsys; s += gridDim.x * blockDim.x) {
+    rho_k[s] = 0.0;
+    start[s] = 0;
+  }
+}
+
 // Per-system copies into the concatenated vectors: b^ = D^-1/2 b, x^ = D^1/2 x
 // with Jacobi (b, x unchanged without); zeros on padding rows.
 __global__ void batch_gather_kernel(const double* const* b, const double* const* x, const int64_t* n,
@@ -678,13 +1003,30 @@ __global__ void batch_diag_kernel(int64_t n, int64_t npad, int64_t r0, const dou
 constexpr int kVariants = 3;
 constexpr int kVariantMinBlocks[kVariants] = {3, 4, 5};
 
-const void* batch_kernel(bool jac, int variant) {
+const void* batch_kernel(bool jac, int variant, bool f32) {
+  if (f32) {
+    switch (variant) {
+      case 0: return jac ? (const void*)batch_ir_kernel<true, 3> : (const void*)batch_ir_kernel<false, 3>;
+      case 1: return jac ? (const void*)batch_ir_kernel<true, 4> : (const void*)batch_ir_kernel<false, 4>;
+      default: return jac ? (const void*)batch_ir_kernel<true, 5> : (const void*)batch_ir_kernel<false, 5>;
+    }
+  }
   switch (variant) {
     case 0: return jac ? (const void*)batch_pcg_kernel<true, 3> : (const void*)batch_pcg_kernel<false, 3>;
     case 1: return jac ? (const void*)batch_pcg_kernel<true, 4> : (const void*)batch_pcg_kernel<false, 4>;
     default: return jac ? (const void*)batch_pcg_kernel<true, 5> : (const void*)batch_pcg_kernel<false, 5>;
   }
 }
+
+// fp32 copy of the loop matrix values (the same rounding as the single-system
+// loop: the scaled fp64 value rounded once).
+__global__ void batch_to_f32_kernel(int64_t count, const double* __restrict__ v, float* __restrict__ w) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+    w[k] = (float)v[k];
+}
+
+// The autotuner's records and the kernels: one slot per (preconditioner, precision kind).
+inline int tune_slot(bool jac, bool f32) { return (jac ? 1 : 0) + (f32 ? 2 : 0); }
 
 unsigned blocks_for(int64_t items) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 4096));
@@ -709,6 +1051,10 @@ struct BatchData {
   double* d_dmin = nullptr;        // smallest A_ii per system
   int64_t *d_n = nullptr, *d_r0 = nullptr;
   double* val[2] = {nullptr, nullptr};  // [precond]: unscaled / Jacobi-scaled
+  float* val32[2] = {nullptr, nullptr}; // fp32 copies (fp32 precisions)
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;  // inner fp32 vectors
+  double *rho_k = nullptr, *beta0 = nullptr, *stopin = nullptr;          // per system (fp32)
+  int* start = nullptr;
   double *dg = nullptr, *dsq = nullptr, *disq = nullptr;
   double *r = nullptr, *p = nullptr, *q = nullptr, *xh = nullptr, *bh = nullptr;
   double *rho = nullptr, *rr = nullptr, *bb = nullptr, *alpha = nullptr, *beta = nullptr,
@@ -722,18 +1068,19 @@ struct BatchData {
   void** host_ptrs = nullptr;      // pinned staging of those pointers (2 nsys)
   int grid_max = 0;                // co-resident CTAs of the most occupant variant
   int vmax[kVariants] = {};        // co-resident CTAs of each kernel variant
-  int grid_tuned[2] = {0, 0};      // chosen CTAs per precond (0: not yet)
-  int var_tuned[2] = {0, 0};       // chosen kernel variant per precond
-  int tune_chosen[2] = {-1, -1};   // index of the chosen candidate
-  float tune_ms[2][kMaxCand] = {}; // autotuner timings of the candidates
-  int tune_grid[2][kMaxCand] = {};
-  int tune_minb[2][kMaxCand] = {};
-  int tune_count[2] = {0, 0};
+  int grid_tuned[4] = {};          // chosen CTAs per tune_slot (0: not yet)
+  int var_tuned[4] = {};           // chosen kernel variant per tune_slot
+  int tune_chosen[4] = {-1, -1, -1, -1};  // index of the chosen candidate
+  float tune_ms[4][kMaxCand] = {}; // autotuner timings of the candidates
+  int tune_grid[4][kMaxCand] = {};
+  int tune_minb[4][kMaxCand] = {};
+  int tune_count[4] = {};
   // graph of one solve: status clear, gather, init, the persistent kernel, scatter
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int gkey_jac = -1, gkey_grid = -1, gkey_var = -1, gkey_maxit = -1, gkey_restarts = -1;
-  double gkey_tol = -1.0, gkey_timeout = -1.0;
+  int gkey_f32 = -1, gkey_carry = -1, gkey_outer = -1;
+  double gkey_tol = -1.0, gkey_timeout = -1.0, gkey_tol_in = -1.0;
   unsigned gkey_skip = 0;
   std::string graph_refused;       // why graph capture failed (then: direct launches)
   cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on
@@ -750,7 +1097,8 @@ void cgi::batch_free(BatchData* b) {
                  b->xh,       b->bh,      b->rho,      b->rr,     b->bb,   b->alpha,  b->beta,
                  b->relres,   b->k,       b->restarts, b->status, b->zero, b->sstate, b->cnt,
                  b->tpart,    (void*)b->d_b, (void*)b->d_x, b->d_gstart, b->d_ngroup, b->d_dmin, b->wrr, b->d_wcost,
-                 b->d_sdia,   b->d_sdelta};
+                 b->d_sdia,   b->d_sdelta, b->val32[0], b->val32[1], b->r32, b->p32, b->q32, b->d32,
+                 b->rho_k,    b->beta0,   b->stopin, b->start};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (b->host_ptrs) cudaFreeHost(b->host_ptrs);
@@ -811,6 +1159,29 @@ cg_status ensure_batch_vals(cg_handle* h, bool jac) {
   return CG_OK;
 }
 
+// fp32 copies of the loop matrix, the inner vectors and the per-system inner state.
+cg_status ensure_batch_f32(cg_handle* h, bool jac) {
+  BatchData* B = h->batch;
+  if (B->val32[jac]) return CG_OK;
+  const cg_status vs = ensure_batch_vals(h, jac);
+  if (vs != CG_OK) return vs;
+  const size_t ent = (size_t)std::max<int64_t>(B->entries, 32);
+  CGB_CUDA(h, cudaMalloc(&B->val32[jac], sizeof(float) * ent));
+  batch_to_f32_kernel<<<blocks_for((int64_t)ent), 256, 0, h->stream>>>((int64_t)ent, B->val[jac], B->val32[jac]);
+  CGB_CUDA(h, cudaGetLastError());
+  if (!B->r32) {
+    const size_t nv = (size_t)B->rows, ns = (size_t)B->nsys;
+    for (float** v : {&B->r32, &B->p32, &B->q32, &B->d32}) {
+      CGB_CUDA(h, cudaMalloc(v, sizeof(float) * nv));
+      CGB_CUDA(h, cudaMemsetAsync(*v, 0, sizeof(float) * nv, h->stream));
+    }
+    for (double** v : {&B->rho_k, &B->beta0, &B->stopin}) CGB_CUDA(h, cudaMalloc(v, sizeof(double) * ns));
+    CGB_CUDA(h, cudaMalloc(&B->start, sizeof(int) * ns));
+  }
+  CGB_CUDA(h, cudaStreamSynchronize(h->stream));
+  return CG_OK;
+}
+
 BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
   BatchData* B = h->batch;
   BatchParams P{};
@@ -852,6 +1223,16 @@ BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
   P.st = h->st;
   P.timeout_ns = (uint64_t)(h->timeout_ms * 1e6);
   P.skip_seq = h->skip_seq;
+  P.val32 = B->val32[jac];
+  P.r32 = B->r32;
+  P.p32 = B->p32;
+  P.q32 = B->q32;
+  P.d32 = B->d32;
+  P.rho_k = B->rho_k;
+  P.beta0 = B->beta0;
+  P.stopin = B->stopin;
+  P.start = B->start;
+  P.max_outer = h->max_outer;
   return P;
 }
 
@@ -859,9 +1240,11 @@ BatchParams make_params(cg_handle* h, bool jac, double tol, int maxit) {
 // x, reset the systems, the persistent kernel on G CTAs and (unless this is
 // an autotuner trial, which must leave x alone) the scatter of x.
 cudaError_t enqueue_solve(cg_handle* h, cudaStream_t s, bool jac, int var, int G, double tol, int maxit,
-                          bool scatter) {
+                          bool scatter, bool f32, bool carry, double tol_in) {
   BatchData* B = h->batch;
   BatchParams P = make_params(h, jac, tol, maxit);
+  P.carry = carry ? 1 : 0;
+  P.tol_in = tol_in;
   const dim3 gg(64, (unsigned)B->nsys);
   cudaError_t e = cudaMemsetAsync(h->st, 0, sizeof(DevState), s);
   if (e != cudaSuccess) return e;
@@ -869,10 +1252,11 @@ cudaError_t enqueue_solve(cg_handle* h, cudaStream_t s, bool jac, int var, int G
                                           jac ? 1 : 0, B->bh, B->xh);
   batch_init_kernel<<<blocks_for(B->nsys), 256, 0, s>>>(B->nsys, B->bb, B->k, B->restarts, B->status,
                                                          B->zero, B->wrr, B->sstate, B->cnt);
+  if (f32) batch_init_f32_kernel<<<blocks_for(B->nsys), 256, 0, s>>>(B->nsys, B->rho_k, B->start);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   void* args[] = {&P};
-  e = cudaLaunchCooperativeKernel(batch_kernel(jac, var), dim3((unsigned)G), dim3(kBlock), args, 0, s);
+  e = cudaLaunchCooperativeKernel(batch_kernel(jac, var, f32), dim3((unsigned)G), dim3(kBlock), args, 0, s);
   if (e != cudaSuccess || !scatter) return e;
   batch_scatter_kernel<<<gg, 256, 0, s>>>(B->d_x, B->d_n, B->d_r0, B->disq, jac ? 1 : 0, B->xh, B->zero);
   return cudaGetLastError();
@@ -881,11 +1265,12 @@ cudaError_t enqueue_solve(cg_handle* h, cudaStream_t s, bool jac, int var, int G
 // Run one solve (through the cached graph when use_graph) between the
 // handle's events; the device time goes to *ms.
 cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxit, bool use_graph,
-                    bool scatter, float* ms) {
+                    bool scatter, float* ms, bool f32, bool carry, double tol_in) {
   BatchData* B = h->batch;
   if (use_graph && B->graph_refused.empty()) {
     const bool same = B->gexec && B->gkey_jac == (int)jac && B->gkey_grid == G && B->gkey_var == var &&
-                      B->gkey_tol == tol &&
+                      B->gkey_tol == tol && B->gkey_f32 == (int)f32 && B->gkey_carry == (int)carry &&
+                      B->gkey_tol_in == tol_in && B->gkey_outer == h->max_outer &&
                       B->gkey_maxit == maxit && B->gkey_restarts == h->max_restarts &&
                       B->gkey_timeout == h->timeout_ms && B->gkey_skip == h->skip_seq;
     if (!same) {
@@ -898,7 +1283,7 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
       // cannot capture); the graph is then launched on the caller's stream
       if (!B->cap_stream) CGB_CUDA(h, cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
       CGB_CUDA(h, cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
-      const cudaError_t e = enqueue_solve(h, B->cap_stream, jac, var, G, tol, maxit, true);
+      const cudaError_t e = enqueue_solve(h, B->cap_stream, jac, var, G, tol, maxit, true, f32, carry, tol_in);
       cudaGraph_t graph = nullptr;
       const cudaError_t e2 = cudaStreamEndCapture(B->cap_stream, &graph);
       cudaError_t e3 = cudaSuccess;
@@ -910,7 +1295,7 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
         B->gexec = nullptr;
         cudaGetLastError();
         B->graph_refused = cudaGetErrorString(e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3));
-        return run_solve(h, jac, var, G, tol, maxit, false, scatter, ms);
+        return run_solve(h, jac, var, G, tol, maxit, false, scatter, ms, f32, carry, tol_in);
       }
       B->graph = graph;
       B->gkey_jac = jac;
@@ -921,6 +1306,10 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
       B->gkey_restarts = h->max_restarts;
       B->gkey_timeout = h->timeout_ms;
       B->gkey_skip = h->skip_seq;
+      B->gkey_f32 = f32;
+      B->gkey_carry = carry;
+      B->gkey_tol_in = tol_in;
+      B->gkey_outer = h->max_outer;
     }
     CGB_CUDA(h, cudaEventRecord(h->ev0, h->stream));
     CGB_CUDA(h, cudaGraphLaunch(B->gexec, h->stream));
@@ -929,7 +1318,7 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
   } else {
     B->ran_graph = false;
     CGB_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-    const cudaError_t e = enqueue_solve(h, h->stream, jac, var, G, tol, maxit, scatter);
+    const cudaError_t e = enqueue_solve(h, h->stream, jac, var, G, tol, maxit, scatter, f32, carry, tol_in);
     if (e != cudaSuccess)
       return bfail(h, e == cudaErrorMemoryAllocation ? CG_ERR_OOM : CG_ERR_CUDA,
                    std::string("cg_solve_batch: launch: ") + cudaGetErrorString(e));
@@ -951,7 +1340,8 @@ cg_status run_solve(cg_handle* h, bool jac, int var, int G, double tol, int maxi
 // variant at its full residency, and the 3-CTA variant at one CTA per SM.
 constexpr int kTrialIters = 40;
 
-cg_status autotune(cg_handle* h, bool jac, double tol, int maxit) {
+cg_status autotune(cg_handle* h, bool jac, double tol, int maxit, bool f32, bool carry, double tol_in) {
+  const int sl = tune_slot(jac, f32);
   BatchData* B = h->batch;
   std::vector<std::pair<int, int>> cand;  // (variant, grid)
   for (int v = 0; v < kVariants; ++v)
@@ -962,21 +1352,21 @@ cg_status autotune(cg_handle* h, bool jac, double tol, int maxit) {
   for (size_t c = 0; c < cand.size() && nt < kMaxCand; ++c) {
     float ms = 0.0f;
     const cg_status ts = run_solve(h, jac, cand[c].first, cand[c].second, tol,
-                                   std::min<int32_t>(maxit, kTrialIters), false, false, &ms);
+                                   std::min<int32_t>(maxit, kTrialIters), false, false, &ms, f32, carry, tol_in);
     if (ts != CG_OK) return ts;
-    B->tune_ms[jac][nt] = ms;
-    B->tune_grid[jac][nt] = cand[c].second;
-    B->tune_minb[jac][nt] = kVariantMinBlocks[cand[c].first];
+    B->tune_ms[sl][nt] = ms;
+    B->tune_grid[sl][nt] = cand[c].second;
+    B->tune_minb[sl][nt] = kVariantMinBlocks[cand[c].first];
     if (ms < best) {
       best = ms;
       best_i = nt;
     }
     ++nt;
   }
-  B->tune_count[jac] = nt;
-  B->tune_chosen[jac] = best_i;
-  B->var_tuned[jac] = cand[(size_t)best_i].first;
-  B->grid_tuned[jac] = cand[(size_t)best_i].second;
+  B->tune_count[sl] = nt;
+  B->tune_chosen[sl] = best_i;
+  B->var_tuned[sl] = cand[(size_t)best_i].first;
+  B->grid_tuned[sl] = cand[(size_t)best_i].second;
   return CG_OK;
 }
 
@@ -1156,10 +1546,13 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
   CGB_CREATE(cudaGetLastError());
   CGB_CREATE(cudaDeviceSynchronize());
   for (int v = 0; v < kVariants; ++v) {
-    int per_sm1 = 0, per_sm2 = 0;
-    CGB_CREATE(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm1, batch_kernel(true, v), kBlock, 0));
-    CGB_CREATE(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm2, batch_kernel(false, v), kBlock, 0));
-    B->vmax[v] = std::min(per_sm1, per_sm2) * h->sm_count;
+    int per_sm = 1 << 20;
+    for (int kind = 0; kind < 4; ++kind) {
+      int ps = 0;
+      CGB_CREATE(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, batch_kernel(kind & 1, v, kind >= 2), kBlock, 0));
+      per_sm = std::min(per_sm, ps);
+    }
+    B->vmax[v] = per_sm * h->sm_count;
     B->grid_max = std::max(B->grid_max, B->vmax[v]);
   }
 #undef CGB_CREATE
@@ -1183,8 +1576,8 @@ cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x,
     return bfail(h, CG_ERR_INVALID, "cg_solve_batch: NULL vector array, tol < 0 or maxit < 0");
   if (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)
     return bfail(h, CG_ERR_INVALID, "cg_solve_batch: unknown preconditioner");
-  if (precision != CG_PREC_FP64)
-    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: batches solve in CG_PREC_FP64 only");
+  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR && precision != CG_PREC_FP32_RU)
+    return bfail(h, CG_ERR_INVALID, "cg_solve_batch: unknown precision");
   if (h->loop_mode == 3)
     return bfail(h, CG_ERR_INVALID, "cg_solve_batch: CG_OPT_LOOP_MODE 3 (unrolled) has no batch form");
   const bool jac = precond == CG_PRECOND_JACOBI;
@@ -1194,9 +1587,13 @@ cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x,
       return bfail(h, CG_ERR_INVALID,
                    "cg_solve_batch: Jacobi needs a positive diagonal (system " + std::to_string(s) + ")");
   }
-  cg_status vs = ensure_batch_vals(h, jac);
+  const bool f32 = precision != CG_PREC_FP64;
+  const bool carry = precision == CG_PREC_FP32_RU;
+  const double tol_in = h->tol_in_set ? h->tol_in : (carry ? 0.1 : 1e-4);
+  cg_status vs = f32 ? ensure_batch_f32(h, jac) : ensure_batch_vals(h, jac);
   if (vs != CG_OK) return vs;
   const size_t ns = (size_t)B->nsys;
+  const int sl = tune_slot(jac, f32);
   // the previous solve's copies out of host_ptrs have completed (it synchronised)
   std::memcpy(B->host_ptrs, b, sizeof(void*) * ns);
   std::memcpy(B->host_ptrs + ns, x, sizeof(void*) * ns);
@@ -1208,16 +1605,16 @@ cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x,
     G = std::min(h->grid_opt, B->grid_max);
     while (var + 1 < kVariants && B->vmax[var] < G) ++var;
   } else {
-    if (B->grid_tuned[jac] == 0) {
-      const cg_status ts = autotune(h, jac, tol, maxit);
+    if (B->grid_tuned[sl] == 0) {
+      const cg_status ts = autotune(h, jac, tol, maxit, f32, carry, tol_in);
       if (ts != CG_OK) return ts;
     }
-    G = B->grid_tuned[jac];
-    var = B->var_tuned[jac];
+    G = B->grid_tuned[sl];
+    var = B->var_tuned[sl];
   }
   const bool use_graph = h->loop_mode != 1;
   float ms = 0.0f;
-  const cg_status rs = run_solve(h, jac, var, G, tol, maxit, use_graph, true, &ms);
+  const cg_status rs = run_solve(h, jac, var, G, tol, maxit, use_graph, true, &ms, f32, carry, tol_in);
   if (rs != CG_OK) return rs;
   CGB_CUDA(h, cudaMemcpyAsync(B->host_iters.data(), B->k, sizeof(int) * ns, cudaMemcpyDeviceToHost, h->stream));
   CGB_CUDA(h, cudaMemcpyAsync(B->host_restarts.data(), B->restarts, sizeof(int) * ns, cudaMemcpyDeviceToHost, h->stream));
@@ -1238,7 +1635,8 @@ cg_status cg_solve_batch(cg_handle* h, const double* const* b, double* const* x,
     relmax = std::max(relmax, B->host_relres[s]);
     const cg_handle* hs = B->sys[s];
     // the single-system traffic model per iteration: CSR matrix and the loop's vectors
-    bytes += (12 * hs->nnz + 4 * (hs->n + 1) + (jac ? 104 : 88) * hs->n) * (int64_t)k;
+    bytes += (f32 ? 8 * hs->nnz + 4 * (hs->n + 1) + (jac ? 52 : 44) * hs->n
+                  : 12 * hs->nnz + 4 * (hs->n + 1) + (jac ? 104 : 88) * hs->n) * (int64_t)k;
   }
   cg_solve_info& I = h->last;
   I.status = worst_err ? (cg_status)worst_err : (nconv ? CG_NOT_CONVERGED : CG_OK);
@@ -1269,11 +1667,13 @@ cg_status cg_batch_get_system(const cg_handle* h, int32_t s, int32_t* status, in
   return CG_OK;
 }
 
-cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t* count, int32_t* grids,
-                              int32_t* ctas_per_sm, float* ms, int32_t* chosen) {
+cg_status cg_batch_get_tuning(const cg_handle* h, int32_t precond, int32_t precision, int32_t* count,
+                              int32_t* grids, int32_t* ctas_per_sm, float* ms, int32_t* chosen) {
   if (!h || !h->batch || (precond != CG_PRECOND_NONE && precond != CG_PRECOND_JACOBI)) return CG_ERR_INVALID;
+  if (precision != CG_PREC_FP64 && precision != CG_PREC_FP32_IR && precision != CG_PREC_FP32_RU)
+    return CG_ERR_INVALID;
   const BatchData* B = h->batch;
-  const int j = precond == CG_PRECOND_JACOBI;
+  const int j = tune_slot(precond == CG_PRECOND_JACOBI, precision != CG_PREC_FP64);
   if (count) *count = B->tune_count[j];
   for (int c = 0; c < B->tune_count[j]; ++c) {
     if (grids) grids[c] = B->tune_grid[j][c];

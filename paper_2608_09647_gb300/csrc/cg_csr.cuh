@@ -6,12 +6,12 @@
 // kBlock rows; a row with more than kCapV nonzeros is a block of its own (a
 // "long" block, which the CTA strides over and reduces).  Two forms:
 //
-//  * spmv_rowblock_fma (the stand-alone kernel): the block's nonzeros are read
-//    with 16-byte loads (four column indices, two pairs of values) starting at
-//    the 16-byte boundary at or below the block's first nonzero, each value is
-//    staged in shared memory beside its gathered x, and one thread per row
-//    sums val * x over the row in storage order with fused multiply-adds: one
-//    fp64 FMA per nonzero.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
+//  * spmv_rowblock_fma (the stand-alone kernel): the block's column indices and
+//    values are copied to shared memory with 16-byte loads (four indices, two
+//    pairs of values) starting at the 16-byte boundary at or below the block's
+//    first nonzero, and one thread per row gathers x for its row and sums
+//    val * x in storage order with fused multiply-adds: one fp64 FMA per
+//    nonzero.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
 //    so a separate multiply and add per nonzero (two fp64 instructions) makes a
 //    7-point SpMV pipe-bound; with one FMA the kernel is HBM-bound.
 //  * spmv_rowblock (inside the persistent solver kernels, twice per solve):
@@ -94,11 +94,16 @@ __device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y,
 // (four nonzeros on a 16-byte boundary) per thread.
 constexpr int kQuadPasses = 2;
 static_assert((kCapV + 3 + 3) / 4 <= kQuadPasses * kBlock, "a row block's window exceeds two quads per thread");
+constexpr int kRowUnroll = 8;  // a row's nonzeros whose gathers are in flight together
 
 // One row block of y = A x with one fused multiply-add per nonzero (header
-// comment).  s_vx holds (val, x[col]) of the block's nonzeros in storage order.
+// comment).  The block's column indices and values are copied with 16-byte
+// loads into s_col / s_val at their offset from the window start a0; then the
+// thread of row i reads its row from shared memory and gathers x itself, so a
+// warp's gathers for one term cover 32 consecutive rows' neighbours (few cache
+// lines per instruction).
 __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const double* __restrict__ x,
-                                                  double* __restrict__ y, int b, double2* s_vx) {
+                                                  double* __restrict__ y, int b, int* s_col, double* s_val) {
   const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
   const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
   const int t = threadIdx.x;
@@ -110,85 +115,75 @@ __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const do
     if (t == 0) y[r0] = v[0];
     return;
   }
-  // every load of the block is issued before the first gather, every gather
-  // before the first shared-memory store
   const int a0 = A.vec ? (k0 & ~3) : k0;
   const int nq = (k1 - a0 + 3) >> 2;
-  int c[kQuadPasses][4];
-  double v[kQuadPasses][4];
+  int4 c4[kQuadPasses];
+  double2 va[kQuadPasses], vb[kQuadPasses];
 #pragma unroll
-  for (int j = 0; j < kQuadPasses; ++j) {
-    const int k = a0 + 4 * (t + j * kBlock);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      c[j][u] = 0;
-      v[j][u] = 0.0;
-    }
-    if (t + j * kBlock >= nq) continue;
+  for (int j = 0; j < kQuadPasses; ++j) {  // every load issued before the first store
+    const int qd = t + j * kBlock;
+    const int k = a0 + 4 * qd;
+    c4[j] = make_int4(0, 0, 0, 0);
+    va[j] = vb[j] = make_double2(0.0, 0.0);
+    if (qd >= nq) continue;
     if (A.vec && k + 4 <= k1) {
-      const int4 c4 = __ldg(reinterpret_cast<const int4*>(A.colind + k));
-      const double2 v01 = __ldg(reinterpret_cast<const double2*>(A.vals + k));
-      const double2 v23 = __ldg(reinterpret_cast<const double2*>(A.vals + k + 2));
-      c[j][0] = c4.x;
-      c[j][1] = c4.y;
-      c[j][2] = c4.z;
-      c[j][3] = c4.w;
-      v[j][0] = v01.x;
-      v[j][1] = v01.y;
-      v[j][2] = v23.x;
-      v[j][3] = v23.y;
-    } else {
+      c4[j] = __ldg(reinterpret_cast<const int4*>(A.colind + k));
+      va[j] = __ldg(reinterpret_cast<const double2*>(A.vals + k));
+      vb[j] = __ldg(reinterpret_cast<const double2*>(A.vals + k + 2));
+    } else {  // the ragged end of the block (or unaligned arrays): entries below k1 only
+      int c[4] = {0, 0, 0, 0};
+      double v[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int kk = k + u;
-        if (kk >= k0 && kk < k1) {
-          c[j][u] = __ldg(A.colind + kk);
-          v[j][u] = __ldg(A.vals + kk);
+      for (int u = 0; u < 4; ++u)
+        if (k + u < k1) {
+          c[u] = __ldg(A.colind + k + u);
+          v[u] = __ldg(A.vals + k + u);
         }
-      }
-    }
-  }
-  double xg[kQuadPasses][4];
-#pragma unroll
-  for (int j = 0; j < kQuadPasses; ++j) {
-    const int k = a0 + 4 * (t + j * kBlock);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = k + u;
-      xg[j][u] = (t + j * kBlock < nq && kk >= k0 && kk < k1) ? __ldg(x + c[j][u]) : 0.0;
+      c4[j] = make_int4(c[0], c[1], c[2], c[3]);
+      va[j] = make_double2(v[0], v[1]);
+      vb[j] = make_double2(v[2], v[3]);
     }
   }
 #pragma unroll
   for (int j = 0; j < kQuadPasses; ++j) {
-    const int k = a0 + 4 * (t + j * kBlock);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = k + u;
-      if (t + j * kBlock < nq && kk >= k0 && kk < k1) s_vx[kk - k0] = make_double2(v[j][u], xg[j][u]);
+    const int qd = t + j * kBlock;
+    if (qd < nq) {
+      *reinterpret_cast<int4*>(s_col + 4 * qd) = c4[j];
+      *reinterpret_cast<double2*>(s_val + 4 * qd) = va[j];
+      *reinterpret_cast<double2*>(s_val + 4 * qd + 2) = vb[j];
     }
   }
   __syncthreads();
   const int i = r0 + t;
   if (i < r1) {
-    const int a = __ldg(A.rowptr + i) - k0, e = __ldg(A.rowptr + i + 1) - k0;
+    const int a = __ldg(A.rowptr + i) - a0, e = __ldg(A.rowptr + i + 1) - a0;
     double s = 0.0;
-    for (int k = a; k < e; ++k) {
-      const double2 p = s_vx[k];
-      s = fma(p.x, p.y, s);
+    for (int k = a; k < e; k += kRowUnroll) {
+      double xv[kRowUnroll], vv[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const bool in = k + u < e;
+        vv[u] = in ? s_val[k + u] : 0.0;
+        xv[u] = in ? __ldg(x + s_col[k + u]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u)
+        if (k + u < e) s = fma(vv[u], xv[u], s);
     }
     y[i] = s;
   }
-  __syncthreads();  // s_vx is reused by the next row block
+  __syncthreads();  // s_col / s_val are reused by the next row block
 }
 
 // Stand-alone y = A x over all row blocks (cg_spmv, the graph form's residuals);
 // CTAs take blocks round-robin, so the grid works on one band of rows at a time
 // and the gathers of neighbouring rows meet in L2.  fp64 only.
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 4) spmv_kernel(Csr<T> A, const T* x, T* y) {
+__global__ void __launch_bounds__(kBlock, 6) spmv_kernel(Csr<T> A, const T* x, T* y) {
   static_assert(sizeof(T) == sizeof(double), "the stand-alone caller-CSR SpMV is fp64");
-  __shared__ double2 s_vx[kCapV];
-  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock_fma(A, x, y, b, s_vx);
+  __shared__ __align__(16) int s_col[kCap];
+  __shared__ __align__(16) double s_val[kCap];
+  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock_fma(A, x, y, b, s_col, s_val);
 }
 
 }  // namespace cg

@@ -40,6 +40,7 @@ CASES = {
     "q1aniso_1024_learned": ("q1aniso", Q1_1024, "ir", 2, 1e-8, 200000, 1e-4),
     "q1aniso_1024_learned_ru": ("q1aniso", Q1_1024, "ru", 2, 1e-8, 200000, 0.1),
     "q1aniso_1024_learned_fp64": ("q1aniso", Q1_1024, "pcg", 2, 1e-8, 200000, None),
+    "graph_spd_12m": ("graph_spd", {"n": 12_000_000, "dmax": 600, "seed": 0}, "pcg", 1, 1e-8, 20000, None),
 }
 
 
