@@ -62,6 +62,12 @@ WORKLOADS = {
                       "3-D 7-point Poisson 256^3, FP64 Jacobi-PCG to 1e-8"),
     "poisson2d_64": ("lap2d", {"N": 64}, "none", "fp64", 1e-8, 1000,
                      "2-D 5-point Poisson 64x64, FP64 CG to 1e-8"),
+    "poisson2d_96": ("lap2d", {"N": 96}, "none", "fp64", 1e-8, 5000,
+                     "2-D 5-point Poisson 96x96 (9216 rows), FP64 CG to 1e-8"),
+    "poisson2d_128": ("lap2d", {"N": 128}, "none", "fp64", 1e-8, 5000,
+                      "2-D 5-point Poisson 128x128 (16384 rows), FP64 CG to 1e-8"),
+    "poisson3d_32": ("lap3d7", {"N": 32}, "jacobi", "fp64", 1e-8, 5000,
+                     "3-D 7-point Poisson 32^3 (32768 rows), FP64 Jacobi-PCG to 1e-8"),
     "poisson3d_128": ("lap3d7", {"N": 128}, "jacobi", "fp64", 1e-8, 10000,
                       "3-D 7-point Poisson 128^3, FP64 Jacobi-PCG to 1e-8"),
     "poisson3d_192": ("lap3d7", {"N": 192}, "jacobi", "fp64", 1e-8, 10000,
@@ -93,6 +99,8 @@ WORKLOADS = {
                       "(the sliced-ELL loop layout with long rows)"),
     "graph_spd_2m": ("graph_spd", {"n": 2_000_000, "dmax": 600, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                      "the same family at n = 2M (profiling size)"),
+    "batch16": ("batch", {"count": 16, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
+                "the first 16 systems of the 512-system batch (small profiling case)"),
     "batch64": ("batch", {"count": 64, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                 "the first 64 systems of the 512-system batch (profiling size)"),
     "batch512": ("batch", {"count": 512, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
@@ -705,7 +713,7 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
     setup_ms = (time.perf_counter() - t0) * 1e3
     if st != cg.CG_OK:
         raise RuntimeError(f"cg_prepare failed: {cg.cg_last_error(h)}")
-    mode = {"auto": 0, "persistent": 1, "graph": 2, "unrolled": 3}[args.loop_mode]
+    mode = {"auto": 0, "persistent": 1, "graph": 2, "unrolled": 3, "cluster": 4}[args.loop_mode]
     assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, mode) == cg.CG_OK
     b = torch.empty_like(xs)
     assert cg.cg_spmv(h, xs, b) == cg.CG_OK        # b = A x* on the device
@@ -767,15 +775,16 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
     peak, peak_kind, fma_peak = load_peaks()
     achieved_model = kern_bytes / (kern_ms / 1e3) / 1e9
     achieved_own = own_bytes / (kern_ms / 1e3) / 1e9
-    form = {1: "persistent", 2: "graph", 3: "unrolled"}.get(infos[0][2]["loop_form"], "?")
+    form = {1: "persistent", 2: "graph", 3: "unrolled", 4: "cluster"}.get(infos[0][2]["loop_form"], "?")
     launches = sum(inf["kernel_launches"] for _, _, inf in infos)
     tr = ncu_traffic(workload, "fsai" if precond_s.startswith("fsai") else "single", form)
     loop_traffic = int(tr["dram_bytes_per_iter"] * statistics.mean(iters)) if tr else None
     loop = {"achieved_gbs": achieved_own, "frac": achieved_own / peak,
             "bytes_per_iter": infos[0][2]["kernel_bytes_per_iter"],
             "iter_us": 1e3 * kern_ms / sum(iters), "loop_form": form,
-            "timed_unit": ("the CG loop of one solve: the persistent kernel" if form == "persistent"
-                           else "the CG loop of one solve: SpMV, r-update and x/p-update kernels"),
+            "timed_unit": {"persistent": "the CG loop of one solve: the persistent kernel",
+                           "cluster": "the CG loop of one solve: one thread-block cluster kernel"}.get(
+                               form, "the CG loop of one solve: SpMV, r-update and x/p-update kernels"),
             "traffic_per_solve": loop_traffic,
             "achieved_gbs_survey_model": achieved_model, "frac_survey_model": achieved_model / peak,
             "bytes_per_iter_survey_model": kern_bytes / max(1, sum(iters)),
@@ -967,7 +976,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the other configurations timed beside the default workload")
     ap.add_argument("--extra-steps", type=int, default=3)
-    ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled"])
+    ap.add_argument("--loop-mode", default="auto", choices=["auto", "persistent", "graph", "unrolled", "cluster"])
     ap.add_argument("--grid", type=int, default=0, help="force the persistent grid (CTAs; 0 = automatic)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -73,14 +73,19 @@ typedef enum {
   CG_OPT_DEBUG_SKIP_ARRIVAL = 5,  /* fault injection: CTA 0 skips arrival at grid barrier #value
                                      (1-based; 0 = off), so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
-  CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: graph from 2^18 rows;
-                                     fp32 FSAI refinement: graph from 2^21 rows; else persistent),
-                                     1 one persistent cooperative launch, 2 CUDA graph with a
-                                     device-side WHILE node (nested WHILE nodes for fp32
-                                     refinement), 3 graphs of 8 unrolled iterations relaunched by
-                                     the host until done (fp64 Jacobi / plain CG and the fp32 FSAI
-                                     refinement; elsewhere as 2).  The Jacobi reliable-update solve
-                                     and the fp64 FSAI solve always take form 1. */
+  CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: cluster form up to
+                                     2^13 rows unless CG_OPT_GRID_CTAS is set, graph from 2^18
+                                     rows; fp32 FSAI refinement: graph
+                                     from 2^21 rows; else persistent), 1 one persistent cooperative
+                                     launch, 2 CUDA graph with a device-side WHILE node (nested
+                                     WHILE nodes for fp32 refinement), 3 graphs of 8 unrolled
+                                     iterations relaunched by the host until done (fp64 Jacobi /
+                                     plain CG and the fp32 FSAI refinement; elsewhere as 2), 4 one
+                                     thread-block cluster of up to 16 CTAs holding the whole
+                                     system in shared memory (fp64 Jacobi / plain CG, at most
+                                     32768 rows; CG_OPT_DEBUG_SKIP_ARRIVAL has no effect there).
+                                     The Jacobi reliable-update solve and the fp64 FSAI solve
+                                     always take form 1. */
 } cg_option;
 
 /* Statistics of the most recent cg_solve on a handle. */
@@ -100,7 +105,8 @@ typedef struct {
                              80 n bytes of vectors (fp64; half that in fp32) */
   double phase_ms[6];     /* with CG_OPT_PHASE_TIMERS: CTA 0 time in the SpMV, r-update and
                              x/p-update phases, each followed by its grid-barrier wait */
-  int32_t loop_form;      /* CG_OPT_LOOP_MODE form that ran: 1 persistent, 2 graph WHILE, 3 unrolled */
+  int32_t loop_form;      /* CG_OPT_LOOP_MODE form that ran: 1 persistent, 2 graph WHILE, 3 unrolled,
+                             4 cluster */
   int32_t kernel_launches;/* kernels of this library launched by the solve */
   int32_t precond_used;   /* cg_precond that ran (CG_PRECOND_FSAI without a factor runs Jacobi) */
 } cg_solve_info;

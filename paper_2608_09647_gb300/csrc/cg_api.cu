@@ -79,10 +79,12 @@ __global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
                                  const double* __restrict__ vals,
                                  const int32_t* __restrict__ ndiag,
                                  const double* __restrict__ disq,
-                                 const int32_t* __restrict__ soff, int32_t* col, T* val) {
+                                 const int32_t* __restrict__ soff, const int32_t* __restrict__ spos,
+                                 int32_t* col, T* val) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = i >> 5, l = i & 31;
+    const int64_t ps = spos ? (int64_t)spos[i] : i;  // slice position of row i
+    const int64_t s = ps >> 5, l = ps & 31;
     const int64_t base = (int64_t)soff[s] * 32 + l;
     const int w = soff[s + 1] - soff[s];
     const int len = rowptr[i + 1] - rowptr[i] - ndiag[i];
@@ -100,6 +102,26 @@ __global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
     for (; m < w; ++m) {
       if (col) col[base + (int64_t)m * 32] = (int32_t)i;
       val[base + (int64_t)m * 32] = T(0);
+    }
+  }
+}
+
+// The CSR loop layout (thread per row): row i's off-diagonal entries in
+// storage order at [lrp[i], lrp[i+1]); with SCALE the Jacobi scaling as above.
+template <typename T, bool SCALE>
+__global__ void fill_csr_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                                const double* __restrict__ vals, const double* __restrict__ disq,
+                                const int32_t* __restrict__ lrp, int32_t* col, T* val) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = lrp[i];
+    const double si = SCALE ? disq[i] : 1.0;
+    for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+      const int c = colind[k];
+      if ((int64_t)c == i) continue;
+      if (col) col[o] = c;
+      val[o] = (T)(SCALE ? vals[k] * (si * disq[c]) : vals[k]);
+      ++o;
     }
   }
 }
@@ -256,6 +278,12 @@ int max_coresident(K kernel, int sm_count) {
   return per_sm * sm_count;
 }
 
+// Loop-matrix bytes beyond the entries read once per SpMV: the row of each
+// slice position (SELL-C-sigma) or the row pointers (CSR layout).
+int64_t loop_index_bytes(const cg_handle* h) {
+  return (h->sperm ? 4 * h->n : 0) + (h->csr ? 4 * (h->n + 1) : 0);
+}
+
 // The caller's CSR for the SpMV kernels; 16-byte loads when both arrays allow them.
 Csr<double> make_csr(const cg_handle* h) {
   return Csr<double>{h->n, h->rowptr, h->colind, h->vals, h->rb, h->nrb,
@@ -367,33 +395,116 @@ cg_status ensure_offdiag(cg_handle* h) {
   std::vector<uint32_t> lmask((size_t)std::max<int64_t>(ns, 1), 0u);
   std::vector<int32_t> lrow, lptr(1, 0);
   std::vector<int32_t> width((size_t)std::max<int64_t>(ns, 1), 0);
+  std::vector<int32_t> slen((size_t)std::max<int64_t>(n, 1), 0);  // slice length of each row (0: long)
   int64_t sumw = 0, nnz_od = 0;
   int maxw = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int len = rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
+    nnz_od += len;
+    if (len > kLongRow) {
+      lrow.push_back((int32_t)i);
+      lptr.push_back(lptr.back() + len);
+    } else {
+      slen[(size_t)i] = len;
+    }
+  }
   for (int64_t s = 0; s < ns; ++s) {
     int w = 0;
-    for (int64_t i = s * 32; i < std::min<int64_t>(n, s * 32 + 32); ++i) {
-      const int len = rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
-      nnz_od += len;
-      if (len > kLongRow) {
-        lmask[(size_t)s] |= 1u << (i & 31);
-        lrow.push_back((int32_t)i);
-        lptr.push_back(lptr.back() + len);
-      } else {
-        w = std::max(w, len);
-      }
-    }
+    for (int64_t i = s * 32; i < std::min<int64_t>(n, s * 32 + 32); ++i) w = std::max(w, slen[(size_t)i]);
     width[(size_t)s] = w;
     sumw += w;
     maxw = std::max(maxw, w);
   }
   // uniform slices (offsets computed, not loaded) when that pads by <= 1/16
   const bool uniform = lrow.empty() && ns > 0 && (int64_t)maxw * ns * 16 <= sumw * 17;
+  std::vector<int32_t> perm, spos;
+  if (!uniform && n > 0) {
+    // SELL-C-sigma: within each window of kSellSigma rows, rows sorted by
+    // descending slice length (stable), so a slice's rows have similar lengths
+    perm.assign((size_t)ns * 32, (int32_t)n);  // dead positions: n
+    spos.assign((size_t)n, 0);
+    std::vector<int32_t> idx;
+    for (int64_t r0 = 0; r0 < n; r0 += kSellSigma) {
+      const int64_t r1 = std::min<int64_t>(n, r0 + kSellSigma);
+      idx.resize((size_t)(r1 - r0));
+      for (int64_t i = r0; i < r1; ++i) idx[(size_t)(i - r0)] = (int32_t)i;
+      std::stable_sort(idx.begin(), idx.end(),
+                       [&](int32_t a, int32_t b) { return slen[(size_t)a] > slen[(size_t)b]; });
+      for (int64_t k = 0; k < r1 - r0; ++k) {
+        perm[(size_t)(r0 + k)] = idx[(size_t)k];
+        spos[(size_t)idx[(size_t)k]] = (int32_t)(r0 + k);
+      }
+    }
+    sumw = 0;
+    for (int64_t s = 0; s < ns; ++s) {
+      int w = 0;
+      for (int64_t ps = s * 32; ps < s * 32 + 32; ++ps) {
+        const int32_t i = perm[(size_t)ps];
+        if (i >= n) continue;
+        w = std::max(w, slen[(size_t)i]);
+        const int len = rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
+        if (len > kLongRow) lmask[(size_t)s] |= 1u << (ps & 31);
+      }
+      width[(size_t)s] = w;
+      sumw += w;
+    }
+  } else {
+    for (int64_t s = 0; s < ns; ++s)
+      for (int64_t i = s * 32; i < std::min<int64_t>(n, s * 32 + 32); ++i) {
+        const int len = rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i];
+        if (len > kLongRow) lmask[(size_t)s] |= 1u << (i & 31);
+      }
+  }
   h->uniform_w = uniform ? maxw : -1;
+  // rows too uneven for slices even after sorting (a heavy tail of row
+  // lengths): the loop matrix becomes a CSR of the off-diagonal entries in row
+  // blocks, summed by the binned row-block kernel
+  if (!uniform && n > 0 && 32 * sumw > (int64_t)(kCsrPadLimit * (double)std::max<int64_t>(1, nnz_od - lptr.back()))) {
+    std::vector<int32_t> lrp((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i)
+      lrp[(size_t)i + 1] = lrp[(size_t)i] + (rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i]);
+    int64_t longs = 0;
+    std::vector<int32_t> lrb = build_row_blocks(lrp.data(), n, &longs);
+    h->csr = 1;
+    h->uniform_w = -1;
+    h->nslices = 0;
+    h->sell_entries = nnz_od;
+    h->nnz_od = nnz_od;
+    h->nlong = 0;
+    h->nnz_long = 0;
+    h->lnrb = (int32_t)(lrb.size() - 1);
+    const size_t nv = (size_t)std::max<int64_t>(n, 1);
+    CG_CUDA(h, cudaMalloc(&h->lrp, sizeof(int32_t) * lrp.size()));
+    CG_CUDA(h, cudaMemcpy(h->lrp, lrp.data(), sizeof(int32_t) * lrp.size(), cudaMemcpyHostToDevice));
+    CG_CUDA(h, cudaMalloc(&h->lrb, sizeof(int32_t) * lrb.size()));
+    CG_CUDA(h, cudaMemcpy(h->lrb, lrb.data(), sizeof(int32_t) * lrb.size(), cudaMemcpyHostToDevice));
+    CG_CUDA(h, cudaMalloc(&h->scol, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz_od, 4)));
+    CG_CUDA(h, cudaMalloc(&h->soff, sizeof(int32_t)));
+    CG_CUDA(h, cudaMalloc(&h->lmask, sizeof(uint32_t)));
+    CG_CUDA(h, cudaMalloc(&h->lrow, sizeof(int32_t)));
+    CG_CUDA(h, cudaMalloc(&h->lptr, sizeof(int32_t)));
+    CG_CUDA(h, cudaMemset(h->lptr, 0, sizeof(int32_t)));
+    CG_CUDA(h, cudaMalloc(&h->lcol, sizeof(int32_t)));
+    CG_CUDA(h, cudaMalloc(&h->dsq, sizeof(double) * nv));
+    CG_CUDA(h, cudaMalloc(&h->disq, sizeof(double) * nv));
+    CG_CUDA(h, cudaMalloc(&h->diag32, sizeof(float) * nv));
+    CG_CUDA(h, cudaMalloc(&h->disq32, sizeof(float) * nv));
+    diag_kernel<<<grid_for(n), 256>>>(n, h->diag, h->dsq, h->disq, h->diag32, h->disq32);
+    CG_CUDA(h, cudaGetLastError());
+    CG_CUDA(h, cudaDeviceSynchronize());
+    return CG_OK;
+  }
   int64_t off = 0;
   for (int64_t s = 0; s < ns; ++s) {
     off += uniform ? maxw : width[(size_t)s];
     if (off >= INT32_MAX / 32) return fail(h, CG_ERR_INVALID, "cg_create: padded matrix too large");
     soff[(size_t)s + 1] = (int32_t)off;
+  }
+  if (!perm.empty()) {
+    CG_CUDA(h, cudaMalloc(&h->sperm, sizeof(int32_t) * perm.size()));
+    CG_CUDA(h, cudaMemcpy(h->sperm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
+    CG_CUDA(h, cudaMalloc(&h->spos, sizeof(int32_t) * spos.size()));
+    CG_CUDA(h, cudaMemcpy(h->spos, spos.data(), sizeof(int32_t) * spos.size(), cudaMemcpyHostToDevice));
   }
   h->nslices = (int32_t)ns;
   h->sell_entries = off * 32;
@@ -406,6 +517,9 @@ cg_status ensure_offdiag(cg_handle* h) {
   CG_CUDA(h, cudaMalloc(&h->lmask, sizeof(uint32_t) * lmask.size()));
   CG_CUDA(h, cudaMemcpy(h->lmask, lmask.data(), sizeof(uint32_t) * lmask.size(), cudaMemcpyHostToDevice));
   CG_CUDA(h, cudaMalloc(&h->scol, sizeof(int32_t) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
+  // lanes without a row (past n, or dead SELL-C-sigma positions) are never filled:
+  // column 0 and value 0 keep their loads in bounds and their products zero
+  CG_CUDA(h, cudaMemset(h->scol, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
   CG_CUDA(h, cudaMalloc(&h->lrow, sizeof(int32_t) * std::max<size_t>(lrow.size(), 1)));
   CG_CUDA(h, cudaMalloc(&h->lptr, sizeof(int32_t) * lptr.size()));
   CG_CUDA(h, cudaMalloc(&h->lcol, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz_long, 1)));
@@ -434,6 +548,20 @@ cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
   const bool write_col = !h->scol_written;
   CG_CUDA(h, cudaMalloc(sval, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
   CG_CUDA(h, cudaMalloc(lval, sizeof(T) * (size_t)std::max<int64_t>(h->nnz_long, 1)));
+  if (h->csr) {
+    if (h->n > 0) {
+      if (scale)
+        fill_csr_kernel<T, true><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq, h->lrp,
+                                                          write_col ? h->scol : nullptr, *sval);
+      else
+        fill_csr_kernel<T, false><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq, h->lrp,
+                                                           write_col ? h->scol : nullptr, *sval);
+      CG_CUDA(h, cudaGetLastError());
+      CG_CUDA(h, cudaDeviceSynchronize());
+    }
+    h->scol_written = true;
+    return CG_OK;
+  }
   if (h->dia) {
     CG_CUDA(h, cudaMemset(*sval, 0, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
     if (scale)
@@ -446,19 +574,20 @@ cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
     CG_CUDA(h, cudaDeviceSynchronize());
     return CG_OK;
   }
+  CG_CUDA(h, cudaMemset(*sval, 0, sizeof(T) * (size_t)std::max<int64_t>(h->sell_entries, 1)));
   if (h->n > 0) {
     int32_t* col = write_col ? h->scol : nullptr;
     int32_t* lcol = write_col ? h->lcol : nullptr;
     if (scale) {
       fill_sell_kernel<T, true><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals,
-                                                         h->ndiag, h->disq, h->soff, col, *sval);
+                                                         h->ndiag, h->disq, h->soff, h->spos, col, *sval);
       if (h->nlong)
         fill_long_kernel<T, true><<<grid_for(h->nlong), 256>>>(h->nlong, h->lrow, h->lptr,
                                                                h->rowptr, h->colind, h->vals,
                                                                h->disq, lcol, *lval);
     } else {
       fill_sell_kernel<T, false><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals,
-                                                          h->ndiag, h->disq, h->soff, col, *sval);
+                                                          h->ndiag, h->disq, h->soff, h->spos, col, *sval);
       if (h->nlong)
         fill_long_kernel<T, false><<<grid_for(h->nlong), 256>>>(h->nlong, h->lrow, h->lptr,
                                                                 h->rowptr, h->colind, h->vals,
@@ -480,6 +609,11 @@ Sell<T> make_sell(const cg_handle* h, const T* val, const T* lval, const T* diag
   S.dia = h->dia;
   for (int m = 0; m < kMaxDiag; ++m) S.delta[m] = h->delta[m];
   S.soff = h->soff;
+  S.perm = h->sperm;
+  S.csr = h->csr;
+  S.nrb = h->lnrb;
+  S.rptr = h->lrp;
+  S.rb = h->lrb;
   S.lmask = h->lmask;
   S.col = h->scol;
   S.val = val;
@@ -521,7 +655,8 @@ void free_all(cg_handle* h) {
                  h->sval32[0], h->sval32[1], h->lval64[0], h->lval64[1], h->lval32[0],
                  h->lval32[1], h->r,         h->p,         h->q,         h->xh,
                  h->r32,       h->p32,       h->q32,       h->xh32,      h->part,
-                 h->st,        h->stage_b,   h->stage_x};
+                 h->st,        h->stage_b,   h->stage_x,   h->sperm,     h->spos,
+                 h->lrp,       h->lrb};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->host_st) cudaFreeHost(h->host_st);
@@ -541,12 +676,13 @@ const void* spmv_kernel_w(int uw) {
     case 4: return (const void*)g_spmv<T, JAC, 4, DIA>;
     case 6: return (const void*)g_spmv<T, JAC, 6, DIA>;
     case 8: return (const void*)g_spmv<T, JAC, 8, DIA>;
-    case 26: return DIA ? (const void*)g_spmv_wide<T, JAC, 26, true> : (const void*)g_spmv<T, JAC, 0, false>;
-    default: return (const void*)g_spmv<T, JAC, 0, false>;
+    case 26: return DIA ? (const void*)g_spmv_wide<T, JAC, 26, true> : (const void*)g_spmv_gen<T, JAC>;
+    default: return (const void*)g_spmv_gen<T, JAC>;
   }
 }
 template <typename T>
-const void* spmv_kernel_for(int uw, bool dia, bool jac) {
+const void* spmv_kernel_for(int uw, bool dia, bool jac, bool csr = false) {
+  if (csr) return jac ? (const void*)g_spmv_csr<T, true> : (const void*)g_spmv_csr<T, false>;
   if (jac) return dia ? spmv_kernel_w<T, true, true>(uw) : spmv_kernel_w<T, true, false>(uw);
   return dia ? spmv_kernel_w<T, false, true>(uw) : spmv_kernel_w<T, false, false>(uw);
 }
@@ -583,7 +719,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   h->graph = g;
   cudaGraphConditionalHandle ch = 0;
   if (unroll == 0) CG_CUDA(h, cudaGraphConditionalHandleCreate(&ch, g, 0, cudaGraphCondAssignDefault));
-  const void* f_spmv = spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac);
+  const void* f_spmv = spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac, h->csr != 0);
   const unsigned G = (unsigned)h->grid_graph;
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count),
                                                      h->grid_part));
@@ -672,6 +808,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
 }
 
 constexpr int64_t kGraphMinRows = 1 << 18;  // auto mode: graph loop from this many rows (fp64)
+constexpr int64_t kClusterAutoRows = 1 << 13; // auto mode: the cluster form up to this many rows (fp64)
 constexpr int kUnrollIters = 8;               // iterations per launch of the unrolled form
 
 // fp64 solve through the graph form of the loop; restarts (true residual
@@ -731,7 +868,7 @@ cg_status solve_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
   h->last.bytes_moved = (12 * nnz + 4 * (n + 1) + (jac ? 104 : 88) * n) * (int64_t)gs.k;
   const int64_t ent = h->sell_entries + h->nnz_long;
   h->last.kernel_bytes_per_iter = (h->dia ? 8 : 12) * ent + 4 * (int64_t)h->nlong + 80 * n +
-                                  (jac && h->dmin != h->dmax ? 8 : 0) * n;
+                                  (jac && h->dmin != h->dmax ? 8 : 0) * n + loop_index_bytes(h);
   if (iters_out) *iters_out = gs.k;
   if (relres_out) *relres_out = gs.relres_true;
   if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
@@ -757,7 +894,7 @@ cg_status build_graph_ir(cg_handle* h, const SolveParams& P, bool jac) {
   CG_CUDA(h, cudaGraphAddNode(&on, g, nullptr, nullptr, 0, &op));
   cudaGraph_t ob = op.conditional.phGraph_out[0];
   CG_CUDA(h, cudaGraphConditionalHandleCreate(&inner_h, ob, 0, cudaGraphCondAssignDefault));
-  const void* f_spmv = spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac);
+  const void* f_spmv = spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac, h->csr != 0);
   const unsigned G = (unsigned)h->grid_graph;
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f_spmv, h->sm_count), h->grid_part));
   GArgs ga{P, h->gs, inner_h, outer_h, Gq, G};
@@ -841,7 +978,8 @@ cg_status solve_graph_ir(cg_handle* h, const SolveParams& P, bool jac, int32_t* 
   h->last.bytes_moved = (8 * nnz + 4 * (n + 1) + (jac ? 52 : 44) * n) * (int64_t)gs.k;
   const int64_t ent = h->sell_entries + h->nnz_long;
   const int64_t cb = h->dia ? 0 : 4;
-  h->last.kernel_bytes_per_iter = (4 + cb) * ent + 4 * (int64_t)h->nlong + (with_rr ? 44 : 40) * n;
+  h->last.kernel_bytes_per_iter = (4 + cb) * ent + 4 * (int64_t)h->nlong + (with_rr ? 44 : 40) * n +
+                                  loop_index_bytes(h);
   if (iters_out) *iters_out = gs.k;
   if (relres_out) *relres_out = gs.relres_true;
   if (status < 0) return fail(h, (cg_status)status, std::string("cg_solve: ") + cg_status_string(status));
@@ -1013,7 +1151,7 @@ cg_status cg_set_option(cg_handle* h, int32_t option, double value) {
       h->timers = (int)value;
       return CG_OK;
     case CG_OPT_LOOP_MODE:
-      if (!(value == 0 || value == 1 || value == 2 || value == 3)) break;
+      if (!(value == 0 || value == 1 || value == 2 || value == 3 || value == 4)) break;
       h->loop_mode = (int)value;
       return CG_OK;
     default:
@@ -1111,6 +1249,11 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   const bool jac = precond == CG_PRECOND_JACOBI;  // FSAI runs on the unscaled matrix
   const bool fp64 = precision == CG_PREC_FP64;
   const bool carry = precision == CG_PREC_FP32_RU;  // reliable updates: persistent form only
+  // small fp64 systems: the whole loop inside one thread-block cluster (no loop matrix needed)
+  if (!fsai && fp64 &&
+      (h->loop_mode == 4 ||
+       (h->loop_mode == 0 && h->grid_opt == 0 && h->n <= kClusterAutoRows && h->n <= cgi::cluster_max_rows())))
+    return cgi::cluster_solve(h, b, x, tol, maxit, jac, iters_out, relres_out);
   cg_status s = prepare_impl(h, jac, fp64);
   if (s != CG_OK) return s;
 
@@ -1161,6 +1304,7 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   const int64_t vb = 80 + (jac && h->dmin != h->dmax ? 8 : 0);  // vector bytes per row (fp64)
   h->last.kernel_bytes_per_iter = fp64 ? (8 + cb) * ent + 4 * (int64_t)h->nlong + vb * n
                                        : (4 + cb) * ent + 4 * (int64_t)h->nlong + vb / 2 * n;
+  h->last.kernel_bytes_per_iter += loop_index_bytes(h);
   for (int j = 0; j < 6; ++j) h->last.phase_ms[j] = ds.tphase[j] * 1e-6;
   if (iters_out) *iters_out = ds.iters;
   if (relres_out) *relres_out = ds.relres_true;
@@ -1246,8 +1390,8 @@ cg_status cg_loop_spmv(cg_handle* h, int32_t precond, int32_t precision, const v
     P.V32.p = static_cast<float*>(const_cast<void*>(p));
     P.V32.q = static_cast<float*>(q);
   }
-  const void* f = fp64 ? spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac)
-                       : spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac);
+  const void* f = fp64 ? spmv_kernel_for<double>(h->uniform_w, h->dia != 0, jac, h->csr != 0)
+                       : spmv_kernel_for<float>(h->uniform_w, h->dia != 0, jac, h->csr != 0);
   const unsigned Gq = (unsigned)std::max(1, std::min(max_coresident(f, h->sm_count), h->grid_part));
   GArgs ga{P, h->gs, 0, 0, Gq, (unsigned)h->grid_graph};
   void* args[] = {&ga};
@@ -1261,7 +1405,8 @@ cg_status cg_loop_spmv(cg_handle* h, int32_t precond, int32_t precision, const v
     const int64_t ent = h->sell_entries + h->nnz_long;
     const int64_t vb = fp64 ? 8 : 4, cb = h->dia ? 0 : 4;
     *bytes_out = (vb + cb) * ent + 4 * (int64_t)h->nlong + 2 * vb * h->n +
-                 (jac ? 0 : vb * h->n);  // the stored diagonal without Jacobi
+                 (jac ? 0 : vb * h->n) +  // the stored diagonal without Jacobi
+                 loop_index_bytes(h);
   }
   return CG_OK;
 }

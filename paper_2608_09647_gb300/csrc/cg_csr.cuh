@@ -9,9 +9,9 @@
 //  * spmv_rowblock_fma (the stand-alone kernel): the block's column indices and
 //    values are copied to shared memory with 16-byte loads (four indices, two
 //    pairs of values) starting at the 16-byte boundary at or below the block's
-//    first nonzero, and one thread per row gathers x for its row and sums
-//    val * x in storage order with fused multiply-adds: one fp64 FMA per
-//    nonzero.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
+//    first nonzero; rows of at most 16 nonzeros are summed by one thread each
+//    (storage order, fused multiply-adds: one fp64 FMA per nonzero), longer
+//    rows by a warp each, and a row beyond the block cap by the whole CTA.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
 //    so a separate multiply and add per nonzero (two fp64 instructions) makes a
 //    7-point SpMV pipe-bound; with one FMA the kernel is HBM-bound.
 //  * spmv_rowblock (inside the persistent solver kernels, twice per solve):
@@ -95,15 +95,19 @@ __device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y,
 constexpr int kQuadPasses = 2;
 static_assert((kCapV + 3 + 3) / 4 <= kQuadPasses * kBlock, "a row block's window exceeds two quads per thread");
 constexpr int kRowUnroll = 8;  // a row's nonzeros whose gathers are in flight together
+constexpr int kThreadRow = 16;  // rows with more nonzeros are summed by a warp each
 
 // One row block of y = A x with one fused multiply-add per nonzero (header
 // comment).  The block's column indices and values are copied with 16-byte
-// loads into s_col / s_val at their offset from the window start a0; then the
-// thread of row i reads its row from shared memory and gathers x itself, so a
-// warp's gathers for one term cover 32 consecutive rows' neighbours (few cache
-// lines per instruction).
+// loads into s_col / s_val at their offset from the window start a0.  Rows of
+// at most kThreadRow nonzeros are then summed by their own thread, in storage
+// order, gathering x themselves (a warp's gathers for one term cover 32
+// consecutive rows' neighbours); longer rows, listed in s_med, by a warp each
+// (lanes stride over the row, a fixed xor tree joins them), so one long row
+// does not hold a warp of short ones.
 __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const double* __restrict__ x,
-                                                  double* __restrict__ y, int b, int* s_col, double* s_val) {
+                                                  double* __restrict__ y, int b, int* s_col, double* s_val,
+                                                  int* s_med, int* s_nmed) {
   const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
   const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
   const int t = threadIdx.x;
@@ -117,6 +121,7 @@ __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const do
   }
   const int a0 = A.vec ? (k0 & ~3) : k0;
   const int nq = (k1 - a0 + 3) >> 2;
+  if (t == 0) *s_nmed = 0;
   int4 c4[kQuadPasses];
   double2 va[kQuadPasses], vb[kQuadPasses];
 #pragma unroll
@@ -157,22 +162,38 @@ __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const do
   const int i = r0 + t;
   if (i < r1) {
     const int a = __ldg(A.rowptr + i) - a0, e = __ldg(A.rowptr + i + 1) - a0;
-    double s = 0.0;
-    for (int k = a; k < e; k += kRowUnroll) {
-      double xv[kRowUnroll], vv[kRowUnroll];
+    if (e - a > kThreadRow) {
+      s_med[atomicAdd(s_nmed, 1)] = i;  // a warp sums it below (the order of the list does not matter)
+    } else {
+      double s = 0.0;
+      for (int k = a; k < e; k += kRowUnroll) {
+        double xv[kRowUnroll], vv[kRowUnroll];
 #pragma unroll
-      for (int u = 0; u < kRowUnroll; ++u) {
-        const bool in = k + u < e;
-        vv[u] = in ? s_val[k + u] : 0.0;
-        xv[u] = in ? __ldg(x + s_col[k + u]) : 0.0;
+        for (int u = 0; u < kRowUnroll; ++u) {
+          const bool in = k + u < e;
+          vv[u] = in ? s_val[k + u] : 0.0;
+          xv[u] = in ? __ldg(x + s_col[k + u]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u)
+          if (k + u < e) s = fma(vv[u], xv[u], s);
       }
-#pragma unroll
-      for (int u = 0; u < kRowUnroll; ++u)
-        if (k + u < e) s = fma(vv[u], xv[u], s);
+      y[i] = s;
     }
-    y[i] = s;
   }
-  __syncthreads();  // s_col / s_val are reused by the next row block
+  __syncthreads();
+  const int nmed = *s_nmed;
+  const int lane = t & 31;
+  for (int m = t >> 5; m < nmed; m += kWarps) {
+    const int row = s_med[m];
+    const int a = __ldg(A.rowptr + row) - a0, e = __ldg(A.rowptr + row + 1) - a0;
+    double acc = 0.0;
+    for (int k = a + lane; k < e; k += 32) acc = fma(s_val[k], __ldg(x + s_col[k]), acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = acc;
+  }
+  __syncthreads();  // s_col / s_val / s_med are reused by the next row block
 }
 
 // Stand-alone y = A x over all row blocks (cg_spmv, the graph form's residuals);
@@ -183,7 +204,9 @@ __global__ void __launch_bounds__(kBlock, 6) spmv_kernel(Csr<T> A, const T* x, T
   static_assert(sizeof(T) == sizeof(double), "the stand-alone caller-CSR SpMV is fp64");
   __shared__ __align__(16) int s_col[kCap];
   __shared__ __align__(16) double s_val[kCap];
-  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock_fma(A, x, y, b, s_col, s_val);
+  __shared__ int s_med[kBlock];
+  __shared__ int s_nmed;
+  for (int b = blockIdx.x; b < A.nrb; b += gridDim.x) spmv_rowblock_fma(A, x, y, b, s_col, s_val, s_med, &s_nmed);
 }
 
 }  // namespace cg

@@ -133,6 +133,7 @@ __device__ __forceinline__ void spmv_body(const GArgs& a) {
   const LoopVecs<T>& V = vecs_of<T>(P);
   double v[1], pq[1];
   if constexpr (W > 0) v[0] = spmv_phase_w<T, JAC, W, DIA>(S, V.p, V.q, g);
+  else if constexpr (W < 0) v[0] = spmv_phase_csr<T, JAC>(S, V.p, V.q, g);
   else v[0] = spmv_phase<T, JAC>(S, V.p, V.q, g);
   if (!publish_last<1>(v, P.part + kSlotPQ * (size_t)P.pstride, g, &gs->ctr_q, pq)) return;
   if (threadIdx.x == 0) {
@@ -155,6 +156,21 @@ __global__ void __launch_bounds__(kBlock) g_spmv(GArgs a) {
 template <typename T, bool JAC, int W, bool DIA>
 __global__ void __launch_bounds__(kBlock, 4) g_spmv_wide(GArgs a) {
   spmv_body<T, JAC, W, DIA>(a);
+}
+
+// Variable-width slices (sliced ELL, SELL-C-sigma and long rows) with a budget
+// of 4 resident CTAs per SM (64 registers): the fp64 form spills below that,
+// and the loop unrolls four slice columns (kUnrollG) to keep its gathers in flight.
+template <typename T, bool JAC>
+__global__ void __launch_bounds__(kBlock, 4) g_spmv_gen(GArgs a) {
+  spmv_body<T, JAC, 0, false>(a);
+}
+
+// The CSR loop layout (W = -1): only the row-block code is compiled in, so
+// the kernel fits 6 resident CTAs per SM (the row gathers wait on memory).
+template <typename T, bool JAC>
+__global__ void __launch_bounds__(kBlock, 6) g_spmv_csr(GArgs a) {
+  spmv_body<T, JAC, -1, false>(a);
 }
 
 // The stopping decision for r.r = rr after iteration k1: fl = done | conv << 1.

@@ -26,6 +26,10 @@ void batch_free(BatchData* b);
 void fsai_free(FsaiData* f);
 void set_create_error(const std::string& msg);  // message of cg_last_error(NULL)
 cg_status ensure_offsets(cg_handle* h);         // cg_handle::offs_all, once (cg_api.cu)
+// the loop in one thread-block cluster (cg_cluster.cu): fp64 CG / Jacobi-PCG of small systems
+int64_t cluster_max_rows();
+cg_status cluster_solve(cg_handle* h, const double* b, double* x, double tol, int32_t maxit, bool jac,
+                        int32_t* iters_out, double* relres_out);
 }  // namespace cgi
 
 // Device memory owned by a handle.  The internal off-diagonal matrices and
@@ -61,6 +65,11 @@ struct cg_handle {
   int32_t* delta_dev = nullptr;
   int32_t* soff = nullptr;
   uint32_t* lmask = nullptr;
+  int32_t csr = 0;                  // 1: the loop matrix is an off-diagonal CSR in row blocks
+  int32_t *lrp = nullptr, *lrb = nullptr;  // its row pointers and row blocks
+  int32_t lnrb = 0;
+  int32_t* sperm = nullptr;         // SELL-C-sigma: row of each slice position (n = none)
+  int32_t* spos = nullptr;          // and slice position of each row
   int32_t* scol = nullptr;
   int64_t sell_entries = 0;         // padded entries (multiple of 32)
   int64_t nnz_od = 0;

@@ -38,9 +38,12 @@ namespace cg {
 
 constexpr int kLongRow = 128;              // off-diagonal entries above which a row leaves SELL
 constexpr int kUnroll = 8;                 // slice columns whose loads are issued together
+constexpr int kUnrollG = 4;                // the same in the generic (variable-width) slice loop
 constexpr double kIrTolInner = 1e-4;       // default inner tolerance: refinement (restarting)
 constexpr double kRuTolInner = 1e-1;       // default update threshold: reliable updates
 constexpr int kMaxDiag = 32;               // most distinct offsets of the diagonal (DIA) layout
+constexpr int kSellSigma = 256;            // rows sorted by length within windows of this many
+constexpr double kCsrPadLimit = 1.3;       // slices padding the entries by more: the CSR loop layout
 
 // --------------------------------------------------------------------------
 // Persistent solver launch
@@ -73,6 +76,11 @@ struct Sell {
   const int32_t* __restrict__ lptr;
   const int32_t* __restrict__ lcol;
   const T* __restrict__ lval;
+  const int32_t* __restrict__ perm;  // row at each slice position (SELL-C-sigma; n = none), or null
+  int32_t csr;                 // 1: the loop matrix is a CSR of the off-diagonal entries (col / val),
+  int32_t nrb;                 //    cut into nrb row blocks rb[] over the row pointers rptr[]
+  const int32_t* __restrict__ rptr;
+  const int32_t* __restrict__ rb;
   const T* __restrict__ dg;    // diagonal of the loop matrix (unused with Jacobi: unit diagonal)
   const T* __restrict__ dn;    // A_ii weights of the true residual norm (Jacobi)
   const T* __restrict__ disq;  // 1/sqrt(A_ii) mapping x^ back to x (Jacobi)
@@ -366,12 +374,141 @@ __device__ __forceinline__ double spmv_phase_dia(const Sell<T>& S, const T* __re
   return dot.get();
 }
 
+// The CSR loop layout (matrices whose rows are too uneven for slices): one row
+// block of q = A^ p, staged as the caller-CSR SpMV stages it (16-byte loads of
+// columns and values into shared memory), rows of at most kThreadRow entries by
+// a thread, longer ones by a warp, a row beyond the block cap by the CTA; the
+// diagonal term starts each row's sum; the row's p_i q_i goes to dot.
+template <typename T> struct Quad;
+template <> struct Quad<double> {
+  __device__ static void load(const double* v, double (&o)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(v));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(v + 2));
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+  __device__ static void store(double* s, const double (&o)[4]) {
+    reinterpret_cast<double2*>(s)[0] = make_double2(o[0], o[1]);
+    reinterpret_cast<double2*>(s)[1] = make_double2(o[2], o[3]);
+  }
+};
+template <> struct Quad<float> {
+  __device__ static void load(const float* v, float (&o)[4]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(v));
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
+  __device__ static void store(float* s, const float (&o)[4]) {
+    reinterpret_cast<float4*>(s)[0] = make_float4(o[0], o[1], o[2], o[3]);
+  }
+};
+
+template <typename T, bool JAC>
+__device__ __forceinline__ void loop_rowblock(const Sell<T>& S, const T* __restrict__ p, T* __restrict__ q, int b,
+                                              int* s_col, T* s_val, int* s_med, int* s_nmed, Acc<T>& dot) {
+  const int r0 = __ldg(S.rb + b), r1 = __ldg(S.rb + b + 1);
+  const int k0 = __ldg(S.rptr + r0), k1 = __ldg(S.rptr + r1);
+  const int t = threadIdx.x;
+  if (k1 - k0 > kCapV) {  // one long row: strided FMA, fixed tree
+    double acc = 0.0;
+    for (int k = k0 + t; k < k1; k += kBlock) acc = fma((double)__ldg(S.val + k), (double)p[__ldg(S.col + k)], acc);
+    double v[1] = {acc};
+    block_sum<1>(v);
+    if (t == 0) {
+      const T pi = p[r0];
+      const T qi = (JAC ? pi : __ldg(S.dg + r0) * pi) + (T)v[0];
+      q[r0] = qi;
+      dot.add(pi, qi);
+    }
+    return;
+  }
+  const int a0 = k0 & ~3;  // the loop arrays start on 256-byte boundaries
+  const int nq = (k1 - a0 + 3) >> 2;
+  if (t == 0) *s_nmed = 0;
+#pragma unroll
+  for (int j = 0; j < kQuadPasses; ++j) {
+    const int qd = t + j * kBlock;
+    if (qd >= nq) continue;
+    const int k = a0 + 4 * qd;
+    int c[4] = {0, 0, 0, 0};
+    T v[4] = {T(0), T(0), T(0), T(0)};
+    if (k + 4 <= k1) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(S.col + k));
+      c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+      Quad<T>::load(S.val + k, v);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k + u < k1) {
+          c[u] = __ldg(S.col + k + u);
+          v[u] = __ldg(S.val + k + u);
+        }
+    }
+    *reinterpret_cast<int4*>(s_col + 4 * qd) = make_int4(c[0], c[1], c[2], c[3]);
+    Quad<T>::store(s_val + 4 * qd, v);
+  }
+  __syncthreads();
+  const int i = r0 + t;
+  if (i < r1) {
+    const int a = __ldg(S.rptr + i) - a0, e = __ldg(S.rptr + i + 1) - a0;
+    if (e - a > kThreadRow) {
+      s_med[atomicAdd(s_nmed, 1)] = i;
+    } else {
+      const T pi = p[i];
+      T acc = JAC ? pi : __ldg(S.dg + i) * pi;
+      for (int k = a; k < e; k += kRowUnroll) {
+        T xv[kRowUnroll], vv[kRowUnroll];
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u) {
+          const bool in = k + u < e;
+          vv[u] = in ? s_val[k + u] : T(0);
+          xv[u] = in ? p[s_col[k + u]] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kRowUnroll; ++u)
+          if (k + u < e) acc = fma(vv[u], xv[u], acc);
+      }
+      q[i] = acc;
+      dot.add(pi, acc);
+    }
+  }
+  __syncthreads();
+  const int nmed = *s_nmed;
+  const int lane = t & 31;
+  for (int m = t >> 5; m < nmed; m += kWarps) {
+    const int row = s_med[m];
+    const int a = __ldg(S.rptr + row) - a0, e = __ldg(S.rptr + row + 1) - a0;
+    T acc = T(0);
+    for (int k = a + lane; k < e; k += 32) acc = fma(s_val[k], p[s_col[k]], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const T pi = p[row];
+      const T qi = (JAC ? pi : __ldg(S.dg + row) * pi) + acc;
+      q[row] = qi;
+      dot.add(pi, qi);
+    }
+  }
+  __syncthreads();  // the staging buffers are reused by the next row block
+}
+
+template <typename T, bool JAC>
+__device__ __forceinline__ double spmv_phase_csr(const Sell<T>& S, const T* __restrict__ p, T* __restrict__ q,
+                                                 const Grid& g) {
+  __shared__ __align__(16) int s_col[kCap];
+  __shared__ __align__(16) T s_val[kCap];
+  __shared__ int s_med[kBlock];
+  __shared__ int s_nmed;
+  Acc<T> dot;
+  for (int b = (int)g.cta; b < S.nrb; b += (int)g.G) loop_rowblock<T, JAC>(S, p, q, b, s_col, s_val, s_med, &s_nmed, dot);
+  return dot.get();
+}
+
 // a1 over the grid: q = A^ p and this thread's share of p.q.  Warps take
 // slices round-robin; long rows are summed by a warp each.  Uniform slices of
 // width 4, 6 or 8 go to the specialised loop.
 template <typename T, bool JAC>
 __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restrict__ p,
                                              T* __restrict__ q, const Grid& g) {
+  if (S.csr) return spmv_phase_csr<T, JAC>(S, p, q, g);
   if (S.dia) {
     if (S.uw == 4) return spmv_phase_w<T, JAC, 4, true>(S, p, q, g);
     if (S.uw == 6) return spmv_phase_w<T, JAC, 6, true>(S, p, q, g);
@@ -388,7 +525,10 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
   const int64_t n = S.n;
   Acc<T> dot;
   for (int s = gw; s < S.nslices; s += W) {
-    const int64_t i = (int64_t)s * 32 + lane;
+    // slice position -> row: with SELL-C-sigma the rows of a window are sorted
+    // by length, so one slice holds rows of similar length (little padding)
+    const int64_t pos = (int64_t)s * 32 + lane;
+    const int64_t i = S.perm ? (int64_t)__ldg(S.perm + pos) : pos;
     int o0, w;
     uint32_t lm;
     if (S.uw >= 0) {  // uniform slices: offsets are arithmetic, no metadata loads
@@ -408,21 +548,21 @@ __device__ __forceinline__ double spmv_phase(const Sell<T>& S, const T* __restri
     const int32_t* cp = S.col + (int64_t)o0 * 32 + lane;
     const T* vp = S.val + (int64_t)o0 * 32 + lane;
     T acc = JAC ? pi : dgi * pi;
-    for (int m0 = 0; m0 < w; m0 += kUnroll) {
-      int c[kUnroll];
-      T v[kUnroll], pc[kUnroll];
+    for (int m0 = 0; m0 < w; m0 += kUnrollG) {
+      int c[kUnrollG];
+      T v[kUnrollG], pc[kUnrollG];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
+      for (int u = 0; u < kUnrollG; ++u) {
         if (m0 + u < w) {
           c[u] = ld_stream(cp + (m0 + u) * 32);
           v[u] = ld_stream(vp + (m0 + u) * 32);
         }
       }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
+      for (int u = 0; u < kUnrollG; ++u)
         if (m0 + u < w) pc[u] = p[c[u]];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u)
+      for (int u = 0; u < kUnrollG; ++u)
         if (m0 + u < w) acc = fma(v[u], pc[u], acc);
     }
     if (i < n && !((lm >> lane) & 1u)) {

@@ -216,8 +216,8 @@ def test_batch_argument_checks():
     # single-system calls refuse a batch handle
     assert cg.cg_solve(B.h, bs[0], xs[0])[0] == cg.CG_ERR_INVALID
     assert cg.cg_spmv(B.h, bs[0], xs[0]) == cg.CG_ERR_INVALID
-    # fp32 refinement has no batch form; unknown preconditioner; loop mode 3
-    st, _, _ = cg.cg_solve_batch(B.h, bs, xs, 1e-8, 10, cg.CG_PRECOND_JACOBI, cg.CG_PREC_FP32_IR)
+    # unknown precision; unknown preconditioner; loop mode 3
+    st, _, _ = cg.cg_solve_batch(B.h, bs, xs, 1e-8, 10, cg.CG_PRECOND_JACOBI, 9)
     assert st == cg.CG_ERR_INVALID
     assert cg.cg_solve_batch(B.h, bs, xs, 1e-8, 10, 7)[0] == cg.CG_ERR_INVALID
     assert cg.cg_solve_batch(B.h, bs, xs, -1.0, 10)[0] == cg.CG_ERR_INVALID

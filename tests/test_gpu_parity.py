@@ -403,10 +403,15 @@ GRAPH_CASES = [
 ]
 
 
+LOOP_MODES = dict(argvalues=[1, 2, 3, 4], ids=["persistent", "graph", "unrolled", "cluster"])
+
+
 @pytest.mark.parametrize("name,make,precond,tol,maxit", GRAPH_CASES, ids=[c[0] for c in GRAPH_CASES])
-@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+@pytest.mark.parametrize("mode", **LOOP_MODES)
 def test_loop_forms_match_oracle(name, make, precond, tol, maxit, mode):
     A = make()
+    if mode == 4 and A.n > 32768:
+        pytest.skip("the cluster form holds at most 32768 rows")
     b = oracle.spmv(A, gen.xstar(A.n, 6))
     ref = oracle.pcg(A, b, tol=tol, maxit=maxit, precond=precond)
     st, it, rel, x, info = solve_mode(A, b, tol, maxit, precond, mode)
@@ -418,7 +423,7 @@ def test_loop_forms_match_oracle(name, make, precond, tol, maxit, mode):
     assert np.linalg.norm(x - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+@pytest.mark.parametrize("mode", **LOOP_MODES)
 def test_loop_form_edge_cases(mode):
     A = gen.lap2d(24)
     xs = gen.xstar(A.n, 3)
@@ -444,7 +449,7 @@ def test_loop_form_edge_cases(mode):
     assert st == cg.CG_ERR_NUMERIC
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3], ids=["persistent", "graph", "unrolled"])
+@pytest.mark.parametrize("mode", **LOOP_MODES)
 def test_residual_replacement_restarts_match_oracle(mode):
     """A tolerance below what fp64 can attain: the recursive residual passes while the
     true residual stagnates, so the solve restarts from x (reading R3) until the restarts
@@ -514,3 +519,24 @@ def test_reliable_updates_match_oracle(name, make, precond):
     x2 = torch.zeros_like(bd)
     st2, it_ir, _ = cg.cg_solve(h, bd, x2, tol, 100000, precond, cg.CG_PREC_FP32_IR)
     assert st2 == cg.CG_OK and it < it_ir
+
+
+def test_cluster_form_is_chosen_for_small_systems_and_refuses_large_ones():
+    """Automatic loop form: the 64 x 64 Poisson system (4096 rows) runs in one thread-block
+    cluster; forcing the cluster form beyond its 32768 rows is refused."""
+    A = gen.lap2d(64)
+    b = oracle.spmv(A, gen.xstar(A.n, 0))
+    st, it, rel, x, info = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE)
+    assert st == cg.CG_OK and info["loop_form"] == 4 and info["kernel_launches"] == 1
+    ref = oracle.pcg(A, b, tol=1e-8, maxit=1000, precond=0)
+    assert abs(it - ref.iters) <= iters_band(ref.iters)
+    rp, ci, va = to_device(A)                # a grid size given: the persistent form
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_GRID_CTAS, 5) == cg.CG_OK
+    st, it2, _, _, info = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
+    assert st == cg.CG_OK and info["loop_form"] == 1 and info["grid_ctas"] == 5
+    assert abs(it2 - ref.iters) <= iters_band(ref.iters)
+    cg.cg_destroy(h)
+    B = gen.lap3d7(33)                       # 35937 rows
+    st, *_ = solve_mode(B, oracle.spmv(B, gen.xstar(B.n, 1)), 1e-8, 100, 1, 4)
+    assert st == cg.CG_ERR_INVALID
