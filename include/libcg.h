@@ -74,18 +74,19 @@ typedef enum {
                                      (1-based; 0 = off), so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
   CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: cluster form up to
-                                     2^13 rows unless CG_OPT_GRID_CTAS is set, graph from 2^18
-                                     rows; fp32 FSAI refinement: graph
-                                     from 2^21 rows; else persistent), 1 one persistent cooperative
-                                     launch, 2 CUDA graph with a device-side WHILE node (nested
-                                     WHILE nodes for fp32 refinement), 3 graphs of 8 unrolled
-                                     iterations relaunched by the host until done (fp64 Jacobi /
-                                     plain CG and the fp32 FSAI refinement; elsewhere as 2), 4 one
-                                     thread-block cluster of up to 16 CTAs holding the whole
-                                     system in shared memory (fp64 Jacobi / plain CG, at most
-                                     32768 rows; CG_OPT_DEBUG_SKIP_ARRIVAL has no effect there).
-                                     The Jacobi reliable-update solve and the fp64 FSAI solve
-                                     always take form 1. */
+                                     12288 rows unless CG_OPT_GRID_CTAS, CG_OPT_DEBUG_SKIP_ARRIVAL
+                                     or CG_OPT_PHASE_TIMERS is set, graph from 2^18 rows; fp32
+                                     FSAI refinement: graph from 2^21 rows; else persistent),
+                                     1 one persistent cooperative launch, 2 CUDA graph with a
+                                     device-side WHILE node (nested WHILE nodes for fp32
+                                     refinement), 3 graphs of 8 unrolled iterations relaunched by
+                                     the host until done (fp64 Jacobi / plain CG and the fp32
+                                     FSAI refinement; elsewhere as 2), 4 one thread-block cluster
+                                     of up to 16 CTAs holding the whole system in shared memory
+                                     (fp64 Jacobi / plain CG, at most 32768 rows; the debug and
+                                     timer options have no effect there).  The Jacobi
+                                     reliable-update solve and the fp64 FSAI solve always take
+                                     form 1. */
 } cg_option;
 
 /* Statistics of the most recent cg_solve on a handle. */

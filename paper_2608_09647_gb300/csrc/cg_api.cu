@@ -808,7 +808,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
 }
 
 constexpr int64_t kGraphMinRows = 1 << 18;  // auto mode: graph loop from this many rows (fp64)
-constexpr int64_t kClusterAutoRows = 1 << 13; // auto mode: the cluster form up to this many rows (fp64)
+constexpr int64_t kClusterAutoRows = 12288;  // auto mode: the cluster form up to this many rows (fp64)
 constexpr int kUnrollIters = 8;               // iterations per launch of the unrolled form
 
 // fp64 solve through the graph form of the loop; restarts (true residual
@@ -1252,7 +1252,8 @@ cg_status solve_impl(cg_handle* h, const double* b, double* x, double tol, int32
   // small fp64 systems: the whole loop inside one thread-block cluster (no loop matrix needed)
   if (!fsai && fp64 &&
       (h->loop_mode == 4 ||
-       (h->loop_mode == 0 && h->grid_opt == 0 && h->n <= kClusterAutoRows && h->n <= cgi::cluster_max_rows())))
+       (h->loop_mode == 0 && h->grid_opt == 0 && h->skip_seq == 0 && h->timers == 0 &&
+        h->n <= kClusterAutoRows && h->n <= cgi::cluster_max_rows())))
     return cgi::cluster_solve(h, b, x, tol, maxit, jac, iters_out, relres_out);
   cg_status s = prepare_impl(h, jac, fp64);
   if (s != CG_OK) return s;

@@ -11,8 +11,8 @@
 // stored by diagonal (a slot per offset, the gather index clamped into the
 // system's own rows, no column array), the others as SELL-32 with global
 // columns.  Every system is padded to whole 256-row tiles (padding rows are
-// identity rows with b = x = 0), so no tile spans two systems; 8 tiles form a
-// 2048-row reduction group.
+// identity rows with b = x = 0), so no tile spans two systems; 16 tiles form a
+// 4096-row reduction group.
 //
 // Schedule.  Rounds of four phases separated by bounded grid barriers:
 //   R  r = b - A x for the systems that need it (start, after their loop,
@@ -46,7 +46,7 @@ using namespace cg;
 namespace {
 
 constexpr int kTile = kBlock;        // rows per tile (kWarps slices, one per warp)
-constexpr int kGroup = 8;            // tiles per reduction group (2048 rows)
+constexpr int kGroup = 16;           // tiles per reduction group (4096 rows)
 constexpr int kMaxBatch = CG_BATCH_MAX_SYSTEMS;
 constexpr int kNP = 4;               // partial sums per (group, warp)
 constexpr int kBatchDiag = 8;        // offsets of a system in the diagonal layout, at most
@@ -290,18 +290,38 @@ __device__ __forceinline__ TA row_spmv_g(const BatchParams& P, const TV* __restr
 }
 
 // Sum of a system's (group, warp) partials in order (warp 0), given to every thread.
+// Lane l adds partials l, l + 32, ... in order; their loads go out kSumBatch at a
+// time (one L2 round trip per batch, not per partial), then an xor tree.
+constexpr int kSumBatch = 4;
 template <int NV>
 __device__ __forceinline__ void system_sum(const BatchParams& P, int sys, double (&out)[NV]) {
   __shared__ double s_out[NV];
   if (threadIdx.x < 32) {
     const int p0 = P.gstart[sys] * kWarps, np = P.ngroup[sys] * kWarps;
+    double a[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) a[j] = 0.0;
+    for (int t0 = threadIdx.x; t0 < np; t0 += 32 * kSumBatch) {
+      double v[kSumBatch][NV];
+#pragma unroll
+      for (int u = 0; u < kSumBatch; ++u) {
+        const int t = t0 + 32 * u;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[u][j] = t < np ? __ldcg(P.tpart + (size_t)(p0 + t) * kNP + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kSumBatch; ++u) {
+        if (t0 + 32 * u < np) {
+#pragma unroll
+          for (int j = 0; j < NV; ++j) a[j] += v[u][j];
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      double a = 0.0;
-      for (int t = threadIdx.x; t < np; t += 32) a += __ldcg(P.tpart + (size_t)(p0 + t) * kNP + j);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (threadIdx.x == 0) s_out[j] = a;
+      for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
+      if (threadIdx.x == 0) s_out[j] = a[j];
     }
   }
   __syncthreads();
@@ -322,16 +342,18 @@ __device__ __forceinline__ void set_stage(const BatchParams& P, int sys, int sta
 // says whether its sums are wanted.  For every row i of a group, row(i) does
 // the row's loads and arithmetic and returns its commit, which stores the
 // results and adds the row's NV contributions to the thread's accumulators.
-// A thread's rows go in groups of ROWS (4, 2 or 1, by the variant's register
+// A thread's rows go in groups of ROWS (8, 4, 2 or 1, by the variant's register
 // budget), every row's loads in flight before the first commit (a store ahead
 // of the next row's loads would serialise them); the accumulation order stays
 // the row order.  The group's sums are then reduced
 // per warp (xor tree) and stored.  Leaving a segment, the CTA adds its group count to the system's
 // counter; the CTA that completes the count sums the system's partials in
 // (group, warp) order, independent of G, and calls done(sys, sums) in thread 0.
-template <int NV, int ROWS, bool WEIGHTED, class Begin, class Row, class Done>
+// Sums NREQ.. NV-1 are reduced only while *opt holds (set by begin for the segment's system).
+template <int NV, int ROWS, bool WEIGHTED, int NREQ = NV, class Begin, class Row, class Done>
 __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pref, int T, const Grid& g,
-                                          SegInfo& seg, Begin begin, Row row, Done done) {
+                                          SegInfo& seg, Begin begin, Row row, Done done,
+                                          const bool* opt = nullptr) {
   __shared__ int s_last;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int j1 = (int)((int64_t)T * (g.cta + 1) / g.G);
@@ -364,6 +386,26 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
 #pragma unroll
       for (int k = 0; k < (NV > 0 ? NV : 1); ++k) acc[k] = 0.0;
       int gt = t0;
+      if constexpr (ROWS >= 8) {
+        for (; gt + 7 < t1; gt += 8) {
+          const auto c0 = row(gt * kTile + t);
+          const auto c1 = row((gt + 1) * kTile + t);
+          const auto c2 = row((gt + 2) * kTile + t);
+          const auto c3 = row((gt + 3) * kTile + t);
+          const auto c4 = row((gt + 4) * kTile + t);
+          const auto c5 = row((gt + 5) * kTile + t);
+          const auto c6 = row((gt + 6) * kTile + t);
+          const auto c7 = row((gt + 7) * kTile + t);
+          c0(acc);
+          c1(acc);
+          c2(acc);
+          c3(acc);
+          c4(acc);
+          c5(acc);
+          c6(acc);
+          c7(acc);
+        }
+      }
       if constexpr (ROWS >= 4) {
         for (; gt + 3 < t1; gt += 4) {
           const auto c0 = row(gt * kTile + t);
@@ -386,15 +428,21 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
       }
       for (; gt < t1; ++gt) row(gt * kTile + t)(acc);
       if (NV > 0 && sums) {
+        // each reduced sum costs 5 warp-wide fp64 adds per group: GB300's fp64 pipe
+        // takes a warp instruction in 16 clocks whatever its active lanes
+        const bool all = NREQ >= NV || (opt && *opt);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
+          if (k < NREQ || all) {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+          }
         }
         if (lane == 0) {
           double* dst = P.tpart + ((size_t)(P.gstart[sys] + grp) * kWarps + warp) * kNP;
 #pragma unroll
-          for (int k = 0; k < NV; ++k) dst[k] = acc[k];
+          for (int k = 0; k < NV; ++k)
+            if (k < NREQ || all) dst[k] = acc[k];
         }
       }
     }
@@ -426,6 +474,8 @@ template <bool JAC, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) {
   // rows in flight per thread within the register budget of MINB CTAs per SM
   constexpr int kRows = MINB <= 3 ? 4 : (MINB == 4 ? 2 : 1);
+  // phase B streams only q and r (two loads a row): twice the rows in flight
+  constexpr int kRowsB = 2 * kRows;
   __shared__ int s_pref[kMaxBatch];
   __shared__ int s_scan[kWarps];
   __shared__ SegInfo s_seg;
@@ -528,7 +578,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
     // ---- B: r -= alpha q, rho' = r^.r^, r.r when near the stopping band, beta, test
     ++seq;
     T = build_list<false>(P, kMaskAB, seq, s_pref, s_scan, &alive);
-    run_phase<2, kRows, false>(
+    run_phase<2, kRowsB, false, 1>(
         P, s_pref, T, g, s_seg,
         [&](int sys) {
           c_alpha = P.alpha[sys];
@@ -568,7 +618,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_pcg_kernel(BatchParams P) 
           }
           if (JAC) P.wrr[sys] = P.dmin[sys] * rho <= kRrMarginB * stop2;
           if (conv || k >= P.maxit) set_stage(P, sys, kStLastX, seq);
-        });
+        },
+        &c_flag);
     if (!g.sync()) return;
     // ---- C: x += alpha p; p = r + beta p unless the loop ended; pending r.D r
     ++seq;
@@ -751,7 +802,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_ir_kernel(BatchParams P) {
     //      the band, beta, the inner test
     ++seq;
     T = build_list<false>(P, kMaskAB, seq, s_pref, s_scan, &alive);
-    run_phase<2, kRows, false>(
+    run_phase<2, kRows, false, 1>(
         P, s_pref, T, g, s_seg,
         [&](int sys) {
           c_alpha = (float)P.alpha[sys];
@@ -799,7 +850,8 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_ir_kernel(BatchParams P) {
           }
           if (JAC) P.wrr[sys] = P.dmin[sys] * rho <= kRrMarginB * stop * stop;
           if (conv || k >= P.maxit) set_stage(P, sys, kStLastX, seq);
-        });
+        },
+        &c_flag);
     if (!g.sync()) return;
     // ---- C: d += alpha p, p = r + beta p; the inner solve's last update x^ += fl64(d + alpha p)
     //      (p stays the last direction); a pending exact r.D r
@@ -1507,14 +1559,14 @@ cg_status cg_batch_create(int32_t nsys, const int64_t* n, const int32_t* const* 
       ngr[s] = (B->ntile[s] + kGroup - 1) / kGroup;
       groups += ngr[s];
       dmin[s] = B->sys[s]->jacobi_ok ? B->sys[s]->dmin : 1.0;
-      // SpMV-phase cost of a row relative to a vector phase's: ~12 bytes per
-      // stored entry (W of them, padding included) and ~24 of vectors, in
-      // units of 24 bytes, rounded up
+      // SpMV-phase cost of a row: W + 2 units for W stored entries a row
+      // (padding included).  The phase is held by GB300's fp64 pipe (W fused
+      // multiply-adds, the p.q term and the reduction) about as much as by the
+      // W values (and columns) it streams; both grow as W + ~1.6
       const int64_t sl0 = (int64_t)B->tstart[s] * kWarps, sl1 = sl0 + (int64_t)B->ntile[s] * kWarps;
       const int64_t wsum = soff[(size_t)sl1] - soff[(size_t)sl0];
       const int64_t wavg = (wsum + (sl1 - sl0) - 1) / std::max<int64_t>(sl1 - sl0, 1);
-      // diagonal layout: ~8 bytes per entry (no column), else ~12
-      wc[s] = (int32_t)std::max<int64_t>(1, B->sdia[s] ? (wavg + 5) / 3 : (wavg + 3) / 2);
+      wc[s] = (int32_t)(wavg + 2);
     }
     B->ngroups = groups;
     CGB_CREATE(cudaMalloc(&B->d_gstart, sizeof(int32_t) * ns));

@@ -145,21 +145,56 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   }
 }
 
-// Fixed-order sum of per-CTA partials part[j*G + c], c < G, for j < NV.  Every
-// CTA computes the identical value (same loads, same order), so decisions
-// made from it agree across the grid without another barrier.
+// The stopping test sqrt(rr) <= stop with the square root (a ~700-clock chain
+// on GB300's fp64 pipe) taken only near the band.  stop2_hi = stop^2 (1 + 1e-12)
+// rounded exceeds stop^2, and rr above it has sqrt(rr) above stop by ~5e-13
+// relative (thousands of ulps), so the test is false without the root and the
+// decision is the one sqrt(rr) <= stop gives.  A stop whose square under- or
+// overflows (or NaN) gets stop2_hi = inf: always the exact test.
+__device__ __forceinline__ double stop2_high(double stop) {
+  const double s = stop * stop * (1.0 + 1e-12);
+  return s >= 1e-300 ? s : INFINITY;
+}
+__device__ __forceinline__ bool below_stop(double rr, double stop, double stop2_hi) {
+  return rr <= stop2_hi && sqrt(rr) <= stop;
+}
+
+// Sum of the G per-CTA partials part[j*G + c] in a fixed order (lane l of
+// warp 0 adds c = l, l + 32, ... in order, then an xor tree), given to every
+// thread.  Every CTA computes the identical value (same loads, same order), so
+// decisions made from it agree across the grid without another barrier.  Each
+// lane's loads go out kGridBatch at a time, so the sum waits for about
+// G / (32 kGridBatch) L2 round trips instead of G / 32.
 template <int NV>
 __device__ __forceinline__ void grid_sum(const double* part, unsigned G, double (&out)[NV]) {
+  constexpr int kGridBatch = NV <= 2 ? 8 : 1;  // NV > 2: the once-per-solve residual sums
   __shared__ double s_out[NV];
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
+    const unsigned lane = threadIdx.x;
+    double t[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) t[j] = 0.0;
+    for (unsigned c0 = lane; c0 < G; c0 += 32u * kGridBatch) {
+      double v[kGridBatch][NV];
+#pragma unroll
+      for (int u = 0; u < kGridBatch; ++u) {
+        const unsigned c = c0 + 32u * u;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[u][j] = c < G ? __ldcg(part + (size_t)j * G + c) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kGridBatch; ++u) {
+        if (c0 + 32u * u < G) {
+#pragma unroll
+          for (int j = 0; j < NV; ++j) t[j] += v[u][j];
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      double t = 0.0;
-      for (unsigned c = lane; c < G; c += 32) t += __ldcg(part + (size_t)j * G + c);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) s_out[j] = t;
+      for (int o = 16; o > 0; o >>= 1) t[j] += __shfl_xor_sync(0xffffffffu, t[j], o);
+      if (lane == 0) s_out[j] = t[j];
     }
   }
   __syncthreads();

@@ -262,6 +262,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
   int status = kNotConverged;
   if (sqrt(rr) <= stop_abs) status = kOk;
   bool done = sqrt(rr) <= stop_abs || k >= maxit;
+  const double stop2_hi = stop2_high(stop_abs);
   T* rc = V.r0;
   T* rn = V.r1;
   while (!done) {
@@ -305,7 +306,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     if (threadIdx.x == 0) {
       s_sc[1] = s2[0] / rho;
-      s_fl = sqrt(s2[1]) <= stop_abs;
+      s_fl = below_stop(s2[1], stop_abs, stop2_hi);
     }
     __syncthreads();
     const T beta = (T)s_sc[1];

@@ -716,6 +716,7 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
   if (rho_last) *rho_last = rho;  // r.z before the last step taken (reliable updates)
   int k = *iters;
   int status = kNotConverged;
+  const double stop2_hi = stop2_high(stop_abs);
   bool done = sqrt(rr) <= stop_abs || k >= maxit;  // a4: tested before every SpMV
   if (sqrt(rr) <= stop_abs) status = kOk;
   while (!done) {
@@ -768,7 +769,7 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
       rr = v3[0];
     }
     ++k;
-    if (threadIdx.x == 0) s_fl[1] = sqrt(rr) <= stop_abs;
+    if (threadIdx.x == 0) s_fl[1] = below_stop(rr, stop_abs, stop2_hi);
     __syncthreads();
     const bool conv = s_fl[1] != 0;
     done = conv || k >= maxit;

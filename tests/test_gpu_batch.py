@@ -6,7 +6,7 @@ max(3, 2% of iters_oracle); the true relative residual of each returned x,
 recomputed by the oracle in fp64, <= tol and equal to the reported one to 1e-6
 relative; ||x - x_oracle|| / ||x_oracle|| <= 1e-4.  The schedule (grid size, graph
 or direct launch) must not change the answer at all: each system's sums are
-formed over its own (2048-row group, warp) partials in a fixed order, so results
+formed over its own (4096-row group, warp) partials in a fixed order, so results
 are compared bit for bit.
 """
 import math

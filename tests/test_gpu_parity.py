@@ -321,6 +321,7 @@ def test_barrier_timeout_is_reported_and_context_survives():
     rp, ci, va = to_device(A)
     h = cg.cg_create(A.n, rp, ci, va)
     assert cg.cg_get_matrix_info(h)["grid_ctas"] > 1
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, 1) == cg.CG_OK   # the grid-barrier form
     assert cg.cg_set_option(h, cg.CG_OPT_BARRIER_TIMEOUT_MS, 100) == cg.CG_OK
     assert cg.cg_set_option(h, cg.CG_OPT_DEBUG_SKIP_ARRIVAL, 2) == cg.CG_OK
     st, *_ = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
@@ -519,6 +520,23 @@ def test_reliable_updates_match_oracle(name, make, precond):
     x2 = torch.zeros_like(bd)
     st2, it_ir, _ = cg.cg_solve(h, bd, x2, tol, 100000, precond, cg.CG_PREC_FP32_IR)
     assert st2 == cg.CG_OK and it < it_ir
+
+
+@pytest.mark.parametrize("make", [lambda: gen.lap2d(1), lambda: gen.lap2d(5), lambda: random_graph_spd(1000, 3, 5),
+                                  lambda: spd_from_pattern(4097, 3, long_rows=[(4096, 900)])],
+                         ids=["n1", "n25", "n1000", "n4097_long_last_row"])
+def test_cluster_form_ragged_shapes(make):
+    """The cluster form's row split (power-of-two rows per CTA, a ragged last CTA, a single
+    CTA, one row) against the oracle, Jacobi and plain CG."""
+    A = make()
+    b = oracle.spmv(A, gen.xstar(A.n, 9))
+    for precond in (0, 1):
+        ref = oracle.pcg(A, b, tol=1e-10, maxit=3000, precond=precond)
+        st, it, rel, x, info = solve_mode(A, b, 1e-10, 3000, precond, 4)
+        assert st == ref.status == cg.CG_OK and info["loop_form"] == 4
+        assert abs(it - ref.iters) <= iters_band(ref.iters), (it, ref.iters)
+        assert oracle.true_relres(A, b, x) <= 1e-10 * (1 + 1e-6)
+        assert np.linalg.norm(x - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
 
 
 def test_cluster_form_is_chosen_for_small_systems_and_refuses_large_ones():
