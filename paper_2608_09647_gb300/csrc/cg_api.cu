@@ -107,14 +107,16 @@ __global__ void fill_sell_kernel(int64_t n, const int32_t* __restrict__ rowptr,
 }
 
 // The CSR loop layout (thread per row): row i's off-diagonal entries in
-// storage order at [lrp[i], lrp[i+1]); with SCALE the Jacobi scaling as above.
+// storage order at [lrp[ps], lrp[ps+1]), ps = spos[i] its position; with
+// SCALE the Jacobi scaling as above.
 template <typename T, bool SCALE>
 __global__ void fill_csr_kernel(int64_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
                                 const double* __restrict__ vals, const double* __restrict__ disq,
-                                const int32_t* __restrict__ lrp, int32_t* col, T* val) {
+                                const int32_t* __restrict__ lrp, const int32_t* __restrict__ spos, int32_t* col,
+                                T* val) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t o = lrp[i];
+    int64_t o = lrp[spos[i]];
     const double si = SCALE ? disq[i] : 1.0;
     for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
       const int c = colind[k];
@@ -465,6 +467,38 @@ cg_status ensure_offdiag(cg_handle* h) {
       lrp[(size_t)i + 1] = lrp[(size_t)i] + (rp[(size_t)i + 1] - rp[(size_t)i] - nd[(size_t)i]);
     int64_t longs = 0;
     std::vector<int32_t> lrb = build_row_blocks(lrp.data(), n, &longs);
+    // within each row block the rows go in order of descending length (stable):
+    // a warp's rows then have similar lengths, and its fp64 FMAs, which GB300
+    // issues per warp whatever the active lanes, run only to its longest row.
+    // Blocks keep their rows and entries, so their boundaries are unchanged;
+    // perm maps a position to its row, spos a row to its position.
+    perm.assign((size_t)n, 0);
+    spos.assign((size_t)n, 0);
+    {
+      std::vector<int32_t> idx;
+      for (size_t b = 0; b + 1 < lrb.size(); ++b) {
+        const int64_t r0 = lrb[b], r1 = lrb[b + 1];
+        idx.resize((size_t)(r1 - r0));
+        for (int64_t i = r0; i < r1; ++i) idx[(size_t)(i - r0)] = (int32_t)i;
+        std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+          return lrp[(size_t)x + 1] - lrp[(size_t)x] > lrp[(size_t)y + 1] - lrp[(size_t)y];
+        });
+        for (int64_t k = 0; k < r1 - r0; ++k) {
+          perm[(size_t)(r0 + k)] = idx[(size_t)k];
+          spos[(size_t)idx[(size_t)k]] = (int32_t)(r0 + k);
+        }
+      }
+      std::vector<int32_t> prp((size_t)n + 1, 0);
+      for (int64_t ps = 0; ps < n; ++ps) {
+        const int32_t i = perm[(size_t)ps];
+        prp[(size_t)ps + 1] = prp[(size_t)ps] + (lrp[(size_t)i + 1] - lrp[(size_t)i]);
+      }
+      lrp.swap(prp);
+    }
+    CG_CUDA(h, cudaMalloc(&h->sperm, sizeof(int32_t) * perm.size()));
+    CG_CUDA(h, cudaMemcpy(h->sperm, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice));
+    CG_CUDA(h, cudaMalloc(&h->spos, sizeof(int32_t) * spos.size()));
+    CG_CUDA(h, cudaMemcpy(h->spos, spos.data(), sizeof(int32_t) * spos.size(), cudaMemcpyHostToDevice));
     h->csr = 1;
     h->uniform_w = -1;
     h->nslices = 0;
@@ -552,10 +586,10 @@ cg_status ensure_vals(cg_handle* h, T** sval, T** lval, bool scale) {
     if (h->n > 0) {
       if (scale)
         fill_csr_kernel<T, true><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq, h->lrp,
-                                                          write_col ? h->scol : nullptr, *sval);
+                                                          h->spos, write_col ? h->scol : nullptr, *sval);
       else
         fill_csr_kernel<T, false><<<grid_for(h->n), 256>>>(h->n, h->rowptr, h->colind, h->vals, h->disq, h->lrp,
-                                                           write_col ? h->scol : nullptr, *sval);
+                                                           h->spos, write_col ? h->scol : nullptr, *sval);
       CG_CUDA(h, cudaGetLastError());
       CG_CUDA(h, cudaDeviceSynchronize());
     }

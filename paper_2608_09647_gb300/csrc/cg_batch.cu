@@ -289,40 +289,39 @@ __device__ __forceinline__ TA row_spmv_g(const BatchParams& P, const TV* __restr
   return acc;
 }
 
-// Sum of a system's (group, warp) partials in order (warp 0), given to every thread.
-// Lane l adds partials l, l + 32, ... in order; their loads go out kSumBatch at a
-// time (one L2 round trip per batch, not per partial), then an xor tree.
+// Sum of a system's (group, warp) partials in a fixed order, given to every
+// thread: thread t adds partials t, t + kBlock, ... in order (its loads four at
+// a time, so the whole CTA waits for about one L2 round trip), then cta_sum0.
+// It runs in the CTA that completes the system while the others wait at the
+// next grid barrier, so its latency is the phase's tail.
 constexpr int kSumBatch = 4;
 template <int NV>
 __device__ __forceinline__ void system_sum(const BatchParams& P, int sys, double (&out)[NV]) {
   __shared__ double s_out[NV];
-  if (threadIdx.x < 32) {
-    const int p0 = P.gstart[sys] * kWarps, np = P.ngroup[sys] * kWarps;
-    double a[NV];
+  const int p0 = P.gstart[sys] * kWarps, np = P.ngroup[sys] * kWarps;
+  double a[NV];
 #pragma unroll
-    for (int j = 0; j < NV; ++j) a[j] = 0.0;
-    for (int t0 = threadIdx.x; t0 < np; t0 += 32 * kSumBatch) {
-      double v[kSumBatch][NV];
+  for (int j = 0; j < NV; ++j) a[j] = 0.0;
+  for (int t0 = threadIdx.x; t0 < np; t0 += kBlock * kSumBatch) {
+    double v[kSumBatch][NV];
 #pragma unroll
-      for (int u = 0; u < kSumBatch; ++u) {
-        const int t = t0 + 32 * u;
+    for (int u = 0; u < kSumBatch; ++u) {
+      const int t = t0 + kBlock * u;
 #pragma unroll
-        for (int j = 0; j < NV; ++j) v[u][j] = t < np ? __ldcg(P.tpart + (size_t)(p0 + t) * kNP + j) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < kSumBatch; ++u) {
-        if (t0 + 32 * u < np) {
-#pragma unroll
-          for (int j = 0; j < NV; ++j) a[j] += v[u][j];
-        }
-      }
+      for (int j = 0; j < NV; ++j) v[u][j] = t < np ? __ldcg(P.tpart + (size_t)(p0 + t) * kNP + j) : 0.0;
     }
 #pragma unroll
-    for (int j = 0; j < NV; ++j) {
+    for (int u = 0; u < kSumBatch; ++u) {
+      if (t0 + kBlock * u < np) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) a[j] += __shfl_xor_sync(0xffffffffu, a[j], o);
-      if (threadIdx.x == 0) s_out[j] = a[j];
+        for (int j = 0; j < NV; ++j) a[j] += v[u][j];
+      }
     }
+  }
+  cta_sum0<NV>(a);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s_out[j] = a[j];
   }
   __syncthreads();
 #pragma unroll

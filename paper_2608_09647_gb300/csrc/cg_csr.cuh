@@ -94,7 +94,7 @@ __device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y,
 // (four nonzeros on a 16-byte boundary) per thread.
 constexpr int kQuadPasses = 2;
 static_assert((kCapV + 3 + 3) / 4 <= kQuadPasses * kBlock, "a row block's window exceeds two quads per thread");
-constexpr int kRowUnroll = 8;  // a row's nonzeros whose gathers are in flight together
+constexpr int kRowUnroll = 4;  // a row's nonzeros whose gathers are in flight together
 constexpr int kThreadRow = 16;  // rows with more nonzeros are summed by a warp each
 
 // One row block of y = A x with one fused multiply-add per nonzero (header
@@ -160,26 +160,42 @@ __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const do
   }
   __syncthreads();
   const int i = r0 + t;
+  int a = 0, len = 0;
   if (i < r1) {
-    const int a = __ldg(A.rowptr + i) - a0, e = __ldg(A.rowptr + i + 1) - a0;
-    if (e - a > kThreadRow) {
+    a = __ldg(A.rowptr + i) - a0;
+    len = __ldg(A.rowptr + i + 1) - a0 - a;
+    if (len > kThreadRow) {
       s_med[atomicAdd(s_nmed, 1)] = i;  // a warp sums it below (the order of the list does not matter)
-    } else {
-      double s = 0.0;
-      for (int k = a; k < e; k += kRowUnroll) {
-        double xv[kRowUnroll], vv[kRowUnroll];
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u) {
-          const bool in = k + u < e;
-          vv[u] = in ? s_val[k + u] : 0.0;
-          xv[u] = in ? __ldg(x + s_col[k + u]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u)
-          if (k + u < e) s = fma(vv[u], xv[u], s);
-      }
-      y[i] = s;
+      len = -1;
     }
+  }
+  // one row a thread; the warp's FMA chain runs to its longest row (GB300 issues
+  // an fp64 warp instruction in full whatever its active lanes), each lane keeping
+  // its sum past its own row's end
+  const int wlen = __reduce_max_sync(0xffffffffu, len);
+  if (i < r1 && len >= 0) {
+    double s = 0.0;
+    int k = 0;
+    for (; k + kRowUnroll <= wlen; k += kRowUnroll) {  // kRowUnroll gathers in flight together
+      double xv[kRowUnroll], vv[kRowUnroll];
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const bool in = k + u < len;
+        vv[u] = in ? s_val[a + k + u] : 0.0;
+        xv[u] = in ? __ldg(x + s_col[a + k + u]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kRowUnroll; ++u) {
+        const double nx = fma(vv[u], xv[u], s);
+        s = k + u < len ? nx : s;
+      }
+    }
+    for (; k < wlen; ++k) {
+      const bool in = k < len;
+      const double nx = fma(in ? s_val[a + k] : 0.0, in ? __ldg(x + s_col[a + k]) : 0.0, s);
+      s = in ? nx : s;
+    }
+    y[i] = s;
   }
   __syncthreads();
   const int nmed = *s_nmed;

@@ -401,9 +401,13 @@ template <> struct Quad<float> {
   }
 };
 
+constexpr int kRowStep = 4;  // a row's gathers in flight together in the CSR loop layout
+
 template <typename T, bool JAC>
 __device__ __forceinline__ void loop_rowblock(const Sell<T>& S, const T* __restrict__ p, T* __restrict__ q, int b,
                                               int* s_col, T* s_val, int* s_med, int* s_nmed, Acc<T>& dot) {
+  // positions [r0, r1) of block b; position ps holds row S.perm[ps] (the rows of a
+  // block sorted by descending length) with entries at [rptr[ps], rptr[ps+1])
   const int r0 = __ldg(S.rb + b), r1 = __ldg(S.rb + b + 1);
   const int k0 = __ldg(S.rptr + r0), k1 = __ldg(S.rptr + r1);
   const int t = threadIdx.x;
@@ -413,9 +417,10 @@ __device__ __forceinline__ void loop_rowblock(const Sell<T>& S, const T* __restr
     double v[1] = {acc};
     block_sum<1>(v);
     if (t == 0) {
-      const T pi = p[r0];
-      const T qi = (JAC ? pi : __ldg(S.dg + r0) * pi) + (T)v[0];
-      q[r0] = qi;
+      const int i = __ldg(S.perm + r0);
+      const T pi = p[i];
+      const T qi = (JAC ? pi : __ldg(S.dg + i) * pi) + (T)v[0];
+      q[i] = qi;
       dot.add(pi, qi);
     }
     return;
@@ -446,38 +451,56 @@ __device__ __forceinline__ void loop_rowblock(const Sell<T>& S, const T* __restr
     Quad<T>::store(s_val + 4 * qd, v);
   }
   __syncthreads();
-  const int i = r0 + t;
-  if (i < r1) {
-    const int a = __ldg(S.rptr + i) - a0, e = __ldg(S.rptr + i + 1) - a0;
-    if (e - a > kThreadRow) {
-      s_med[atomicAdd(s_nmed, 1)] = i;
-    } else {
-      const T pi = p[i];
-      T acc = JAC ? pi : __ldg(S.dg + i) * pi;
-      for (int k = a; k < e; k += kRowUnroll) {
-        T xv[kRowUnroll], vv[kRowUnroll];
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u) {
-          const bool in = k + u < e;
-          vv[u] = in ? s_val[k + u] : T(0);
-          xv[u] = in ? p[s_col[k + u]] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < kRowUnroll; ++u)
-          if (k + u < e) acc = fma(vv[u], xv[u], acc);
-      }
-      q[i] = acc;
-      dot.add(pi, acc);
+  const int ps = r0 + t;
+  int a = 0, len = 0, i = 0;
+  if (ps < r1) {
+    a = __ldg(S.rptr + ps) - a0;
+    len = __ldg(S.rptr + ps + 1) - a0 - a;
+    i = __ldg(S.perm + ps);
+    if (len > kThreadRow) {
+      s_med[atomicAdd(s_nmed, 1)] = ps;
+      len = -1;
     }
+  }
+  // a warp's rows, one a thread: the FMA chain runs to the warp's longest row
+  // (one fp64 warp instruction per step), each lane adding exact zeros past its
+  // own row's end
+  const int wlen = __reduce_max_sync(0xffffffffu, len);
+  if (len >= 0 && ps < r1) {
+    const T pi = p[i];
+    T acc = JAC ? pi : __ldg(S.dg + i) * pi;
+    int k = 0;
+    for (; k + kRowStep <= wlen; k += kRowStep) {  // kRowStep gathers in flight together
+      T xv[kRowStep], vv[kRowStep];
+#pragma unroll
+      for (int u = 0; u < kRowStep; ++u) {
+        const bool in = k + u < len;
+        vv[u] = in ? s_val[a + k + u] : T(0);
+        xv[u] = in ? p[s_col[a + k + u]] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kRowStep; ++u) {
+        const T nx = fma(vv[u], xv[u], acc);
+        acc = k + u < len ? nx : acc;
+      }
+    }
+    for (; k < wlen; ++k) {  // the warp's last steps, one at a time
+      const bool in = k < len;
+      const T nx = fma(in ? s_val[a + k] : T(0), in ? p[s_col[a + k]] : T(0), acc);
+      acc = in ? nx : acc;
+    }
+    q[i] = acc;
+    dot.add(pi, acc);
   }
   __syncthreads();
   const int nmed = *s_nmed;
   const int lane = t & 31;
   for (int m = t >> 5; m < nmed; m += kWarps) {
-    const int row = s_med[m];
-    const int a = __ldg(S.rptr + row) - a0, e = __ldg(S.rptr + row + 1) - a0;
+    const int pm = s_med[m];
+    const int row = __ldg(S.perm + pm);
+    const int am = __ldg(S.rptr + pm) - a0, em = __ldg(S.rptr + pm + 1) - a0;
     T acc = T(0);
-    for (int k = a + lane; k < e; k += 32) acc = fma(s_val[k], p[s_col[k]], acc);
+    for (int k = am + lane; k < em; k += 32) acc = fma(s_val[k], p[s_col[k]], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
