@@ -96,7 +96,7 @@ WORKLOADS = {
     "graph_spd_12m": ("graph_spd", {"n": 12_000_000, "dmax": 600, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                       "general sparse SPD (graph Laplacian, power-law degrees 1-223 nonzeros per row, "
                       "70 % local / 30 % random couplings), n = 12M, nnz = 71M; FP64 Jacobi-PCG to 1e-8 "
-                      "(the sliced-ELL loop layout with long rows)"),
+                      "(the row-block CSR loop layout)"),
     "graph_spd_2m": ("graph_spd", {"n": 2_000_000, "dmax": 600, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
                      "the same family at n = 2M (profiling size)"),
     "batch16": ("batch", {"count": 16, "seed": 0}, "jacobi", "fp64", 1e-8, 20000,
@@ -558,10 +558,20 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
     row_iters = int(sum(n_i * k_i for n_i, k_i in zip(ns, its)))
     tr = ncu_traffic(workload, "batch") if precision_s == "fp64" else None
     traffic = int(tr["dram_bytes_per_row_iter"] * row_iters) if tr else None
-    # this kernel's own bytes: the row-iterations it performs times its bytes per row
-    # and iteration as ncu measured them are the traffic; the design's algorithmic
-    # figure is the survey's CSR model, so both are reported
-    own_achieved = traffic / (kern_ms / steps / 1e3) / 1e9 if traffic else None
+    # the fp64 kernel's algorithmic bytes: a member whose off-diagonal entries lie on
+    # d <= 8 offsets is stored by diagonal, and one of its row-iterations streams the d
+    # slot values (8 B each) plus p, q (phase A), q, r read and r written (B), and
+    # x, p, r read and x, p written (C): 8 d + 80 bytes
+    own_bytes = None
+    if precision_s == "fp64":
+        own_bytes = 0
+        for A, k_i in zip(systems, its):
+            rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+            offs = np.unique(A.colind.astype(np.int64) - rows)
+            d = int(np.count_nonzero(offs))
+            w = d if d <= 8 else int(np.max(np.diff(A.rowptr)))
+            own_bytes += ((8 if d <= 8 else 12) * w + 80) * A.n * int(k_i)
+    own_achieved = own_bytes / (kern_ms / steps / 1e3) / 1e9 if own_bytes else None
 
     e2e = None
     if full and not args.no_e2e:
@@ -637,9 +647,10 @@ def bench_batch(args, workload, steps, warmup, world, rank, dev, torch, cg, full
         "roofline": {"bound": "hbm", "achieved": own_achieved, "peak": peak, "unit": "GB/s",
                      "frac": own_achieved / peak if own_achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind,
-                     "achieved_is": "ncu DRAM bytes of the batched kernel per row-iteration x the "
-                                    "row-iterations / the launch's device time (null without a "
-                                    "current ncu figure)",
+                     "achieved_is": "the fp64 kernel's algorithmic bytes (8 d + 80 per row-iteration "
+                                    "of a member stored by its d diagonals) / the launch's device "
+                                    "time; traffic = ncu DRAM bytes per row-iteration x the "
+                                    "row-iterations (null without a current ncu figure)",
                      "timed_unit": "one batched solve: the persistent batch kernel (whole launch)",
                      "loop_form": form,
                      "achieved_survey_model": achieved, "frac_survey_model": achieved / peak,
@@ -793,7 +804,8 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
                             "nor the diagonal in the loop"}
 
     dom = None
-    if not args.no_dominant and not precond_s.startswith("fsai"):
+    if not args.no_dominant and not precond_s.startswith("fsai") and form != "cluster":
+        # (the cluster form runs no separate SpMV kernel: its loop is one kernel)
         dom = dominant_kernel(h, A, precond, precision, torch, cg, dev, peak, fma_peak)
     if dom is not None:
         trd = ncu_traffic(workload + ":g_spmv", "single")
