@@ -78,3 +78,23 @@ def random_graph_spd(n, seed, matchings=2):
     M.sort_indices()
     return gen.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
                    M.data.astype(np.float64), f"graph_spd_n{n}_s{seed}")
+
+
+def hub_graph_spd(n, seed, hub_len):
+    """A power-law graph Laplacian (cgproblems.graph_spd, the CSR loop layout's input
+    class) plus the Laplacian of a star joining row 0 to hub_len random rows (weight 0.5):
+    still SPD, with one row longer than a row block's 2044-entry cap."""
+    import scipy.sparse as sp
+    import cgproblems as gen
+    A = gen.graph_spd(n, 600, seed).to_scipy().tocoo()
+    rng = np.random.default_rng(seed)
+    leaves = rng.choice(np.arange(1, n), size=hub_len, replace=False)
+    w = 0.5
+    r = np.concatenate([np.zeros(hub_len, np.int64), leaves, [0], leaves])
+    c = np.concatenate([leaves, np.zeros(hub_len, np.int64), [0], leaves])
+    v = np.concatenate([np.full(2 * hub_len, -w), [w * hub_len], np.full(hub_len, w)])
+    M = (A + sp.coo_matrix((v, (r, c)), shape=(n, n))).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return gen.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64),
+                   f"hub_graph_n{n}_s{seed}_h{hub_len}")

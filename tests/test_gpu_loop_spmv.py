@@ -15,7 +15,7 @@ import scipy.sparse as sp
 
 import cgproblems as gen
 import oracle
-from helpers import random_graph_spd, spd_from_pattern, to_device
+from helpers import hub_graph_spd, random_graph_spd, spd_from_pattern, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -40,6 +40,8 @@ MATS = [
     ("q1_45", lambda: gen.q1aniso(45, 1.5, 0.3, 0.05, 2)),  # diagonal layout, 8 offsets
     ("graph_5000", lambda: random_graph_spd(5000, 2, 3)),   # uniform sliced ELL
     ("pattern_long", lambda: spd_from_pattern(6000, 5, long_rows=[(3, 400), (4100, 900)])),
+    ("powerlaw_20000", lambda: gen.graph_spd(20000, 600, 1)),   # row-block CSR layout, bulk-staged blocks
+    ("powerlaw_hub", lambda: hub_graph_spd(20000, 2, 3000)),    # ... and a row past the block cap
 ]
 
 

@@ -18,7 +18,7 @@ import pytest
 
 import cgproblems as gen
 import oracle
-from helpers import adversarial, random_graph_spd, spd_from_pattern, to_device
+from helpers import adversarial, hub_graph_spd, random_graph_spd, spd_from_pattern, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -401,6 +401,10 @@ GRAPH_CASES = [
     ("graph_uniform_jac", lambda: random_graph_spd(6000, 2, 4), 1, 1e-10, 3000),
     ("graph_uniform_none", lambda: random_graph_spd(5000, 5, 3), 0, 1e-10, 3000),
     ("diff27_40_jac", lambda: gen.diff3d27(40, 1.0, 2), 1, 1e-8, 5000),
+    # power-law rows: the row-block CSR loop layout (rows sorted by length per block;
+    # the graph forms stage its blocks with bulk copies), one with a row past the cap
+    ("powerlaw_jac", lambda: gen.graph_spd(20000, 600, 1), 1, 1e-8, 5000),
+    ("powerlaw_hub_jac", lambda: hub_graph_spd(20000, 2, 3000), 1, 1e-8, 8000),
 ]
 
 
