@@ -1,32 +1,27 @@
 // SpMV on the caller's CSR matrix (Sec. 3.1: y_i = sum_k vals[k] x[colind[k]]
 // over row i's stored entries): cg_spmv, the residuals b - A x of the graph
-// form, and the once-per-solve true residual of the persistent kernels.
+// form, and the true residuals and refinement residuals of the persistent
+// kernels.
 //
 // The rows are cut on the host into row blocks of at most kCapV nonzeros and
 // kBlock rows; a row with more than kCapV nonzeros is a block of its own (a
-// "long" block, which the CTA strides over and reduces).  Two forms:
-//
-//  * spmv_rowblock_fma (the stand-alone kernel): the block's column indices and
-//    values are copied to shared memory with 16-byte loads (four indices, two
-//    pairs of values) starting at the 16-byte boundary at or below the block's
-//    first nonzero; rows of at most 16 nonzeros are summed by one thread each
-//    (storage order, fused multiply-adds: one fp64 FMA per nonzero), longer
-//    rows by a warp each, and a row beyond the block cap by the whole CTA.  GB300's fp64 pipe issues 2 FMAs per clock per SM,
-//    so a separate multiply and add per nonzero (two fp64 instructions) makes a
-//    7-point SpMV pipe-bound; with one FMA the kernel is HBM-bound.
-//  * spmv_rowblock (inside the persistent solver kernels, twice per solve):
-//    products rounded, then summed in storage order, the oracle's arithmetic
-//    exactly, staged in a smaller shared buffer so the persistent kernels keep
-//    their occupancy.
+// "long" block, which the CTA strides over and reduces).  spmv_rowblock_fma:
+// the block's column indices and values are copied to shared memory with
+// 16-byte loads (four indices, two pairs of values) starting at the 16-byte
+// boundary at or below the block's first nonzero; short rows (kThreadRow)
+// are summed by one thread each (storage order, fused multiply-adds: one fp64
+// FMA per nonzero), longer rows by a warp each, and a row beyond the block cap
+// by the whole CTA.  GB300's fp64 pipe issues 2 FMAs per clock per SM, so a
+// separate multiply and add per nonzero (two fp64 instructions) makes a
+// 7-point SpMV pipe-bound; with one FMA the kernel is HBM-bound.
 #pragma once
 
 #include "cg_device.cuh"
 
 namespace cg {
 
-constexpr int kCap = 2048;                 // shared staging of one row block (persistent kernels)
+constexpr int kCap = 2048;                 // shared staging of one row block
 constexpr int kCapV = kCap - 4;            // nonzeros of a row block: its 16-byte window fits kCap
-constexpr int kPerThread = kCap / kBlock;  // nonzeros per thread
 
 // CSR matrix view plus its row-block schedule.  Row block b covers rows
 // [rb[b], rb[b+1]).  vec != 0: colind and vals start on 16-byte boundaries, so
@@ -42,60 +37,26 @@ struct Csr {
   int32_t vec;
 };
 
-// One row block of y = A x, the oracle's arithmetic: stream blocks sum each row
-// in storage order over rounded products, so fp64 results match it bit for
-// bit; long rows use a strided multiply-add and a fixed tree.
-template <typename T>
-__device__ __forceinline__ void spmv_rowblock(const Csr<T>& A, const T* x, T* y, int b, T* s_prod) {
-  const int r0 = __ldg(A.rb + b), r1 = __ldg(A.rb + b + 1);
-  const int k0 = __ldg(A.rowptr + r0), k1 = __ldg(A.rowptr + r1);
-  const int nk = k1 - k0;
-  const int t = threadIdx.x;
-  if (nk > kCap) {  // long row (r1 == r0 + 1 by construction)
-    T acc = T(0);
-    for (int k = k0 + t; k < k1; k += kBlock) acc += __ldg(A.vals + k) * x[__ldg(A.colind + k)];
-    double v[1] = {(double)acc};
-    block_sum<1>(v);
-    if (t == 0) y[r0] = (T)v[0];
-    return;
-  }
-  T prod[kPerThread];
-  int col[kPerThread];
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) {
-      col[j] = __ldg(A.colind + k0 + k);
-      prod[j] = __ldg(A.vals + k0 + k);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) prod[j] = prod[j] * x[col[j]];
-  }
-#pragma unroll
-  for (int j = 0; j < kPerThread; ++j) {
-    const int k = t + j * kBlock;
-    if (k < nk) s_prod[k] = prod[j];
-  }
-  __syncthreads();
-  const int i = r0 + t;
-  if (i < r1) {
-    const int a = __ldg(A.rowptr + i) - k0, e = __ldg(A.rowptr + i + 1) - k0;
-    T s = T(0);
-    for (int k = a; k < e; ++k) s += s_prod[k];
-    y[i] = s;
-  }
-  __syncthreads();  // s_prod is reused by the next row block
-}
-
-// A row block's 16-byte window holds at most kCapV + 3 nonzeros: two quads
-// (four nonzeros on a 16-byte boundary) per thread.
 constexpr int kQuadPasses = 2;
 static_assert((kCapV + 3 + 3) / 4 <= kQuadPasses * kBlock, "a row block's window exceeds two quads per thread");
 constexpr int kRowUnroll = 4;  // a row's nonzeros whose gathers are in flight together
-constexpr int kThreadRow = 16;  // rows with more nonzeros are summed by a warp each
+// Rows with more nonzeros than a thread takes are summed by a warp each.  A
+// thread takes a row of up to kThreadRow entries; in the caller's CSR, when
+// more than kWideRows of a warp's 32 rows have kThreadRow + 1 .. kThreadRowWide
+// entries (a 27-point stencil) it takes those too: one
+// thread a row costs the warp one FMA step per entry, where a warp per row adds
+// a 5-level fp64 tree to every row (27 entries: ~0.84 fp64 warp instructions a
+// row against ~6); a few such rows among short ones go to warps, so they do not
+// hold a warp of short rows.
+constexpr int kThreadRow = 16;
+constexpr int kThreadRowWide = 32;
+constexpr int kWideRows = 4;
+
+// The longest row a thread of this warp keeps (all 32 lanes call it).
+__device__ __forceinline__ int thread_row_limit(int len) {
+  const unsigned wide = __ballot_sync(0xffffffffu, len > kThreadRow && len <= kThreadRowWide);
+  return __popc(wide) > kWideRows ? kThreadRowWide : kThreadRow;
+}
 
 // One row block of y = A x with one fused multiply-add per nonzero (header
 // comment).  The block's column indices and values are copied with 16-byte
@@ -164,10 +125,10 @@ __device__ __forceinline__ void spmv_rowblock_fma(const Csr<double>& A, const do
   if (i < r1) {
     a = __ldg(A.rowptr + i) - a0;
     len = __ldg(A.rowptr + i + 1) - a0 - a;
-    if (len > kThreadRow) {
-      s_med[atomicAdd(s_nmed, 1)] = i;  // a warp sums it below (the order of the list does not matter)
-      len = -1;
-    }
+  }
+  if (len > thread_row_limit(len)) {
+    s_med[atomicAdd(s_nmed, 1)] = i;  // a warp sums it below (the order of the list does not matter)
+    len = -1;
   }
   // one row a thread; the warp's FMA chain runs to its longest row (GB300 issues
   // an fp64 warp instruction in full whatever its active lanes), each lane keeping

@@ -334,7 +334,6 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
 // fp64 PCG with G^T G: true-residual check and restarts as cg_solve (R1-R5, R7).
 template <int W>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
-  __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
   Grid g(P.st, P.timeout_ns, P.skip_seq);
   const int64_t n = P.A.n;
@@ -343,7 +342,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
   double relres_true = 0.0, bb = 0.0;
   bool first = true;
   for (;;) {
-    spmv_orig(P.A, P.x, V.q, g, s_prod);
+    spmv_orig(P.A, P.x, V.q, g);
     if (!g.sync()) { status = kTimeout; break; }
     double v[2] = {0.0, 0.0};
     for (int64_t i = g.gtid; i < n; i += g.gstride) {
@@ -387,7 +386,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
     if (st == kTimeout) { status = kTimeout; break; }
     if (st == kNumeric || st == kBreakdown) {
       status = st;
-      spmv_orig(P.A, P.x, V.q, g, s_prod);  // the true residual of the last iterate
+      spmv_orig(P.A, P.x, V.q, g);  // the true residual of the last iterate
       if (!g.sync()) { status = kTimeout; break; }
       double w[1] = {0.0};
       for (int64_t i = g.gtid; i < n; i += g.gstride) {
@@ -415,7 +414,6 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
 // CARRY: reliable updates (R8), the search direction survives each fp64 update.
 template <int W, bool CARRY>
 __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
-  __shared__ double s_prod[kCap];
   const SolveParams& P = F.P;
   Grid g(P.st, P.timeout_ns, P.skip_seq);
   const int64_t n = P.A.n;
@@ -423,7 +421,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai_ir_kernel(FsaiParams F) {
   int status = kNotConverged, inner = 0, outer = 0;
   double relres = 0.0, bb = 0.0, rho_k = 0.0;
   for (;;) {
-    spmv_orig(P.A, P.x, F.V64.q, g, s_prod);
+    spmv_orig(P.A, P.x, F.V64.q, g);
     if (!g.sync()) { status = kTimeout; break; }
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t i = g.gtid; i < n; i += g.gstride) {

@@ -457,13 +457,15 @@ __device__ __forceinline__ void loop_rowblock(const Sell<T>& S, const T* __restr
     a = __ldg(S.rptr + ps) - a0;
     len = __ldg(S.rptr + ps + 1) - a0 - a;
     i = __ldg(S.perm + ps);
-    if (len > kThreadRow) {
-      s_med[atomicAdd(s_nmed, 1)] = ps;
-      len = -1;
-    }
+  }
+  // (the rows of a block are sorted by length, so the first warps hold the long
+  // ones: those are shared out among all warps instead of kept by one)
+  if (len > kThreadRow) {
+    s_med[atomicAdd(s_nmed, 1)] = ps;
+    len = -1;
   }
   // a warp's rows, one a thread: the FMA chain runs to the warp's longest row
-  // (one fp64 warp instruction per step), each lane adding exact zeros past its
+  // (one fp64 warp instruction per step), each lane keeping its sum past its
   // own row's end
   const int wlen = __reduce_max_sync(0xffffffffu, len);
   if (len >= 0 && ps < r1) {
@@ -818,17 +820,22 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
   return status;
 }
 
-// Caller's-matrix SpMV q = A x over the original row blocks (a5, restarts).
-__device__ __forceinline__ void spmv_orig(const Csr<double>& A, const double* x, double* q,
-                                          const Grid& g, double* s_prod) {
-  for (int b = (int)g.cta; b < A.nrb; b += (int)g.G) spmv_rowblock<double>(A, x, q, b, s_prod);
+// Caller's-matrix SpMV q = A x over the original row blocks (a5, restarts,
+// the refinement's fp64 residual): the row-block kernel of cg_spmv (one fused
+// multiply-add per nonzero in storage order, half the fp64 instructions of a
+// separate multiply and add on GB300's narrow fp64 pipe).
+__device__ __forceinline__ void spmv_orig(const Csr<double>& A, const double* x, double* q, const Grid& g) {
+  __shared__ __align__(16) int s_col[kCap];
+  __shared__ __align__(16) double s_val[kCap];
+  __shared__ int s_med[kBlock];
+  __shared__ int s_nmed;
+  for (int b = (int)g.cta; b < A.nrb; b += (int)g.G) spmv_rowblock_fma(A, x, q, b, s_col, s_val, s_med, &s_nmed);
 }
 
 // fp64 (Jacobi-)PCG with true-residual check and residual-replacement
 // restarts (readings R1-R5 of the method, see the oracle's header).
 template <bool JAC>
 __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
-  __shared__ double s_prod[kCap];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
   PhaseClock clk(P.timers != 0);
   const int64_t n = P.A.n;
@@ -838,7 +845,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
   bool first = true;
   for (;;) {
     // a5 / (re)start: r = b - A x; r^ = D^-1/2 r; x^ = D^1/2 x
-    spmv_orig(P.A, P.x, V.q, g, s_prod);
+    spmv_orig(P.A, P.x, V.q, g);
     if (!g.sync()) { status = kTimeout; break; }
     double v[3] = {0.0, 0.0, 0.0};
     for (int64_t i = g.gtid; i < n; i += g.gstride) {
@@ -879,7 +886,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
     if (st == kTimeout) { status = kTimeout; break; }
     if (st == kNumeric || st == kBreakdown) {
       status = st;
-      spmv_orig(P.A, P.x, V.q, g, s_prod);  // report the true residual of the last iterate
+      spmv_orig(P.A, P.x, V.q, g);  // report the true residual of the last iterate
       if (!g.sync()) { status = kTimeout; break; }
       double w[1] = {0.0};
       for (int64_t i = g.gtid; i < n; i += g.gstride) {
@@ -918,7 +925,6 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
 // rho_k) p_k, instead of restarting from p = r^'.
 template <bool JAC, bool CARRY>
 __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
-  __shared__ double s_prod[kCap];
   Grid g(P.st, P.timeout_ns, P.skip_seq);
   PhaseClock clk(P.timers != 0);
   const int64_t n = P.A.n;
@@ -928,7 +934,7 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_ir_kernel(SolveParams P) {
   for (;;) {
     // outer fp64 residual r = b - A x fused with the inner start:
     // r^32 = fl32(D^-1/2 r), d^ = 0
-    spmv_orig(P.A, P.x, P.V64.q, g, s_prod);
+    spmv_orig(P.A, P.x, P.V64.q, g);
     if (!g.sync()) { status = kTimeout; break; }
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = g.gtid; i < n; i += g.gstride) {
