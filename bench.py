@@ -817,6 +817,16 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
                     "fp64_pipe": dom.get("fp64_pipe"),
                     "bytes_are": "the loop matrix slots (8 B each in the diagonal layout, +4 B column "
                                  "otherwise), p read once and q written: this kernel's algorithmic bytes"}
+    elif form == "cluster" and loop["bytes_per_iter"] == 0:
+        # vectors and CSR in the cluster's shared memory: nothing moves from outside the
+        # SMs, and the iteration's time is a latency chain (row products, two exchanges
+        # of partial sums across the cluster, two fp64 divisions), not a throughput
+        roofline = {"bound": "latency", "achieved": loop["iter_us"], "peak": None, "unit": "us/iteration",
+                    "frac": None, "traffic": None, "peak_kind": None,
+                    "kernel": "the whole CG loop (" + loop["timed_unit"] + ")",
+                    "note": "no bytes from outside the SMs per iteration: vectors and CSR held in the "
+                            "cluster's shared memory"}
+        loop["frac"] = None
     else:
         roofline = {"bound": "hbm", "achieved": achieved_own, "peak": peak, "unit": "GB/s",
                     "frac": achieved_own / peak, "traffic": loop_traffic, "peak_kind": peak_kind,
@@ -825,7 +835,7 @@ def bench_single(args, workload, steps, warmup, world, rank, dev, torch, cg, ful
     # move its own bytes faster than HBM: its fraction is not an HBM roofline
     ws = loop["bytes_per_iter"]
     loop["l2_resident"] = bool(ws and ws < 129e6)
-    if dom is None:
+    if dom is None and roofline["bound"] != "latency":
         if loop["l2_resident"]:
             roofline["bound"] = "l2"
         if roofline["frac"] is not None and roofline["frac"] > 1.0:

@@ -41,7 +41,8 @@ typedef enum {
   CG_ERR_INVALID = -1,    /* bad argument, malformed CSR, missing/non-positive diagonal */
   CG_ERR_BREAKDOWN = -2,  /* p.q <= 0: A is not SPD on the Krylov space */
   CG_ERR_NUMERIC = -3,    /* NaN or Inf in a reduction */
-  CG_ERR_TIMEOUT = -4,    /* a grid barrier of the persistent kernel gave up waiting */
+  CG_ERR_TIMEOUT = -4,    /* a bounded wait gave up: a grid barrier of the persistent kernel or an
+                             exchange of partial sums in the cluster form */
   CG_ERR_CUDA = -5,       /* a CUDA runtime call failed */
   CG_ERR_OOM = -6         /* device or pinned-host allocation failed */
 } cg_status;
@@ -65,13 +66,14 @@ typedef enum {
 
 typedef enum {
   CG_OPT_MAX_RESTARTS = 0,        /* residual-replacement restarts after a false convergence (default 3) */
-  CG_OPT_BARRIER_TIMEOUT_MS = 1,  /* grid-barrier wait limit in ms (default 2000) */
+  CG_OPT_BARRIER_TIMEOUT_MS = 1,  /* limit of every bounded wait in ms (default 2000) */
   CG_OPT_GRID_CTAS = 2,           /* persistent-kernel CTAs; 0 = choose automatically (default) */
   CG_OPT_IR_TOL_INNER = 3,        /* inner relative tolerance of fp32 refinement (default 1e-4), or the
                                      residual reduction that triggers a reliable update (default 0.1) */
   CG_OPT_IR_MAX_OUTER = 4,        /* refinement steps / reliable updates cap (default 30) */
   CG_OPT_DEBUG_SKIP_ARRIVAL = 5,  /* fault injection: CTA 0 skips arrival at grid barrier #value
-                                     (1-based; 0 = off), so every wait runs into its limit */
+                                     (cluster form: does not push exchange #value; 1-based; 0 = off),
+                                     so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
   CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: cluster form up to
                                      12288 rows unless CG_OPT_GRID_CTAS, CG_OPT_DEBUG_SKIP_ARRIVAL

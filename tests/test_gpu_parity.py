@@ -543,6 +543,50 @@ def test_cluster_form_ragged_shapes(make):
         assert np.linalg.norm(x - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
 
 
+@pytest.mark.parametrize("make,in_smem", [(lambda: gen.lap3d7(24), True),
+                                          (lambda: gen.diff3d27(32, 1.0, 5), False)],
+                         ids=["lap3d7_24_smem", "diff27_32_global"])
+def test_cluster_form_csr_placement(make, in_smem):
+    """Each CTA holds its rows of the CSR in shared memory when they fit beside its
+    vectors (no bytes from outside the SMs per iteration), else reads them from global
+    memory; both against the oracle, and a rerun gives the same bits."""
+    A = make()
+    b = oracle.spmv(A, gen.xstar(A.n, 2))
+    ref = oracle.pcg(A, b, tol=1e-9, maxit=3000, precond=1)
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, 4) == cg.CG_OK
+    st, it, rel, x, info = gpu_solve(A, b, 1e-9, 3000, cg.CG_PRECOND_JACOBI, h=h)
+    assert st == ref.status == cg.CG_OK and info["loop_form"] == 4
+    assert (info["kernel_bytes_per_iter"] == 0) == in_smem
+    assert abs(it - ref.iters) <= iters_band(ref.iters), (it, ref.iters)
+    assert oracle.true_relres(A, b, x) <= 1e-9 * (1 + 1e-6)
+    assert np.linalg.norm(x - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    st2, it2, rel2, x2, _ = gpu_solve(A, b, 1e-9, 3000, cg.CG_PRECOND_JACOBI, h=h)
+    assert st2 == st and it2 == it and rel2 == rel and np.array_equal(x2, x)
+    cg.cg_destroy(h)
+
+
+def test_cluster_form_exchange_timeout_is_reported_and_context_survives():
+    """Fault injection on the host's request: CTA 0 of the cluster does not push its
+    partial sum of the second exchange (the first p.q), so every CTA's bounded wait runs
+    out; the solve returns CG_ERR_TIMEOUT and the next solve on the handle works."""
+    A = gen.lap2d(64)
+    b = oracle.spmv(A, gen.xstar(A.n, 0))
+    rp, ci, va = to_device(A)
+    h = cg.cg_create(A.n, rp, ci, va)
+    assert cg.cg_set_option(h, cg.CG_OPT_LOOP_MODE, 4) == cg.CG_OK
+    assert cg.cg_set_option(h, cg.CG_OPT_BARRIER_TIMEOUT_MS, 100) == cg.CG_OK
+    assert cg.cg_set_option(h, cg.CG_OPT_DEBUG_SKIP_ARRIVAL, 2) == cg.CG_OK
+    st, *_, info = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
+    assert st == cg.CG_ERR_TIMEOUT and info["loop_form"] == 4
+    assert "timed out" in cg.cg_last_error(h)
+    assert cg.cg_set_option(h, cg.CG_OPT_DEBUG_SKIP_ARRIVAL, 0) == cg.CG_OK
+    st, it, rel, x, info = gpu_solve(A, b, 1e-8, 1000, cg.CG_PRECOND_NONE, h=h)
+    assert st == cg.CG_OK and rel <= 1e-8 and info["loop_form"] == 4
+    cg.cg_destroy(h)
+
+
 def test_cluster_form_is_chosen_for_small_systems_and_refuses_large_ones():
     """Automatic loop form: the 64 x 64 Poisson system (4096 rows) runs in one thread-block
     cluster; forcing the cluster form beyond its 32768 rows is refused."""
