@@ -142,6 +142,18 @@ __device__ __forceinline__ cg_exact::i128 warp_sum(cg_exact::i128 S) {
   return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44) + (i128)s3 * ((i128)1 << 66);
 }
 
+// warp_sum for 64-bit terms: three limbs (two unsigned 22-bit ones and the signed rest).
+__device__ __forceinline__ cg_exact::i128 warp_sum64(long long X) {
+  using cg_exact::i128;
+  const unsigned l0 = (unsigned)((unsigned long long)X & 0x3FFFFFull);
+  const unsigned l1 = (unsigned)(((unsigned long long)X >> 22) & 0x3FFFFFull);
+  const int l2 = (int)(X >> 44);
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, l0);
+  const unsigned s1 = __reduce_add_sync(0xffffffffu, l1);
+  const int s2 = __reduce_add_sync(0xffffffffu, l2);
+  return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44);
+}
+
 // In every lane of a warp: the packed entries held by its lanes (lanes without
 // one hold zero at scale 1) moved to their largest scale and added exactly.
 __device__ __forceinline__ cg_exact::i128 sum_entries(const ulonglong2& w, bool has, int* Em, bool* bad) {
@@ -163,9 +175,11 @@ __device__ __forceinline__ void push_sums(const double (&v)[NV], Exchange& X, in
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     const cg_exact::Parts p = cg_exact::parts(v[j]);
-    const int E = (int)__reduce_max_sync(0xffffffffu, (unsigned)p.e);
-    const bool bad = __reduce_or_sync(0xffffffffu, p.bad ? 1u : 0u) != 0u;
-    const cg_exact::i128 S = warp_sum((cg_exact::i128)cg_exact::to_fixed(p, E));
+    // one redux for the scale and the NaN flag (a bad term makes the scale irrelevant)
+    const unsigned eb = __reduce_max_sync(0xffffffffu, (unsigned)p.e | (p.bad ? 0x10000u : 0u));
+    const bool bad = eb > 0xFFFFu;
+    const int E = bad ? 2046 : (int)(eb & 0xFFFFu);  // (a bad sum is NaN; any scale >= every e will do)
+    const cg_exact::i128 S = warp_sum64(cg_exact::to_fixed(p, E));
     unsigned long long lo, hi;
     cg_exact::pack(S, E, bad, &lo, &hi);
     if (lane == 0) X.warp[warp][j] = make_ulonglong2(lo, hi);
@@ -221,6 +235,16 @@ __device__ __forceinline__ void cluster_sums(const Exchange& X, int par, int C, 
     const cg_exact::i128 T = sum_entries(X.part[par][lane < C ? lane : 0][j], lane < C, &E, &bad);
     out[j] = cg_exact::to_fp64(T, E, bad);
   }
+}
+
+// below_stop with the square root kept inside its branch (a register dependence on
+// an empty asm): it is needed only within the stopping band, and on GB300's fp64
+// pipe a square root is ~700 clocks of the iteration's critical path.
+__device__ __forceinline__ bool below_stop_lazy(double rr, double stop, double stop2_hi) {
+  if (!(rr <= stop2_hi)) return false;
+  double r = rr;
+  asm volatile("" : "+d"(r));
+  return sqrt(r) <= stop;
 }
 
 // ---- this CTA's rows of the CSR
@@ -404,6 +428,7 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
   // of every CTA on the cluster-wide sums; the other threads follow the
   // broadcast words.  Thread 0 of every CTA takes the same decisions.
   __shared__ double s_alpha, s_beta;
+  __shared__ double s_rho, s_inv_rho;  // rho (thread 0's), and 1 / rho formed by warp 1
   __shared__ int s_go;   // inner loop: 1 = run the next phase
   __shared__ int s_act;  // outer loop: 0 = leave, 1 = iterate, 2 = leave with x = 0
   __shared__ int s_act2; // after the inner loop: 0 = leave, 1 = recompute the true residual
@@ -509,12 +534,13 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
           was_first = first;
           first = false;
           rho = s3[0];
+          s_rho = rho;
           rr = rr0 = s3[1];
           stop = P.tol * sqrt(bb);
           stop2_hi = stop2_high(stop);
           k_before = k;
           st_in = kNotConverged;
-          if (below_stop(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
+          if (below_stop_lazy(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
           else if (k < P.maxit) go = 1;
         }
         s_act = act;
@@ -566,6 +592,10 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
         }
       }
       push_sums<1>(v1, X, rank, C, (int)(e & 1u), P.skip_seq == e + 1u && rank == 0);
+      // 1 / rho for this iteration's beta, on another SM sub-partition while warp 0
+      // waits for p.q and forms alpha: beta = rho' (1 / rho) costs a multiply on
+      // the path where rho' / rho cost a division (within 1.5 ulp of it)
+      if (t == 32) s_inv_rho = 1.0 / s_rho;
       if (t < 32) {
         const bool ok = wait_sums(X, e, tmo);
         double pq[1];
@@ -631,11 +661,12 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
             record_timeout();
             st_in = kTimeout;
           } else {
-            s_beta = s2[0] / rho;
+            s_beta = s2[0] * s_inv_rho;
             rho = s2[0];
+            s_rho = rho;
             rr = s2[1];
             ++k;
-            if (below_stop(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
+            if (below_stop_lazy(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
             else if (k < P.maxit) go = 1;
           }
           s_go = go;
