@@ -76,7 +76,7 @@ typedef enum {
                                      so every wait runs into its limit */
   CG_OPT_PHASE_TIMERS = 6,        /* 1: record CTA 0's time per loop phase in cg_solve_info */
   CG_OPT_LOOP_MODE = 7            /* loop form: 0 auto (fp64 Jacobi / plain CG: cluster form up to
-                                     12288 rows unless CG_OPT_GRID_CTAS, CG_OPT_DEBUG_SKIP_ARRIVAL
+                                     16384 rows unless CG_OPT_GRID_CTAS, CG_OPT_DEBUG_SKIP_ARRIVAL
                                      or CG_OPT_PHASE_TIMERS is set, graph from 2^18 rows; fp32
                                      FSAI refinement: graph from 2^21 rows; else persistent),
                                      1 one persistent cooperative launch, 2 CUDA graph with a

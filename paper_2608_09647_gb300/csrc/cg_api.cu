@@ -842,7 +842,7 @@ cg_status build_graph64(cg_handle* h, const SolveParams& P, bool jac, int unroll
 }
 
 constexpr int64_t kGraphMinRows = 1 << 18;  // auto mode: graph loop from this many rows (fp64)
-constexpr int64_t kClusterAutoRows = 12288;  // auto mode: the cluster form up to this many rows (fp64)
+constexpr int64_t kClusterAutoRows = 16384;  // auto mode: the cluster form up to this many rows (fp64)
 constexpr int kUnrollIters = 8;               // iterations per launch of the unrolled form
 
 // fp64 solve through the graph form of the loop; restarts (true residual
