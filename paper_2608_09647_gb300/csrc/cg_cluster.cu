@@ -127,44 +127,6 @@ struct Exchange {
   unsigned long long bar[2];                // mbarrier per parity: 1 arrival + the pushed bytes
 };
 
-// Sum over the warp of an integer with |S| < 2^72: four limbs (three unsigned
-// 22-bit ones and the signed rest), each summed by one redux.sync, recombined exactly.
-__device__ __forceinline__ cg_exact::i128 warp_sum(cg_exact::i128 S) {
-  using cg_exact::i128;
-  const unsigned l0 = (unsigned)((unsigned long long)S & 0x3FFFFFull);
-  const unsigned l1 = (unsigned)((unsigned long long)(S >> 22) & 0x3FFFFFull);
-  const unsigned l2 = (unsigned)((unsigned long long)(S >> 44) & 0x3FFFFFull);
-  const int l3 = (int)(S >> 66);
-  const unsigned s0 = __reduce_add_sync(0xffffffffu, l0);
-  const unsigned s1 = __reduce_add_sync(0xffffffffu, l1);
-  const unsigned s2 = __reduce_add_sync(0xffffffffu, l2);
-  const int s3 = __reduce_add_sync(0xffffffffu, l3);
-  return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44) + (i128)s3 * ((i128)1 << 66);
-}
-
-// warp_sum for 64-bit terms: three limbs (two unsigned 22-bit ones and the signed rest).
-__device__ __forceinline__ cg_exact::i128 warp_sum64(long long X) {
-  using cg_exact::i128;
-  const unsigned l0 = (unsigned)((unsigned long long)X & 0x3FFFFFull);
-  const unsigned l1 = (unsigned)(((unsigned long long)X >> 22) & 0x3FFFFFull);
-  const int l2 = (int)(X >> 44);
-  const unsigned s0 = __reduce_add_sync(0xffffffffu, l0);
-  const unsigned s1 = __reduce_add_sync(0xffffffffu, l1);
-  const int s2 = __reduce_add_sync(0xffffffffu, l2);
-  return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44);
-}
-
-// In every lane of a warp: the packed entries held by its lanes (lanes without
-// one hold zero at scale 1) moved to their largest scale and added exactly.
-__device__ __forceinline__ cg_exact::i128 sum_entries(const ulonglong2& w, bool has, int* Em, bool* bad) {
-  int E = 1;
-  bool b = false;
-  const cg_exact::i128 S = has ? cg_exact::unpack(w.x, w.y, &E, &b) : (cg_exact::i128)0;
-  *Em = (int)__reduce_max_sync(0xffffffffu, (unsigned)E);
-  *bad = __reduce_or_sync(0xffffffffu, b ? 1u : 0u) != 0u;
-  return warp_sum(cg_exact::shift_down(S, *Em - E));
-}
-
 // This CTA's NV sums, exact and order-free, pushed by lanes 0..C-1 of warp 0 into
 // row `rank` of slot table `par` of CTA `lane`.  Every warp first sums its lanes'
 // values at the warp's own scale (the largest exponent among them); warp 0 then
@@ -174,15 +136,8 @@ __device__ __forceinline__ void push_sums(const double (&v)[NV], Exchange& X, in
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
-    const cg_exact::Parts p = cg_exact::parts(v[j]);
-    // one redux for the scale and the NaN flag (a bad term makes the scale irrelevant)
-    const unsigned eb = __reduce_max_sync(0xffffffffu, (unsigned)p.e | (p.bad ? 0x10000u : 0u));
-    const bool bad = eb > 0xFFFFu;
-    const int E = bad ? 2046 : (int)(eb & 0xFFFFu);  // (a bad sum is NaN; any scale >= every e will do)
-    const cg_exact::i128 S = warp_sum64(cg_exact::to_fixed(p, E));
-    unsigned long long lo, hi;
-    cg_exact::pack(S, E, bad, &lo, &hi);
-    if (lane == 0) X.warp[warp][j] = make_ulonglong2(lo, hi);
+    const ulonglong2 w = warp_exact(v[j]);
+    if (lane == 0) X.warp[warp][j] = w;
   }
   __syncthreads();  // every warp's sums, and the CTA's stores of this phase, before the push
   if (warp == 0) {
@@ -235,16 +190,6 @@ __device__ __forceinline__ void cluster_sums(const Exchange& X, int par, int C, 
     const cg_exact::i128 T = sum_entries(X.part[par][lane < C ? lane : 0][j], lane < C, &E, &bad);
     out[j] = cg_exact::to_fp64(T, E, bad);
   }
-}
-
-// below_stop with the square root kept inside its branch (a register dependence on
-// an empty asm): it is needed only within the stopping band, and on GB300's fp64
-// pipe a square root is ~700 clocks of the iteration's critical path.
-__device__ __forceinline__ bool below_stop_lazy(double rr, double stop, double stop2_hi) {
-  if (!(rr <= stop2_hi)) return false;
-  double r = rr;
-  asm volatile("" : "+d"(r));
-  return sqrt(r) <= stop;
 }
 
 // ---- this CTA's rows of the CSR
@@ -540,7 +485,7 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
           stop2_hi = stop2_high(stop);
           k_before = k;
           st_in = kNotConverged;
-          if (below_stop_lazy(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
+          if (below_stop(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
           else if (k < P.maxit) go = 1;
         }
         s_act = act;
@@ -666,7 +611,7 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
             s_rho = rho;
             rr = s2[1];
             ++k;
-            if (below_stop_lazy(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
+            if (below_stop(rr, stop, stop2_hi)) st_in = kOk;  // a4, before every SpMV
             else if (k < P.maxit) go = 1;
           }
           s_go = go;

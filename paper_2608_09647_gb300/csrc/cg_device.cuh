@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "cg_exact.cuh"
+
 namespace cg {
 
 constexpr int kBlock = 256;          // threads per CTA of every libcg kernel
@@ -91,6 +93,90 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks, uin
   return s_ok != 0;
 }
 
+// ---- exact sums on the integer pipes (cg_exact.cuh).  GB300's fp64 unit issues
+// one warp instruction per ~64 clocks per SM sub-partition, so a tree of fp64
+// adds in one warp (5 levels for a warp, 8 for a CTA) sits on every reduction's
+// critical path; these sums use integer instructions and redux.sync, and give
+// the exact sum rounded once, whatever the order of the terms.
+
+// Sum over the warp of an integer with |S| < 2^72: four limbs (three unsigned
+// 22-bit ones and the signed rest), each summed by one redux.sync, recombined exactly.
+__device__ __forceinline__ cg_exact::i128 warp_sum_i128(cg_exact::i128 S) {
+  using cg_exact::i128;
+  const unsigned l0 = (unsigned)((unsigned long long)S & 0x3FFFFFull);
+  const unsigned l1 = (unsigned)((unsigned long long)(S >> 22) & 0x3FFFFFull);
+  const unsigned l2 = (unsigned)((unsigned long long)(S >> 44) & 0x3FFFFFull);
+  const int l3 = (int)(S >> 66);
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, l0);
+  const unsigned s1 = __reduce_add_sync(0xffffffffu, l1);
+  const unsigned s2 = __reduce_add_sync(0xffffffffu, l2);
+  const int s3 = __reduce_add_sync(0xffffffffu, l3);
+  return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44) + (i128)s3 * ((i128)1 << 66);
+}
+
+// warp_sum_i128 for 64-bit terms: three limbs (two unsigned 22-bit ones and the signed rest).
+__device__ __forceinline__ cg_exact::i128 warp_sum64(long long X) {
+  using cg_exact::i128;
+  const unsigned l0 = (unsigned)((unsigned long long)X & 0x3FFFFFull);
+  const unsigned l1 = (unsigned)(((unsigned long long)X >> 22) & 0x3FFFFFull);
+  const int l2 = (int)(X >> 44);
+  const unsigned s0 = __reduce_add_sync(0xffffffffu, l0);
+  const unsigned s1 = __reduce_add_sync(0xffffffffu, l1);
+  const int s2 = __reduce_add_sync(0xffffffffu, l2);
+  return (i128)s0 + (i128)s1 * ((i128)1 << 22) + (i128)s2 * ((i128)1 << 44);
+}
+
+// In every lane: the exact sum of the lanes' fp64 values at the warp's scale
+// (the largest exponent field among them), packed with that scale.
+__device__ __forceinline__ ulonglong2 warp_exact(double v) {
+  const cg_exact::Parts p = cg_exact::parts(v);
+  // one redux for the scale and the NaN flag (a bad sum is NaN; any scale >= every e will do)
+  const unsigned eb = __reduce_max_sync(0xffffffffu, (unsigned)p.e | (p.bad ? 0x10000u : 0u));
+  const bool bad = eb > 0xFFFFu;
+  const int E = bad ? 2046 : (int)(eb & 0xFFFFu);
+  unsigned long long lo, hi;
+  cg_exact::pack(warp_sum64(cg_exact::to_fixed(p, E)), E, bad, &lo, &hi);
+  return make_ulonglong2(lo, hi);
+}
+
+// In every lane of a warp: the packed entries held by its lanes (lanes without
+// one hold zero at scale 1) moved to their largest scale and added exactly.
+__device__ __forceinline__ cg_exact::i128 sum_entries(const ulonglong2& w, bool has, int* Em, bool* bad) {
+  int E = 1;
+  bool b = false;
+  const cg_exact::i128 S = has ? cg_exact::unpack(w.x, w.y, &E, &b) : (cg_exact::i128)0;
+  *Em = (int)__reduce_max_sync(0xffffffffu, (unsigned)E);
+  *bad = __reduce_or_sync(0xffffffffu, b ? 1u : 0u) != 0u;
+  return warp_sum_i128(cg_exact::shift_down(S, *Em - E));
+}
+
+// Sum of v over the CTA, valid in warp 0: each warp's exact sum (warp_exact),
+// then warp 0 adds the 8 warp sums exactly and rounds once to fp64.  The result
+// does not depend on which thread held which value.
+template <int NV>
+__device__ __forceinline__ void cta_sum0_exact(double (&v)[NV]) {
+  __shared__ ulonglong2 s_w[NV][kWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ulonglong2 w[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) w[j] = warp_exact(v[j]);
+  __syncthreads();  // s_w may still be read by warp 0 of a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) s_w[j][warp] = w[j];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      int E;
+      bool bad;
+      const cg_exact::i128 T = sum_entries(s_w[j][lane < kWarps ? lane : 0], lane < kWarps, &E, &bad);
+      v[j] = cg_exact::to_fp64(T, E, bad);
+    }
+  }
+}
+
 // Sum of v over the CTA in a fixed order, valid in thread 0 only.  A warp-wide
 // fp64 add occupies GB300's fp64 pipe (2 lanes per clock per SM) for 16
 // clocks, so the tree is kept to one warp: every thread stores its values,
@@ -99,7 +185,7 @@ __device__ __forceinline__ bool grid_barrier(DevState* st, unsigned nblocks, uin
 // 3,328 for an xor-tree in every warp followed by every thread summing the
 // warp sums (block_sum).
 template <int NV>
-__device__ __forceinline__ void cta_sum0(double (&v)[NV]) {
+__device__ __forceinline__ void cta_sum0_fp64(double (&v)[NV]) {
   __shared__ double s_v[NV][kBlock];
   __syncthreads();  // s_v may still be read by warp 0 of a previous call
 #pragma unroll
@@ -117,6 +203,16 @@ __device__ __forceinline__ void cta_sum0(double (&v)[NV]) {
       v[j] = t;
     }
   }
+}
+
+
+// The CTA sum used by the loops: exact (cta_sum0_exact) or, in the fp64 persistent
+// kernels, whose 128-register budget has no room for the 128-bit integer steps,
+// the one-warp fp64 tree (cta_sum0_fp64).  Valid in warp 0.
+template <int NV, bool EXACT = true>
+__device__ __forceinline__ void cta_sum0(double (&v)[NV]) {
+  if constexpr (EXACT) cta_sum0_exact<NV>(v);
+  else cta_sum0_fp64<NV>(v);
 }
 
 // Sum of v over the CTA in a fixed order (warp xor-tree, then warp 0 over the
@@ -155,8 +251,79 @@ __device__ __forceinline__ double stop2_high(double stop) {
   const double s = stop * stop * (1.0 + 1e-12);
   return s >= 1e-300 ? s : INFINITY;
 }
+// The root stays inside its branch through a register dependence on an empty
+// asm: the compiler had been computing it on every call.
 __device__ __forceinline__ bool below_stop(double rr, double stop, double stop2_hi) {
-  return rr <= stop2_hi && sqrt(rr) <= stop;
+  if (!(rr <= stop2_hi)) return false;
+  double r = rr;
+  asm volatile("" : "+d"(r));
+  return sqrt(r) <= stop;
+}
+
+// Sum of the G per-CTA partials part[j*G + c], exact and rounded once, given to
+// every thread.  Lane l of warp 0 takes partials l, l + 32, ..., kGridBatch loads
+// in flight at a time, and adds them exactly at a running scale (the largest
+// exponent seen: a larger one shifts the lane's sum down first); the 32 lane sums
+// meet at the largest scale (sum_entries' alignment, one redux.sync a limb).
+// Every CTA computes the identical value (same loads, same order), so decisions
+// made from it agree across the grid without another barrier.
+template <int NV>
+__device__ __forceinline__ void grid_sum_exact(const double* part, unsigned G, double (&out)[NV]) {
+  constexpr int kGridBatch = NV <= 2 ? 8 : 1;  // NV > 2: the once-per-solve residual sums
+  __shared__ double s_out[NV];
+  if (threadIdx.x < 32) {
+    const unsigned lane = threadIdx.x;
+    cg_exact::i128 acc[NV];
+    int Ea[NV];
+    bool bad[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      acc[j] = 0;
+      Ea[j] = 1;
+      bad[j] = false;
+    }
+    for (unsigned c0 = lane; c0 < G; c0 += 32u * kGridBatch) {
+      double v[kGridBatch][NV];
+#pragma unroll
+      for (int u = 0; u < kGridBatch; ++u) {
+        const unsigned c = c0 + 32u * u;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[u][j] = c < G ? __ldcg(part + (size_t)j * G + c) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        // the batch's largest exponent field from the bits, then one value at a
+        // time (few registers live: the persistent kernels are register-budgeted)
+        int Eb = Ea[j];
+#pragma unroll
+        for (int u = 0; u < kGridBatch; ++u) {
+          const int f = (int)((cg_exact::bits_of(v[u][j]) >> 52) & 0x7FF);
+          bad[j] = bad[j] || f == 0x7FF;
+          Eb = max(Eb, f == 0x7FF ? 1 : max(f, 1));
+        }
+        if (Eb > Ea[j]) {
+          acc[j] = cg_exact::shift_down(acc[j], Eb - Ea[j]);
+          Ea[j] = Eb;
+        }
+#pragma unroll
+        for (int u = 0; u < kGridBatch; ++u) acc[j] += (cg_exact::i128)cg_exact::to_fixed(cg_exact::parts(v[u][j]), Eb);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      unsigned long long lo, hi;
+      cg_exact::pack(acc[j], Ea[j], bad[j], &lo, &hi);
+      int E;
+      bool bd;
+      const cg_exact::i128 T = sum_entries(make_ulonglong2(lo, hi), true, &E, &bd);
+      const double r = cg_exact::to_fp64(T, E, bd);
+      if (lane == 0) s_out[j] = r;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = s_out[j];
+  __syncthreads();
 }
 
 // Sum of the G per-CTA partials part[j*G + c] in a fixed order (lane l of
@@ -166,7 +333,7 @@ __device__ __forceinline__ bool below_stop(double rr, double stop, double stop2_
 // lane's loads go out kGridBatch at a time, so the sum waits for about
 // G / (32 kGridBatch) L2 round trips instead of G / 32.
 template <int NV>
-__device__ __forceinline__ void grid_sum(const double* part, unsigned G, double (&out)[NV]) {
+__device__ __forceinline__ void grid_sum_fp64(const double* part, unsigned G, double (&out)[NV]) {
   constexpr int kGridBatch = NV <= 2 ? 8 : 1;  // NV > 2: the once-per-solve residual sums
   __shared__ double s_out[NV];
   if (threadIdx.x < 32) {
@@ -201,6 +368,15 @@ __device__ __forceinline__ void grid_sum(const double* part, unsigned G, double 
 #pragma unroll
   for (int j = 0; j < NV; ++j) out[j] = s_out[j];
   __syncthreads();
+}
+
+
+// The sum of the G per-CTA partials used by the loops: exact, or the fp64 form in
+// the fp64 persistent kernels (see cta_sum0).
+template <int NV, bool EXACT = true>
+__device__ __forceinline__ void grid_sum(const double* part, unsigned G, double (&out)[NV]) {
+  if constexpr (EXACT) grid_sum_exact<NV>(part, G, out);
+  else grid_sum_fp64<NV>(part, G, out);
 }
 
 }  // namespace cg

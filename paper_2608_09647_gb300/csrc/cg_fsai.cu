@@ -225,6 +225,7 @@ struct FsaiParams {
 template <int W, typename T>
 __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, const T* r, int64_t n,
                            double* part, int pstride, Grid& g, double* rho, double rho_prev = 0.0) {
+  constexpr bool kExact = sizeof(T) == 4;  // the fp64 loop keeps the fp64 sums (register budget)
   Acc<T> a;
   rows_x2(
       g, n, [&](int64_t i) { return ell_row<W>(G, i, n, [&](int j) { return r[j]; }); },
@@ -233,9 +234,9 @@ __device__ bool fsai_start(const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>&
         a.add(s, s);
       });
   double v[1] = {a.get()};
-  publish<1>(v, part + kSlotRes * (size_t)pstride, g);
+  publish<1, kExact>(v, part + kSlotRes * (size_t)pstride, g);
   if (!g.sync()) return false;
-  grid_sum<1>(part + kSlotRes * (size_t)pstride, g.G, v);
+  grid_sum<1, kExact>(part + kSlotRes * (size_t)pstride, g.G, v);
   *rho = v[0];
   const bool carry = rho_prev > 0.0;
   const T beta = carry ? (T)(v[0] / rho_prev) : T(0);
@@ -256,6 +257,7 @@ template <int W, typename T>
 __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, const FsaiVecs<T>& V, double rho,
                          double rr, double stop_abs, int maxit, int* iters, double* part, int pstride, Grid& g,
                          double* rho_last = nullptr) {
+  constexpr bool kExact = sizeof(T) == 4;  // the fp64 loop keeps the fp64 sums (register budget)
   const int64_t n = S.n;
   if (rho_last) *rho_last = rho;
   int k = *iters;
@@ -267,10 +269,10 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
   T* rn = V.r1;
   while (!done) {
     double v1[1] = {spmv_phase<T, false>(S, V.p, V.q, g)};
-    publish<1>(v1, part + kSlotPQ * (size_t)pstride, g);
+    publish<1, kExact>(v1, part + kSlotPQ * (size_t)pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
     double pq[1];
-    grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
+    grid_sum<1, kExact>(part + kSlotPQ * (size_t)pstride, g.G, pq);
     // the scalars once per CTA (an fp64 divide or square root in every
     // thread would load GB300's narrow fp64 pipe), shared through shared memory
     __shared__ double s_sc[2];
@@ -300,10 +302,10 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
           V.x[i] = u.x;
         });
     double v2[2] = {a_rho.get(), a_rr.get()};
-    publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
+    publish<2, kExact>(v2, part + kSlotUpd * (size_t)pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
     double s2[2];
-    grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
+    grid_sum<2, kExact>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     if (threadIdx.x == 0) {
       s_sc[1] = s2[0] / rho;
       s_fl = below_stop(s2[1], stop_abs, stop2_hi);
@@ -352,10 +354,10 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
       v[0] += ri * ri;
       v[1] += bi * bi;
     }
-    publish<2>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+    publish<2, false>(v, P.part + kSlotRes * (size_t)P.pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
     double s2[2];
-    grid_sum<2>(P.part + kSlotRes * (size_t)P.pstride, g.G, s2);
+    grid_sum<2, false>(P.part + kSlotRes * (size_t)P.pstride, g.G, s2);
     const double rr_start = s2[0];
     if (first) {
       bb = s2[1];
@@ -393,9 +395,9 @@ __global__ void __launch_bounds__(kBlock, 2) pcg_fsai64_kernel(FsaiParams F) {
         const double ri = P.b[i] - V.q[i];
         w[0] += ri * ri;
       }
-      publish<1>(w, P.part + kSlotRes * (size_t)P.pstride, g);
+      publish<1, false>(w, P.part + kSlotRes * (size_t)P.pstride, g);
       if (!g.sync()) { status = kTimeout; break; }
-      grid_sum<1>(P.part + kSlotRes * (size_t)P.pstride, g.G, w);
+      grid_sum<1, false>(P.part + kSlotRes * (size_t)P.pstride, g.G, w);
       relres_true = sqrt(w[0]) / sqrt(bb);
       break;
     }

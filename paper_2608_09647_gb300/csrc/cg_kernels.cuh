@@ -162,9 +162,9 @@ struct Grid {
 
 // Write this CTA's block sums of v[0..NV) into part[j*G + cta] (v is
 // consumed: afterwards it holds the sums in thread 0 only).
-template <int NV>
+template <int NV, bool EXACT = true>
 __device__ __forceinline__ void publish(double (&v)[NV], double* part, const Grid& g) {
-  cta_sum0<NV>(v);
+  cta_sum0<NV, EXACT>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) part[(size_t)j * g.G + g.cta] = v[j];
@@ -738,6 +738,7 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
                        double stop_abs, int maxit, int* iters, double* rr_out, double* out,
                        double* part, int pstride, Grid& g, PhaseClock& clk,
                        double* rho_last = nullptr) {
+  constexpr bool kExact = sizeof(T) == 4;  // the fp64 loop keeps the fp64 sums (register budget)
   if (rho_last) *rho_last = rho;  // r.z before the last step taken (reliable updates)
   int k = *iters;
   int status = kNotConverged;
@@ -747,12 +748,12 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
   while (!done) {
     // a1: q = A^ p; p.q
     double v1[1] = {spmv_phase<T, JAC>(S, V.p, V.q, g)};
-    publish<1>(v1, part + kSlotPQ * (size_t)pstride, g);
+    publish<1, kExact>(v1, part + kSlotPQ * (size_t)pstride, g);
     clk.lap(g.st, 0);
     if (!g.sync()) { status = kTimeout; break; }
     clk.lap(g.st, 1);
     double pq[1];
-    grid_sum<1>(part + kSlotPQ * (size_t)pstride, g.G, pq);
+    grid_sum<1, kExact>(part + kSlotPQ * (size_t)pstride, g.G, pq);
     // scalars once per CTA in thread 0, shared (fp64 divisions and tests in every
     // thread would load GB300's narrow fp64 pipe)
     __shared__ double s_sc[3];
@@ -769,12 +770,12 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     const bool want_rr = s_fl[1] != 0;
     double v2[2] = {0.0, 0.0};
     update_r_phase<T, JAC>(S, V, alpha, want_rr, v2[0], v2[1], g);
-    publish<2>(v2, part + kSlotUpd * (size_t)pstride, g);
+    publish<2, kExact>(v2, part + kSlotUpd * (size_t)pstride, g);
     clk.lap(g.st, 2);
     if (!g.sync()) { status = kTimeout; break; }
     clk.lap(g.st, 3);
     double s2[2];
-    grid_sum<2>(part + kSlotUpd * (size_t)pstride, g.G, s2);
+    grid_sum<2, kExact>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     if (threadIdx.x == 0) {
       double rr_ = s2[1];
       s_sc[1] = s2[0] / rho;
@@ -788,9 +789,9 @@ __device__ int cg_loop(const Sell<T>& S, const LoopVecs<T>& V, double rho, doubl
     rr = s_sc[2];
     if (s_fl[0]) {
       double v3[1] = {rr_phase<T>(S, V, g)};  // rho fell into the band early: exact r.r
-      publish<1>(v3, part + kSlotRr * (size_t)pstride, g);
+      publish<1, kExact>(v3, part + kSlotRr * (size_t)pstride, g);
       if (!g.sync()) { status = kTimeout; break; }
-      grid_sum<1>(part + kSlotRr * (size_t)pstride, g.G, v3);
+      grid_sum<1, kExact>(part + kSlotRr * (size_t)pstride, g.G, v3);
       rr = v3[0];
     }
     ++k;
@@ -859,10 +860,10 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
       v[1] += ri * ri;
       v[2] += bi * bi;
     }
-    publish<3>(v, P.part + kSlotRes * (size_t)P.pstride, g);
+    publish<3, false>(v, P.part + kSlotRes * (size_t)P.pstride, g);
     if (!g.sync()) { status = kTimeout; break; }
     double s3[3];
-    grid_sum<3>(P.part + kSlotRes * (size_t)P.pstride, g.G, s3);
+    grid_sum<3, false>(P.part + kSlotRes * (size_t)P.pstride, g.G, s3);
     if (first) {
       bb = s3[2];
       if (bb == 0.0) {  // b = 0: x = 0 solves it
@@ -893,10 +894,10 @@ __global__ void __launch_bounds__(kBlock, 2) pcg64_kernel(SolveParams P) {
         const double ri = P.b[i] - V.q[i];
         w[0] += ri * ri;
       }
-      publish<1>(w, P.part + kSlotRes * (size_t)P.pstride, g);
+      publish<1, false>(w, P.part + kSlotRes * (size_t)P.pstride, g);
       if (!g.sync()) { status = kTimeout; break; }
       double s1[1];
-      grid_sum<1>(P.part + kSlotRes * (size_t)P.pstride, g.G, s1);
+      grid_sum<1, false>(P.part + kSlotRes * (size_t)P.pstride, g.G, s1);
       relres_true = sqrt(s1[0]) / sqrt(bb);
       break;
     }
