@@ -268,7 +268,7 @@ __device__ __forceinline__ bool below_stop(double rr, double stop, double stop2_
 // Every CTA computes the identical value (same loads, same order), so decisions
 // made from it agree across the grid without another barrier.
 template <int NV>
-__device__ __forceinline__ void grid_sum_exact(const double* part, unsigned G, double (&out)[NV]) {
+__device__ __forceinline__ void grid_sum_exact_lanes(const double* part, unsigned G, double (&out)[NV]) {
   constexpr int kGridBatch = NV <= 2 ? 8 : 1;  // NV > 2: the once-per-solve residual sums
   __shared__ double s_out[NV];
   if (threadIdx.x < 32) {
@@ -370,6 +370,57 @@ __device__ __forceinline__ void grid_sum_fp64(const double* part, unsigned G, do
   __syncthreads();
 }
 
+
+// The same sum with every thread loading: thread t takes partials t, t + 256, ...
+// (at most kPer = 4 of them, all loads in flight: one L2 round trip), each warp
+// sums each of its kPer loads exactly (warp_exact), and warp 0 adds the warps'
+// entries, one a lane, exactly and rounds once.  For G > 1024, or in the
+// one-warp scalar kernels of the graph forms, the lane form.
+template <int NV>
+__device__ __forceinline__ void grid_sum_exact(const double* part, unsigned G, double (&out)[NV]) {
+  constexpr int kPer = 4;
+  if (G > (unsigned)(kPer * kBlock) || blockDim.x != (unsigned)kBlock) {
+    grid_sum_exact_lanes<NV>(part, G, out);
+    return;
+  }
+  __shared__ ulonglong2 s_w[NV][kPer * kWarps];
+  __shared__ double s_out[NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (int)((G + kBlock - 1) / kBlock);  // loads a thread makes (uniform)
+  double v[kPer][NV];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const unsigned c = threadIdx.x + (unsigned)(k * kBlock);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v[k][j] = (k < per && c < G) ? __ldcg(part + (size_t)j * G + c) : 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    if (k < per) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const ulonglong2 w = warp_exact(v[k][j]);
+        if (lane == 0) s_w[j][k * kWarps + warp] = w;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int ne = per * kWarps;  // <= 32 entries: one a lane
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      int E;
+      bool bad;
+      const cg_exact::i128 T = sum_entries(s_w[j][lane < ne ? lane : 0], lane < ne, &E, &bad);
+      const double r = cg_exact::to_fp64(T, E, bad);
+      if (lane == 0) s_out[j] = r;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) out[j] = s_out[j];
+  __syncthreads();
+}
 
 // The sum of the G per-CTA partials used by the loops: exact, or the fp64 form in
 // the fp64 persistent kernels (see cta_sum0).

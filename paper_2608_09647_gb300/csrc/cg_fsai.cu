@@ -284,6 +284,10 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     __syncthreads();
     if (s_fl) { status = s_fl; break; }
     const T alpha = (T)s_sc[0];
+    // 1 / rho for this iteration's beta, in warp 1 during the r update: beta =
+    // rho' (1 / rho) is a multiply after the next grid sum (within 1.5 ulp of rho' / rho)
+    __shared__ double s_inv_rho;
+    if (threadIdx.x == 32) s_inv_rho = 1.0 / rho;
     Acc<T> a_rho, a_rr;
     rows_x2(
         g, n,
@@ -307,7 +311,7 @@ __device__ int fsai_loop(const Sell<T>& S, const Ell<T>& G, const Ell<T>& GT, co
     double s2[2];
     grid_sum<2, kExact>(part + kSlotUpd * (size_t)pstride, g.G, s2);
     if (threadIdx.x == 0) {
-      s_sc[1] = s2[0] / rho;
+      s_sc[1] = s2[0] * s_inv_rho;
       s_fl = below_stop(s2[1], stop_abs, stop2_hi);
     }
     __syncthreads();

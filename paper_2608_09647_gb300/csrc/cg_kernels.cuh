@@ -307,7 +307,46 @@ __device__ __forceinline__ double spmv_phase_w(const Sell<T>& S, const T* __rest
   const int Wt = (int)g.G * kWarps;
   const int n = (int)S.n;
   Acc<T> dot;
-  for (int s = gw; s < S.nslices; s += Wt) {
+  int s = gw;
+  if constexpr (sizeof(T) == 4 && W <= 8) {
+    // fp32 loops at 2 CTAs per SM: a warp's slices cost one L2 round trip each, so
+    // two slices go together, every load of both issued before the first product
+    // (the same arithmetic and order as one slice at a time)
+    const int nm1 = n - 1;
+    for (; s + Wt < S.nslices; s += 2 * Wt) {
+      T v[2][W], pc[2][W], pi[2], acc[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int sh = s + h * Wt, i = sh * 32 + lane;
+        const bool live = i < n;
+        pi[h] = T(0);
+        T dgi = T(1);
+        if (live) {
+          pi[h] = p[i];
+          if (!JAC) dgi = __ldg(S.dg + i);
+        }
+        acc[h] = JAC ? pi[h] : dgi * pi[h];
+        const T* vp = S.val + (int64_t)sh * (W * 32) + lane;
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+          v[h][m] = ld_stream(vp + m * 32);
+          const int c = DIA ? min(max(i + S.delta[m], 0), nm1) : ld_stream(S.col + (int64_t)sh * (W * 32) + lane + m * 32);
+          pc[h][m] = p[c];
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int m = 0; m < W; ++m) acc[h] = fma(v[h][m], pc[h][m], acc[h]);
+        const int i = (s + h * Wt) * 32 + lane;
+        if (i < n) {
+          q[i] = acc[h];
+          dot.add(pi[h], acc[h]);
+        }
+      }
+    }
+  }
+  for (; s < S.nslices; s += Wt) {
     const int i = s * 32 + lane;
     const bool live = i < n;
     T pi = T(0), dgi = T(1);
