@@ -150,9 +150,10 @@ def fp64_fma_peak(sm_mhz, sms=152, dfma_per_clk_per_sm=2):
 # Sources that define each workload's timed kernels: a committed traffic figure
 # counts only while these files are unchanged.
 KERNEL_SOURCES = {
-    "single": ("cg_device.cuh", "cg_kernels.cuh", "cg_graph.cuh"),
-    "batch": ("cg_device.cuh", "cg_kernels.cuh", "cg_batch.cu"),
-    "fsai": ("cg_device.cuh", "cg_kernels.cuh", "cg_graph.cuh", "cg_fsai.cu", "cg_fsai.cuh"),
+    "single": ("cg_exact.cuh", "cg_device.cuh", "cg_csr.cuh", "cg_kernels.cuh", "cg_graph.cuh"),
+    "batch": ("cg_exact.cuh", "cg_device.cuh", "cg_csr.cuh", "cg_kernels.cuh", "cg_batch.cu"),
+    "fsai": ("cg_exact.cuh", "cg_device.cuh", "cg_csr.cuh", "cg_kernels.cuh", "cg_graph.cuh", "cg_fsai.cu",
+             "cg_fsai.cuh"),
 }
 
 
