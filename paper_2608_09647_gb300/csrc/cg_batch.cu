@@ -427,15 +427,13 @@ __device__ __forceinline__ void run_phase(const BatchParams& P, const int* s_pre
       }
       for (; gt < t1; ++gt) row(gt * kTile + t)(acc);
       if (NV > 0 && sums) {
-        // each reduced sum costs 5 warp-wide fp64 adds per group: GB300's fp64 pipe
-        // takes a warp instruction in 16 clocks whatever its active lanes
+        // the warp's sum of each reduced value, exact and rounded once on the integer
+        // pipes: an fp64 xor tree would take 5 warp instructions of the fp64 pipe
+        // (one per ~64 clocks per SM sub-partition) that the rows' FMAs need
         const bool all = NREQ >= NV || (opt && *opt);
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-          if (k < NREQ || all) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-          }
+          if (k < NREQ || all) acc[k] = warp_sum_exact(acc[k]);
         }
         if (lane == 0) {
           double* dst = P.tpart + ((size_t)(P.gstart[sys] + grp) * kWarps + warp) * kNP;

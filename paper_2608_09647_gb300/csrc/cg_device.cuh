@@ -139,6 +139,17 @@ __device__ __forceinline__ ulonglong2 warp_exact(double v) {
   return make_ulonglong2(lo, hi);
 }
 
+// In every lane: the exact sum of the lanes' fp64 values rounded once, with no
+// fp64 instruction (for loops bound by GB300's fp64 pipe, where a 5-level fp64
+// xor tree would take 5 of its warp instructions).
+__device__ __forceinline__ double warp_sum_exact(double v) {
+  const ulonglong2 w = warp_exact(v);
+  int E;
+  bool bad;
+  const cg_exact::i128 S = cg_exact::unpack(w.x, w.y, &E, &bad);
+  return cg_exact::to_fp64_int(S, E, bad);
+}
+
 // In every lane of a warp: the packed entries held by its lanes (lanes without
 // one hold zero at scale 1) moved to their largest scale and added exactly.
 __device__ __forceinline__ cg_exact::i128 sum_entries(const ulonglong2& w, bool has, int* Em, bool* bad) {

@@ -126,12 +126,20 @@ CG_EXACT_HD bool to_fp64_fast(i128 T, int E, double* out) {
   return true;
 }
 
+CG_EXACT_HD double to_fp64_int(i128 T, int E, bool bad);
+
 // T 2^(E - 1075 - kGuard) rounded to the nearest fp64 value, ties to even; NaN if bad.
 CG_EXACT_HD double to_fp64(i128 T, int E, bool bad) {
+  double f;
+  if (!bad && T != 0 && to_fp64_fast(T, E, &f)) return f;
+  return to_fp64_int(T, E, bad);
+}
+
+// The same rounding with integer instructions only (the result's bits built from
+// the integer), for code whose fp64 pipe is the bottleneck.
+CG_EXACT_HD double to_fp64_int(i128 T, int E, bool bad) {
   if (bad) return double_of(0x7FF8000000000000ull);
   if (T == 0) return 0.0;
-  double f;
-  if (to_fp64_fast(T, E, &f)) return f;
   const bool neg = T < 0;
   const u128 M = neg ? (u128)0 - (u128)T : (u128)T;
   const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;

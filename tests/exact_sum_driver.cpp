@@ -2,6 +2,7 @@
 // (paper_2608_09647_gb300/csrc/cg_exact.cuh), run by tests/test_exact_sum.py.
 // Reads commands on stdin, one per line, numbers in hex:
 //   conv <T as 32 hex digits, two's complement> <E>   -> bits of to_fp64(T, E)
+//   convi <T> <E>                                      -> bits of to_fp64_int(T, E) (integer path only)
 //   sum <w> <g> <n> <bits_1> ... <bits_n>             -> bits of the three-level sum:
 //        groups of w terms at their own scale (a warp), groups of g of those
 //        moved to their largest scale and added (a CTA), then all of those (the
@@ -18,13 +19,14 @@ using namespace cg_exact;
 int main() {
   char cmd[16];
   while (std::scanf("%15s", cmd) == 1) {
-    if (!std::strcmp(cmd, "conv")) {
+    if (!std::strcmp(cmd, "conv") || !std::strcmp(cmd, "convi")) {
       char hex[40];
       int E;
       if (std::scanf("%39s %d", hex, &E) != 2) return 1;
       u128 t = 0;
       for (const char* c = hex; *c; ++c) t = (t << 4) | (u128)std::stoul(std::string(1, *c), nullptr, 16);
-      std::printf("%016llx\n", bits_of(to_fp64((i128)t, E, false)));
+      const double r = cmd[4] == 'i' ? to_fp64_int((i128)t, E, false) : to_fp64((i128)t, E, false);
+      std::printf("%016llx\n", bits_of(r));
     } else if (!std::strcmp(cmd, "sum")) {
       int w, g, n;
       if (std::scanf("%d %d %d", &w, &g, &n) != 3) return 1;

@@ -67,10 +67,11 @@ def test_integer_to_fp64_rounds_to_nearest_even(driver):
             cases.append((m, E))
             cases.append((2 * m + 1, E))
     cases += [(0, 1075), ((1 << 79) - 1, 2046), (-(1 << 79), 2046), (1, 1)]
-    got = run(driver, [conv_line(T, E) for T, E in cases])
-    for (T, E), g in zip(cases, got):
-        want = rounded(Fraction(T) * Fraction(2) ** (E - 1075 - GUARD))
-        assert bits(g) == bits(want) or (g == 0.0 and want == 0.0), (T, E, g, want)
+    for cmd in ("conv", "convi"):   # the rounding as used, and its integer-only path on every case
+        got = run(driver, [conv_line(T, E).replace("conv", cmd, 1) for T, E in cases])
+        for (T, E), g in zip(cases, got):
+            want = rounded(Fraction(T) * Fraction(2) ** (E - 1075 - GUARD))
+            assert bits(g) == bits(want) or (g == 0.0 and want == 0.0), (cmd, T, E, g, want)
 
 
 def random_term(rng):
