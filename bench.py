@@ -19,7 +19,8 @@ Printed JSON line (rank 0):
                        HBM copy bandwidth; "fp64_pipe" gives the same kernel's
                        fp64 FMA rate against the pipe's peak (it co-limits);
   loop                 the whole CG loop's own bytes per iteration over its time,
-                       and the survey's CSR byte model as a separate figure;
+                       and the caller-CSR byte model (column indices, row pointers and
+                       the diagonal streamed too) as a separate figure;
   config.setup_ms      cg_create + cg_prepare (validation, loop matrix, vectors);
   cpu_baseline         the CPU oracle on all host cores (OpenMP row-split build)
                        and on one core, each on a bounded sample of iterations

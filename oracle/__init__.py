@@ -2,7 +2,7 @@
 
 Plain sequential fp64 restatement of the sparse CG hot path (``oracle.c``),
 used by the tests, the smoke check and the benchmark's CPU-baseline leg to
-judge the CUDA library.  The product path never imports this package, and this
+check the CUDA library.  The product path never imports this package, and this
 package imports nothing from the product package.
 
 Citations (the paper: "A Preliminary Study on Simultaneous Coscheduling for
@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 
 def openmp():
     """The all-core build of the same oracle (row loops split over OpenMP threads, Sec.
-    3.3), for timing only: its reductions sum per thread, so it never judges results.
+    3.3), for timing only: its reductions sum per thread, so it never checks results.
     Returns (library, threads) or (None, 0) when no OpenMP build exists."""
     global _lib_omp
     if _lib_omp is None:

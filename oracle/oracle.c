@@ -2,7 +2,7 @@
  * CG ORACLE — TEST INFRASTRUCTURE ONLY.
  *
  * A plain, sequential, fp64 restatement of what the sparse conjugate-gradient
- * hot path computes, used to judge the CUDA library.  Only the test suite,
+ * hot path computes, used to check the CUDA library.  Only the test suite,
  * the smoke check and the benchmark's CPU-baseline leg may load it.  It shares
  * no code, header or constant with the CUDA path; both sides only consume the
  * same generated inputs (cgproblems).
@@ -44,7 +44,7 @@
  * checker build (no -fopenmp) ignores them and stays sequential, in index
  * order; a second build with -fopenmp exists only to time the same loops on
  * all host cores (its reductions then sum per thread, so its rounding differs
- * and it is never used to judge results).
+ * and it is never used to check results).
  */
 #include <math.h>
 #include <stdint.h>
