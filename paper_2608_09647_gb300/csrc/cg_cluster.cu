@@ -11,14 +11,15 @@
 // loop never touches global memory: a global load costs ~170 clocks even when
 // it hits L1, and every cluster-scope acquire sends the next one to L2.
 //
-// Dot products: each CTA sums its threads' values in a fixed order and pushes
-// the sum into a slot table of every CTA with st.async, whose bytes complete a
-// transaction count on the receiving CTA's mbarrier; each CTA waits (bounded)
-// on its own mbarrier, then warp 0 adds the C partials in a fixed order and
-// thread 0 forms the scalars and takes the loop decisions, so every CTA holds
-// the same scalars and takes the same decisions.  An exchange costs ~830
-// clocks where remote stores and a cluster barrier took ~1,270; the two slot
-// tables and mbarriers alternate, so a CTA can run one exchange ahead.
+// Dot products: each CTA sums its threads' values exactly on the integer pipes
+// (cg_exact.cuh: each warp at its own scale, then warp 0 over the 8 warp sums)
+// and pushes the sum into a slot table of every CTA with st.async, whose bytes
+// complete a transaction count on the receiving CTA's mbarrier; each CTA waits
+// (bounded) on its own mbarrier, then warp 0 adds the C entries exactly and
+// rounds once, and thread 0 forms the scalars and takes the loop decisions, so
+// every CTA holds the same scalars and takes the same decisions.  An exchange
+// costs ~830 clocks where remote stores and a cluster barrier took ~1,270; the
+// two slot tables and mbarriers alternate, so a CTA can run one exchange ahead.
 //
 // One iteration has two exchanges.  Phase A forms p = z + beta p_old for its
 // rows, then q = A p and p.q; a neighbour in another CTA has its p recomputed
@@ -26,10 +27,10 @@
 // own.  Phase B updates r and z and forms r.z and r.r; x += alpha p runs after
 // the push, while the partials are in flight.  The true residual reads other
 // CTAs' x, so it follows an exchange with no payload that every CTA makes after
-// its last x update.  GB300's fp64 pipe issues one warp instruction per 16
-// clocks per SM, so fp64 work is kept to what the iteration needs: block sums
-// in warp 0 only, scalars in thread 0, and the recomputed p only in warps that
-// hold a neighbour of another CTA.
+// its last x update.  GB300's fp64 unit issues one warp instruction per ~64
+// clocks per SM sub-partition, so fp64 work is kept to what the iteration
+// needs: no fp64 in the sums, scalars in thread 0 (1 / rho in warp 1, off the
+// path), and the recomputed p only in warps that hold a neighbour of another CTA.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(kBlock, 1) pcg_cluster_kernel(ClusterParams P)
   unsigned e = 0;   // every thread: exchanges made so far
   bool pass0 = true;
   const uint64_t tmo = P.timeout_ns;
-  // every exchange: thread 0 arms this CTA's mbarrier, the block sum is pushed,
+  // every exchange: thread 0 arms this CTA's mbarrier, the CTA's exact sum is pushed,
   // warp 0 waits; on a timeout thread 0 records it and the CTA leaves
   auto arm = [&](int nv) {
     if (t == 0) mbar_arrive_expect(smem_addr(&X.bar[e & 1u]), (unsigned)(C * nv * 16));

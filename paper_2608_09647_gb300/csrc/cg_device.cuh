@@ -189,8 +189,9 @@ __device__ __forceinline__ void cta_sum0_exact(double (&v)[NV]) {
 }
 
 // Sum of v over the CTA in a fixed order, valid in thread 0 only.  A warp-wide
-// fp64 add occupies GB300's fp64 pipe (2 lanes per clock per SM) for 16
-// clocks, so the tree is kept to one warp: every thread stores its values,
+// fp64 add occupies GB300's fp64 pipe (2 lanes per clock per SM, ~64 clocks of
+// one sub-partition's unit) whatever its active lanes, so the tree is kept to
+// one warp: every thread stores its values,
 // lane l of warp 0 sums threads l, l+32, ... in that order and the 32 lane
 // sums meet in an xor-tree: 416 fp64 lane operations per value, against
 // 3,328 for an xor-tree in every warp followed by every thread summing the
